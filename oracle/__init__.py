@@ -1,0 +1,306 @@
+"""FP64 CPU oracle for per-point rank-one convexification (arXiv 2211.14318).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The CUDA product path never imports
+it, and it shares no code with that path.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64, one function per step of
+the paper); this module compiles it with gcc and exposes it through ctypes.
+Functions marked "parity unpinned" in their docstring have no external pin.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+
+NODE_DTYPE = np.dtype(
+    [
+        ("F", "<f8", (4,)),
+        ("w", "<f8"),
+        ("h", "<f8"),
+        ("xi", "<f8"),
+        ("weight", "<f8"),
+        ("margin", "<f8"),
+        ("dir", "<i4"),
+        ("m_minus", "<i4"),
+        ("m_plus", "<i4"),
+        ("flags", "<i4"),
+    ]
+)
+EXISTS, SCANNED, LAMINATED, LEAF = 1, 2, 4, 8
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [
+        ("mu", ctypes.c_double),
+        ("lam", ctypes.c_double),
+        ("Dinf", ctypes.c_double),
+        ("D0", ctypes.c_double),
+        ("energy", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+    ]
+
+
+class _Scan(ctypes.Structure):
+    _fields_ = [
+        ("n_dir", ctypes.c_int32),
+        ("L", ctypes.c_int32),
+        ("dir", ctypes.POINTER(ctypes.c_double)),
+        ("t_half", ctypes.c_double),
+        ("depth", ctypes.c_int32),
+        ("round32", ctypes.c_int32),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``_liboracle.so`` (gcc, OpenMP, no FP contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = [
+        "gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+        "-o", tmp, _SRC, "-lm",
+    ]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+        vp = ctypes.c_void_p
+        L.orc_psi0_nh.restype = d
+        L.orc_psi0_nh.argtypes = [d, d, d, d]
+        L.orc_damage.restype = d
+        L.orc_damage.argtypes = [d, d, d]
+        L.orc_W_of_psi0.restype = d
+        L.orc_W_of_psi0.argtypes = [d, d, d, d]
+        L.orc_energy.restype = d
+        L.orc_energy.argtypes = [vp, vp, d]
+        L.orc_stress.restype = None
+        L.orc_stress.argtypes = [vp, vp, d, vp]
+        L.orc_psi0_F.restype = d
+        L.orc_psi0_F.argtypes = [vp, vp]
+        L.orc_history_update.restype = None
+        L.orc_history_update.argtypes = [vp, i64, vp, vp, vp]
+        L.orc_angle_directions.restype = None
+        L.orc_angle_directions.argtypes = [i32, i32, vp]
+        L.orc_sample_line.restype = None
+        L.orc_sample_line.argtypes = [vp, vp, d, vp, i32, d, i32, vp, vp]
+        L.orc_lower_hull.restype = i32
+        L.orc_lower_hull.argtypes = [i32, vp, vp, vp]
+        L.orc_line_bridge.restype = d
+        L.orc_line_bridge.argtypes = [i32, vp, vp, vp, vp, vp]
+        L.orc_scan_node.restype = i32
+        L.orc_scan_node.argtypes = [vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_convexify.restype = None
+        L.orc_convexify.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, i32]
+        L.orc_tree_size.restype = i32
+        L.orc_tree_size.argtypes = [i32]
+        L.orc_node_size.restype = i32
+        L.orc_node_size.argtypes = []
+        assert L.orc_node_size() == NODE_DTYPE.itemsize, "node layout mismatch"
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class Material:
+    """Material of Sec. 2: Lame (mu, lam), damage (D_inf, D_0); energy 0 = NH
+    with damage (Eq. 2.9), 1 = separable double-well test energy."""
+
+    def __init__(self, mu=1.0, lam=5.0, Dinf=0.99, D0=0.5, energy=0):
+        self.mu, self.lam, self.Dinf, self.D0, self.energy = mu, lam, Dinf, D0, energy
+        self._c = _Material(mu, lam, Dinf, D0, energy, 0)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+def psi0_nh(I1: float, J: float, mu: float, lam: float) -> float:
+    """Eq. (2.3) in the invariants."""
+    return lib().orc_psi0_nh(I1, J, mu, lam)
+
+
+def W_of_psi0(s: float, beta_k: float, Dinf: float, D0: float) -> float:
+    """Eq. (2.9) as a function of s = psi0."""
+    return lib().orc_W_of_psi0(s, beta_k, Dinf, D0)
+
+
+def damage(beta: float, Dinf: float, D0: float) -> float:
+    """Eq. (2.6)."""
+    return lib().orc_damage(beta, Dinf, D0)
+
+
+def energy(mat: Material, F, beta_k: float) -> float:
+    """W(F), Eq. (2.9), plane strain."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    return lib().orc_energy(mat.ref, _p(F), beta_k)
+
+
+def stress(mat: Material, F, beta_k: float) -> np.ndarray:
+    """P = dW/dF, Eq. (2.12)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    P = np.zeros(4)
+    lib().orc_stress(mat.ref, _p(F), beta_k, _p(P))
+    return P
+
+
+def psi0_F(mat: Material, F) -> float:
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    return lib().orc_psi0_F(mat.ref, _p(F))
+
+
+def history_update(mat: Material, F: np.ndarray, beta_in: Optional[np.ndarray] = None) -> np.ndarray:
+    """Eq. (2.5): beta_new = max(beta_in, psi0(F)) per point (beta_in = 0 if None)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 4)
+    n = F.shape[0]
+    out = np.zeros(n)
+    bi = None
+    if beta_in is not None:
+        bi = np.ascontiguousarray(beta_in, dtype=np.float64).reshape(n)
+    lib().orc_history_update(mat.ref, n, _p(F), _p(bi) if bi is not None else None, _p(out))
+    return out
+
+
+def angle_directions(Na: int, Nb: int) -> np.ndarray:
+    """(Na*Nb, 4) table of (a1, a2, b1, b2), a_i = (cos pi i/Na, sin pi i/Na)."""
+    d = np.zeros((Na * Nb, 4))
+    lib().orc_angle_directions(Na, Nb, _p(d))
+    return d
+
+
+class Scan:
+    """Direction set, line (L samples on [-t_half, t_half]) and depth K."""
+
+    def __init__(self, dirs: np.ndarray, L: int, t_half: float, depth: int, round32: bool = False):
+        self.dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 4)
+        self.L, self.t_half, self.depth, self.round32 = int(L), float(t_half), int(depth), bool(round32)
+        self._c = _Scan(
+            self.dirs.shape[0], self.L,
+            self.dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            self.t_half, self.depth, int(self.round32),
+        )
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+    @property
+    def m0(self) -> int:
+        return (self.L - 1) // 2
+
+    @property
+    def h(self) -> float:
+        return 2.0 * self.t_half / (self.L - 1)
+
+
+def rank_one(d) -> np.ndarray:
+    d = np.asarray(d, dtype=np.float64)
+    return np.array([d[0] * d[2], d[0] * d[3], d[1] * d[2], d[1] * d[3]])
+
+
+def sample_line(mat: Material, F, beta_k: float, R, L: int, t_half: float, round32: bool = False):
+    """Samples of W along F + t R (Eq. 4.4 restated per point); returns (w, valid)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(4)
+    w = np.zeros(L)
+    v = np.zeros(L, dtype=np.uint8)
+    lib().orc_sample_line(mat.ref, _p(F), beta_k, _p(R), L, t_half, int(round32), _p(w), _p(v))
+    return w, v.astype(bool)
+
+
+def lower_hull(x: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Algorithm 1: indices of the strict lower-hull vertices of (x, w)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    vtx = np.zeros(max(len(x), 1), dtype=np.int32)
+    k = lib().orc_lower_hull(len(x), _p(x), _p(w), _p(vtx))
+    return vtx[:k].copy()
+
+
+def line_bridge(w: np.ndarray, valid: Optional[np.ndarray] = None):
+    """Hull at x = 0 of samples at integer abscissae m - m0.
+
+    Returns (h, m_minus, m_plus, margin)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    L = w.shape[0]
+    v = np.ones(L, dtype=np.uint8) if valid is None else np.ascontiguousarray(valid, dtype=np.uint8)
+    mm = np.zeros(1, dtype=np.int32)
+    mp = np.zeros(1, dtype=np.int32)
+    mg = np.zeros(1)
+    h = lib().orc_line_bridge(L, _p(w), _p(v), _p(mm), _p(mp), _p(mg))
+    return h, int(mm[0]), int(mp[0]), float(mg[0])
+
+
+def scan_node(mat: Material, sc: Scan, F, beta_k: float, per_direction: bool = False):
+    """Min over directions at one node (Eq. 4.3).  Returns a dict."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    nd = sc.dirs.shape[0]
+    hs = np.zeros(nd)
+    mm = np.zeros(nd, dtype=np.int32)
+    mp = np.zeros(nd, dtype=np.int32)
+    mg = np.zeros(nd)
+    hb = np.zeros(1)
+    a = np.zeros(1, dtype=np.int32)
+    b = np.zeros(1, dtype=np.int32)
+    margin = np.zeros(1)
+    j = lib().orc_scan_node(mat.ref, sc.ref, _p(F), beta_k, _p(hs), _p(mm), _p(mp), _p(mg),
+                            _p(hb), _p(a), _p(b), _p(margin))
+    out = dict(dir=int(j), h=float(hb[0]), m_minus=int(a[0]), m_plus=int(b[0]),
+               margin=float(margin[0]))
+    if per_direction:
+        out.update(h_dir=hs, m_minus_dir=mm, m_plus_dir=mp, margin_dir=mg)
+    return out
+
+
+def tree_size(depth: int) -> int:
+    return (1 << (depth + 1)) - 1
+
+
+def convexify(mat: Material, sc: Scan, F: np.ndarray, beta_k: np.ndarray, nthreads: int = 0):
+    """Per-point W^R, P and lamination tree (Eq. 3.3 top-down, Alg. 2/3).
+
+    Returns (W_R (n,), P (n, 4), tree (n, 2^{K+1}-1) NODE_DTYPE, status (n,))."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 4)
+    n = F.shape[0]
+    beta_k = np.ascontiguousarray(beta_k, dtype=np.float64).reshape(n)
+    WR = np.zeros(n)
+    P = np.zeros((n, 4))
+    tree = np.zeros((n, tree_size(sc.depth)), dtype=NODE_DTYPE)
+    st = np.zeros(n, dtype=np.int32)
+    lib().orc_convexify(mat.ref, sc.ref, n, _p(F), _p(beta_k), _p(WR), _p(P), _p(tree), _p(st),
+                        int(nthreads))
+    return WR, P, tree, st
+
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+if __name__ == "__main__":  # pragma: no cover
+    build(force="--force" in sys.argv)
+    print(_LIB)

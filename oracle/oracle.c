@@ -1,0 +1,554 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for per-point rank-one convexification.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
+ * leg of bench.py may load this library.  The CUDA product path shares no code,
+ * header, table or constant generator with it.
+ *
+ * Every function follows the paper (arXiv 2211.14318) step by step, without
+ * blocking, fusion or reordering:
+ *   - energy:      Sec. 2, Eqs. (2.1)-(2.9), stress Eq. (2.12);
+ *   - line:        Sec. 4.1, Eqs. (4.3)-(4.4) restated per point (symmetric
+ *                  1-D grid centred at the point, samples with det <= 0 dropped);
+ *   - 1-D hull:    Sec. 4.2, Algorithm 1 (Graham scan);
+ *   - min over R:  Sec. 4.1, Eq. (4.3);
+ *   - recursion:   Sec. 3.1, Eq. (3.3), realised top-down per point
+ *                  (lamination tree of Sec. 4.3 / Algorithm 2);
+ *   - derivative:  Sec. 5.3, Eq. (5.2) and Algorithm 3.
+ *
+ * Readings of the paper (where it is silent or garbled) are listed in
+ * the design doc; the ones used here are named at the point of use.
+ *
+ * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (no FMA contraction,
+ * so x86_64 and aarch64 hosts give identical results).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Types (the oracle's own; deliberately not the C-ABI's header).            */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double mu;      /* Lame mu                                   */
+    double lam;     /* Lame lambda                               */
+    double Dinf;    /* asymptotic damage D_inf, Eq. (2.6)         */
+    double D0;      /* damage saturation D_0, Eq. (2.6)           */
+    int32_t energy; /* 0: NH with damage; 1: double-well test energy */
+    int32_t pad;
+} orc_material;
+
+typedef struct {
+    int32_t n_dir;      /* number of rank-one directions R = a (x) b     */
+    int32_t L;          /* samples per line (odd)                         */
+    const double *dir;  /* n_dir x 4: (a1, a2, b1, b2)                   */
+    double t_half;      /* line covers t in [-t_half, t_half]            */
+    int32_t depth;      /* lamination depth K                            */
+    int32_t round32;    /* 1: hull decisions on samples rounded to FP32  */
+} orc_scan;
+
+/* One node of the per-point lamination tree in heap layout: node i has
+ * children 2i+1 (F-) and 2i+2 (F+). */
+typedef struct {
+    double F[4];     /* F11 F12 F21 F22                                   */
+    double w;        /* W(F) in FP64                                      */
+    double h;        /* hull value at t=0 along the chosen direction      */
+    double xi;       /* weight of F+ in the split (Algorithm 2)          */
+    double weight;   /* product of split weights from the root            */
+    double margin;   /* decision margin (see orc_scan_node)               */
+    int32_t dir;     /* chosen direction index, -1 if not scanned         */
+    int32_t m_minus; /* bridge vertex sample index (0..L-1)               */
+    int32_t m_plus;
+    int32_t flags;   /* bit0 exists, bit1 scanned, bit2 laminated, bit3 leaf */
+} orc_node;
+
+enum { ORC_EXISTS = 1, ORC_SCANNED = 2, ORC_LAMINATED = 4, ORC_LEAF = 8 };
+enum { ORC_OK = 0, ORC_NONPOS_DET = 1 };
+
+/* ------------------------------------------------------------------------- */
+/* Energy, Sec. 2                                                            */
+/* ------------------------------------------------------------------------- */
+
+/* Eq. (2.3): compressible Neo-Hooke in the invariants I1 = tr C and J. */
+double orc_psi0_nh(double I1, double J, double mu, double lam)
+{
+    double lj = log(J);
+    return 0.5 * mu * (I1 - 3.0) - mu * lj + 0.5 * lam * lj * lj;
+}
+
+/* Eq. (2.6): D(beta) = D_inf (1 - exp(-beta / D_0)). */
+double orc_damage(double beta, double Dinf, double D0)
+{
+    return Dinf * (1.0 - exp(-beta / D0));
+}
+
+/* Antiderivative of Eq. (2.6): Dbar(beta) = D_inf (beta + D_0 exp(-beta/D_0)). */
+double orc_damage_antiderivative(double beta, double Dinf, double D0)
+{
+    return Dinf * (beta + D0 * exp(-beta / D0));
+}
+
+/* Eq. (2.9) written term by term, as a function of s = psi0(F):
+ *   W = psi(F, D) - psi(F_k, D_k) + beta D - beta_k D_k - Dbar + Dbar_k,
+ * with psi = (1 - D) psi0 (Eq. 2.4), beta = max(beta_k, s) (Eq. 2.5) and the
+ * reading psi(F_k, D_k) = (1 - D_k) beta_k (the history value is the largest
+ * effective energy seen so far). */
+double orc_W_of_psi0(double s, double beta_k, double Dinf, double D0)
+{
+    double beta = s > beta_k ? s : beta_k;
+    double D = orc_damage(beta, Dinf, D0);
+    double Dk = orc_damage(beta_k, Dinf, D0);
+    double psi = (1.0 - D) * s;
+    double psik = (1.0 - Dk) * beta_k;
+    return psi - psik + beta * D - beta_k * Dk
+         - orc_damage_antiderivative(beta, Dinf, D0)
+         + orc_damage_antiderivative(beta_k, Dinf, D0);
+}
+
+/* Plane strain: C = F^T F of the 3x3 deformation diag-embedded F, so that
+ * I1 = |F|_F^2 + 1 and J = det F (Eq. 2.1 with F33 = 1). */
+static void nh_invariants(const double F[4], double *I1, double *J)
+{
+    *I1 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3] + 1.0;
+    *J = F[0] * F[3] - F[1] * F[2];
+}
+
+double orc_psi0_F(const orc_material *m, const double F[4])
+{
+    double I1, J;
+    nh_invariants(F, &I1, &J);
+    return orc_psi0_nh(I1, J, m->mu, m->lam);
+}
+
+/* Test energy (not in the paper): separable double well
+ *   W = (F11^2 - 1)^2 + F12^2 + F21^2 + (F22 - 1)^2,
+ * whose rank-one convex envelope is known in closed form. */
+static double dw_energy(const double F[4])
+{
+    double a = F[0] * F[0] - 1.0, d = F[3] - 1.0;
+    return a * a + F[1] * F[1] + F[2] * F[2] + d * d;
+}
+
+/* Incremental stress potential W(F), Eq. (2.9); NaN where det F <= 0. */
+double orc_energy(const orc_material *m, const double F[4], double beta_k)
+{
+    if (m->energy == 1)
+        return dw_energy(F);
+    double I1, J;
+    nh_invariants(F, &I1, &J);
+    if (!(J > 0.0))
+        return NAN;
+    double s = orc_psi0_nh(I1, J, m->mu, m->lam);
+    return orc_W_of_psi0(s, beta_k, m->Dinf, m->D0);
+}
+
+/* P = dW/dF, Eq. (2.12).  By the chain rule through s = psi0(F) (beta is the
+ * minimiser of Eq. (2.8), so its own variation drops out):
+ *   dW/ds = 1 - D(max(s, beta_k)),
+ *   dpsi0/dF = mu F - mu F^{-T} + lam ln J F^{-T}. */
+void orc_stress(const orc_material *m, const double F[4], double beta_k, double P[4])
+{
+    if (m->energy == 1) {
+        P[0] = 4.0 * F[0] * (F[0] * F[0] - 1.0);
+        P[1] = 2.0 * F[1];
+        P[2] = 2.0 * F[2];
+        P[3] = 2.0 * (F[3] - 1.0);
+        return;
+    }
+    double I1, J;
+    nh_invariants(F, &I1, &J);
+    if (!(J > 0.0)) {
+        P[0] = P[1] = P[2] = P[3] = NAN;
+        return;
+    }
+    double s = orc_psi0_nh(I1, J, m->mu, m->lam);
+    double beta = s > beta_k ? s : beta_k;
+    double g = 1.0 - orc_damage(beta, m->Dinf, m->D0);
+    /* F^{-T} = cof F / J, with cof F = [[F22, -F21], [-F12, F11]] */
+    double FiT[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    double lj = log(J);
+    for (int i = 0; i < 4; ++i)
+        P[i] = g * (m->mu * F[i] - m->mu * FiT[i] + m->lam * lj * FiT[i]);
+}
+
+/* History update between load steps, Eq. (2.5): beta_new = max(beta_k, psi0(F)). */
+void orc_history_update(const orc_material *m, int64_t n, const double *F,
+                        const double *beta_in, double *beta_out)
+{
+    for (int64_t p = 0; p < n; ++p) {
+        double s = orc_psi0_F(m, F + 4 * p);
+        double b = beta_in ? beta_in[p] : 0.0;
+        beta_out[p] = s > b ? s : b;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Rank-one lines, Sec. 4.1, Eq. (4.4) restated per point                    */
+/* ------------------------------------------------------------------------- */
+
+/* Direction table for the angle grid: a_i = (cos(pi i/Na), sin(pi i/Na)),
+ * b_j likewise, direction index j_dir = i * Nb + j. */
+void orc_angle_directions(int32_t Na, int32_t Nb, double *dir)
+{
+    for (int i = 0; i < Na; ++i) {
+        double ta = M_PI * (double)i / (double)Na;
+        for (int j = 0; j < Nb; ++j) {
+            double tb = M_PI * (double)j / (double)Nb;
+            double *d = dir + 4 * ((int64_t)i * Nb + j);
+            d[0] = cos(ta);
+            d[1] = sin(ta);
+            d[2] = cos(tb);
+            d[3] = sin(tb);
+        }
+    }
+}
+
+/* R = a (x) b, row-major (R11 R12 R21 R22). */
+static void rank_one(const double *d, double R[4])
+{
+    R[0] = d[0] * d[2];
+    R[1] = d[0] * d[3];
+    R[2] = d[1] * d[2];
+    R[3] = d[1] * d[3];
+}
+
+/* Samples of W along F + t_m R, t_m = (m - m0) h, h = 2 t_half / (L - 1),
+ * m0 = (L - 1) / 2.  valid[m] = 0 where det(F + t_m R) <= 0 (NH only). */
+void orc_sample_line(const orc_material *mat, const double F[4], double beta_k,
+                     const double R[4], int32_t L, double t_half, int32_t round32,
+                     double *w, uint8_t *valid)
+{
+    int m0 = (L - 1) / 2;
+    double h = 2.0 * t_half / (double)(L - 1);
+    for (int m = 0; m < L; ++m) {
+        double t = (double)(m - m0) * h;
+        double G[4];
+        for (int i = 0; i < 4; ++i)
+            G[i] = F[i] + t * R[i];
+        double v = orc_energy(mat, G, beta_k);
+        if (mat->energy != 1 && !(G[0] * G[3] - G[1] * G[2] > 0.0)) {
+            valid[m] = 0;
+            w[m] = NAN;
+            continue;
+        }
+        valid[m] = 1;
+        w[m] = round32 ? (double)(float)v : v;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* One-dimensional convexification, Sec. 4.2, Algorithm 1                    */
+/* ------------------------------------------------------------------------- */
+
+/* Algorithm 1 (Graham scan) on points (x[i], w[i]), x strictly increasing.
+ * Writes the indices of the hull vertices to vtx and returns their number.
+ * Readings: the start uses the first two points (x, w); the pop loop runs
+ * while at least two vertices remain; ">=" pops collinear points, so the
+ * returned vertices are strict. */
+int32_t orc_lower_hull(int32_t n, const double *x, const double *w, int32_t *vtx)
+{
+    if (n <= 0)
+        return 0;
+    vtx[0] = 0;
+    if (n == 1)
+        return 1;
+    vtx[1] = 1;
+    int32_t k = 2;
+    for (int32_t i = 2; i < n; ++i) {
+        while (k >= 2) {
+            int32_t p = vtx[k - 2], q = vtx[k - 1];
+            /* slope(p->q) >= slope(q->i)  <=>  q is not strictly below */
+            if ((w[q] - w[p]) * (x[i] - x[q]) >= (w[i] - w[q]) * (x[q] - x[p]))
+                --k;
+            else
+                break;
+        }
+        vtx[k++] = i;
+    }
+    return k;
+}
+
+/* Hull of the valid samples of one line, read at x = 0 (the point F itself).
+ * Abscissae are the integers m - m0.  Returns the value at 0 and the bridge
+ * vertices m_minus <= m0 <= m_plus (both m0 when m0 is itself a vertex).
+ * If margin_out is non-NULL it receives the decision margin: the largest eps
+ * such that perturbing every sample by at most eps cannot change the result
+ *  - bridge a < 0 < b:  min over other samples i of
+ *        (w_i - chord(x_i)) / (1 + (|x_i - x_a| + |x_i - x_b|) / (x_b - x_a));
+ *  - vertex at 0:       (hull of the samples without m0, read at 0, - w_m0) / 2
+ *                       (+inf when one side is empty). */
+double orc_line_bridge(int32_t L, const double *w, const uint8_t *valid,
+                       int32_t *m_minus, int32_t *m_plus, double *margin_out)
+{
+    int32_t m0 = (L - 1) / 2;
+    double *xs = (double *)malloc(sizeof(double) * L);
+    double *ws = (double *)malloc(sizeof(double) * L);
+    int32_t *id = (int32_t *)malloc(sizeof(int32_t) * L);
+    int32_t *vtx = (int32_t *)malloc(sizeof(int32_t) * L);
+    int32_t n = 0;
+    for (int32_t m = 0; m < L; ++m)
+        if (valid[m]) {
+            xs[n] = (double)(m - m0);
+            ws[n] = w[m];
+            id[n] = m;
+            ++n;
+        }
+    int32_t nv = orc_lower_hull(n, xs, ws, vtx);
+    double h = w[m0];
+    int32_t a = m0, b = m0;
+    for (int32_t k = 0; k + 1 < nv; ++k) {
+        double xa = xs[vtx[k]], xb = xs[vtx[k + 1]];
+        if (xa < 0.0 && xb > 0.0) {
+            a = id[vtx[k]];
+            b = id[vtx[k + 1]];
+            /* linear interpolation of the hull at x = 0 */
+            h = (xb * ws[vtx[k]] - xa * ws[vtx[k + 1]]) / (xb - xa);
+            break;
+        }
+    }
+    *m_minus = a;
+    *m_plus = b;
+    if (margin_out) {
+        double mg = INFINITY;
+        if (a != b) {
+            double xa = (double)(a - m0), xb = (double)(b - m0);
+            for (int32_t i = 0; i < n; ++i) {
+                if (id[i] == a || id[i] == b)
+                    continue;
+                double x = xs[i];
+                double chord = (w[a] * (xb - x) + w[b] * (x - xa)) / (xb - xa);
+                double kappa = (fabs(x - xa) + fabs(x - xb)) / (xb - xa);
+                double r = (ws[i] - chord) / (1.0 + kappa);
+                if (r < mg)
+                    mg = r;
+            }
+        } else {
+            /* hull of all valid samples except m0, read at 0 */
+            int32_t n2 = 0;
+            for (int32_t i = 0; i < n; ++i)
+                if (id[i] != m0) {
+                    xs[n2] = xs[i];
+                    ws[n2] = ws[i];
+                    ++n2;
+                }
+            int32_t nv2 = orc_lower_hull(n2, xs, ws, vtx);
+            double h2 = INFINITY;
+            for (int32_t k = 0; k + 1 < nv2; ++k) {
+                double xa = xs[vtx[k]], xb = xs[vtx[k + 1]];
+                if (xa < 0.0 && xb > 0.0) {
+                    h2 = (xb * ws[vtx[k]] - xa * ws[vtx[k + 1]]) / (xb - xa);
+                    break;
+                }
+            }
+            mg = 0.5 * (h2 - w[m0]);
+        }
+        *margin_out = mg;
+    }
+    free(xs);
+    free(ws);
+    free(id);
+    free(vtx);
+    return h;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Minimum over directions, Sec. 4.1, Eq. (4.3)                              */
+/* ------------------------------------------------------------------------- */
+
+/* Scans every direction at one node F.  For direction j: h_j, bridge
+ * (m_minus_j, m_plus_j).  The node picks j* = argmin h_j (lowest j on equal
+ * values) and laminates iff the bridge at j* excludes m0.
+ * Optional per-direction outputs (NULL to skip).
+ * The node margin is min(bridge margin at j*, (h_(2) - h_(1)) / 2) for a
+ * laminating node and min_j (no-lamination margin of j) otherwise. */
+int32_t orc_scan_node(const orc_material *mat, const orc_scan *sc, const double F[4],
+                      double beta_k, double *h_out, int32_t *mm_out, int32_t *mp_out,
+                      double *margin_dir_out, double *h_best, int32_t *m_minus,
+                      int32_t *m_plus, double *node_margin)
+{
+    int32_t L = sc->L;
+    if (sc->n_dir <= 0)
+        return -1;
+    double *w = (double *)malloc(sizeof(double) * L);
+    uint8_t *valid = (uint8_t *)malloc(L);
+    double *hs = (double *)malloc(sizeof(double) * sc->n_dir);
+    double *mg = (double *)malloc(sizeof(double) * sc->n_dir);
+    int32_t *mm = (int32_t *)malloc(sizeof(int32_t) * sc->n_dir);
+    int32_t *mp = (int32_t *)malloc(sizeof(int32_t) * sc->n_dir);
+    for (int32_t j = 0; j < sc->n_dir; ++j) {
+        double R[4];
+        rank_one(sc->dir + 4 * j, R);
+        orc_sample_line(mat, F, beta_k, R, L, sc->t_half, sc->round32, w, valid);
+        hs[j] = orc_line_bridge(L, w, valid, &mm[j], &mp[j], &mg[j]);
+    }
+    int32_t best = 0;
+    for (int32_t j = 1; j < sc->n_dir; ++j)
+        if (hs[j] < hs[best])
+            best = j;
+    int32_t m0 = (L - 1) / 2;
+    int laminated = mm[best] != m0;
+    double margin;
+    if (laminated) {
+        double second = INFINITY;
+        for (int32_t j = 0; j < sc->n_dir; ++j)
+            if (j != best && hs[j] < second)
+                second = hs[j];
+        margin = mg[best];
+        double g = 0.5 * (second - hs[best]);
+        if (g < margin)
+            margin = g;
+    } else {
+        margin = INFINITY;
+        for (int32_t j = 0; j < sc->n_dir; ++j)
+            if (mg[j] < margin)
+                margin = mg[j];
+    }
+    if (h_out)
+        memcpy(h_out, hs, sizeof(double) * sc->n_dir);
+    if (mm_out)
+        memcpy(mm_out, mm, sizeof(int32_t) * sc->n_dir);
+    if (mp_out)
+        memcpy(mp_out, mp, sizeof(int32_t) * sc->n_dir);
+    if (margin_dir_out)
+        memcpy(margin_dir_out, mg, sizeof(double) * sc->n_dir);
+    *h_best = hs[best];
+    *m_minus = mm[best];
+    *m_plus = mp[best];
+    *node_margin = margin;
+    free(w);
+    free(valid);
+    free(hs);
+    free(mg);
+    free(mm);
+    free(mp);
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lamination to depth K, Eq. (3.3), and derivative, Eq. (5.2)/Algorithm 3   */
+/* ------------------------------------------------------------------------- */
+
+/* Node value V_K(G) (reading of "lamination depth" for a per-point method):
+ *   V_0(G) = W(G);
+ *   V_K(G) = W(G)                              if G does not laminate;
+ *   V_K(G) = xi V_{K-1}(F+) + (1-xi) V_{K-1}(F-) otherwise,
+ * with (R*, F+-, xi) from the line scan of W at G.  The tree is stored in
+ * heap layout; leaves carry the product of split weights (Algorithm 2's xi). */
+static void build_tree(const orc_material *mat, const orc_scan *sc, double beta_k,
+                       orc_node *tree, int32_t i, int32_t depth_left)
+{
+    orc_node *nd = &tree[i];
+    nd->w = orc_energy(mat, nd->F, beta_k);
+    nd->flags |= ORC_EXISTS;
+    nd->dir = -1;
+    nd->m_minus = nd->m_plus = (sc->L - 1) / 2;
+    nd->h = nd->w;
+    nd->xi = 0.0;
+    nd->margin = INFINITY;
+    if (depth_left == 0) {
+        nd->flags |= ORC_LEAF;
+        return;
+    }
+    double h, margin;
+    int32_t mm, mp;
+    int32_t j = orc_scan_node(mat, sc, nd->F, beta_k, NULL, NULL, NULL, NULL, &h, &mm, &mp,
+                              &margin);
+    nd->flags |= ORC_SCANNED;
+    nd->dir = j;
+    nd->h = h;
+    nd->m_minus = mm;
+    nd->m_plus = mp;
+    nd->margin = margin;
+    int32_t m0 = (sc->L - 1) / 2;
+    if (mm == m0) {
+        nd->flags |= ORC_LEAF;
+        return;
+    }
+    nd->flags |= ORC_LAMINATED;
+    double R[4];
+    rank_one(sc->dir + 4 * j, R);
+    double hstep = 2.0 * sc->t_half / (double)(sc->L - 1);
+    double tm = (double)(mm - m0) * hstep, tp = (double)(mp - m0) * hstep;
+    /* Algorithm 2: xi = |F - F-|_1 / |F+ - F-|_1 = (m0 - m-)/(m+ - m-) */
+    nd->xi = (double)(m0 - mm) / (double)(mp - mm);
+    orc_node *cm = &tree[2 * i + 1], *cp = &tree[2 * i + 2];
+    for (int k = 0; k < 4; ++k) {
+        cm->F[k] = nd->F[k] + tm * R[k];
+        cp->F[k] = nd->F[k] + tp * R[k];
+    }
+    cm->weight = nd->weight * (1.0 - nd->xi);
+    cp->weight = nd->weight * nd->xi;
+    build_tree(mat, sc, beta_k, tree, 2 * i + 1, depth_left - 1);
+    build_tree(mat, sc, beta_k, tree, 2 * i + 2, depth_left - 1);
+}
+
+/* Algorithm 3: recursive evaluation of W, P as the xi-weighted sum over
+ * children; leaves evaluate the non-convex W and its derivative. */
+static void eval_tree(const orc_material *mat, double beta_k, const orc_node *tree,
+                      int32_t i, double *W, double P[4])
+{
+    const orc_node *nd = &tree[i];
+    if (!(nd->flags & ORC_LAMINATED)) {
+        *W = orc_energy(mat, nd->F, beta_k);
+        orc_stress(mat, nd->F, beta_k, P);
+        return;
+    }
+    double Wm, Wp, Pm[4], Pp[4];
+    eval_tree(mat, beta_k, tree, 2 * i + 1, &Wm, Pm);
+    eval_tree(mat, beta_k, tree, 2 * i + 2, &Wp, Pp);
+    *W = (1.0 - nd->xi) * Wm + nd->xi * Wp;
+    for (int k = 0; k < 4; ++k)
+        P[k] = (1.0 - nd->xi) * Pm[k] + nd->xi * Pp[k];
+}
+
+int32_t orc_tree_size(int32_t depth)
+{
+    return (1 << (depth + 1)) - 1;
+}
+
+/* Per-point convexification: W^R, P and the tree (n x (2^{K+1}-1) nodes,
+ * may be NULL).  status[p] = 1 where det F <= 0 (W^R, P = NaN). */
+void orc_convexify(const orc_material *mat, const orc_scan *sc, int64_t n, const double *F,
+                   const double *beta_k, double *W_R, double *P, orc_node *tree,
+                   int32_t *status, int32_t nthreads)
+{
+    int32_t nt = orc_tree_size(sc->depth);
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t p = 0; p < n; ++p) {
+        orc_node *tr = tree ? tree + p * nt : (orc_node *)calloc(nt, sizeof(orc_node));
+        if (tree)
+            memset(tr, 0, sizeof(orc_node) * nt);
+        const double *Fp = F + 4 * p;
+        double J = Fp[0] * Fp[3] - Fp[1] * Fp[2];
+        if (mat->energy != 1 && !(J > 0.0)) {
+            W_R[p] = NAN;
+            for (int k = 0; k < 4; ++k)
+                P[4 * p + k] = NAN;
+            status[p] = ORC_NONPOS_DET;
+            if (!tree)
+                free(tr);
+            continue;
+        }
+        memcpy(tr[0].F, Fp, sizeof(double) * 4);
+        tr[0].weight = 1.0;
+        build_tree(mat, sc, beta_k[p], tr, 0, sc->depth);
+        eval_tree(mat, beta_k[p], tr, 0, &W_R[p], P + 4 * p);
+        status[p] = ORC_OK;
+        if (!tree)
+            free(tr);
+    }
+}
+
+int32_t orc_node_size(void)
+{
+    return (int32_t)sizeof(orc_node);
+}

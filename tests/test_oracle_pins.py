@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of the expected values comes from
+the CUDA path: they are the paper's printed numbers (tests/golden, cited in the
+file headers), closed forms, invariants or brute force on tiny inputs.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from conftest import load_golden
+
+# Material of Tables tab:biaxialperturbation / tab:3Dconvexification (NH rows).
+MU, LAM, D0, DINF = 1.0, 0.5, 0.3, 0.9
+
+
+def _fit_beta(orc, mat, W_identity):
+    """beta_k is not printed (or printed rounded): fit it from W(I) = -(1 - D_k) beta_k
+    by bisection (W(I) is monotone in beta_k)."""
+    lo, hi = 1e-9, 1.0
+    f = lambda b: orc.energy(mat, [1, 0, 0, 1], b) - W_identity  # noqa: E731
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (f(lo) > 0) == (f(mid) > 0):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_energy_2d_printed_lines(orc):
+    """Eq. (2.9), plane strain: the printed W along diag(s, 1) and diag(s, s)
+    (Sec. 6.6, NH biaxial figures) with one fitted constant beta_k."""
+    g = load_golden("nh2d_biaxial_lines.txt")
+    mat = orc.Material(MU, LAM, DINF, D0)
+    beta = _fit_beta(orc, mat, g[0, 1])
+    for s, w1, _, w2, _ in g[1:]:
+        assert abs(orc.energy(mat, [s, 0, 0, 1], beta) - w1) < 1e-14
+        assert abs(orc.energy(mat, [s, 0, 0, s], beta) - w2) < 1e-14
+
+
+def test_energy_3d_printed_paths(orc):
+    """Eq. (2.9) in 3-D invariants along the uni/bi/triaxial paths of Sec. 6.8
+    (figure 3dconvexification-lines).  Uniaxial diag(s,1,1) and biaxial
+    diag(s,s,1) coincide with plane strain diag(s,1), diag(s,s); triaxial uses
+    I1 = 3 s^2, J = s^3 in Eq. (2.3).  The fitted beta_k must round to the
+    printed 0.0625 (Table tab:3Dconvexification)."""
+    g = load_golden("nh3d_paths.txt")
+    mat = orc.Material(MU, LAM, DINF, D0)
+    beta = _fit_beta(orc, mat, g[0, 1])
+    assert abs(beta - 0.0625) < 5e-5
+    for s, wu, _, wb, _, wt, _ in g:
+        assert abs(orc.energy(mat, [s, 0, 0, 1], beta) - wu) < 1e-14
+        assert abs(orc.energy(mat, [s, 0, 0, s], beta) - wb) < 1e-14
+        psi = orc.psi0_nh(3 * s * s, s ** 3, MU, LAM)
+        assert abs(orc.W_of_psi0(psi, beta, DINF, D0) - wt) < 1e-14
+
+
+def test_alg1_reproduces_printed_uniaxial_hull(orc):
+    """Algorithm 1 on the printed uniaxial W samples gives the printed relaxed
+    curve (the uniaxial path is a rank-one line, Sec. 6.8)."""
+    g = load_golden("nh3d_paths.txt")
+    x, w, wrc = g[:, 0], g[:, 1], g[:, 2]
+    v = orc.lower_hull(x, w)
+    assert list(np.round(x[v], 2)) == [1.0, 1.15, 3.1, 3.25, 3.4]
+    interp = np.interp(x, x[v], w[v])
+    # the printed curve carries ~1e-12 of the paper's own interpolation noise
+    assert np.max(np.abs(interp - wrc)) < 5e-12
+
+
+def test_line_scan_reproduces_printed_rank_one_relaxation(orc):
+    """Per-point line scan (Eq. 4.4 + Alg. 1 + value at l = 0) along e1 (x) e1
+    on the grid delta = 0.15, F11 in [1.0, 3.4] gives the printed W^15 on the
+    rank-one line diag(s, 1) (Sec. 6.6).  Beyond the grid the paper's values
+    are unrelaxed."""
+    g = load_golden("nh2d_biaxial_lines.txt")
+    mat = orc.Material(MU, LAM, DINF, D0)
+    beta = _fit_beta(orc, mat, g[0, 1])
+    R = np.array([1.0, 0.0, 0.0, 0.0])
+    half = 16
+    L = 2 * half + 1
+    worst = 0.0
+    for s, w_plain, w15, _, _ in g:
+        if s > 3.4 + 1e-9:
+            assert abs(w15 - w_plain) < 1e-14
+            continue
+        w, valid = orc.sample_line(mat, [s, 0, 0, 1], beta, R, L, 0.15 * half)
+        f11 = s + 0.15 * (np.arange(L) - half)
+        valid &= (f11 > 1.0 - 1e-9) & (f11 < 3.4 + 1e-9)
+        h, mm, mp, _ = orc.line_bridge(w, valid)
+        worst = max(worst, abs(h - w15))
+    assert worst < 1e-9
+
+
+def _brute_vertices(x, w):
+    """Strict lower-hull vertices by definition: the end points, and every k
+    that lies strictly below every chord (i, j) with i < k < j."""
+    n = len(x)
+    out = []
+    for k in range(n):
+        ok = True
+        for i in range(k):
+            for j in range(k + 1, n):
+                chord = (w[i] * (x[j] - x[k]) + w[j] * (x[k] - x[i])) / (x[j] - x[i])
+                if not w[k] < chord:
+                    ok = False
+                    break
+            if not ok:
+                break
+        if ok:
+            out.append(k)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_alg1_matches_brute_force_vertices(orc, seed):
+    """Algorithm 1 returns exactly the strict lower-hull vertices (O(n^3) brute
+    force).  Small integer values make collinear triples frequent, so the ">="
+    pop rule is exercised; the arithmetic is exact."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 25))
+    x = np.sort(rng.choice(np.arange(-30, 31), size=n, replace=False)).astype(float)
+    w = rng.integers(-4, 5, size=n).astype(float)
+    assert list(orc.lower_hull(x, w)) == _brute_vertices(x, w)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_bridge_is_min_over_pairs(orc, seed):
+    """Value of the hull at x = 0 equals min(w_0, min over pairs a < 0 < b of
+    the chord at 0) (Caratheodory in 1-D); the bridge vertices attain it."""
+    rng = np.random.default_rng(1000 + seed)
+    L = int(rng.integers(1, 21)) * 2 + 1
+    m0 = (L - 1) // 2
+    w = rng.normal(size=L) + 0.02 * (np.arange(L) - m0) ** 2
+    valid = rng.random(L) > 0.2
+    valid[m0] = True
+    h, mm, mp, margin = orc.line_bridge(w, valid)
+    best = w[m0]
+    for a in range(m0):
+        for b in range(m0 + 1, L):
+            if valid[a] and valid[b]:
+                xa, xb = a - m0, b - m0
+                best = min(best, (xb * w[a] - xa * w[b]) / (xb - xa))
+    assert abs(h - best) < 1e-12
+    if mm != mp:
+        xa, xb = mm - m0, mp - m0
+        assert abs((xb * w[mm] - xa * w[mp]) / (xb - xa) - best) < 1e-12
+        assert margin >= 0
+    else:
+        assert mm == m0 and abs(best - w[m0]) < 1e-12
+
+
+def test_margin_certifies_decision(orc):
+    """The bridge margin is a certificate: perturbing each sample by less than
+    it never changes the bridge (random perturbations, many trials)."""
+    rng = np.random.default_rng(7)
+    L = 41
+    m0 = 20
+    checked = 0
+    for trial in range(200):
+        w = rng.normal(size=L) * 0.3 + 0.01 * (np.arange(L) - m0) ** 2
+        h, mm, mp, margin = orc.line_bridge(w)
+        if not (0 < margin < 10):
+            continue
+        for _ in range(20):
+            d = rng.uniform(-0.999, 0.999, size=L) * margin
+            _, mm2, mp2, _ = orc.line_bridge(w + d)
+            assert (mm2, mp2) == (mm, mp)
+        checked += 1
+    assert checked > 50
+
+
+def _dw_scan(orc, Na=8, L=301, t_half=1.5, depth=1):
+    return orc.Scan(orc.angle_directions(Na, Na), L, t_half, depth)
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_double_well_closed_form_at_origin(orc, depth):
+    """Double well W = (F11^2-1)^2 + F12^2 + F21^2 + (F22-1)^2: at F = diag(0, 1)
+    the rank-one convex envelope is 0, reached by the laminate diag(+-1, 1) with
+    xi = 1/2 along e1 (x) e1 (direction 0), and P = 0 for every depth."""
+    mat = orc.Material(energy=1)
+    sc = _dw_scan(orc, depth=depth)
+    WR, P, tree, st = orc.convexify(mat, sc, np.array([[0.0, 0, 0, 1]]), np.zeros(1))
+    assert abs(WR[0]) < 1e-15 and np.max(np.abs(P[0])) < 1e-12
+    root = tree[0, 0]
+    assert root["dir"] == 0 and root["flags"] & orc.LAMINATED
+    assert abs(root["xi"] - 0.5) < 1e-15
+    np.testing.assert_allclose(tree[0, 1]["F"], [-1, 0, 0, 1], atol=1e-14)
+    np.testing.assert_allclose(tree[0, 2]["F"], [1, 0, 0, 1], atol=1e-14)
+
+
+def test_double_well_separable_envelope(orc):
+    """Closed form away from the origin: for |F11| <= 1 on the line grid,
+    W^rc = F12^2 + F21^2 + (F22 - 1)^2 (convex envelope of the separable double
+    well, both wells inside the line window); for |F11| > 1 the point is on the
+    convex part and W^R = W."""
+    mat = orc.Material(energy=1)
+    sc = _dw_scan(orc, depth=2)
+    F = np.array([[0.3, 0.1, -0.2, 1.2], [-0.4, 0.0, 0.05, 0.9], [1.2, 0.1, 0.0, 1.0]])
+    WR, P, tree, st = orc.convexify(mat, sc, F, np.zeros(3))
+    rest = F[:, 1] ** 2 + F[:, 2] ** 2 + (F[:, 3] - 1) ** 2
+    assert abs(WR[0] - rest[0]) < 1e-12 and abs(WR[1] - rest[1]) < 1e-12
+    assert abs(WR[2] - orc.energy(mat, F[2], 0.0)) < 1e-12
+
+
+def test_stress_is_gradient_of_energy(orc):
+    """Eq. (2.12): P = dW/dF against central differences of Eq. (2.9), on both
+    branches of the history (s < beta_k and s > beta_k); P(I) = 0."""
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        F = np.array([1, 0, 0, 1.0]) + rng.normal(0, 0.25, 4)
+        if F[0] * F[3] - F[1] * F[2] < 0.3:
+            continue
+        beta = rng.choice([0.0, 0.05, 0.4, 3.0])
+        P = orc.stress(mat, F, beta)
+        s = orc.psi0_F(mat, F)
+        e = 1e-6
+        for k in range(4):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[k] += e
+            Fm[k] -= e
+            if (orc.psi0_F(mat, Fp) - beta) * (orc.psi0_F(mat, Fm) - beta) < 0:
+                continue  # kink of max(s, beta_k) inside the stencil
+            fd = (orc.energy(mat, Fp, beta) - orc.energy(mat, Fm, beta)) / (2 * e)
+            assert abs(fd - P[k]) < 1e-7 * max(1.0, abs(P[k])), (F, beta, k, fd, P[k], s)
+    assert np.max(np.abs(orc.stress(mat, [1, 0, 0, 1], 0.2))) < 1e-15
+
+
+def test_undamaged_neo_hooke_is_not_relaxed(orc):
+    """With D_inf = 0, W = psi0 - beta_k is convex along every rank-one line
+    where ln J <= 1 + mu/lam (second derivative along the line is
+    mu|R|^2 + (c_J/J)^2 (mu + lam (1 - ln J)) >= 0), so W^R = W exactly."""
+    mat = orc.Material(1.0, 5.0, 0.0, 0.5)
+    F = np.array([[1.3, 0.1, -0.05, 0.9], [1.1, 0.0, 0.0, 1.1], [0.95, 0.2, 0.1, 1.05]])
+    sc = orc.Scan(orc.angle_directions(8, 8), 101, 0.5, 2)
+    for p in range(len(F)):
+        for d in sc.dirs:
+            R = orc.rank_one(d)
+            t = np.linspace(-0.5, 0.5, 101)
+            J = np.array([np.linalg.det((F[p] + ti * R).reshape(2, 2)) for ti in t])
+            assert np.all(np.log(J[J > 0]) <= 1.0 + 1.0 / 5.0)
+    WR, P, tree, st = orc.convexify(mat, sc, F, np.zeros(3))
+    for p in range(3):
+        assert WR[p] == orc.energy(mat, F[p], 0.0)
+        assert not tree[p, 0]["flags"] & orc.LAMINATED
+
+
+def _tree_leaves(orc, tr):
+    leaves = []
+
+    def rec(i):
+        if tr[i]["flags"] & orc.LAMINATED:
+            rec(2 * i + 1)
+            rec(2 * i + 2)
+        else:
+            leaves.append(i)
+
+    rec(0)
+    return leaves
+
+
+def test_tree_invariants_and_depth_chain(orc):
+    """Lamination tree (Sec. 4.3, Alg. 2): leaves form an H_M sequence (Eq. 3.4):
+    weights sum to 1, the weighted mean of the leaves is F, every split is
+    rank-one and lies on the chosen line; and the depth chain
+    W^R(K=3) <= W^R(K=2) <= W^R(K=1) <= W (Eq. 3.3)."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F, Fp = inputs.material_points(16, seed=5)
+    beta = orc.history_update(mat, Fp)
+    dirs = orc.angle_directions(8, 8)
+    prev = np.array([orc.energy(mat, F[p], beta[p]) for p in range(16)])
+    for K in (1, 2, 3):
+        sc = orc.Scan(dirs, 101, 0.5, K)
+        WR, P, tree, st = orc.convexify(mat, sc, F, beta)
+        assert np.all(WR <= prev + 1e-14)
+        prev = WR
+        for p in range(16):
+            tr = tree[p]
+            leaves = _tree_leaves(orc, tr)
+            wsum = sum(tr[i]["weight"] for i in leaves)
+            assert abs(wsum - 1.0) < 1e-14
+            mean = sum(tr[i]["weight"] * tr[i]["F"] for i in leaves)
+            np.testing.assert_allclose(mean, F[p], atol=1e-13)
+            for i in range(len(tr)):
+                if tr[i]["flags"] & orc.LAMINATED:
+                    d = (tr[2 * i + 2]["F"] - tr[2 * i + 1]["F"]).reshape(2, 2)
+                    assert abs(np.linalg.det(d)) < 1e-13
+                    R = orc.rank_one(dirs[tr[i]["dir"]])
+                    tp = (tr[i]["m_plus"] - sc.m0) * sc.h
+                    np.testing.assert_allclose(tr[2 * i + 2]["F"], tr[i]["F"] + tp * R, atol=1e-14)
+            Wsum = sum(tr[i]["weight"] * orc.energy(mat, tr[i]["F"], beta[p]) for i in leaves)
+            assert abs(Wsum - WR[p]) < 1e-13
+
+
+def _exact_lamination(orc, mat, dirs, L, t_half, K, F, beta):
+    """Bottom-up discrete lamination by brute force on a tiny grid:
+    W^0 = W, W^K(F) = min over R of hull_t[W^{K-1}(F + t_m R)](0)."""
+    if K == 0:
+        return orc.energy(mat, F, beta)
+    m0 = (L - 1) // 2
+    h = 2 * t_half / (L - 1)
+    best = math.inf
+    for d in dirs:
+        R = orc.rank_one(d)
+        w = np.full(L, np.nan)
+        valid = np.zeros(L, dtype=bool)
+        for m in range(L):
+            G = F + (m - m0) * h * R
+            if G[0] * G[3] - G[1] * G[2] > 0:
+                valid[m] = True
+                w[m] = _exact_lamination(orc, mat, dirs, L, t_half, K - 1, G, beta)
+        hv, _, _, _ = orc.line_bridge(np.where(valid, w, 0.0), valid)
+        best = min(best, hv)
+    return best
+
+
+def test_top_down_bounds_exact_lamination(orc):
+    """Eq. (3.3) chain on tiny grids: W^2_exact <= V_2 <= V_1 = W^1_exact <= W,
+    where V_K is the top-down per-point value and W^K_exact the bottom-up
+    discrete lamination computed by brute force."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F, Fp = inputs.material_points(6, seed=11, lam_lo=1.2, lam_hi=1.6)
+    beta = orc.history_update(mat, Fp)
+    dirs = orc.angle_directions(2, 2)
+    L, t_half = 7, 0.5
+    V = {}
+    for K in (1, 2):
+        V[K] = orc.convexify(mat, orc.Scan(dirs, L, t_half, K), F, beta)[0]
+    for p in range(6):
+        W = orc.energy(mat, F[p], beta[p])
+        e1 = _exact_lamination(orc, mat, dirs, L, t_half, 1, F[p], beta[p])
+        e2 = _exact_lamination(orc, mat, dirs, L, t_half, 2, F[p], beta[p])
+        assert abs(V[1][p] - e1) < 1e-14
+        assert e2 <= V[2][p] + 1e-14 and V[2][p] <= V[1][p] + 1e-14 and V[1][p] <= W + 1e-14
+
+
+def test_history_update(orc):
+    """Eq. (2.5): beta_new = max(beta_k, psi0(F))."""
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F = np.array([[1.3, 0, 0, 1.0], [1.0, 0, 0, 1.0]])
+    b = orc.history_update(mat, F, np.array([0.0, 0.3]))
+    assert abs(b[0] - orc.psi0_F(mat, F[0])) < 1e-15 and b[1] == 0.3
+
+
+def test_directions_cover_half_circle(orc):
+    """Angle grid: a_i = (cos pi i/Na, sin pi i/Na), |a| = |b| = 1 (so |R|_F = 1),
+    index j = i Nb + j."""
+    d = orc.angle_directions(4, 3)
+    assert d.shape == (12, 4)
+    np.testing.assert_allclose(d[:, 0] ** 2 + d[:, 1] ** 2, 1.0, atol=1e-15)
+    np.testing.assert_allclose(d[5], [math.cos(math.pi / 4), math.sin(math.pi / 4),
+                                      math.cos(2 * math.pi / 3), math.sin(2 * math.pi / 3)])
