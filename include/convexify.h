@@ -1,0 +1,223 @@
+/*
+ * convexify.h -- C ABI of the GB300 per-point rank-one convexification library
+ * (libconvexify.so).
+ *
+ * Method: Balzani, Koehler, Neumeier, Peter, Peterseim, "Multidimensional
+ * rank-one convexification of incremental damage models at finite strains"
+ * (arXiv 2211.14318).  For every quadrature point F in R^{2x2} with history
+ * beta_k, the incremental stress potential W (Eq. 2.9) is sampled along rank-one
+ * lines F + t a (x) b (Eq. 4.4, restated per point), each line is convexified
+ * (Algorithm 1) and read at t = 0, the minimum over directions is taken
+ * (Eq. 4.3), and the split is recursed to the lamination depth K (Eq. 3.3).
+ * W^R and P = dW^R/dF are evaluated over the resulting lamination tree
+ * (Eq. 5.2, Algorithm 3).
+ *
+ * Conventions
+ *  - Every function returns an int status: CVX_OK (0) or a negative CVX_ERR_*.
+ *    cvx_last_error() returns the message of the calling thread's last error.
+ *    No C++ exception crosses this boundary.
+ *  - F is row-major (F11, F12, F21, F22).  All array arguments of the compute
+ *    calls are caller-owned DEVICE pointers unless stated otherwise; the caller
+ *    keeps them alive until the stream has reached the end of the call.
+ *  - Calls are asynchronous on the given stream (NULL = legacy default stream),
+ *    except where marked "synchronous".  Arguments are validated (parameters
+ *    first, then the handle and pointers) before anything is enqueued or any
+ *    CUDA call is made.  Kernel faults surface as
+ *    CVX_ERR_CUDA from this or a later call.
+ *  - The library owns the handle's workspace (grown on demand with cudaMalloc)
+ *    and its direction tables.  A handle may be used by one host thread at a
+ *    time; work of one handle is serialised on the streams it is given.
+ *  - Arithmetic: W is sampled in FP32 on the CUDA cores; the hull predicates
+ *    are exact (FP32 filter with an exact FP64 fallback), directions are
+ *    compared in FP64, and the split points, W^R and P are evaluated in FP64.
+ */
+#ifndef CONVEXIFY_H
+#define CONVEXIFY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum cvx_error {
+    CVX_OK = 0,
+    CVX_ERR_INVALID_ARG = -1, /* argument out of range, NULL where required     */
+    CVX_ERR_CUDA = -2,        /* CUDA runtime error (message has the CUDA text) */
+    CVX_ERR_OOM = -3,         /* workspace allocation failed                    */
+    CVX_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up             */
+    CVX_ERR_NOT_TRAINED = -5, /* surrogate used before training or loading      */
+    CVX_ERR_UNSUPPORTED = -6  /* configuration not built into this library      */
+};
+
+/* per-point status bits (int32 per point) */
+enum cvx_point_status {
+    CVX_PT_OK = 0,
+    CVX_PT_NONPOS_DET = 1, /* det F <= 0: W^R and P are NaN, no tree          */
+    CVX_PT_TIE = 2,        /* some node's two best directions were closer than
+                              the FP32 sampling error bound (warning only)     */
+    CVX_PT_EDGE = 4,       /* some split point lies on the end of its line     */
+    CVX_PT_ITER_CAP = 8    /* a hull search hit its iteration cap (warning)    */
+};
+
+/* energy kinds */
+enum cvx_energy_kind {
+    CVX_ENERGY_NH_DAMAGE = 0,  /* plane-strain Neo-Hooke with exponential damage,
+                                  Eqs. (2.3)-(2.9)                              */
+    CVX_ENERGY_DOUBLE_WELL = 1 /* test energy (F11^2-1)^2 + F12^2 + F21^2 +
+                                  (F22-1)^2, closed-form envelope; not in the
+                                  paper                                         */
+};
+
+typedef struct cvx_handle cvx_handle;
+typedef struct CUstream_st *cvx_stream; /* same object as cudaStream_t */
+
+/* Problem parameters.  Material of Sec. 2 (mu, lambda, D_inf, D_0 of Eq. 2.6).
+ * Directions: the angle grid a_i = (cos pi i/Na, sin pi i/Na), b_j likewise,
+ * direction index j_dir = i * Nb + j (a discrete subset of the rank-one cone
+ * of Sec. 4.1); or, if dirs != NULL, n_dirs custom (a1, a2, b1, b2) rows
+ * (HOST pointer, copied), e.g. the reduced set R^1_1 of Eq. (5.1).
+ * Line: L = line_points samples t_m = (m - m0) h, m0 = (L-1)/2,
+ * h = 2 t_half / (L-1), so t = 0 (the point itself) is sampled exactly;
+ * samples with det(F + t R) <= 0 are excluded.  depth = K, 0 <= K <= 8. */
+typedef struct cvx_params {
+    double mu;
+    double lambda_L;
+    double D_inf;
+    double D0;
+    double t_half;
+    const double *dirs; /* host, n_dirs x 4, or NULL for the angle grid */
+    int32_t energy;     /* enum cvx_energy_kind                          */
+    int32_t n_theta_a;
+    int32_t n_theta_b;
+    int32_t n_dirs;
+    int32_t line_points; /* odd, 3 <= L <= 2079                          */
+    int32_t depth;
+    int32_t flags; /* reserved, must be 0                                */
+    int32_t reserved;
+} cvx_params;
+
+/* Node of the per-point lamination tree (Sec. 4.3, Algorithm 2), heap layout:
+ * node i has children 2i+1 (F-) and 2i+2 (F+); 2^{K+1}-1 nodes per point. */
+typedef struct cvx_node {
+    double F[4];     /* deformation gradient of this node                     */
+    double w;        /* W(F), FP64                                            */
+    double h;        /* hull of the FP32 samples at t = 0 along the chosen
+                        direction (= W(F) sample if the node does not split)  */
+    double xi;       /* weight of F+ in this node's split, (m0-m-)/(m+-m-)    */
+    double weight;   /* product of split weights from the root                */
+    int32_t dir;     /* chosen direction index, -1 if the node was not scanned */
+    int32_t m_minus; /* sample index of F- on the chosen line (0..L-1)         */
+    int32_t m_plus;  /* sample index of F+                                     */
+    int32_t flags;   /* CVX_NODE_* bits                                        */
+    float gap;       /* FP32 gap between the two best directions' hull values  */
+    int32_t pad;
+} cvx_node;
+
+enum cvx_node_flags {
+    CVX_NODE_EXISTS = 1,
+    CVX_NODE_SCANNED = 2,
+    CVX_NODE_LAMINATED = 4,
+    CVX_NODE_LEAF = 8,
+    CVX_NODE_TIE = 16,
+    CVX_NODE_EDGE = 32
+};
+
+/* Root laminate of a point: direction a (x) b = dirs[dir], volume fraction xi
+ * of F+, and F+- (Fig. fig:RankOneConvexification1D). */
+typedef struct cvx_laminate {
+    int32_t laminated; /* 0: the point is rank-one convex on its lines */
+    int32_t dir;
+    int32_t m_minus;
+    int32_t m_plus;
+    double xi;
+    double h;
+    double F_plus[4];
+    double F_minus[4];
+} cvx_laminate;
+
+/* Counters accumulated on the device over all calls since the last reset. */
+typedef struct cvx_stats {
+    int64_t points;         /* points convexified                          */
+    int64_t nodes_scanned;  /* tree nodes whose lines were scanned         */
+    int64_t lines;          /* (node, direction) lines sampled             */
+    int64_t valid_samples;  /* samples with det > 0 (algorithmic work)     */
+    int64_t laminated;      /* nodes that split                            */
+    int64_t fp64_checks;    /* exact FP64 predicate evaluations            */
+    int64_t full_passes;    /* full-line argmin passes of the hull search  */
+    int64_t rare_paths;     /* hull searches that left the fast path       */
+    int64_t ties;           /* nodes flagged CVX_NODE_TIE                  */
+    int64_t iter_caps;      /* hull searches that hit the iteration cap    */
+} cvx_stats;
+
+/* ----------------------------------------------------------------- handles */
+
+/* Creates a handle bound to CUDA device `device` (the calling thread's current
+ * device is left unchanged).  Synchronous.  Errors: INVALID_ARG, CUDA. */
+int cvx_create(cvx_handle **out, int device);
+
+/* Frees the handle's workspace and tables.  Synchronous (waits for the
+ * device).  NULL is accepted. */
+int cvx_destroy(cvx_handle *h);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to len) into buf.  Returns the length of the full message. */
+int cvx_last_error(char *buf, size_t len);
+
+/* Reads (synchronous: waits for the handle's device) and optionally resets
+ * the counters. */
+int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset);
+
+/* sizeof of the ABI structs, for bindings to check their layouts:
+ * which = 0 cvx_params, 1 cvx_node, 2 cvx_laminate, 3 cvx_stats; -1 otherwise. */
+int cvx_struct_size(int which);
+
+/* Sets the launch shape of the line-scan kernel: warps per CTA (1..16) and
+ * directions per work item (>= 1; 0 = automatic).  Used by the autotuner. */
+int cvx_set_tuning(cvx_handle *h, int warps_per_cta, int dirs_per_item);
+
+/* ----------------------------------------------------- steps of the method */
+
+/* W(F) and P = dW/dF in FP64 at n points (Eqs. 2.9, 2.12), plane strain.
+ * F: n x 4, beta_k: n, W: n, P: n x 4 (P may be NULL).  det F <= 0 gives NaN. */
+int cvx_energy(cvx_handle *h, const cvx_params *p, int64_t n, const double *F,
+               const double *beta_k, double *W, double *P, cvx_stream s);
+
+/* History update between load steps, Eq. (2.5): beta_out = max(beta_in,
+ * psi0(F)).  beta_in may be NULL (treated as 0); beta_out may alias beta_in. */
+int cvx_history_update(cvx_handle *h, const cvx_params *p, int64_t n, const double *F,
+                       const double *beta_in, double *beta_out, cvx_stream s);
+
+/* FP32 samples of W along n_lines lines F_i + t a (x) b with direction
+ * dir_i (Eq. 4.4 per point): w is n_lines x L, NaN where det <= 0.
+ * F: n_lines x 4, beta_k: n_lines, dir: n_lines (int32).  The same samples
+ * the convexification kernel computes. */
+int cvx_sample_lines(cvx_handle *h, const cvx_params *p, int64_t n_lines, const double *F,
+                     const double *beta_k, const int32_t *dir, float *w, cvx_stream s);
+
+/* Lower hull (Algorithm 1) of n_lines given FP32 lines of L samples at the
+ * integer abscissae m - m0 (NaN = excluded; the non-NaN samples must be
+ * contiguous and include m0), read at x = 0: bridge vertices m_minus <= m0 <=
+ * m_plus (both m0 if m0 is a strict vertex) and the value h in FP64.
+ * Exact: the result is the hull of the FP32 values.  3 <= L <= 2079, odd. */
+int cvx_hull_bridge(cvx_handle *h, int64_t n_lines, int32_t L, const float *w,
+                    int32_t *m_minus, int32_t *m_plus, double *hval, cvx_stream s);
+
+/* --------------------------------------------------------- the hot path */
+
+/* Per-point rank-one convexification of n points (Sec. 4-5):
+ *   W_R (n), P (n x 4)            relaxed energy and stress, FP64;
+ *   status (n)                    CVX_PT_* bits;
+ *   root (n, nullable)            root laminate;
+ *   tree (n x (2^{K+1}-1), nullable) full lamination tree.
+ * Workspace: the handle's (grown with cudaMalloc when needed). */
+int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double *F,
+                     const double *beta_k, double *W_R, double *P, cvx_laminate *root,
+                     cvx_node *tree, int32_t *status, cvx_stream s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONVEXIFY_H */

@@ -1,0 +1,286 @@
+"""Python binding of libconvexify (C ABI in include/convexify.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Tensors are torch CUDA tensors; calls are enqueued on the current
+torch stream.  There is no CPU fallback: if the library is missing or no GPU
+is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libconvexify.so")
+
+CVX_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NOT_TRAINED",
+          -6: "UNSUPPORTED"}
+ENERGY_NH_DAMAGE, ENERGY_DOUBLE_WELL = 0, 1
+PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP = 1, 2, 4, 8
+NODE_EXISTS, NODE_SCANNED, NODE_LAMINATED, NODE_LEAF, NODE_TIE, NODE_EDGE = 1, 2, 4, 8, 16, 32
+
+NODE_DTYPE = np.dtype([
+    ("F", "<f8", (4,)), ("w", "<f8"), ("h", "<f8"), ("xi", "<f8"), ("weight", "<f8"),
+    ("dir", "<i4"), ("m_minus", "<i4"), ("m_plus", "<i4"), ("flags", "<i4"),
+    ("gap", "<f4"), ("pad", "<i4"),
+])
+LAMINATE_DTYPE = np.dtype([
+    ("laminated", "<i4"), ("dir", "<i4"), ("m_minus", "<i4"), ("m_plus", "<i4"),
+    ("xi", "<f8"), ("h", "<f8"), ("F_plus", "<f8", (4,)), ("F_minus", "<f8", (4,)),
+])
+
+
+class CvxError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("mu", ctypes.c_double), ("lambda_L", ctypes.c_double), ("D_inf", ctypes.c_double),
+        ("D0", ctypes.c_double), ("t_half", ctypes.c_double),
+        ("dirs", ctypes.POINTER(ctypes.c_double)),
+        ("energy", ctypes.c_int32), ("n_theta_a", ctypes.c_int32), ("n_theta_b", ctypes.c_int32),
+        ("n_dirs", ctypes.c_int32), ("line_points", ctypes.c_int32), ("depth", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
+        "full_passes", "rare_paths", "ties", "iter_caps")]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libconvexify.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise CvxError(f"{LIB_PATH} is missing: build it with paper_2211_14318_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sigs = {
+        "cvx_create": [ctypes.POINTER(vp), ctypes.c_int],
+        "cvx_destroy": [vp],
+        "cvx_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+        "cvx_get_stats": [vp, ctypes.POINTER(_Stats), ctypes.c_int],
+        "cvx_set_tuning": [vp, ctypes.c_int, ctypes.c_int],
+        "cvx_struct_size": [ctypes.c_int],
+        "cvx_energy": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp],
+        "cvx_history_update": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp],
+        "cvx_sample_lines": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp],
+        "cvx_hull_bridge": [vp, i64, i32, vp, vp, vp, vp, vp],
+        "convexify_points": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp, vp, vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols() -> Sequence[str]:
+    return ("cvx_create", "cvx_destroy", "cvx_last_error", "cvx_get_stats", "cvx_struct_size",
+            "cvx_set_tuning",
+            "cvx_energy", "cvx_history_update", "cvx_sample_lines", "cvx_hull_bridge",
+            "convexify_points")
+
+
+def _check(rc: int, what: str):
+    if rc != CVX_OK:
+        buf = ctypes.create_string_buffer(512)
+        lib().cvx_last_error(buf, 512)
+        raise CvxError(f"{what}: {ERRORS.get(rc, rc)}: {buf.value.decode(errors='replace')}")
+
+
+@dataclass
+class Params:
+    """cvx_params: material (Sec. 2), directions, line, depth."""
+    mu: float = 1.0
+    lambda_L: float = 5.0
+    D_inf: float = 0.99
+    D0: float = 0.5
+    n_theta_a: int = 16
+    n_theta_b: int = 16
+    line_points: int = 201
+    t_half: float = 0.5
+    depth: int = 2
+    energy: int = ENERGY_NH_DAMAGE
+    dirs: Optional[np.ndarray] = None  # custom (n, 4) rows (a1, a2, b1, b2)
+    _keep: list = field(default_factory=list, repr=False)
+
+    def c(self) -> _Params:
+        p = _Params()
+        p.mu, p.lambda_L, p.D_inf, p.D0, p.t_half = self.mu, self.lambda_L, self.D_inf, self.D0, self.t_half
+        p.energy, p.n_theta_a, p.n_theta_b = self.energy, self.n_theta_a, self.n_theta_b
+        p.line_points, p.depth, p.flags, p.reserved = self.line_points, self.depth, 0, 0
+        if self.dirs is not None:
+            d = np.ascontiguousarray(self.dirs, dtype=np.float64).reshape(-1, 4)
+            self._keep = [d]
+            p.dirs = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            p.n_dirs = d.shape[0]
+        else:
+            p.dirs = None
+            p.n_dirs = 0
+        return p
+
+    @property
+    def n_dirs(self) -> int:
+        return self.dirs.shape[0] if self.dirs is not None else self.n_theta_a * self.n_theta_b
+
+    @property
+    def tree_size(self) -> int:
+        return (1 << (self.depth + 1)) - 1
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None) -> Optional[int]:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Convexifier:
+    """A library handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise CvxError("no CUDA device: the convexification path has no CPU fallback")
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().cvx_create(ctypes.byref(h), device), "cvx_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cvx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ utilities
+    def stats(self, reset: bool = False) -> dict:
+        s = _Stats()
+        _check(lib().cvx_get_stats(self._h, ctypes.byref(s), int(reset)), "cvx_get_stats")
+        return {n: int(getattr(s, n)) for n, _ in _Stats._fields_}
+
+    def set_tuning(self, warps_per_cta: int = 8, dirs_per_item: int = 0):
+        _check(lib().cvx_set_tuning(self._h, warps_per_cta, dirs_per_item), "cvx_set_tuning")
+
+    def _dev(self, t, dtype):
+        import torch
+
+        t = torch.as_tensor(t, dtype=dtype)
+        return t.to(f"cuda:{self.device}").contiguous()
+
+    # -------------------------------------------------------- single steps
+    def energy(self, p: Params, F, beta, want_P: bool = True, stream=None):
+        import torch
+
+        F = self._dev(F, torch.float64).reshape(-1, 4)
+        beta = self._dev(beta, torch.float64).reshape(-1)
+        n = F.shape[0]
+        W = torch.empty(n, dtype=torch.float64, device=F.device)
+        P = torch.empty(n, 4, dtype=torch.float64, device=F.device) if want_P else None
+        c = p.c()
+        _check(lib().cvx_energy(self._h, ctypes.byref(c), n, _ptr(F), _ptr(beta), _ptr(W), _ptr(P),
+                                _stream(stream)), "cvx_energy")
+        return W, P
+
+    def history_update(self, p: Params, F, beta_in=None, stream=None):
+        import torch
+
+        F = self._dev(F, torch.float64).reshape(-1, 4)
+        n = F.shape[0]
+        bi = None if beta_in is None else self._dev(beta_in, torch.float64).reshape(n)
+        out = torch.empty(n, dtype=torch.float64, device=F.device)
+        c = p.c()
+        _check(lib().cvx_history_update(self._h, ctypes.byref(c), n, _ptr(F), _ptr(bi), _ptr(out),
+                                        _stream(stream)), "cvx_history_update")
+        return out
+
+    def sample_lines(self, p: Params, F, beta, dirs, stream=None):
+        import torch
+
+        F = self._dev(F, torch.float64).reshape(-1, 4)
+        n = F.shape[0]
+        beta = self._dev(beta, torch.float64).reshape(n)
+        d = self._dev(dirs, torch.int32).reshape(n)
+        w = torch.empty(n, p.line_points, dtype=torch.float32, device=F.device)
+        c = p.c()
+        _check(lib().cvx_sample_lines(self._h, ctypes.byref(c), n, _ptr(F), _ptr(beta), _ptr(d),
+                                      _ptr(w), _stream(stream)), "cvx_sample_lines")
+        return w
+
+    def hull_bridge(self, w, stream=None):
+        import torch
+
+        w = self._dev(w, torch.float32)
+        n, L = w.shape
+        mm = torch.empty(n, dtype=torch.int32, device=w.device)
+        mp = torch.empty(n, dtype=torch.int32, device=w.device)
+        h = torch.empty(n, dtype=torch.float64, device=w.device)
+        _check(lib().cvx_hull_bridge(self._h, n, L, _ptr(w), _ptr(mm), _ptr(mp), _ptr(h),
+                                     _stream(stream)), "cvx_hull_bridge")
+        return mm, mp, h
+
+    # ----------------------------------------------------------- hot path
+    def convexify_points(self, p: Params, F, beta, want_tree: bool = False,
+                         want_root: bool = False, out: Optional[dict] = None, stream=None):
+        """W^R, P (and optionally the tree / root laminate) for n points.
+
+        ``out`` may hold preallocated tensors (W_R, P, status, tree, root)."""
+        import torch
+
+        F = self._dev(F, torch.float64).reshape(-1, 4)
+        n = F.shape[0]
+        beta = self._dev(beta, torch.float64).reshape(n)
+        dev = F.device
+        o = dict(out) if out else {}
+        W_R = o.get("W_R") if o.get("W_R") is not None else torch.empty(n, dtype=torch.float64, device=dev)
+        P = o.get("P") if o.get("P") is not None else torch.empty(n, 4, dtype=torch.float64, device=dev)
+        st = o.get("status") if o.get("status") is not None else torch.empty(n, dtype=torch.int32, device=dev)
+        tree = None
+        if want_tree:
+            tree = o.get("tree")
+            if tree is None:
+                tree = torch.empty(n * p.tree_size * NODE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        root = None
+        if want_root:
+            root = o.get("root")
+            if root is None:
+                root = torch.empty(n * LAMINATE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        c = p.c()
+        _check(lib().convexify_points(self._h, ctypes.byref(c), n, _ptr(F), _ptr(beta), _ptr(W_R),
+                                      _ptr(P), _ptr(root), _ptr(tree), _ptr(st), _stream(stream)),
+               "convexify_points")
+        return dict(W_R=W_R, P=P, status=st, tree=tree, root=root)
+
+
+def tree_numpy(tree_bytes, n: int, tree_size: int) -> np.ndarray:
+    """Device tree bytes -> (n, tree_size) structured array (host)."""
+    return tree_bytes.cpu().numpy().view(NODE_DTYPE).reshape(n, tree_size)
+
+
+def root_numpy(root_bytes, n: int) -> np.ndarray:
+    return root_bytes.cpu().numpy().view(LAMINATE_DTYPE).reshape(n)

@@ -1,0 +1,183 @@
+// cvx_device.cuh -- device building blocks of the per-point convexification:
+// the material law in FP64 (node and leaf evaluation) and in FP32 line form
+// (sampling), shared by the kernels of this library only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "convexify.h"
+
+namespace cvx {
+
+constexpr float kU32 = 5.9604644775390625e-8f;  // unit roundoff of FP32, 2^-24
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr double kLn2d = 0.693147180559945309417232;
+constexpr double kLog2e = 1.442695040888963407359924;
+
+// Material constants in FP64 (one per call).
+struct Material {
+    double mu, lam, Dinf, D0;
+    int energy;
+};
+
+// -------------------------------------------------------------------------
+// FP64 energy at a point, plane strain (Eqs. 2.1-2.9) and stress (Eq. 2.12).
+// W is written through the closed form of Eq. (2.9) in s = psi0(F):
+//   s <= beta_k : W = (1 - D(beta_k)) (s - beta_k)
+//   s >  beta_k : W = (1 - D_inf)(s - beta_k) + D_inf D_0 (e^{-beta_k/D_0} - e^{-s/D_0})
+// and dW/ds = 1 - D(max(s, beta_k)).
+// -------------------------------------------------------------------------
+__host__ __device__ inline double psi0_nh64(const double F[4], const Material &m, double *lnJ,
+                                            double *J) {
+    double j = F[0] * F[3] - F[1] * F[2];
+    double i1 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3] + 1.0;
+    double lj = log(j);
+    *lnJ = lj;
+    *J = j;
+    return 0.5 * m.mu * (i1 - 3.0) - m.mu * lj + 0.5 * m.lam * lj * lj;
+}
+
+__host__ __device__ inline double energy64(const double F[4], double beta_k, const Material &m) {
+    if (m.energy == CVX_ENERGY_DOUBLE_WELL) {
+        double a = F[0] * F[0] - 1.0, d = F[3] - 1.0;
+        return a * a + F[1] * F[1] + F[2] * F[2] + d * d;
+    }
+    double lj, J;
+    double s = psi0_nh64(F, m, &lj, &J);
+    if (!(J > 0.0)) return nan("");
+    if (s <= beta_k) return (1.0 - m.Dinf * (1.0 - exp(-beta_k / m.D0))) * (s - beta_k);
+    return (1.0 - m.Dinf) * (s - beta_k) + m.Dinf * m.D0 * (exp(-beta_k / m.D0) - exp(-s / m.D0));
+}
+
+__host__ __device__ inline void stress64(const double F[4], double beta_k, const Material &m,
+                                         double P[4]) {
+    if (m.energy == CVX_ENERGY_DOUBLE_WELL) {
+        P[0] = 4.0 * F[0] * (F[0] * F[0] - 1.0);
+        P[1] = 2.0 * F[1];
+        P[2] = 2.0 * F[2];
+        P[3] = 2.0 * (F[3] - 1.0);
+        return;
+    }
+    double lj, J;
+    double s = psi0_nh64(F, m, &lj, &J);
+    if (!(J > 0.0)) {
+        P[0] = P[1] = P[2] = P[3] = nan("");
+        return;
+    }
+    double beta = s > beta_k ? s : beta_k;
+    double g = 1.0 - m.Dinf * (1.0 - exp(-beta / m.D0));
+    double iJ = 1.0 / J;
+    double FiT[4] = {F[3] * iJ, -F[2] * iJ, -F[1] * iJ, F[0] * iJ};  // F^{-T}
+    for (int k = 0; k < 4; ++k) P[k] = g * (m.mu * (F[k] - FiT[k]) + m.lam * lj * FiT[k]);
+}
+
+// -------------------------------------------------------------------------
+// FP32 line form.  Along G(t) = F + t R with R = a (x) b rank one:
+//   I1(t) - 3 = |F|^2 - 2 + 2 t (F:R) + t^2 |R|^2,   J(t) = J0 + t (cof F : R).
+// With lg = log2 J(t) and d = psi0(t) - beta_k:
+//   d = A0 + A1 t + A2 t^2 + lg (B1 + B2 lg),
+//   A0 = mu/2 (|F|^2 - 2) - beta_k, A1 = mu F:R, A2 = mu/2 |R|^2,
+//   B1 = -mu ln2, B2 = lam/2 ln2^2,
+// and the damage branch of Eq. (2.9) becomes, with e = exp2(ce max(d, 0)),
+// ce = -log2(e)/D_0, e_k = exp(-beta_k/D_0):
+//   W = (1 - D_inf) d + K1 (1 - e) + K2 min(d, 0),  K1 = D_inf D_0 e_k, K2 = D_inf e_k.
+// (d <= 0 gives (1 - D_inf + D_inf e_k) d = (1 - D(beta_k)) d; d > 0 gives the
+// second branch.)  J <= 0 yields +inf or NaN, which the hull search ignores.
+// -------------------------------------------------------------------------
+struct NodeLine {
+    float A0, B1, B2, ce, a1, K1, K2, mu;
+    float J0;
+    float F[4];
+    float cof[4];
+    // double-well coefficients are built per direction from F
+};
+
+struct DirLine {
+    float A1, A2, cJ, J0;  // NH
+    float c[5];            // double well: W(t) = sum c_i t^i
+};
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Node constants from F (FP64) and beta_k, rounded to FP32.
+__device__ inline NodeLine make_node_line(const double F[4], double beta_k, const Material &m) {
+    NodeLine nl;
+    double fsq = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
+    double ek = exp(-beta_k / m.D0);
+    nl.A0 = (float)(0.5 * m.mu * (fsq - 2.0) - beta_k);
+    nl.B1 = (float)(-m.mu * kLn2d);
+    nl.B2 = (float)(0.5 * m.lam * kLn2d * kLn2d);
+    nl.ce = (float)(-kLog2e / m.D0);
+    nl.a1 = (float)(1.0 - m.Dinf);
+    nl.K1 = (float)(m.Dinf * m.D0 * ek);
+    nl.K2 = (float)(m.Dinf * ek);
+    nl.mu = (float)m.mu;
+    nl.J0 = (float)(F[0] * F[3] - F[1] * F[2]);
+    for (int k = 0; k < 4; ++k) nl.F[k] = (float)F[k];
+    nl.cof[0] = (float)F[3];
+    nl.cof[1] = (float)(-F[2]);
+    nl.cof[2] = (float)(-F[1]);
+    nl.cof[3] = (float)F[0];
+    return nl;
+}
+
+template <int EK>
+__device__ __forceinline__ DirLine make_dir_line(const NodeLine &nl, float4 d) {
+    DirLine dl;
+    // R = a (x) b, a = (d.x, d.y), b = (d.z, d.w)
+    float R0 = d.x * d.z, R1 = d.x * d.w, R2 = d.y * d.z, R3 = d.y * d.w;
+    if (EK == CVX_ENERGY_NH_DAMAGE) {
+        float c1 = nl.F[0] * R0 + nl.F[1] * R1 + nl.F[2] * R2 + nl.F[3] * R3;
+        float cJ = nl.cof[0] * R0 + nl.cof[1] * R1 + nl.cof[2] * R2 + nl.cof[3] * R3;
+        float rr = (d.x * d.x + d.y * d.y) * (d.z * d.z + d.w * d.w);
+        dl.A1 = nl.mu * c1;
+        dl.A2 = 0.5f * nl.mu * rr;
+        dl.cJ = cJ;
+        dl.J0 = nl.J0;
+    } else {
+        // (G11^2 - 1)^2 + G12^2 + G21^2 + (G22 - 1)^2 as a quartic in t
+        float q0 = nl.F[0] * nl.F[0] - 1.0f, q1 = 2.0f * nl.F[0] * R0, q2 = R0 * R0;
+        float g22 = nl.F[3] - 1.0f;
+        dl.c[0] = q0 * q0 + nl.F[1] * nl.F[1] + nl.F[2] * nl.F[2] + g22 * g22;
+        dl.c[1] = 2.0f * q0 * q1 + 2.0f * (nl.F[1] * R1 + nl.F[2] * R2 + g22 * R3);
+        dl.c[2] = q1 * q1 + 2.0f * q0 * q2 + R1 * R1 + R2 * R2 + R3 * R3;
+        dl.c[3] = 2.0f * q1 * q2;
+        dl.c[4] = q2 * q2;
+    }
+    return dl;
+}
+
+// One FP32 sample of W at parameter t (12 FP32-pipe instructions and 2 MUFU
+// for the damage energy).
+template <int EK>
+__device__ __forceinline__ float sample_w(const NodeLine &nl, const DirLine &dl, float t) {
+    if (EK == CVX_ENERGY_NH_DAMAGE) {
+        float p = __fmaf_rn(t, __fmaf_rn(t, dl.A2, dl.A1), nl.A0);
+        float J = __fmaf_rn(t, dl.cJ, dl.J0);
+        float lg = lg2_approx(J);
+        float d = __fmaf_rn(lg, __fmaf_rn(lg, nl.B2, nl.B1), p);
+        float z = fminf(d * nl.ce, 0.0f);
+        float e = ex2_approx(z);
+        float w = __fmaf_rn(d, nl.a1, nl.K1);
+        w = __fmaf_rn(-nl.K1, e, w);
+        return __fmaf_rn(nl.K2, fminf(d, 0.0f), w);
+    } else {
+        float w = __fmaf_rn(dl.c[4], t, dl.c[3]);
+        w = __fmaf_rn(w, t, dl.c[2]);
+        w = __fmaf_rn(w, t, dl.c[1]);
+        return __fmaf_rn(w, t, dl.c[0]);
+    }
+}
+
+}  // namespace cvx

@@ -1,0 +1,118 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, exports every
+function include/convexify.h declares, its struct layouts match the binding,
+and argument validation rejects bad input before any CUDA call.  No compute
+call is made here (there is no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "convexify.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return re.findall(r"^int\s+(\w+)\s*\(", txt, flags=re.M)
+
+
+@pytest.fixture(scope="module")
+def cvxlib():
+    from paper_2211_14318_gb300 import api, build
+
+    build.build()
+    api._lib = None
+    return api.lib()
+
+
+def test_header_declares_the_boundary():
+    names = set(_declared())
+    for n in ("convexify_points", "cvx_create", "cvx_destroy", "cvx_last_error",
+              "cvx_hull_bridge", "cvx_sample_lines", "cvx_energy", "cvx_history_update"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(cvxlib):
+    from paper_2211_14318_gb300 import api
+
+    for n in _declared():
+        assert hasattr(cvxlib, n), n
+    assert set(api.exported_symbols()) <= set(_declared())
+
+
+def test_struct_layouts_match_binding(cvxlib):
+    from paper_2211_14318_gb300 import api
+
+    assert cvxlib.cvx_struct_size(0) == ctypes.sizeof(api._Params)
+    assert cvxlib.cvx_struct_size(1) == api.NODE_DTYPE.itemsize
+    assert cvxlib.cvx_struct_size(2) == api.LAMINATE_DTYPE.itemsize
+    assert cvxlib.cvx_struct_size(3) == ctypes.sizeof(api._Stats)
+    assert cvxlib.cvx_struct_size(7) == -1
+
+
+def _err(cvxlib):
+    buf = ctypes.create_string_buffer(256)
+    cvxlib.cvx_last_error(buf, 256)
+    return buf.value.decode()
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("line_points", 200, "line_points"),
+    ("line_points", 1, "line_points"),
+    ("line_points", 4001, "line_points"),
+    ("depth", 9, "depth"),
+    ("depth", -1, "depth"),
+    ("t_half", 0.0, "t_half"),
+    ("D_inf", 1.0, "material"),
+    ("mu", -1.0, "material"),
+    ("energy", 7, "energy"),
+    ("n_theta_a", 0, "angle grid"),
+    ("flags", 3, "flags"),
+])
+def test_invalid_params_rejected_before_cuda(cvxlib, field, value, msg):
+    from paper_2211_14318_gb300 import api
+
+    p = api.Params(line_points=201, depth=2)
+    c = p.c()
+    setattr(c, field, value)
+    rc = cvxlib.convexify_points(None, ctypes.byref(c), 4, None, None, None, None, None, None, None,
+                                 None)
+    assert rc == -1
+    assert msg in _err(cvxlib)
+
+
+def test_null_handle_and_arrays_rejected(cvxlib):
+    from paper_2211_14318_gb300 import api
+
+    c = api.Params().c()
+    assert cvxlib.convexify_points(None, ctypes.byref(c), 4, None, None, None, None, None, None,
+                                   None, None) == -1
+    assert "handle" in _err(cvxlib)
+    assert cvxlib.cvx_hull_bridge(None, 1, 4, None, None, None, None, None) == -1
+    assert "odd" in _err(cvxlib)
+    assert cvxlib.cvx_set_tuning(None, 8, 0) == -1
+    assert cvxlib.cvx_energy(None, None, 1, None, None, None, None, None) == -1
+    assert "params" in _err(cvxlib)
+
+
+def test_create_without_gpu_fails_cleanly(cvxlib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = cvxlib.cvx_create(ctypes.byref(h), 0)
+    assert rc in (-1, -2) and not h.value
+
+
+def test_binding_refuses_cpu_fallback():
+    import torch
+
+    from paper_2211_14318_gb300 import api
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(api.CvxError):
+        api.Convexifier(0)
