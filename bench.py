@@ -1,0 +1,368 @@
+"""Throughput of per-point rank-one convexification on GB300.
+
+Workload (one GPU): a 128 x 128 Q1 mesh x 4 Gauss points = 65,536 quadrature
+points, F from a seeded synthetic displacement (affine stretch 1.3 + 8 Fourier
+modes + a 45 degree shear band), history from the previous load step; NH with
+exponential damage (mu=1, lambda=5, D_inf=0.99, D_0=0.5); 64 x 64 angle grid
+(4096 rank-one directions), 1025 samples per line on t in [-0.5, 0.5],
+lamination depth 3.  A step is the whole path: history update (Eq. 2.5) and
+the convexification with W^R and P (Secs. 4-5).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank convexifies
+its own mesh (weak scaling, no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "quadrature points convexified/s (W^R+P) at 1e-6 rel. error, surrogate vs full-scan"
+MAT = dict(mu=1.0, lambda_L=5.0, D_inf=0.99, D0=0.5)
+NX, STRETCH, ANGLES, LINE, DEPTH, T_HALF = 128, 1.3, 64, 1025, 3, 0.5
+FLOP_PER_SAMPLE = 30  # algorithmic FP32 work per valid line sample (energy 22 + hull 8)
+FP32_LANES_PER_SM = 128
+
+
+def workload_desc(n):
+    return (f"mesh {NX}x{NX} Q1 x 4 Gauss points = {n} points, stretch {STRETCH}, "
+            f"{ANGLES}x{ANGLES} angles, L={LINE}, t in [-{T_HALF},{T_HALF}], depth {DEPTH}, full scan")
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=NX, help="mesh size (default 128 -> 65,536 points)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def make_inputs(nx, rank):
+    from paper_2211_14318_gb300 import inputs
+
+    F, F_prev = inputs.mesh_points(nx, stretch=STRETCH, seed=rank)
+    return F, F_prev
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm),
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- roofline
+def fp32_peak_tflops(torch, dev):
+    props = torch.cuda.get_device_properties(dev)
+    mhz = 2070.0
+    src = "sm_max_mhz 2070 (nominal)"
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if mp.get("sm_max_mhz"):
+            mhz = float(mp["sm_max_mhz"])
+            src = "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, ValueError):
+        pass
+    sms = props.multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz, src
+
+
+def scan_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2211_14318_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(valid_per_launch):
+    """DRAM bytes per scan launch from the committed ncu summary, scaled to
+    this launch's work; None if the kernel changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_scan_traffic.json")
+    try:
+        t = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if t.get("source_sha") != scan_source_hash():
+        return None
+    per_sample = t["dram_bytes"] / max(1, t["valid_samples"])
+    return per_sample * valid_per_launch
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_rate(F, F_prev, npts, cores):
+    """The CPU oracle (as it stands) on npts points of the same workload."""
+    import oracle
+
+    mat = oracle.Material(MAT["mu"], MAT["lambda_L"], MAT["D_inf"], MAT["D0"])
+    sc = oracle.Scan(oracle.angle_directions(ANGLES, ANGLES), LINE, T_HALF, DEPTH)
+    idx = [int(i) for i in __import__("numpy").linspace(0, F.shape[0] - 1, npts)]
+    Fs, Fps = F[idx], F_prev[idx]
+    t0 = time.perf_counter()
+    beta = oracle.history_update(mat, Fps)
+    oracle.convexify(mat, sc, Fs, beta, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return npts / dt, dt
+
+
+def run_reference(a):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cores = host_cores()
+    F, F_prev = make_inputs(a.nx, 0)
+    npts = a.cpu_points or max(cores, 2 * cores)
+    for _ in range(a.warmup):
+        oracle_rate(F, F_prev, max(1, cores // 4), cores)
+    rates, times = [], []
+    for _ in range(a.steps):
+        r, dt = oracle_rate(F, F_prev, npts, cores)
+        rates.append(r)
+        times.append(dt)
+    value = npts * a.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * sum(times) / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(F.shape[0]), "form": "full-scan"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{npts} evenly spaced points of the workload per step"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api
+
+    F, F_prev = make_inputs(a.nx, rank)
+    n = F.shape[0]
+    p = api.Params(n_theta_a=ANGLES, n_theta_b=ANGLES, line_points=LINE, t_half=T_HALF,
+                   depth=DEPTH, **MAT)
+    cv = api.Convexifier(local)
+    Fd = torch.from_numpy(F).to(dev)
+    Fpd = torch.from_numpy(F_prev).to(dev)
+    out = dict(W_R=torch.empty(n, dtype=torch.float64, device=dev),
+               P=torch.empty(n, 4, dtype=torch.float64, device=dev),
+               status=torch.empty(n, dtype=torch.int32, device=dev))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(Fx, Fpx):
+        beta = cv.history_update(p, Fpx)
+        return cv.convexify_points(p, Fx, beta, out=out)
+
+    for _ in range(a.warmup):
+        step(Fd, Fpd)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    cv.stats(reset=True)
+    cv.set_profiling(True)
+    cv.scan_timing(reset=True)
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(a.steps):
+        flush.zero_()
+        ev[k][0].record()
+        step(Fd, Fpd)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    scan_ms, scan_launches = cv.scan_timing(reset=True)
+    cv.set_profiling(False)
+    st = cv.stats(reset=True)
+    t_max = dev_ms
+    if ws > 1:
+        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * n * a.steps / (t_max / 1e3)
+
+    # ---- end to end through the public API from pinned host buffers
+    Fh = torch.from_numpy(F).pin_memory()
+    Fph = torch.from_numpy(F_prev).pin_memory()
+    Wh = torch.empty(n, dtype=torch.float64).pin_memory()
+    Ph = torch.empty(n, 4, dtype=torch.float64).pin_memory()
+    e2e_ev = []
+    for k in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Fx = Fh.to(dev, non_blocking=True)
+        Fpx = Fph.to(dev, non_blocking=True)
+        o = step(Fx, Fpx)
+        Wh.copy_(o["W_R"], non_blocking=True)
+        Ph.copy_(o["P"], non_blocking=True)
+        e1.record()
+        e2e_ev.append((e0, e1))
+    torch.cuda.synchronize()
+    e2e_ms = sum(e0.elapsed_time(e1) for e0, e1 in e2e_ev)
+    if ws > 1:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = ws * n * a.steps / (e2e_ms / 1e3)
+
+    peak, sms, mhz, peak_src = fp32_peak_tflops(torch, dev)
+    flop = FLOP_PER_SAMPLE * st["valid_samples"]
+    achieved = flop / (scan_ms / 1e3) / 1e12 if scan_ms > 0 else None
+    valid_per_launch = st["valid_samples"] / max(1, scan_launches)
+    traffic = traffic_per_launch(valid_per_launch)
+
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not a.no_cpu_baseline:
+            import oracle
+
+            oracle.build()
+            cores = host_cores()
+            npts = a.cpu_points or 2 * cores
+            rate, dt = oracle_rate(F, F_prev, npts, cores)
+            cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{npts} evenly spaced points of the workload ({dt:.1f} s of CPU time)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": workload_desc(n), "form": "full-scan",
+                       "points_per_gpu": n, "angles": [ANGLES, ANGLES], "line_points": LINE,
+                       "depth": DEPTH, "l2": "flushed between steps (512 MiB write)",
+                       "wall_s_timed_region": wall},
+            "roofline": {"bound": "alu", "kernel": "k_scan", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic,
+                         "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz ({peak_src})",
+                         "flop_per_valid_sample": FLOP_PER_SAMPLE,
+                         "kernel_share_of_step": scan_ms / dev_ms if dev_ms else None,
+                         "launches": scan_launches},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "points/s",
+                    "h2d_bytes_per_step": 2 * n * 4 * 8, "d2h_bytes_per_step": n * 8 + n * 4 * 8},
+            "gpu_launches": a.steps * (3 + 2 * DEPTH),
+            "clocks": ck,
+            "stats": st,
+        }
+        print(json.dumps(line), flush=True)
+    cv.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -150,6 +150,12 @@ typedef struct cvx_stats {
     int64_t rare_paths;     /* hull searches that left the fast path       */
     int64_t ties;           /* nodes flagged CVX_NODE_TIE                  */
     int64_t iter_caps;      /* hull searches that hit the iteration cap    */
+    int64_t window_steps;   /* supporting-slope steps inside the windows   */
+    int64_t rounds;         /* verification rounds of the hull searches    */
+    int64_t fp64_window;    /* FP64 fallbacks in the window checks         */
+    int64_t fp64_rare;      /* FP64 fallbacks on the rare path             */
+    int64_t fp64_center;    /* FP64 fallbacks deciding the centre          */
+    int64_t dir_fp64;       /* FP64 comparisons between directions         */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */
@@ -169,6 +175,14 @@ int cvx_last_error(char *buf, size_t len);
 /* Reads (synchronous: waits for the handle's device) and optionally resets
  * the counters. */
 int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset);
+
+/* Enables (1) or disables (0) CUDA-event timing of every line-scan kernel
+ * launch (events recorded on the launching stream around each launch). */
+int cvx_set_profiling(cvx_handle *h, int enable);
+
+/* Synchronous: total device time in ms and number of line-scan kernel launches
+ * timed since the last reset (requires cvx_set_profiling(h, 1)). */
+int cvx_get_scan_timing(cvx_handle *h, double *ms, int64_t *launches, int reset);
 
 /* sizeof of the ABI structs, for bindings to check their layouts:
  * which = 0 cvx_params, 1 cvx_node, 2 cvx_laminate, 3 cvx_stats; -1 otherwise. */

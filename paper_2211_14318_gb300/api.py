@@ -53,7 +53,8 @@ class _Params(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
-        "full_passes", "rare_paths", "ties", "iter_caps")]
+        "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
+        "fp64_rare", "fp64_center", "dir_fp64")]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -75,6 +76,9 @@ def lib() -> ctypes.CDLL:
         "cvx_get_stats": [vp, ctypes.POINTER(_Stats), ctypes.c_int],
         "cvx_set_tuning": [vp, ctypes.c_int, ctypes.c_int],
         "cvx_struct_size": [ctypes.c_int],
+        "cvx_set_profiling": [vp, ctypes.c_int],
+        "cvx_get_scan_timing": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                ctypes.c_int],
         "cvx_energy": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp],
         "cvx_history_update": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp],
         "cvx_sample_lines": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp],
@@ -91,7 +95,7 @@ def lib() -> ctypes.CDLL:
 
 def exported_symbols() -> Sequence[str]:
     return ("cvx_create", "cvx_destroy", "cvx_last_error", "cvx_get_stats", "cvx_struct_size",
-            "cvx_set_tuning",
+            "cvx_set_tuning", "cvx_set_profiling", "cvx_get_scan_timing",
             "cvx_energy", "cvx_history_update", "cvx_sample_lines", "cvx_hull_bridge",
             "convexify_points")
 
@@ -186,6 +190,17 @@ class Convexifier:
 
     def set_tuning(self, warps_per_cta: int = 8, dirs_per_item: int = 0):
         _check(lib().cvx_set_tuning(self._h, warps_per_cta, dirs_per_item), "cvx_set_tuning")
+
+    def set_profiling(self, enable: bool = True):
+        _check(lib().cvx_set_profiling(self._h, int(enable)), "cvx_set_profiling")
+
+    def scan_timing(self, reset: bool = True):
+        """(total ms, launches) of the line-scan kernel since the last reset."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(lib().cvx_get_scan_timing(self._h, ctypes.byref(ms), ctypes.byref(n), int(reset)),
+               "cvx_get_scan_timing")
+        return ms.value, n.value
 
     def _dev(self, t, dtype):
         import torch

@@ -32,6 +32,9 @@ struct cvx_handle {
     unsigned long long *d_counters = nullptr;
     int tune_warps = 8;
     int tune_dpi = 0;
+    // optional CUDA-event timing of the scan launches
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_pool;
 };
 
 namespace {
@@ -229,6 +232,11 @@ int cvx_destroy(cvx_handle *h) {
     if (!h) return CVX_OK;
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
+    for (auto *v : {&h->ev_pending, &h->ev_pool})
+        for (auto &e : *v) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
     cudaFree(h->d_dir32);
     cudaFree(h->d_dir64);
     cudaFree(h->ws);
@@ -253,7 +261,38 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->rare_paths = (int64_t)c[C_RARE];
     out->ties = (int64_t)c[C_TIES];
     out->iter_caps = (int64_t)c[C_CAPS];
+    out->window_steps = (int64_t)c[C_WSTEPS];
+    out->rounds = (int64_t)c[C_ROUNDS];
+    out->fp64_window = (int64_t)c[C_FP64W];
+    out->fp64_rare = (int64_t)c[C_FP64R];
+    out->fp64_center = (int64_t)c[C_FP64C];
+    out->dir_fp64 = (int64_t)c[C_DIR64];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
+    return CVX_OK;
+}
+
+int cvx_set_profiling(cvx_handle *h, int enable) {
+    if (!h) return fail(CVX_ERR_INVALID_ARG, "handle is NULL");
+    h->profiling = enable != 0;
+    return CVX_OK;
+}
+
+int cvx_get_scan_timing(cvx_handle *h, double *ms, int64_t *launches, int reset) {
+    if (!h || !ms || !launches) return fail(CVX_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(h->device);
+    double tot = 0.0;
+    for (auto &e : h->ev_pending) {
+        CK(cudaEventSynchronize(e.second), "cvx_get_scan_timing");
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, e.first, e.second), "cvx_get_scan_timing");
+        tot += t;
+    }
+    *ms = tot;
+    *launches = (int64_t)h->ev_pending.size();
+    if (reset) {
+        for (auto &e : h->ev_pending) h->ev_pool.push_back(e);
+        h->ev_pending.clear();
+    }
     return CVX_OK;
 }
 
@@ -430,7 +469,22 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
         sa.line = ln;
         sa.out = (ItemBest *)(ws + o_items);
         sa.counters = h->d_counters;
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (h->profiling) {
+            if (!h->ev_pool.empty()) {
+                ev = h->ev_pool.back();
+                h->ev_pool.pop_back();
+            } else {
+                CK(cudaEventCreate(&ev.first), "profiling");
+                CK(cudaEventCreate(&ev.second), "profiling");
+            }
+            CK(cudaEventRecord(ev.first, s), "profiling");
+        }
         CK(launch_scan(sa, p->energy, ns, warps, grid, s), "convexify_points/scan");
+        if (h->profiling) {
+            CK(cudaEventRecord(ev.second, s), "profiling");
+            h->ev_pending.push_back(ev);
+        }
 
         ExpandArgs ea;
         ea.tree = tr;

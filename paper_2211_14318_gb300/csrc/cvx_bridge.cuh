@@ -41,7 +41,8 @@ struct LineGeom {
 };
 
 struct HullCounters {
-    unsigned fp64, full_passes, rare, caps;
+    unsigned fp64, full_passes, rare, caps;   // fp64: per lane; others: lane 0
+    unsigned wsteps, rounds, fp64r, fp64c;    // wsteps/rounds/fp64c: lane 0; fp64r: per lane
 };
 
 struct BridgeOut {
@@ -147,6 +148,7 @@ __device__ BridgeOut warp_bridge(const float (&w)[NS], const float *sw, const Li
     bool done = false;
     int round = 0;
     for (; round < kHullCap && !done; ++round) {
+        if (lane == 0) ++hc.rounds;
         // ---- 2. supporting-slope iteration inside the windows (FP32) -------
         if (fp32_steps) {
             for (int it = 0; it < 32; ++it) {
@@ -162,6 +164,7 @@ __device__ BridgeOut warp_bridge(const float (&w)[NS], const float *sw, const Li
                 unsigned bA = __ballot_sync(kFull, keyA == mA), bB = __ballot_sync(kFull, keyB == mB);
                 int na = ((bA >> (a - loA)) & 1u) ? a : loA + __ffs(bA) - 1;
                 int nb = ((bB >> (b - loB)) & 1u) ? b : loB + __ffs(bB) - 1;
+                if (lane == 0) ++hc.wsteps;
                 if (na == a && nb == b) break;
                 a = na;
                 b = nb;
@@ -241,8 +244,8 @@ __device__ BridgeOut warp_bridge(const float (&w)[NS], const float *sw, const Li
             if (__any_sync(kFull, cnd)) {
                 int sd = 1;
                 if (cnd) {
-                    if (k < m0) sd = side_exact(v, k, wa, a, wb, b, s, wa, a, hc.fp64);
-                    else sd = side_exact(v, k, wa, a, wb, b, s, wb, b, hc.fp64);
+                    if (k < m0) sd = side_exact(v, k, wa, a, wb, b, s, wa, a, hc.fp64r);
+                    else sd = side_exact(v, k, wa, a, wb, b, s, wb, b, hc.fp64r);
                 }
                 int key = f2key(c - s * (float)(lane - m0));
                 if (sd < 0 && k < m0 && key < bestKeyL) { bestKeyL = key; bestKL = k; }
@@ -274,7 +277,9 @@ __device__ BridgeOut warp_bridge(const float (&w)[NS], const float *sw, const Li
     // ---- centre: strict vertex iff strictly below the bridge chord ---------
     const float wa = sw[a], wb = sw[b];
     const float s = slope_of(wa, a, wb, b);
-    int sc = side_exact(out.w0, m0, wa, a, wb, b, s, wa, a, hc.fp64);
+    unsigned c64 = 0;
+    int sc = side_exact(out.w0, m0, wa, a, wb, b, s, wa, a, c64);
+    if (lane == 0) hc.fp64c += c64;
     out.a = a;
     out.b = b;
     out.wa = wa;

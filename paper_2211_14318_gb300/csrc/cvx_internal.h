@@ -23,7 +23,7 @@ static_assert(sizeof(ItemBest) == 32, "ItemBest layout");
 
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
-    C_CAPS, C_NUM
+    C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_DIR64, C_NUM
 };
 
 struct LineSpec {

@@ -83,8 +83,8 @@ __global__ void __launch_bounds__(512) k_scan(const ScanArgs A) {
     const LineGeom g{ln.L, ln.m0, ln.m0 >> 5, ln.m0 & 31};
     const int n_nodes = *A.q_count;
     const long long n_items = (long long)n_nodes * A.chunks;
-    HullCounters hc{0u, 0u, 0u, 0u};
-    unsigned long long n_valid = 0, n_lines = 0;
+    HullCounters hc{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    unsigned long long n_valid = 0, n_lines = 0, n_dir64 = 0;
 
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int qi = (int)(item / A.chunks), ch = (int)(item % A.chunks);
@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(512) k_scan(const ScanArgs A) {
             else if (h32 + err < b_h32 - b_err) better = true;
             else if (h32 - err > b_h32 + b_err) better = false;
             else {
+                ++n_dir64;
                 double hn = h64_of(o.lam, o.a, o.b, o.wa, o.wb, o.w0, ln.m0);
                 double hb = h64_of(b_lam, b_a, b_b, b_wa, b_wb, w0, ln.m0);
                 better = hn < hb;  // equal -> keep the lower direction index
@@ -192,10 +193,17 @@ __global__ void __launch_bounds__(512) k_scan(const ScanArgs A) {
     }
     // counters: per-lane FP64 checks summed, warp-uniform ones from lane 0
     unsigned fp64 = __reduce_add_sync(kFull, hc.fp64);
+    unsigned fp64r = __reduce_add_sync(kFull, hc.fp64r);
     if (lane == 0) {
+        add_counter(A.counters, C_FP64W, fp64);
+        add_counter(A.counters, C_FP64R, fp64r);
+        add_counter(A.counters, C_FP64C, hc.fp64c);
+        add_counter(A.counters, C_WSTEPS, hc.wsteps);
+        add_counter(A.counters, C_ROUNDS, hc.rounds);
+        add_counter(A.counters, C_DIR64, n_dir64);
         add_counter(A.counters, C_LINES, n_lines);
         add_counter(A.counters, C_VALID, n_valid);
-        add_counter(A.counters, C_FP64, fp64);
+        add_counter(A.counters, C_FP64, fp64 + fp64r + hc.fp64c);
         add_counter(A.counters, C_FULL, hc.full_passes);
         add_counter(A.counters, C_RARE, hc.rare);
         add_counter(A.counters, C_CAPS, hc.caps);
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(128) k_hull(int64_t n, int L, const float *w_i
     __syncwarp();
     const int m0 = (L - 1) / 2;
     const LineGeom g{L, m0, m0 >> 5, m0 & 31};
-    HullCounters hc{0u, 0u, 0u, 0u};
+    HullCounters hc{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
     const BridgeOut o = warp_bridge<NS>(w, sw, g, lane, -1, -1, hc);
     if (lane == 0) {
         mm[line] = o.lam ? o.a : m0;
