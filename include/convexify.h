@@ -27,9 +27,13 @@
  *  - The library owns the handle's workspace (grown on demand with cudaMalloc)
  *    and its direction tables.  A handle may be used by one host thread at a
  *    time; work of one handle is serialised on the streams it is given.
- *  - Arithmetic: W is sampled in FP32 on the CUDA cores; the hull predicates
- *    are exact (FP32 filter with an exact FP64 fallback), directions are
- *    compared in FP64, and the split points, W^R and P are evaluated in FP64.
+ *  - Arithmetic: every line is first sampled in FP32 on the CUDA cores and its
+ *    lower hull found exactly for those FP32 values (FP32 filter with an exact
+ *    FP64 fallback).  That FP32 pass screens the directions: only those whose
+ *    FP32 hull value lies within a tolerance of the best (several times the
+ *    FP32 sampling error) are resampled in FP64, and the node's direction,
+ *    split and value are decided on those FP64 samples.  Split points, W^R
+ *    and P are evaluated in FP64.
  */
 #ifndef CONVEXIFY_H
 #define CONVEXIFY_H
@@ -59,7 +63,9 @@ enum cvx_point_status {
     CVX_PT_TIE = 2,        /* some node's two best directions were closer than
                               the FP32 sampling error bound (warning only)     */
     CVX_PT_EDGE = 4,       /* some split point lies on the end of its line     */
-    CVX_PT_ITER_CAP = 8    /* a hull search hit its iteration cap (warning)    */
+    CVX_PT_ITER_CAP = 8,   /* a hull search hit its iteration cap (warning)    */
+    CVX_PT_OVERFLOW = 16   /* more directions passed the FP32 screen than the
+                              16 refined in FP64 at some node (warning)        */
 };
 
 /* energy kinds */
@@ -155,7 +161,8 @@ typedef struct cvx_stats {
     int64_t fp64_window;    /* FP64 fallbacks in the window checks         */
     int64_t fp64_rare;      /* FP64 fallbacks on the rare path             */
     int64_t fp64_center;    /* FP64 fallbacks deciding the centre          */
-    int64_t dir_fp64;       /* FP64 comparisons between directions         */
+    int64_t refined;        /* candidate lines resampled and decided in FP64 */
+    int64_t overflow;       /* nodes with more screened candidates than kept */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */

@@ -21,7 +21,7 @@ CVX_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NOT_TRAINED",
           -6: "UNSUPPORTED"}
 ENERGY_NH_DAMAGE, ENERGY_DOUBLE_WELL = 0, 1
-PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP = 1, 2, 4, 8
+PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP, PT_OVERFLOW = 1, 2, 4, 8, 16
 NODE_EXISTS, NODE_SCANNED, NODE_LAMINATED, NODE_LEAF, NODE_TIE, NODE_EDGE = 1, 2, 4, 8, 16, 32
 
 NODE_DTYPE = np.dtype([
@@ -54,7 +54,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
-        "fp64_rare", "fp64_center", "dir_fp64")]
+        "fp64_rare", "fp64_center", "refined", "overflow")]
 
 
 _lib: Optional[ctypes.CDLL] = None

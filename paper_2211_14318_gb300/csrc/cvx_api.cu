@@ -123,6 +123,8 @@ LineSpec line_of(const cvx_params *p) {
     l.m0 = (p->line_points - 1) / 2;
     l.h64 = 2.0 * p->t_half / (double)(p->line_points - 1);
     l.h32 = (float)l.h64;
+    l.nfull = l.L >> 7;
+    l.stride = line_stride(l.L);
     return l;
 }
 
@@ -266,7 +268,8 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->fp64_window = (int64_t)c[C_FP64W];
     out->fp64_rare = (int64_t)c[C_FP64R];
     out->fp64_center = (int64_t)c[C_FP64C];
-    out->dir_fp64 = (int64_t)c[C_DIR64];
+    out->refined = (int64_t)c[C_REFINED];
+    out->overflow = (int64_t)c[C_OVERFLOW];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }
@@ -352,8 +355,8 @@ int cvx_sample_lines(cvx_handle *h, const cvx_params *p, int64_t n_lines, const 
     rc = ensure_dirs(h, p, (cudaStream_t)s);
     if (rc) return rc;
     const LineSpec ln = line_of(p);
-    CK(launch_sample_lines(n_lines, F, beta_k, dir, h->d_dir32, h->D, material_of(p), ln,
-                           slots_for(ln.L), w, (cudaStream_t)s),
+    CK(launch_sample_lines(n_lines, F, beta_k, dir, h->d_dir32, h->D, material_of(p), ln, w,
+                           (cudaStream_t)s),
        "cvx_sample_lines");
     return CVX_OK;
 }
@@ -367,7 +370,7 @@ int cvx_hull_bridge(cvx_handle *h, int64_t n_lines, int32_t L, const float *w, i
     if (n_lines > 0 && (!w || !m_minus || !m_plus || !hval))
         return fail(CVX_ERR_INVALID_ARG, "NULL array");
     DeviceGuard g(h->device);
-    CK(launch_hull(n_lines, L, slots_for(L), w, m_minus, m_plus, hval, h->d_counters,
+    CK(launch_hull(n_lines, L, w, m_minus, m_plus, hval, h->d_counters,
                    (cudaStream_t)s),
        "cvx_hull_bridge");
     return CVX_OK;
@@ -390,12 +393,11 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     if (rc) return rc;
 
     const LineSpec ln = line_of(p);
-    const int ns = slots_for(ln.L);
     const int K = p->depth;
     const int NT = (1 << (K + 1)) - 1;
     const int D = h->D;
     const int warps = h->tune_warps;
-    int bpsm = scan_max_blocks_per_sm(p->energy, ns, warps);
+    const int bpsm = scan_max_blocks_per_sm(p->energy, warps, ln.stride);
     if (bpsm < 1) return fail(CVX_ERR_UNSUPPORTED, "scan kernel cannot launch with %d warps", warps);
     const int grid = h->sm_count * bpsm;
     // directions per work item: whole nodes when there are enough of them,
@@ -405,14 +407,15 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
         const int64_t want_items = (int64_t)grid * 4;
         if (n >= want_items) dpi = D;
         else {
-            int64_t chunks = (want_items + n - 1) / n;
+            const int64_t chunks = (want_items + n - 1) / n;
             dpi = (int)std::max<int64_t>(warps * 2, (D + chunks - 1) / chunks);
         }
     }
     dpi = std::min(dpi, D);
     const int chunks = (D + dpi - 1) / dpi;
 
-    // workspace layout
+    // workspace layout (level l holds at most n 2^l nodes)
+    const size_t maxq = K > 0 ? ((size_t)n << (K - 1)) : 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -425,16 +428,20 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
         o_qp[l] = take(sizeof(int32_t) * ((size_t)n << l));
         o_qh[l] = take(sizeof(int32_t) * ((size_t)n << l));
     }
-    const size_t o_cnt = take(sizeof(int32_t) * (K + 1));
-    const size_t o_items = K > 0 ? take(sizeof(ItemBest) * ((size_t)n << (K - 1)) * chunks) : 0;
+    const size_t o_cnt = take(sizeof(int32_t) * 2 * (K + 1));
+    const size_t o_items = take(sizeof(ItemCands) * maxq * chunks);
+    const size_t o_cands = take(sizeof(NodeCands) * maxq);
+    const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
+    const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
     rc = ensure_ws(h, off, s);
     if (rc) return rc;
     char *ws = h->ws;
     cvx_node *tr = tree ? tree : (cvx_node *)(ws + o_tree);
-    int32_t *cnt = (int32_t *)(ws + o_cnt);
+    int32_t *cnt = (int32_t *)(ws + o_cnt);      // node counts per level
+    int32_t *wcnt = cnt + (K + 1);               // refine work counts per level
 
     CK(cudaMemsetAsync(tr, 0, sizeof(cvx_node) * (size_t)n * NT, s), "convexify_points");
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (K + 1), s), "convexify_points");
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 2 * (K + 1), s), "convexify_points");
 
     const Material mat = material_of(p);
     InitArgs ia;
@@ -453,13 +460,19 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     ia.counters = h->d_counters;
     CK(launch_init(ia, s), "convexify_points/init");
 
+    ItemCands *items = (ItemCands *)(ws + o_items);
+    NodeCands *cands = (NodeCands *)(ws + o_cands);
+    int2 *work = (int2 *)(ws + o_work);
+    RefineOut *refined = (RefineOut *)(ws + o_ref);
     for (int l = 0; l < K; ++l) {
+        const int64_t max_nodes = (int64_t)n << l;
+        int32_t *qp = (int32_t *)(ws + o_qp[l]), *qh = (int32_t *)(ws + o_qh[l]);
         ScanArgs sa;
         sa.tree = tr;
         sa.NT = NT;
         sa.beta = beta_k;
-        sa.q_point = (int32_t *)(ws + o_qp[l]);
-        sa.q_heap = (int32_t *)(ws + o_qh[l]);
+        sa.q_point = qp;
+        sa.q_heap = qh;
         sa.q_count = cnt + l;
         sa.dir32 = h->d_dir32;
         sa.D = D;
@@ -467,7 +480,7 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
         sa.dirs_per_item = dpi;
         sa.mat = mat;
         sa.line = ln;
-        sa.out = (ItemBest *)(ws + o_items);
+        sa.out = items;
         sa.counters = h->d_counters;
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
         if (h->profiling) {
@@ -480,31 +493,57 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
             }
             CK(cudaEventRecord(ev.first, s), "profiling");
         }
-        CK(launch_scan(sa, p->energy, ns, warps, grid, s), "convexify_points/scan");
+        CK(launch_scan(sa, warps, grid, s), "convexify_points/scan");
         if (h->profiling) {
             CK(cudaEventRecord(ev.second, s), "profiling");
             h->ev_pending.push_back(ev);
         }
 
-        ExpandArgs ea;
-        ea.tree = tr;
-        ea.NT = NT;
-        ea.level = l;
-        ea.depth = K;
-        ea.beta = beta_k;
-        ea.q_point = sa.q_point;
-        ea.q_heap = sa.q_heap;
-        ea.q_count = cnt + l;
-        ea.nq_point = l + 1 < K ? (int32_t *)(ws + o_qp[l + 1]) : nullptr;
-        ea.nq_heap = l + 1 < K ? (int32_t *)(ws + o_qh[l + 1]) : nullptr;
-        ea.nq_count = cnt + l + 1;
-        ea.items = sa.out;
-        ea.chunks = chunks;
-        ea.dir64 = h->d_dir64;
-        ea.mat = mat;
-        ea.line = ln;
-        ea.counters = h->d_counters;
-        CK(launch_expand(ea, (int64_t)n << l, s), "convexify_points/expand");
+        SelectArgs se;
+        se.q_count = cnt + l;
+        se.items = items;
+        se.chunks = chunks;
+        se.kappa = (float)line_kappa(mat);
+        se.cands = cands;
+        se.work = work;
+        se.work_count = wcnt + l;
+        se.counters = h->d_counters;
+        CK(launch_select(se, max_nodes, s), "convexify_points/select");
+
+        RefineArgs ra;
+        ra.tree = tr;
+        ra.NT = NT;
+        ra.beta = beta_k;
+        ra.q_point = qp;
+        ra.q_heap = qh;
+        ra.cands = cands;
+        ra.work = work;
+        ra.work_count = wcnt + l;
+        ra.dir64 = h->d_dir64;
+        ra.mat = mat;
+        ra.line = ln;
+        ra.out = refined;
+        CK(launch_refine(ra, max_nodes * kNodeCand, s), "convexify_points/refine");
+
+        CommitArgs ca;
+        ca.tree = tr;
+        ca.NT = NT;
+        ca.level = l;
+        ca.depth = K;
+        ca.beta = beta_k;
+        ca.q_point = qp;
+        ca.q_heap = qh;
+        ca.q_count = cnt + l;
+        ca.nq_point = l + 1 < K ? (int32_t *)(ws + o_qp[l + 1]) : nullptr;
+        ca.nq_heap = l + 1 < K ? (int32_t *)(ws + o_qh[l + 1]) : nullptr;
+        ca.nq_count = cnt + l + 1;
+        ca.cands = cands;
+        ca.refined = refined;
+        ca.dir64 = h->d_dir64;
+        ca.mat = mat;
+        ca.line = ln;
+        ca.counters = h->d_counters;
+        CK(launch_commit(ca, max_nodes, s), "convexify_points/commit");
     }
 
     LeafArgs la;

@@ -80,18 +80,21 @@ __host__ __device__ inline void stress64(const double F[4], double beta_k, const
 //   d = A0 + A1 t + A2 t^2 + lg (B1 + B2 lg),
 //   A0 = mu/2 (|F|^2 - 2) - beta_k, A1 = mu F:R, A2 = mu/2 |R|^2,
 //   B1 = -mu ln2, B2 = lam/2 ln2^2,
-// and the damage branch of Eq. (2.9) becomes, with e = exp2(ce max(d, 0)),
-// ce = -log2(e)/D_0, e_k = exp(-beta_k/D_0):
-//   W = (1 - D_inf) d + K1 (1 - e) + K2 min(d, 0),  K1 = D_inf D_0 e_k, K2 = D_inf e_k.
-// (d <= 0 gives (1 - D_inf + D_inf e_k) d = (1 - D(beta_k)) d; d > 0 gives the
-// second branch.)  J <= 0 yields +inf or NaN, which the hull search ignores.
+// and the two branches of Eq. (2.9) become, with e_k = exp(-beta_k/D_0),
+//   W = (1 - D_inf) d + K1 (1 - exp(-max(d, 0)/D_0)) + K2 min(d, 0),
+//   K1 = D_inf D_0 e_k, K2 = D_inf e_k
+// (d <= 0 gives (1 - D_inf + D_inf e_k) d = (1 - D(beta_k)) d; d > 0 gives
+// (1 - D_inf)(s - beta_k) + D_inf D_0 (e_k - e^{-s/D_0})).  The kernels sample
+// kappa W with kappa = log2(e)/D_0 > 0, so that the exponential is one ex2 of
+// -max(kappa d, 0): all coefficients carry the factor kappa, which changes no
+// hull or direction decision.  J <= 0 yields +inf or NaN, which the hull
+// search ignores.
 // -------------------------------------------------------------------------
 struct NodeLine {
-    float A0, B1, B2, ce, a1, K1, K2, mu;
+    float A0, B1, B2, a1, K1, K2, mu;  // kappa-scaled (K2 and a1 are ratios)
     float J0;
     float F[4];
     float cof[4];
-    // double-well coefficients are built per direction from F
 };
 
 struct DirLine {
@@ -110,19 +113,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Node constants from F (FP64) and beta_k, rounded to FP32.
+// Sample scale kappa: log2(e)/D_0 for the damage energy, 1 for the test energy.
+__host__ __device__ inline double line_kappa(const Material &m) {
+    return m.energy == CVX_ENERGY_NH_DAMAGE ? kLog2e / m.D0 : 1.0;
+}
+
+// Node constants from F (FP64) and beta_k, rounded to FP32 (kappa-scaled).
 __device__ inline NodeLine make_node_line(const double F[4], double beta_k, const Material &m) {
     NodeLine nl;
+    const double kap = line_kappa(m);
     double fsq = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
     double ek = exp(-beta_k / m.D0);
-    nl.A0 = (float)(0.5 * m.mu * (fsq - 2.0) - beta_k);
-    nl.B1 = (float)(-m.mu * kLn2d);
-    nl.B2 = (float)(0.5 * m.lam * kLn2d * kLn2d);
-    nl.ce = (float)(-kLog2e / m.D0);
+    nl.A0 = (float)(kap * (0.5 * m.mu * (fsq - 2.0) - beta_k));
+    nl.B1 = (float)(kap * (-m.mu * kLn2d));
+    nl.B2 = (float)(kap * (0.5 * m.lam * kLn2d * kLn2d));
     nl.a1 = (float)(1.0 - m.Dinf);
-    nl.K1 = (float)(m.Dinf * m.D0 * ek);
+    nl.K1 = (float)(kap * m.Dinf * m.D0 * ek);
     nl.K2 = (float)(m.Dinf * ek);
-    nl.mu = (float)m.mu;
+    nl.mu = (float)(kap * m.mu);
     nl.J0 = (float)(F[0] * F[3] - F[1] * F[2]);
     for (int k = 0; k < 4; ++k) nl.F[k] = (float)F[k];
     nl.cof[0] = (float)F[3];
@@ -158,17 +166,16 @@ __device__ __forceinline__ DirLine make_dir_line(const NodeLine &nl, float4 d) {
     return dl;
 }
 
-// One FP32 sample of W at parameter t (12 FP32-pipe instructions and 2 MUFU
-// for the damage energy).
+// One FP32 sample of kappa W at parameter t: 11 FP32-pipe instructions and
+// 2 MUFU for the damage energy.
 template <int EK>
 __device__ __forceinline__ float sample_w(const NodeLine &nl, const DirLine &dl, float t) {
     if (EK == CVX_ENERGY_NH_DAMAGE) {
-        float p = __fmaf_rn(t, __fmaf_rn(t, dl.A2, dl.A1), nl.A0);
-        float J = __fmaf_rn(t, dl.cJ, dl.J0);
-        float lg = lg2_approx(J);
-        float d = __fmaf_rn(lg, __fmaf_rn(lg, nl.B2, nl.B1), p);
-        float z = fminf(d * nl.ce, 0.0f);
-        float e = ex2_approx(z);
+        const float p = __fmaf_rn(t, __fmaf_rn(t, dl.A2, dl.A1), nl.A0);
+        const float J = __fmaf_rn(t, dl.cJ, dl.J0);
+        const float lg = lg2_approx(J);
+        const float d = __fmaf_rn(lg, __fmaf_rn(lg, nl.B2, nl.B1), p);
+        const float e = ex2_approx(-fmaxf(d, 0.0f));
         float w = __fmaf_rn(d, nl.a1, nl.K1);
         w = __fmaf_rn(-nl.K1, e, w);
         return __fmaf_rn(nl.K2, fminf(d, 0.0f), w);
@@ -178,6 +185,16 @@ __device__ __forceinline__ float sample_w(const NodeLine &nl, const DirLine &dl,
         w = __fmaf_rn(w, t, dl.c[1]);
         return __fmaf_rn(w, t, dl.c[0]);
     }
+}
+
+// FP64 sample of W along the line: G = F + t R with t = (m - m0) h and R, G
+// rounded exactly as the split points are (no contraction).
+__device__ __forceinline__ double sample_w64(const double F[4], const double R[4], int m, int m0,
+                                             double h, double beta_k, const Material &mat) {
+    const double t = __dmul_rn((double)(m - m0), h);
+    double G[4];
+    for (int k = 0; k < 4; ++k) G[k] = __dadd_rn(F[k], __dmul_rn(t, R[k]));
+    return energy64(G, beta_k, mat);
 }
 
 }  // namespace cvx

@@ -10,26 +10,47 @@
 
 namespace cvx {
 
-enum { CVX_NODE_ITER_CAP = 64 };
+enum { CVX_NODE_ITER_CAP = 64, CVX_NODE_OVERFLOW = 128 };
 
-// Best line of one work item (a node and a block of its directions).
-struct ItemBest {
-    double h;    // hull value at 0 (FP64 of the FP32 samples)
-    float h32;   // FP32 estimate of h
-    float h2;    // FP32 second-best hull value seen in the item
-    int32_t dir, mm, mp, flags;
+constexpr int kWarpTop = 4;    // best directions kept per warp
+constexpr int kItemTop = 8;    // per work item
+constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
+// Screening tolerance (kappa-scaled units, relative to max(kappa, |q|)):
+// several times twice the FP32 sampling error bound.
+constexpr float kScreen = 4e-6f;
+
+// Best directions of one work item (a node and a block of its directions),
+// ranked by q = FP32 value at t = 0 of the chord between the left and right
+// sets' bridge (the hull value when the centre does not lie below it).
+struct ItemCands {
+    float q[kItemTop];
+    int dir[kItemTop];
+    float w0;       // FP32 centre sample
+    float dropped;  // smallest q not kept
+    int n, flags;
 };
-static_assert(sizeof(ItemBest) == 32, "ItemBest layout");
+
+struct NodeCands {
+    int dir[kNodeCand];
+    int n, flags;
+    float qmin, w0;
+};
+
+struct RefineOut {
+    double q;  // FP64 chord value at 0 of the bridge of the left and right sets
+    int a, b;
+    int ok, pad;
+};
 
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
-    C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_DIR64, C_NUM
+    C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_NUM
 };
 
 struct LineSpec {
-    int L, m0;
-    float h32;    // sample spacing, FP32
-    double h64;   // sample spacing, FP64
+    int L, m0, nfull, stride;  // samples, centre, full 128-chunks, per-warp buffer floats
+    float h32;                 // sample spacing, FP32
+    double h64;                // sample spacing, FP64
 };
 
 struct ScanArgs {
@@ -41,18 +62,43 @@ struct ScanArgs {
     int D, chunks, dirs_per_item;
     Material mat;
     LineSpec line;
-    ItemBest *out;
+    ItemCands *out;
     unsigned long long *counters;
 };
 
-struct ExpandArgs {
+struct SelectArgs {
+    const int32_t *q_count;
+    const ItemCands *items;
+    int chunks;
+    float kappa;
+    NodeCands *cands;
+    int2 *work;  // (queue index, candidate index)
+    int32_t *work_count;
+    unsigned long long *counters;
+};
+
+struct RefineArgs {
+    const cvx_node *tree;
+    int NT;
+    const double *beta;
+    const int32_t *q_point, *q_heap;
+    const NodeCands *cands;
+    const int2 *work;
+    const int32_t *work_count;
+    const double *dir64;
+    Material mat;
+    LineSpec line;
+    RefineOut *out;
+};
+
+struct CommitArgs {
     cvx_node *tree;
     int NT, level, depth;
     const double *beta;
     const int32_t *q_point, *q_heap, *q_count;
     int32_t *nq_point, *nq_heap, *nq_count;
-    const ItemBest *items;
-    int chunks;
+    const NodeCands *cands;
+    const RefineOut *refined;
     const double *dir64;
     Material mat;
     LineSpec line;
@@ -84,10 +130,11 @@ struct LeafArgs {
 
 // kernel launchers (cvx_kernels.cu)
 cudaError_t launch_init(const InitArgs &a, cudaStream_t s);
-cudaError_t launch_scan(const ScanArgs &a, int energy, int ns, int warps, int grid,
-                        cudaStream_t s);
-int scan_max_blocks_per_sm(int energy, int ns, int warps);
-cudaError_t launch_expand(const ExpandArgs &a, int64_t max_nodes, cudaStream_t s);
+cudaError_t launch_scan(const ScanArgs &a, int warps, int grid, cudaStream_t s);
+int scan_max_blocks_per_sm(int energy, int warps, int stride);
+cudaError_t launch_select(const SelectArgs &a, int64_t max_nodes, cudaStream_t s);
+cudaError_t launch_refine(const RefineArgs &a, int64_t max_work, cudaStream_t s);
+cudaError_t launch_commit(const CommitArgs &a, int64_t max_nodes, cudaStream_t s);
 cudaError_t launch_leaf(const LeafArgs &a, cudaStream_t s);
 cudaError_t launch_energy(int64_t n, const double *F, const double *beta, double *W, double *P,
                           Material m, cudaStream_t s);
@@ -95,17 +142,11 @@ cudaError_t launch_history(int64_t n, const double *F, const double *bin, double
                            Material m, cudaStream_t s);
 cudaError_t launch_sample_lines(int64_t n, const double *F, const double *beta,
                                 const int32_t *dir, const float4 *dir32, int D, Material m,
-                                LineSpec line, int ns, float *w, cudaStream_t s);
-cudaError_t launch_hull(int64_t n, int L, int ns, const float *w, int32_t *mm, int32_t *mp,
-                        double *h, unsigned long long *counters, cudaStream_t s);
+                                LineSpec line, float *w, cudaStream_t s);
+cudaError_t launch_hull(int64_t n, int L, const float *w, int32_t *mm, int32_t *mp, double *h,
+                        unsigned long long *counters, cudaStream_t s);
 
-inline int slots_for(int L) {
-    int ns = (L + 31) / 32;
-    if (ns <= 8) return 8;
-    if (ns <= 17) return 17;
-    if (ns <= 33) return 33;
-    if (ns <= 65) return 65;
-    return -1;
-}
+// Per-warp shared-memory stride of a line of L samples (16-byte aligned).
+__host__ __device__ inline int line_stride(int L) { return (L + 3) & ~3; }
 
 }  // namespace cvx

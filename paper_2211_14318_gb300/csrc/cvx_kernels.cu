@@ -1,96 +1,126 @@
 // cvx_kernels.cu -- kernels of the per-point rank-one convexification.
 //
-//   k_init          roots of the lamination trees, level-0 node queue
-//   k_scan          line sampling + exact hull bridge + min over directions
-//                   (the hot loop: Eq. 4.4, Algorithm 1, Eq. 4.3)
-//   k_expand        per node: best direction over work items, split into
-//                   F+- (Eq. 3.3 / Algorithm 2), next-level node queue
-//   k_leaf          W^R and P over the tree leaves (Eq. 5.2, Algorithm 3)
+// Per lamination level (Eq. 3.3, top-down):
+//   k_scan    FP32 screening: every direction's line is sampled (Eq. 4.4),
+//             its exact FP32 hull bridge found (Algorithm 1 read at t = 0) and
+//             the best directions kept per work item (the hot loop)
+//   k_select  per node: the directions whose FP32 value lies within the
+//             screening tolerance of the best (any other direction provably
+//             loses in FP64), or none if the node provably does not split
+//   k_refine  per candidate: the line resampled in FP64 and its bridge found
+//             in FP64 -- the decisions whose stability needs it
+//   k_commit  per node: minimum over directions in FP64 (Eq. 4.3), split into
+//             F+- (Algorithm 2), next-level node queue
+// and around them:
+//   k_init    roots of the lamination trees, level-0 node queue
+//   k_leaf    W^R and P over the tree leaves (Eq. 5.2, Algorithm 3)
 //   k_energy, k_history, k_sample_lines, k_hull   single steps of the method
 #include <cuda_runtime.h>
+#include <limits.h>
 
 #include "cvx_bridge.cuh"
 #include "cvx_internal.h"
 
 namespace cvx {
 
-// -------------------------------------------------------------------------
-// Sampling of one line into registers (slot j of lane l = sample 32 j + l)
-// and into the warp's shared-memory copy.  Returns (on every lane) the number
-// of finite samples.
-// -------------------------------------------------------------------------
-template <int NS, int EK>
-__device__ __forceinline__ int sample_line(float (&w)[NS], float *sw, const NodeLine &nl,
-                                           const DirLine &dl, const LineSpec &ln, int lane) {
-    const float tl = (float)(lane - ln.m0) * ln.h32;
-    const float h32x = 32.0f * ln.h32;
-    int valid = 0;
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-        const int k = 32 * j + lane;
-        float v = __int_as_float(0x7fffffff);
-        if (32 * j < ln.L) {
-            const float t = __fmaf_rn(h32x, (float)j, tl);
-            v = sample_w<EK>(nl, dl, t);
-            if (k >= ln.L) v = __int_as_float(0x7fffffff);
-            valid += __popc(__ballot_sync(kFull, v < INFINITY));
-        }
-        w[j] = v;
-        sw[k] = v;
-    }
-    return valid;
-}
-
-__device__ __forceinline__ float h32_of(const BridgeOut &o, int m0, float *err) {
-    if (!o.lam) {
-        *err = 0.0f;
-        return o.w0;
-    }
-    float xa = (float)(o.a - m0), xb = (float)(o.b - m0);
-    float alpha = -xa / (xb - xa);
-    *err = 6.0f * kU32 * (fabsf(o.wa) + fabsf(o.wb)) + 1e-30f;
-    return o.wa + (o.wb - o.wa) * alpha;
-}
-
-__device__ __forceinline__ double h64_of(int lam, int a, int b, float wa, float wb, float w0,
-                                         int m0) {
-    if (!lam) return (double)w0;
-    double xa = (double)(a - m0), xb = (double)(b - m0);
-    return (xb * (double)wa - xa * (double)wb) / (xb - xa);
-}
-
 __device__ __forceinline__ void add_counter(unsigned long long *c, int idx, unsigned long long v) {
     if (v) atomicAdd(c + idx, v);
 }
 
 // -------------------------------------------------------------------------
-// k_scan: persistent over work items (node, block of directions).  Each warp
-// scans a contiguous run of directions (warm-starting every hull search from
-// the previous direction's bridge), keeps its best line, and the CTA reduces
-// the warps' bests in FP64 (ties -> lowest direction index).
+// Sampling of one line into the warp's shared buffer: in chunk q lane l
+// computes samples 128 q + 4 l + i (one 16-byte store); the tail past the
+// last full chunk is one sample per lane.  tl[i] = (4 l + i - m0) h.
 // -------------------------------------------------------------------------
-template <int NS, int EK>
-__global__ void __launch_bounds__(512) k_scan(const ScanArgs A) {
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float *sw = smem + warp * (NS * 32);
-    __shared__ NodeLine s_nl;
-    __shared__ double s_h[16];
-    __shared__ float s_h32[16], s_h2[16];
-    __shared__ int s_dir[16], s_mm[16], s_mp[16], s_fl[16];
+template <int EK>
+__device__ __forceinline__ void sample_line(float *sw, const NodeLine &nl, const DirLine &dl,
+                                            const LineSpec &ln, int lane, const float (&tl)[4]) {
+    const float h128 = 128.0f * ln.h32;
+    float fq = 0.0f;
+#pragma unroll 2
+    for (int q = 0; q < ln.nfull; ++q, fq += 1.0f) {
+        float4 v;
+        v.x = sample_w<EK>(nl, dl, __fmaf_rn(h128, fq, tl[0]));
+        v.y = sample_w<EK>(nl, dl, __fmaf_rn(h128, fq, tl[1]));
+        v.z = sample_w<EK>(nl, dl, __fmaf_rn(h128, fq, tl[2]));
+        v.w = sample_w<EK>(nl, dl, __fmaf_rn(h128, fq, tl[3]));
+        *reinterpret_cast<float4 *>(sw + 128 * q + 4 * lane) = v;
+    }
+    for (int k = 128 * ln.nfull + lane; k < ln.L; k += 32)
+        sw[k] = sample_w<EK>(nl, dl, (float)(k - ln.m0) * ln.h32);
+}
 
+// Number of samples with J(t) > 0 on a line (the algorithmic work count).
+__device__ __forceinline__ int valid_samples(const DirLine &dl, const LineSpec &ln, int energy) {
+    if (energy != CVX_ENERGY_NH_DAMAGE || dl.cJ == 0.0f) return ln.L;
+    const float xs = -dl.J0 / (dl.cJ * ln.h32);  // J = 0 at x = m - m0 = xs
+    const float lim = (float)ln.L;
+    if (dl.cJ > 0.0f) {  // valid for x > xs
+        const float lo = fminf(fmaxf(floorf(xs) + 1.0f, -lim), lim);
+        return max(0, min(ln.L, ln.m0 - max((int)lo, -ln.m0) + 1));
+    }
+    const float hi = fminf(fmaxf(ceilf(xs) - 1.0f, -lim), lim);  // valid for x < xs
+    return max(0, min(ln.L, (int)hi + ln.m0 + 1));
+}
+
+// Sorted insertion into a warp's best list (uniform across the warp).
+__device__ __forceinline__ void top_insert(float (&q)[kWarpTop], int (&d)[kWarpTop],
+                                           float &dropped, float v, int dir) {
+    if (!(v < q[kWarpTop - 1])) {
+        dropped = fminf(dropped, v);
+        return;
+    }
+    dropped = fminf(dropped, q[kWarpTop - 1]);
+    int k = kWarpTop - 1;
+#pragma unroll
+    for (int i = kWarpTop - 1; i > 0; --i) {
+        if (v < q[i - 1]) {
+            q[i] = q[i - 1];
+            d[i] = d[i - 1];
+            k = i - 1;
+        }
+    }
+    // place at the first slot whose predecessor is <= v
+#pragma unroll
+    for (int i = 0; i < kWarpTop; ++i)
+        if (i == k) {
+            q[i] = v;
+            d[i] = dir;
+        }
+}
+
+// -------------------------------------------------------------------------
+// k_scan: persistent over work items (node, block of directions).  Each warp
+// scans a contiguous run of directions, warm-starting every hull search from
+// the previous direction's bridge, and keeps its best directions by q.
+// -------------------------------------------------------------------------
+template <int EK>
+__global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const LineSpec ln = A.line;
-    const LineGeom g{ln.L, ln.m0, ln.m0 >> 5, ln.m0 & 31};
+    float *sw = reinterpret_cast<float *>(smem4) + warp * ln.stride;
+    __shared__ NodeLine s_nl;
+    __shared__ float s_q[16][kWarpTop];
+    __shared__ int s_d[16][kWarpTop];
+    __shared__ float s_drop[16];
+    __shared__ int s_fl[16];
+    __shared__ float s_w0;
+
+    const LineGeom g{ln.L, ln.m0, ln.nfull};
+    float tl[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
     const int n_nodes = *A.q_count;
     const long long n_items = (long long)n_nodes * A.chunks;
-    HullCounters hc{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    unsigned long long n_valid = 0, n_lines = 0, n_dir64 = 0;
+    HullCounters hc{};
+    unsigned long long n_valid = 0, n_lines = 0;
 
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int qi = (int)(item / A.chunks), ch = (int)(item % A.chunks);
-        const int p = A.q_point[qi], hi = A.q_heap[qi];
         __syncthreads();
         if (threadIdx.x == 0) {
+            const int p = A.q_point[qi], hi = A.q_heap[qi];
             const cvx_node &nd = A.tree[(long long)p * A.NT + hi];
             double F[4] = {nd.F[0], nd.F[1], nd.F[2], nd.F[3]};
             s_nl = make_node_line(F, A.beta[p], A.mat);
@@ -101,166 +131,375 @@ __global__ void __launch_bounds__(512) k_scan(const ScanArgs A) {
         const int per = (d1 - d0 + nw - 1) / nw;
         const int jb = d0 + warp * per, je = min(d1, jb + per);
 
-        float b_h32 = INFINITY, b_err = 0.0f, b_h2 = INFINITY, b_wa = 0.0f, b_wb = 0.0f;
-        float w0 = 0.0f;
-        int b_dir = -1, b_a = ln.m0, b_b = ln.m0, b_lam = 0, b_fl = 0;
+        float tq[kWarpTop];
+        int td[kWarpTop];
+#pragma unroll
+        for (int i = 0; i < kWarpTop; ++i) {
+            tq[i] = INFINITY;
+            td[i] = -1;
+        }
+        float dropped = INFINITY, w0 = 0.0f;
+        int fl = 0;
         int warm_a = -1, warm_b = -1;
         for (int dj = jb; dj < je; ++dj) {
             const DirLine dl = make_dir_line<EK>(nl, A.dir32[dj]);
-            float w[NS];
-            n_valid += sample_line<NS, EK>(w, sw, nl, dl, ln, lane);
+            sample_line<EK>(sw, nl, dl, ln, lane, tl);
             __syncwarp();
             const unsigned caps0 = hc.caps;
-            const BridgeOut o = warp_bridge<NS>(w, sw, g, lane, warm_a, warm_b, hc);
+            const BridgeOut o = warp_bridge(sw, g, lane, warm_a, warm_b, hc);
             __syncwarp();
-            ++n_lines;
+            if (lane == 0) {
+                ++n_lines;
+                n_valid += valid_samples(dl, ln, EK);
+                if (hc.caps != caps0) fl |= CVX_NODE_ITER_CAP;
+            }
             w0 = o.w0;
+            float q = INFINITY;
             if (o.a >= 0) {
                 warm_a = o.a;
                 warm_b = o.b;
+                const float xa = (float)(o.a - ln.m0), xb = (float)(o.b - ln.m0);
+                q = o.wa + (o.wb - o.wa) * __fdividef(-xa, xb - xa);
             }
-            float err;
-            const float h32 = h32_of(o, ln.m0, &err);
-            bool better;
-            if (b_dir < 0) better = true;
-            else if (h32 + err < b_h32 - b_err) better = true;
-            else if (h32 - err > b_h32 + b_err) better = false;
-            else {
-                ++n_dir64;
-                double hn = h64_of(o.lam, o.a, o.b, o.wa, o.wb, o.w0, ln.m0);
-                double hb = h64_of(b_lam, b_a, b_b, b_wa, b_wb, w0, ln.m0);
-                better = hn < hb;  // equal -> keep the lower direction index
-            }
-            const int fl = (__shfl_sync(kFull, hc.caps, 0) != __shfl_sync(kFull, caps0, 0))
-                               ? CVX_NODE_ITER_CAP : 0;
-            if (better) {
-                b_h2 = fminf(b_h2, b_h32);
-                b_h32 = h32;
-                b_err = err;
-                b_dir = dj;
-                b_lam = o.lam;
-                b_a = o.lam ? o.a : ln.m0;
-                b_b = o.lam ? o.b : ln.m0;
-                b_wa = o.wa;
-                b_wb = o.wb;
-                b_fl = fl;
-            } else {
-                b_h2 = fminf(b_h2, h32);
-            }
+            top_insert(tq, td, dropped, q, dj);
         }
         if (lane == 0) {
-            s_h[warp] = b_dir >= 0 ? h64_of(b_lam, b_a, b_b, b_wa, b_wb, w0, ln.m0) : INFINITY;
-            s_h32[warp] = b_h32;
-            s_h2[warp] = b_h2;
-            s_dir[warp] = b_dir;
-            s_mm[warp] = b_a;
-            s_mp[warp] = b_b;
-            s_fl[warp] = b_fl;
+#pragma unroll
+            for (int i = 0; i < kWarpTop; ++i) {
+                s_q[warp][i] = tq[i];
+                s_d[warp][i] = td[i];
+            }
+            s_drop[warp] = dropped;
+            s_fl[warp] = fl;
+            if (jb < je) s_w0 = w0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int bw = -1;
+            // merge the warps' lists (ties -> lower direction index)
+            ItemCands r;
+            float drop = INFINITY;
+            int f = 0;
             for (int k = 0; k < nw; ++k) {
-                if (s_dir[k] < 0) continue;
-                if (bw < 0 || s_h[k] < s_h[bw] || (s_h[k] == s_h[bw] && s_dir[k] < s_dir[bw])) bw = k;
+                drop = fminf(drop, s_drop[k]);
+                f |= s_fl[k];
             }
-            ItemBest r;
-            if (bw < 0) {
-                r.h = INFINITY;
-                r.h32 = INFINITY;
-                r.h2 = INFINITY;
-                r.dir = -1;
-                r.mm = r.mp = ln.m0;
-                r.flags = 0;
-            } else {
-                float sec = s_h2[bw];
-                int fl = 0;
+            int taken[16];
+            for (int k = 0; k < nw; ++k) taken[k] = 0;
+            int n = 0;
+            for (; n < kItemTop; ++n) {
+                int bk = -1;
                 for (int k = 0; k < nw; ++k) {
-                    if (s_dir[k] < 0) continue;
-                    fl |= s_fl[k];
-                    if (k != bw) sec = fminf(sec, fminf(s_h32[k], s_h2[k]));
+                    if (taken[k] >= kWarpTop || s_d[k][taken[k]] < 0) continue;
+                    if (bk < 0 || s_q[k][taken[k]] < s_q[bk][taken[bk]] ||
+                        (s_q[k][taken[k]] == s_q[bk][taken[bk]] &&
+                         s_d[k][taken[k]] < s_d[bk][taken[bk]]))
+                        bk = k;
                 }
-                r.h = s_h[bw];
-                r.h32 = s_h32[bw];
-                r.h2 = sec;
-                r.dir = s_dir[bw];
-                r.mm = s_mm[bw];
-                r.mp = s_mp[bw];
-                r.flags = fl;
+                if (bk < 0) break;
+                r.q[n] = s_q[bk][taken[bk]];
+                r.dir[n] = s_d[bk][taken[bk]];
+                ++taken[bk];
             }
+            for (int k = 0; k < nw; ++k)
+                if (taken[k] < kWarpTop && s_d[k][taken[k]] >= 0) drop = fminf(drop, s_q[k][taken[k]]);
+            for (int i = n; i < kItemTop; ++i) {
+                r.q[i] = INFINITY;
+                r.dir[i] = -1;
+            }
+            r.n = n;
+            r.w0 = s_w0;
+            r.dropped = drop;
+            r.flags = f;
             A.out[item] = r;
         }
     }
-    // counters: per-lane FP64 checks summed, warp-uniform ones from lane 0
-    unsigned fp64 = __reduce_add_sync(kFull, hc.fp64);
-    unsigned fp64r = __reduce_add_sync(kFull, hc.fp64r);
+    const unsigned fp64w = __reduce_add_sync(kFull, hc.fp64w);
+    const unsigned fp64r = __reduce_add_sync(kFull, hc.fp64r);
     if (lane == 0) {
-        add_counter(A.counters, C_FP64W, fp64);
-        add_counter(A.counters, C_FP64R, fp64r);
-        add_counter(A.counters, C_FP64C, hc.fp64c);
-        add_counter(A.counters, C_WSTEPS, hc.wsteps);
-        add_counter(A.counters, C_ROUNDS, hc.rounds);
-        add_counter(A.counters, C_DIR64, n_dir64);
         add_counter(A.counters, C_LINES, n_lines);
         add_counter(A.counters, C_VALID, n_valid);
-        add_counter(A.counters, C_FP64, fp64 + fp64r + hc.fp64c);
+        add_counter(A.counters, C_FP64, (unsigned long long)fp64w + fp64r + hc.fp64c);
+        add_counter(A.counters, C_FP64W, fp64w);
+        add_counter(A.counters, C_FP64R, fp64r);
+        add_counter(A.counters, C_FP64C, hc.fp64c);
         add_counter(A.counters, C_FULL, hc.full_passes);
         add_counter(A.counters, C_RARE, hc.rare);
         add_counter(A.counters, C_CAPS, hc.caps);
+        add_counter(A.counters, C_WSTEPS, hc.wsteps);
+        add_counter(A.counters, C_ROUNDS, hc.rounds);
     }
 }
 
-template <int NS, int EK>
+static size_t scan_smem(int warps, int stride) { return (size_t)warps * stride * sizeof(float); }
+
+template <int EK>
 static cudaError_t launch_scan_t(const ScanArgs &a, int warps, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)warps * NS * 32 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_scan<NS, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = scan_smem(warps, a.line.stride);
+    cudaError_t e = cudaFuncSetAttribute(k_scan<EK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_scan<NS, EK><<<grid, warps * 32, smem, s>>>(a);
+    k_scan<EK><<<grid, warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int NS, int EK>
-static int occ_t(int warps) {
-    const size_t smem = (size_t)warps * NS * 32 * sizeof(float);
-    cudaFuncSetAttribute(k_scan<NS, EK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_scan(const ScanArgs &a, int warps, int grid, cudaStream_t s) {
+    return a.mat.energy == CVX_ENERGY_NH_DAMAGE
+               ? launch_scan_t<CVX_ENERGY_NH_DAMAGE>(a, warps, grid, s)
+               : launch_scan_t<CVX_ENERGY_DOUBLE_WELL>(a, warps, grid, s);
+}
+
+template <int EK>
+static int occ_t(int warps, int stride) {
+    const size_t smem = scan_smem(warps, stride);
+    if (cudaFuncSetAttribute(k_scan<EK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<NS, EK>, warps * 32, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<EK>, warps * 32, smem) !=
         cudaSuccess)
         return 0;
     return nb;
 }
 
-cudaError_t launch_scan(const ScanArgs &a, int energy, int ns, int warps, int grid,
-                        cudaStream_t s) {
-#define SC(N)                                                                          \
-    case N:                                                                            \
-        return energy == CVX_ENERGY_NH_DAMAGE                                          \
-                   ? launch_scan_t<N, CVX_ENERGY_NH_DAMAGE>(a, warps, grid, s)         \
-                   : launch_scan_t<N, CVX_ENERGY_DOUBLE_WELL>(a, warps, grid, s);
-    switch (ns) {
-        SC(8)
-        SC(17)
-        SC(33)
-        SC(65)
-    default: return cudaErrorInvalidValue;
-    }
-#undef SC
+int scan_max_blocks_per_sm(int energy, int warps, int stride) {
+    return energy == CVX_ENERGY_NH_DAMAGE ? occ_t<CVX_ENERGY_NH_DAMAGE>(warps, stride)
+                                          : occ_t<CVX_ENERGY_DOUBLE_WELL>(warps, stride);
 }
 
-int scan_max_blocks_per_sm(int energy, int ns, int warps) {
-#define OCC(N)                                                                              \
-    case N:                                                                                 \
-        return energy == CVX_ENERGY_NH_DAMAGE ? occ_t<N, CVX_ENERGY_NH_DAMAGE>(warps)       \
-                                              : occ_t<N, CVX_ENERGY_DOUBLE_WELL>(warps);
-    switch (ns) {
-        OCC(8)
-        OCC(17)
-        OCC(33)
-        OCC(65)
-    default: return 0;
+// -------------------------------------------------------------------------
+// k_select: one thread per queued node.  With Qmin the smallest FP32 q over
+// all directions and tol the screening tolerance (> twice the FP32 sampling
+// error), a direction with q > Qmin + tol cannot be the FP64 minimiser, and
+// if Qmin > w0 + tol the centre is a strict vertex on every line in FP64.
+// -------------------------------------------------------------------------
+__global__ void k_select(const SelectArgs A) {
+    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= *A.q_count) return;
+    const ItemCands *r = A.items + (long long)qi * A.chunks;
+    float qmin = INFINITY, drop = INFINITY;
+    int fl = 0;
+    const float w0 = r[0].w0;
+    for (int c = 0; c < A.chunks; ++c) {
+        qmin = fminf(qmin, r[c].q[0]);
+        drop = fminf(drop, r[c].dropped);
+        fl |= r[c].flags;
     }
-#undef OCC
+    NodeCands nc;
+    nc.qmin = qmin;
+    nc.w0 = w0;
+    nc.n = 0;
+    const float tol = kScreen * fmaxf(A.kappa, fmaxf(fabsf(qmin), fabsf(w0)));
+    if (qmin <= w0 + tol) {
+        const float lim = qmin + tol;
+        for (int c = 0; c < A.chunks; ++c)
+            for (int i = 0; i < r[c].n; ++i) {
+                if (!(r[c].q[i] <= lim)) break;
+                if (nc.n < kNodeCand) nc.dir[nc.n++] = r[c].dir[i];
+                else fl |= CVX_NODE_OVERFLOW;
+            }
+        if (drop <= lim) fl |= CVX_NODE_OVERFLOW;
+    }
+    nc.flags = fl;
+    if (fl & CVX_NODE_OVERFLOW) atomicAdd(A.counters + C_OVERFLOW, 1ull);
+    A.cands[qi] = nc;
+    if (nc.n) {
+        const int pos = atomicAdd(A.work_count, nc.n);
+        for (int c = 0; c < nc.n; ++c) A.work[pos + c] = make_int2(qi, c);
+        atomicAdd(A.counters + C_REFINED, (unsigned long long)nc.n);
+    }
+}
+
+cudaError_t launch_select(const SelectArgs &a, int64_t max_nodes, cudaStream_t s) {
+    if (max_nodes == 0) return cudaSuccess;
+    k_select<<<(unsigned)((max_nodes + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------------
+// FP64 bridge of the left and right sets of one line held in shared memory:
+// supporting-slope iteration with full passes; ties go to the outermost sample
+// (Algorithm 1 keeps the outermost of collinear points).
+// -------------------------------------------------------------------------
+__device__ __forceinline__ void warp_min_dk(double &v, int &k, bool prefer_low) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double v2 = __shfl_xor_sync(kFull, v, o);
+        const int k2 = __shfl_xor_sync(kFull, k, o);
+        if (v2 < v || (v2 == v && (prefer_low ? k2 < k : k2 > k))) {
+            v = v2;
+            k = k2;
+        }
+    }
+}
+
+__device__ void bridge64(const double *sw, int L, int m0, int lane, int &a, int &b) {
+    double s = 0.0;
+    a = b = -1;
+    for (int it = 0; it < 128; ++it) {
+        double bl = INFINITY, br = INFINITY;
+        int kl = INT_MAX, kr = -1;
+        for (int k = lane; k < L; k += 32) {
+            if (k == m0) continue;
+            const double v = sw[k];
+            if (!(v < INFINITY)) continue;
+            const double e = v - s * (double)(k - m0);
+            if (k < m0) {
+                if (e < bl || (e == bl && k < kl)) { bl = e; kl = k; }
+            } else if (e < br || (e == br && k > kr)) {
+                br = e;
+                kr = k;
+            }
+        }
+        warp_min_dk(bl, kl, true);
+        warp_min_dk(br, kr, false);
+        if (kl == INT_MAX || kr < 0) {
+            a = b = -1;
+            return;
+        }
+        if (kl == a && kr == b) return;
+        a = kl;
+        b = kr;
+        s = (sw[b] - sw[a]) / (double)(b - a);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_refine(const RefineArgs A) {
+    extern __shared__ double sm64[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const LineSpec ln = A.line;
+    double *sw = sm64 + warp * ln.stride;
+    const int nwork = *A.work_count;
+    for (int w = blockIdx.x * (blockDim.x >> 5) + warp; w < nwork;
+         w += gridDim.x * (blockDim.x >> 5)) {
+    const int2 wk = A.work[w];
+    const int qi = wk.x, c = wk.y;
+    const int p = A.q_point[qi], hi = A.q_heap[qi];
+    const int dir = A.cands[qi].dir[c];
+    const cvx_node &nd = A.tree[(long long)p * A.NT + hi];
+    const double F[4] = {nd.F[0], nd.F[1], nd.F[2], nd.F[3]};
+    const double *d = A.dir64 + 4 * (long long)dir;
+    const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
+                         __dmul_rn(d[1], d[3])};
+    const double beta = A.beta[p];
+    for (int k = lane; k < ln.L; k += 32) sw[k] = sample_w64(F, R, k, ln.m0, ln.h64, beta, A.mat);
+    __syncwarp();
+    int a, b;
+    bridge64(sw, ln.L, ln.m0, lane, a, b);
+    if (lane == 0) {
+        RefineOut o;
+        o.a = a;
+        o.b = b;
+        o.pad = 0;
+        if (a >= 0) {
+            const double xa = (double)(a - ln.m0), xb = (double)(b - ln.m0);
+            o.q = (xb * sw[a] - xa * sw[b]) / (xb - xa);
+            o.ok = 1;
+        } else {
+            o.q = INFINITY;
+            o.ok = 0;
+        }
+        A.out[(long long)qi * kNodeCand + c] = o;
+    }
+    __syncwarp();
+    }
+}
+
+cudaError_t launch_refine(const RefineArgs &a, int64_t max_work, cudaStream_t s) {
+    if (max_work == 0) return cudaSuccess;
+    const int warps = 4;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (max_work + warps - 1) / warps;
+    const unsigned grid = (unsigned)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
+    k_refine<<<grid, warps * 32, (size_t)warps * a.line.stride * sizeof(double), s>>>(a);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------------
+// k_commit: one thread per queued node.  Split points in FP64 with explicit
+// rounding (no contraction): t = (m - m0) h, F+- = F + t R, xi = (m0-m-)/(m+-m-).
+// -------------------------------------------------------------------------
+__global__ void k_commit(const CommitArgs A) {
+    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= *A.q_count) return;
+    const int p = A.q_point[qi], hi = A.q_heap[qi];
+    const NodeCands &nc = A.cands[qi];
+    cvx_node &nd = A.tree[(long long)p * A.NT + hi];
+    nd.flags |= CVX_NODE_SCANNED | (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW));
+    atomicAdd(A.counters + C_NODES, 1ull);
+    const RefineOut *ro = A.refined + (long long)qi * kNodeCand;
+    int bc = -1;
+    double second = INFINITY;
+    for (int c = 0; c < nc.n; ++c) {
+        if (!ro[c].ok) continue;
+        if (bc < 0 || ro[c].q < ro[bc].q || (ro[c].q == ro[bc].q && nc.dir[c] < nc.dir[bc])) {
+            if (bc >= 0) second = fmin(second, ro[bc].q);
+            bc = c;
+        } else {
+            second = fmin(second, ro[c].q);
+        }
+    }
+    const int m0 = A.line.m0;
+    nd.gap = (float)(second - (bc >= 0 ? ro[bc].q : nd.w));
+    // the centre splits off iff the chord lies strictly below W(F) (FP64)
+    if (bc < 0 || !(ro[bc].q < nd.w)) {
+        nd.dir = bc >= 0 ? nc.dir[bc] : -1;
+        nd.flags |= CVX_NODE_LEAF;
+        return;
+    }
+    const RefineOut b = ro[bc];
+    int fl = CVX_NODE_LAMINATED;
+    if (b.a == 0 || b.b == A.line.L - 1) fl |= CVX_NODE_EDGE;
+    if (second == b.q) {
+        fl |= CVX_NODE_TIE;
+        atomicAdd(A.counters + C_TIES, 1ull);
+    }
+    nd.flags |= fl;
+    nd.dir = nc.dir[bc];
+    nd.m_minus = b.a;
+    nd.m_plus = b.b;
+    nd.h = b.q;
+    atomicAdd(A.counters + C_LAMINATED, 1ull);
+    const double xi = (double)(m0 - b.a) / (double)(b.b - b.a);
+    nd.xi = xi;
+    const double *d = A.dir64 + 4 * (long long)nd.dir;
+    const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
+                         __dmul_rn(d[1], d[3])};
+    const double tm = __dmul_rn((double)(b.a - m0), A.line.h64);
+    const double tp = __dmul_rn((double)(b.b - m0), A.line.h64);
+    const bool leaf_children = A.level + 1 >= A.depth;
+    const double beta = A.beta[p];
+    for (int side = 0; side < 2; ++side) {
+        const int ci = 2 * hi + 1 + side;  // 2i+1: F-, 2i+2: F+
+        cvx_node &c = A.tree[(long long)p * A.NT + ci];
+        const double t = side ? tp : tm;
+        double F[4];
+        for (int k = 0; k < 4; ++k) F[k] = __dadd_rn(nd.F[k], __dmul_rn(t, R[k]));
+        for (int k = 0; k < 4; ++k) c.F[k] = F[k];
+        c.weight = side ? __dmul_rn(nd.weight, xi) : __dmul_rn(nd.weight, __dsub_rn(1.0, xi));
+        c.w = energy64(F, beta, A.mat);
+        c.h = c.w;
+        c.xi = 0.0;
+        c.dir = -1;
+        c.m_minus = c.m_plus = m0;
+        c.gap = 0.0f;
+        c.pad = 0;
+        c.flags = CVX_NODE_EXISTS | (leaf_children ? CVX_NODE_LEAF : 0);
+    }
+    if (!leaf_children) {
+        const int pos = atomicAdd(A.nq_count, 2);
+        A.nq_point[pos] = p;
+        A.nq_heap[pos] = 2 * hi + 1;
+        A.nq_point[pos + 1] = p;
+        A.nq_heap[pos + 1] = 2 * hi + 2;
+    }
+}
+
+cudaError_t launch_commit(const CommitArgs &a, int64_t max_nodes, cudaStream_t s) {
+    if (max_nodes == 0) return cudaSuccess;
+    k_commit<<<(unsigned)((max_nodes + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 // -------------------------------------------------------------------------
@@ -300,7 +539,7 @@ __global__ void k_init(const InitArgs A) {
         nd.flags = CVX_NODE_EXISTS | CVX_NODE_LEAF;
     } else {
         nd.flags = CVX_NODE_EXISTS;
-        int pos = atomicAdd(A.q_count, 1);
+        const int pos = atomicAdd(A.q_count, 1);
         A.q_point[pos] = (int32_t)p;
         A.q_heap[pos] = 0;
     }
@@ -309,94 +548,6 @@ __global__ void k_init(const InitArgs A) {
 cudaError_t launch_init(const InitArgs &a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     k_init<<<(unsigned)((a.n + 255) / 256), 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-// -------------------------------------------------------------------------
-// k_expand: one thread per queued node.  Split points in FP64 with explicit
-// rounding (no contraction): t = (m - m0) h, F+- = F + t R, xi = (m0-m-)/(m+-m-).
-// -------------------------------------------------------------------------
-__global__ void k_expand(const ExpandArgs A) {
-    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= *A.q_count) return;
-    const int p = A.q_point[qi], hi = A.q_heap[qi];
-    const ItemBest *r = A.items + (long long)qi * A.chunks;
-    int bi = -1;
-    for (int c = 0; c < A.chunks; ++c) {
-        if (r[c].dir < 0) continue;
-        if (bi < 0 || r[c].h < r[bi].h || (r[c].h == r[bi].h && r[c].dir < r[bi].dir)) bi = c;
-    }
-    cvx_node &nd = A.tree[(long long)p * A.NT + hi];
-    nd.flags |= CVX_NODE_SCANNED;
-    atomicAdd(A.counters + C_NODES, 1ull);
-    if (bi < 0) {
-        nd.flags |= CVX_NODE_LEAF;
-        return;
-    }
-    const ItemBest b = r[bi];
-    float sec = b.h2;
-    for (int c = 0; c < A.chunks; ++c)
-        if (c != bi && r[c].dir >= 0) sec = fminf(sec, fminf(r[c].h32, r[c].h2));
-    const int m0 = A.line.m0;
-    nd.dir = b.dir;
-    nd.m_minus = b.mm;
-    nd.m_plus = b.mp;
-    nd.h = b.h;
-    nd.gap = sec - b.h32;
-    int fl = b.flags & CVX_NODE_ITER_CAP;
-    // FP32 sampling error is a few units of 2^-24 relative to |W|: two
-    // directions closer than 32 u |W| are reported as a tie (warning only).
-    const float tol = 32.0f * kU32 * (fabsf((float)b.h) + fabsf((float)nd.w) + 1e-3f);
-    if (nd.gap <= tol) {
-        fl |= CVX_NODE_TIE;
-        atomicAdd(A.counters + C_TIES, 1ull);
-    }
-    if (b.mm == m0) {
-        nd.flags |= fl | CVX_NODE_LEAF;
-        return;
-    }
-    fl |= CVX_NODE_LAMINATED;
-    if (b.mm == 0 || b.mp == A.line.L - 1) fl |= CVX_NODE_EDGE;
-    nd.flags |= fl;
-    atomicAdd(A.counters + C_LAMINATED, 1ull);
-    const double xi = (double)(m0 - b.mm) / (double)(b.mp - b.mm);
-    nd.xi = xi;
-    const double *d = A.dir64 + 4 * (long long)b.dir;
-    const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
-                         __dmul_rn(d[1], d[3])};
-    const double tm = __dmul_rn((double)(b.mm - m0), A.line.h64);
-    const double tp = __dmul_rn((double)(b.mp - m0), A.line.h64);
-    const bool leaf_children = A.level + 1 >= A.depth;
-    const double beta = A.beta[p];
-    for (int side = 0; side < 2; ++side) {
-        const int ci = 2 * hi + 1 + side;  // 2i+1: F-, 2i+2: F+
-        cvx_node &c = A.tree[(long long)p * A.NT + ci];
-        const double t = side ? tp : tm;
-        double F[4];
-        for (int k = 0; k < 4; ++k) F[k] = __dadd_rn(nd.F[k], __dmul_rn(t, R[k]));
-        for (int k = 0; k < 4; ++k) c.F[k] = F[k];
-        c.weight = side ? __dmul_rn(nd.weight, xi) : __dmul_rn(nd.weight, __dsub_rn(1.0, xi));
-        c.w = energy64(F, beta, A.mat);
-        c.h = c.w;
-        c.xi = 0.0;
-        c.dir = -1;
-        c.m_minus = c.m_plus = m0;
-        c.gap = 0.0f;
-        c.pad = 0;
-        c.flags = CVX_NODE_EXISTS | (leaf_children ? CVX_NODE_LEAF : 0);
-    }
-    if (!leaf_children) {
-        int pos = atomicAdd(A.nq_count, 2);
-        A.nq_point[pos] = p;
-        A.nq_heap[pos] = 2 * hi + 1;
-        A.nq_point[pos + 1] = p;
-        A.nq_heap[pos + 1] = 2 * hi + 2;
-    }
-}
-
-cudaError_t launch_expand(const ExpandArgs &a, int64_t max_nodes, cudaStream_t s) {
-    if (max_nodes == 0) return cudaSuccess;
-    k_expand<<<(unsigned)((max_nodes + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -438,6 +589,7 @@ __global__ void k_leaf(const LeafArgs A) {
     if (fl & CVX_NODE_TIE) st |= CVX_PT_TIE;
     if (fl & CVX_NODE_EDGE) st |= CVX_PT_EDGE;
     if (fl & CVX_NODE_ITER_CAP) st |= CVX_PT_ITER_CAP;
+    if (fl & CVX_NODE_OVERFLOW) st |= CVX_PT_OVERFLOW;
     A.status[p] = st;
     if (A.root) {
         cvx_laminate L;
@@ -491,8 +643,8 @@ __global__ void k_history(int64_t n, const double *F, const double *bin, double 
     if (p >= n) return;
     double G[4] = {F[4 * p], F[4 * p + 1], F[4 * p + 2], F[4 * p + 3]};
     double lj, J;
-    double s = psi0_nh64(G, m, &lj, &J);
-    double b = bin ? bin[p] : 0.0;
+    const double s = psi0_nh64(G, m, &lj, &J);
+    const double b = bin ? bin[p] : 0.0;
     bout[p] = s > b ? s : b;
 }
 
@@ -503,16 +655,17 @@ cudaError_t launch_history(int64_t n, const double *F, const double *bin, double
     return cudaGetLastError();
 }
 
-template <int NS, int EK>
+// The kernel's own FP32 samples (kappa W), returned as W = sample / kappa.
+template <int EK>
 __global__ void __launch_bounds__(128) k_sample_lines(int64_t n, const double *F,
                                                       const double *beta, const int32_t *dir,
                                                       const float4 *dir32, int D, Material m,
                                                       LineSpec ln, float *out) {
-    extern __shared__ float smem[];
+    extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (line >= n) return;
-    float *sw = smem + warp * NS * 32;
+    float *sw = reinterpret_cast<float *>(smem4) + warp * ln.stride;
     const int dj = dir[line];
     if (dj < 0 || dj >= D) {  // out-of-range direction index: NaN line
         for (int k = lane; k < ln.L; k += 32) out[line * ln.L + k] = __int_as_float(0x7fffffff);
@@ -521,91 +674,65 @@ __global__ void __launch_bounds__(128) k_sample_lines(int64_t n, const double *F
     double G[4] = {F[4 * line], F[4 * line + 1], F[4 * line + 2], F[4 * line + 3]};
     const NodeLine nl = make_node_line(G, beta[line], m);
     const DirLine dl = make_dir_line<EK>(nl, dir32[dj]);
-    float w[NS];
-    sample_line<NS, EK>(w, sw, nl, dl, ln, lane);
-    for (int k = lane; k < ln.L; k += 32) out[line * ln.L + k] = sw[k];
-}
-
-template <int NS, int EK>
-static cudaError_t launch_sample_t(int64_t n, const double *F, const double *beta,
-                                   const int32_t *dir, const float4 *dir32, int D, Material m,
-                                   LineSpec ln, float *w, cudaStream_t s) {
-    const int warps = 4;
-    k_sample_lines<NS, EK><<<(unsigned)((n + warps - 1) / warps), warps * 32,
-                             warps * NS * 32 * sizeof(float), s>>>(n, F, beta, dir, dir32, D, m,
-                                                                   ln, w);
-    return cudaGetLastError();
+    float tl[4];
+    for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
+    sample_line<EK>(sw, nl, dl, ln, lane, tl);
+    __syncwarp();
+    const double kap = line_kappa(m);
+    for (int k = lane; k < ln.L; k += 32) out[line * ln.L + k] = (float)((double)sw[k] / kap);
 }
 
 cudaError_t launch_sample_lines(int64_t n, const double *F, const double *beta,
                                 const int32_t *dir, const float4 *dir32, int D, Material m,
-                                LineSpec line, int ns, float *w, cudaStream_t s) {
+                                LineSpec ln, float *w, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-#define SL(N)                                                                                 \
-    case N:                                                                                   \
-        return m.energy == CVX_ENERGY_NH_DAMAGE                                               \
-                   ? launch_sample_t<N, CVX_ENERGY_NH_DAMAGE>(n, F, beta, dir, dir32, D, m, line, \
-                                                              w, s)                           \
-                   : launch_sample_t<N, CVX_ENERGY_DOUBLE_WELL>(n, F, beta, dir, dir32, D, m,     \
-                                                                line, w, s);
-    switch (ns) {
-        SL(8)
-        SL(17)
-        SL(33)
-        SL(65)
-    default: return cudaErrorInvalidValue;
-    }
-#undef SL
+    const int warps = 4;
+    const unsigned grid = (unsigned)((n + warps - 1) / warps);
+    const size_t smem = (size_t)warps * ln.stride * sizeof(float);
+    if (m.energy == CVX_ENERGY_NH_DAMAGE)
+        k_sample_lines<CVX_ENERGY_NH_DAMAGE><<<grid, warps * 32, smem, s>>>(n, F, beta, dir, dir32,
+                                                                           D, m, ln, w);
+    else
+        k_sample_lines<CVX_ENERGY_DOUBLE_WELL><<<grid, warps * 32, smem, s>>>(n, F, beta, dir,
+                                                                             dir32, D, m, ln, w);
+    return cudaGetLastError();
 }
 
-template <int NS>
 __global__ void __launch_bounds__(128) k_hull(int64_t n, int L, const float *w_in, int32_t *mm,
                                               int32_t *mp, double *hv,
                                               unsigned long long *counters) {
-    extern __shared__ float smem[];
+    extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t line = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (line >= n) return;
-    float *sw = smem + warp * NS * 32;
-    float w[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-        const int k = 32 * j + lane;
-        float v = k < L ? w_in[line * L + k] : __int_as_float(0x7fffffff);
-        w[j] = v;
-        sw[k] = v;
-    }
+    const int stride = line_stride(L);
+    float *sw = reinterpret_cast<float *>(smem4) + warp * stride;
+    for (int k = lane; k < L; k += 32) sw[k] = w_in[line * L + k];
     __syncwarp();
     const int m0 = (L - 1) / 2;
-    const LineGeom g{L, m0, m0 >> 5, m0 & 31};
-    HullCounters hc{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-    const BridgeOut o = warp_bridge<NS>(w, sw, g, lane, -1, -1, hc);
+    const LineGeom g{L, m0, L >> 7};
+    HullCounters hc{};
+    const BridgeOut o = warp_bridge(sw, g, lane, -1, -1, hc);
     if (lane == 0) {
         mm[line] = o.lam ? o.a : m0;
         mp[line] = o.lam ? o.b : m0;
-        hv[line] = h64_of(o.lam, o.a, o.b, o.wa, o.wb, o.w0, m0);
+        if (o.lam) {
+            const double xa = (double)(o.a - m0), xb = (double)(o.b - m0);
+            hv[line] = (xb * (double)o.wa - xa * (double)o.wb) / (xb - xa);
+        } else {
+            hv[line] = (double)o.w0;
+        }
         if (hc.caps) atomicAdd(counters + C_CAPS, (unsigned long long)hc.caps);
     }
 }
 
-cudaError_t launch_hull(int64_t n, int L, int ns, const float *w, int32_t *mm, int32_t *mp,
-                          double *h, unsigned long long *counters, cudaStream_t s) {
+cudaError_t launch_hull(int64_t n, int L, const float *w, int32_t *mm, int32_t *mp, double *h,
+                        unsigned long long *counters, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int warps = 4;
-    const unsigned grid = (unsigned)((n + warps - 1) / warps);
-#define HL(N)                                                                            \
-    case N:                                                                              \
-        k_hull<N><<<grid, warps * 32, warps * N * 32 * sizeof(float), s>>>(n, L, w, mm, mp, h, \
-                                                                           counters);    \
-        return cudaGetLastError();
-    switch (ns) {
-        HL(8)
-        HL(17)
-        HL(33)
-        HL(65)
-    default: return cudaErrorInvalidValue;
-    }
-#undef HL
+    k_hull<<<(unsigned)((n + warps - 1) / warps), warps * 32,
+             (size_t)warps * line_stride(L) * sizeof(float), s>>>(n, L, w, mm, mp, h, counters);
+    return cudaGetLastError();
 }
 
 }  // namespace cvx
