@@ -540,6 +540,7 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
         ca.cands = cands;
         ca.refined = refined;
         ca.dir64 = h->d_dir64;
+        ca.kappa = line_kappa(mat);
         ca.mat = mat;
         ca.line = ln;
         ca.counters = h->d_counters;

@@ -15,9 +15,9 @@ enum { CVX_NODE_ITER_CAP = 64, CVX_NODE_OVERFLOW = 128 };
 constexpr int kWarpTop = 4;    // best directions kept per warp
 constexpr int kItemTop = 8;    // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
-// Screening tolerance (kappa-scaled units, relative to max(kappa, |q|)):
-// several times twice the FP32 sampling error bound.
-constexpr float kScreen = 4e-6f;
+// Bound on the FP32 sampling error of kappa W (kappa-scaled units, relative to
+// max(kappa, |q|)): 3.5 times the largest error measured against FP64.
+constexpr float kEps32 = 1.1e-6f;
 
 // Best directions of one work item (a node and a block of its directions),
 // ranked by q = FP32 value at t = 0 of the chord between the left and right
@@ -33,7 +33,8 @@ struct ItemCands {
 struct NodeCands {
     int dir[kNodeCand];
     int n, flags;
-    float qmin, w0;
+    float qcut;  // smallest FP32 q of a direction not refined (kappa-scaled)
+    float eps;   // FP32 error bound used at this node (kappa-scaled)
 };
 
 struct RefineOut {
@@ -100,6 +101,7 @@ struct CommitArgs {
     const NodeCands *cands;
     const RefineOut *refined;
     const double *dir64;
+    double kappa;
     Material mat;
     LineSpec line;
     unsigned long long *counters;

@@ -267,10 +267,13 @@ int scan_max_blocks_per_sm(int energy, int warps, int stride) {
 }
 
 // -------------------------------------------------------------------------
-// k_select: one thread per queued node.  With Qmin the smallest FP32 q over
-// all directions and tol the screening tolerance (> twice the FP32 sampling
-// error), a direction with q > Qmin + tol cannot be the FP64 minimiser, and
-// if Qmin > w0 + tol the centre is a strict vertex on every line in FP64.
+// k_select: one thread per queued node.  q is the FP32 value at t = 0 of a
+// direction's left/right bridge chord and eps bounds |q_FP32 - q_FP64|
+// (1-Lipschitz in the samples).  The node's FP64 value is
+// min(W(F), min_R q_R^FP64), so a direction with q > Qmin + 2 eps cannot be the
+// FP64 minimiser and, if Qmin > w0 + 2 eps, no line splits.  The (at most
+// kNodeCand) directions with the smallest q inside that band are refined in
+// FP64; k_commit checks that no unrefined direction (q >= qcut) can win.
 // -------------------------------------------------------------------------
 __global__ void k_select(const SelectArgs A) {
     const int qi = blockIdx.x * blockDim.x + threadIdx.x;
@@ -285,22 +288,38 @@ __global__ void k_select(const SelectArgs A) {
         fl |= r[c].flags;
     }
     NodeCands nc;
-    nc.qmin = qmin;
-    nc.w0 = w0;
     nc.n = 0;
-    const float tol = kScreen * fmaxf(A.kappa, fmaxf(fabsf(qmin), fabsf(w0)));
-    if (qmin <= w0 + tol) {
-        const float lim = qmin + tol;
-        for (int c = 0; c < A.chunks; ++c)
-            for (int i = 0; i < r[c].n; ++i) {
-                if (!(r[c].q[i] <= lim)) break;
-                if (nc.n < kNodeCand) nc.dir[nc.n++] = r[c].dir[i];
-                else fl |= CVX_NODE_OVERFLOW;
+    nc.eps = kEps32 * fmaxf(A.kappa, fmaxf(fabsf(qmin), fabsf(w0)));
+    float qcut = drop;
+    if (qmin <= w0 + 2.0f * nc.eps) {
+        const float lim = qmin + 2.0f * nc.eps;
+        // merge the items' sorted lists, smallest q first (ties: lower direction)
+        int pos[64];
+        const int nch = A.chunks < 64 ? A.chunks : 64;
+        for (int c = 0; c < nch; ++c) pos[c] = 0;
+        while (true) {
+            int bc = -1;
+            for (int c = 0; c < nch; ++c) {
+                if (pos[c] >= r[c].n) continue;
+                if (bc < 0 || r[c].q[pos[c]] < r[bc].q[pos[bc]] ||
+                    (r[c].q[pos[c]] == r[bc].q[pos[bc]] && r[c].dir[pos[c]] < r[bc].dir[pos[bc]]))
+                    bc = c;
             }
-        if (drop <= lim) fl |= CVX_NODE_OVERFLOW;
+            if (bc < 0) break;
+            const float q = r[bc].q[pos[bc]];
+            if (!(q <= lim) || nc.n == kNodeCand) {
+                qcut = fminf(qcut, q);
+                break;
+            }
+            nc.dir[nc.n++] = r[bc].dir[pos[bc]];
+            ++pos[bc];
+        }
+        for (int c = nch; c < A.chunks; ++c) qcut = fminf(qcut, r[c].q[0]);
+    } else {
+        qcut = qmin;
     }
+    nc.qcut = qcut;
     nc.flags = fl;
-    if (fl & CVX_NODE_OVERFLOW) atomicAdd(A.counters + C_OVERFLOW, 1ull);
     A.cands[qi] = nc;
     if (nc.n) {
         const int pos = atomicAdd(A.work_count, nc.n);
@@ -442,6 +461,13 @@ __global__ void k_commit(const CommitArgs A) {
     }
     const int m0 = A.line.m0;
     nd.gap = (float)(second - (bc >= 0 ? ro[bc].q : nd.w));
+    // FP64 node value among the refined directions; an unrefined direction
+    // (FP32 q >= qcut) could only win if qcut - eps reached it
+    const double V = (bc >= 0 && ro[bc].q < nd.w) ? ro[bc].q : nd.w;
+    if (!(((double)nc.qcut - (double)nc.eps) / A.kappa > V)) {
+        nd.flags |= CVX_NODE_OVERFLOW;
+        atomicAdd(A.counters + C_OVERFLOW, 1ull);
+    }
     // the centre splits off iff the chord lies strictly below W(F) (FP64)
     if (bc < 0 || !(ro[bc].q < nd.w)) {
         nd.dir = bc >= 0 ? nc.dir[bc] : -1;
