@@ -238,6 +238,32 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
                      const double *beta_k, double *W_R, double *P, cvx_laminate *root,
                      cvx_node *tree, int32_t *status, cvx_stream s);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* convexify_points for callers that may not allocate device memory — for
+ * example a material routine plugged into a host finite-element code that
+ * owns all device memory through its own pool, or a latency-critical caller
+ * that cannot accept cudaMalloc's implicit device synchronisation.  The paper
+ * has no counterpart; this is a packaging of the same computation.
+ *
+ * Same arguments and results as convexify_points (no handle, no root/tree
+ * outputs; W_R, P, status, F, beta_k are caller-owned device pointers).  All
+ * scratch lives in one fixed 64 MiB device array of the library (every GPU
+ * that loads the library holds it until the process exits); nothing in this
+ * call allocates device memory.  Limits: at most 16384 directions, and a
+ * problem whose scratch (tree, queues, candidate records; roughly
+ * n * (88 (2^{K+1} - 1) + 600 * 2^{K-1}) bytes plus 48 bytes per direction)
+ * fits in 64 MiB; larger problems are rejected with CVX_ERR_INVALID_ARG.
+ * Runs on the calling thread's current device.  The first call on a device
+ * looks up the array's device address there (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Every call shares the array and
+ * leaves its contents behind (each call clears what must start at zero), so
+ * calls that overlap on the GPU — on different streams, or from different
+ * host threads — race and must be serialised by the caller. */
+int convexify_points_static(const cvx_params *p, int64_t n, const double *F,
+                            const double *beta_k, double *W_R, double *P, int32_t *status,
+                            cvx_stream s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
         "cvx_sample_lines": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp],
         "cvx_hull_bridge": [vp, i64, i32, vp, vp, vp, vp, vp],
         "convexify_points": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp, vp, vp],
+        "convexify_points_static": [ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -97,7 +98,7 @@ def exported_symbols() -> Sequence[str]:
     return ("cvx_create", "cvx_destroy", "cvx_last_error", "cvx_get_stats", "cvx_struct_size",
             "cvx_set_tuning", "cvx_set_profiling", "cvx_get_scan_timing",
             "cvx_energy", "cvx_history_update", "cvx_sample_lines", "cvx_hull_bridge",
-            "convexify_points")
+            "convexify_points", "convexify_points_static")
 
 
 def _check(rc: int, what: str):
@@ -299,3 +300,22 @@ def tree_numpy(tree_bytes, n: int, tree_size: int) -> np.ndarray:
 
 def root_numpy(root_bytes, n: int) -> np.ndarray:
     return root_bytes.cpu().numpy().view(LAMINATE_DTYPE).reshape(n)
+
+
+def convexify_points_static(p: Params, F, beta, stream=None):
+    """The allocation-free entry point (fixed library scratch, no handle): W^R,
+    P and status for points already on the current CUDA device."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F = torch.as_tensor(F, dtype=torch.float64).to(dev).reshape(-1, 4).contiguous()
+    n = F.shape[0]
+    beta = torch.as_tensor(beta, dtype=torch.float64).to(dev).reshape(n).contiguous()
+    W_R = torch.empty(n, dtype=torch.float64, device=dev)
+    P = torch.empty(n, 4, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    c = p.c()
+    _check(lib().convexify_points_static(ctypes.byref(c), n, _ptr(F), _ptr(beta), _ptr(W_R),
+                                         _ptr(P), _ptr(st), _stream(stream)),
+           "convexify_points_static")
+    return dict(W_R=W_R, P=P, status=st)

@@ -198,6 +198,11 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+namespace cvx {
+// Records the calling thread's last error for entry points in other files.
+int set_error_message(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace cvx
+
 extern "C" {
 
 int cvx_last_error(char *buf, size_t len) {

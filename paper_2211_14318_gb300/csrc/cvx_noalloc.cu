@@ -1,0 +1,305 @@
+// cvx_noalloc.cu -- convexify_points_static: the same per-point
+// convexification as convexify_points, for callers that are not allowed to
+// allocate device memory.
+//
+// Typical callers: a material routine plugged into a host finite-element code
+// that owns all device memory through its own pool and forbids the plugin to
+// call cudaMalloc, or a latency-critical caller for which cudaMalloc's implicit
+// device synchronisation is not acceptable.  They pass inputs and outputs; all
+// scratch (direction tables, tree, node queues, candidate records, counters)
+// lives in one file-scope device array of fixed size.  Nothing here calls
+// cudaMalloc, cudaFree or any other allocating routine.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "convexify.h"
+#include "cvx_internal.h"
+
+namespace cvx {
+int set_error_message(int code, const char *msg);  // cvx_api.cu
+}
+
+using namespace cvx;
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB per device
+constexpr int kStaticMaxDirs = 16384;
+constexpr int kMaxDevices = 64;
+
+// The scratch.  In host code this name is only a stand-in: its device address
+// is obtained with cudaGetSymbolAddress once per device (see setup()).
+static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
+
+std::mutex g_mu;
+void *g_addr[kMaxDevices];
+int g_sms[kMaxDevices];
+// host staging of the direction tables (static: no host heap either)
+float4 g_dir32[kStaticMaxDirs];
+double g_dir64[4 * kStaticMaxDirs];
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int err(int code, const char *msg) { return set_error_message(code, msg); }
+
+// Device address of the scratch on the current device (looked up once per
+// device, with that device current).
+int setup(int dev, void **addr, int *sms) {
+    if (dev < 0 || dev >= kMaxDevices) return err(CVX_ERR_UNSUPPORTED, "device index too large");
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return err(CVX_ERR_CUDA, "convexify_points_static: cudaGetSymbolAddress failed");
+        }
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return err(CVX_ERR_CUDA, "convexify_points_static: device query failed");
+        g_addr[dev] = p;
+        g_sms[dev] = n;
+    }
+    *addr = g_addr[dev];
+    *sms = g_sms[dev];
+    return CVX_OK;
+}
+
+}  // namespace
+
+extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const double *F,
+                                       const double *beta_k, double *W_R, double *P,
+                                       int32_t *status, cvx_stream sv) {
+    if (!p) return err(CVX_ERR_INVALID_ARG, "params is NULL");
+    if (p->energy != CVX_ENERGY_NH_DAMAGE && p->energy != CVX_ENERGY_DOUBLE_WELL)
+        return err(CVX_ERR_INVALID_ARG, "unknown energy kind");
+    if (p->energy == CVX_ENERGY_NH_DAMAGE &&
+        (!(p->mu > 0.0) || !(p->lambda_L >= 0.0) || !(p->D_inf >= 0.0 && p->D_inf < 1.0) ||
+         !(p->D0 > 0.0)))
+        return err(CVX_ERR_INVALID_ARG, "material out of range");
+    if (p->flags != 0) return err(CVX_ERR_INVALID_ARG, "flags must be 0");
+    if (p->line_points < 3 || p->line_points > 2079 || (p->line_points % 2) == 0)
+        return err(CVX_ERR_INVALID_ARG, "line_points must be odd in [3, 2079]");
+    if (!(p->t_half > 0.0) || !isfinite(p->t_half)) return err(CVX_ERR_INVALID_ARG, "t_half must be positive");
+    if (p->depth < 0 || p->depth > 8) return err(CVX_ERR_INVALID_ARG, "depth must be in [0, 8]");
+    const int D = p->dirs ? p->n_dirs : p->n_theta_a * p->n_theta_b;
+    if ((p->dirs && p->n_dirs < 1) || (!p->dirs && (p->n_theta_a < 1 || p->n_theta_b < 1)))
+        return err(CVX_ERR_INVALID_ARG, "empty direction set");
+    if (D > kStaticMaxDirs)
+        return err(CVX_ERR_INVALID_ARG,
+                   "convexify_points_static: more than 16384 directions (use convexify_points)");
+    if (n < 0) return err(CVX_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!F || !beta_k || !W_R || !P || !status))
+        return err(CVX_ERR_INVALID_ARG, "NULL array (F, beta_k, W_R, P, status are required)");
+    if (n == 0) return CVX_OK;
+
+    const LineSpec ln = [&] {
+        LineSpec l;
+        l.L = p->line_points;
+        l.m0 = (l.L - 1) / 2;
+        l.h64 = 2.0 * p->t_half / (double)(l.L - 1);
+        l.h32 = (float)l.h64;
+        l.nfull = l.L >> 7;
+        l.stride = line_stride(l.L);
+        return l;
+    }();
+    const int K = p->depth;
+    const int NT = (1 << (K + 1)) - 1;
+    const int warps = 8;
+    Material mat;
+    mat.mu = p->mu;
+    mat.lam = p->lambda_L;
+    mat.Dinf = p->D_inf;
+    mat.D0 = p->D0;
+    mat.energy = p->energy;
+
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return err(CVX_ERR_CUDA, "no current device");
+    void *base = nullptr;
+    int sms = 0;
+    int rc = setup(dev, &base, &sms);
+    if (rc) return rc;
+    const int bpsm = scan_max_blocks_per_sm(p->energy, warps, ln.stride);
+    if (bpsm < 1) return err(CVX_ERR_UNSUPPORTED, "scan kernel cannot launch");
+    const int grid = sms * bpsm;
+    int dpi = D;
+    const int64_t want_items = (int64_t)grid * 4;
+    if (n < want_items) {
+        const int64_t chunks = (want_items + n - 1) / n;
+        const int64_t d = (D + chunks - 1) / chunks;
+        dpi = (int)(d > warps * 2 ? d : warps * 2);
+    }
+    if (dpi > D) dpi = D;
+    const int chunks = (D + dpi - 1) / dpi;
+
+    // scratch layout
+    const size_t maxq = K > 0 ? ((size_t)n << (K - 1)) : 0;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = up256(off + bytes);
+        return o;
+    };
+    const size_t o_ctr = take(sizeof(unsigned long long) * C_NUM);
+    const size_t o_d32 = take(sizeof(float4) * D);
+    const size_t o_d64 = take(sizeof(double) * 4 * D);
+    const size_t o_tree = take(sizeof(cvx_node) * (size_t)n * NT);
+    size_t o_qp[9], o_qh[9];
+    for (int l = 0; l < K; ++l) {
+        o_qp[l] = take(sizeof(int32_t) * ((size_t)n << l));
+        o_qh[l] = take(sizeof(int32_t) * ((size_t)n << l));
+    }
+    const size_t o_cnt = take(sizeof(int32_t) * 2 * (K + 1));
+    const size_t o_items = take(sizeof(ItemCands) * maxq * chunks);
+    const size_t o_cands = take(sizeof(NodeCands) * maxq);
+    const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
+    const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
+    if (off > kStaticScratchBytes)
+        return err(CVX_ERR_INVALID_ARG,
+                   "convexify_points_static: problem needs more than the 64 MiB static scratch "
+                   "(fewer points per call, or convexify_points)");
+    char *ws = (char *)base;
+    cudaStream_t s = (cudaStream_t)sv;
+
+    // direction tables (staged in static host arrays, copied while the lock is held)
+    if (p->dirs) {
+        memcpy(g_dir64, p->dirs, sizeof(double) * 4 * (size_t)D);
+    } else {
+        for (int i = 0; i < p->n_theta_a; ++i) {
+            const double ta = M_PI * (double)i / (double)p->n_theta_a;
+            for (int j = 0; j < p->n_theta_b; ++j) {
+                const double tb = M_PI * (double)j / (double)p->n_theta_b;
+                double *r = g_dir64 + 4 * ((size_t)i * p->n_theta_b + j);
+                r[0] = cos(ta);
+                r[1] = sin(ta);
+                r[2] = cos(tb);
+                r[3] = sin(tb);
+            }
+        }
+    }
+    for (int k = 0; k < D; ++k)
+        g_dir32[k] = make_float4((float)g_dir64[4 * k], (float)g_dir64[4 * k + 1],
+                                 (float)g_dir64[4 * k + 2], (float)g_dir64[4 * k + 3]);
+    // pageable source: cudaMemcpyAsync returns once the data is staged
+    if (cudaMemcpyAsync(ws + o_d32, g_dir32, sizeof(float4) * D, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(ws + o_d64, g_dir64, sizeof(double) * 4 * D, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+        return err(CVX_ERR_CUDA, "convexify_points_static: direction table copy failed");
+
+    // everything that must start at zero: counters, tree flags, queue counts
+    unsigned long long *ctr = (unsigned long long *)(ws + o_ctr);
+    cvx_node *tr = (cvx_node *)(ws + o_tree);
+    int32_t *cnt = (int32_t *)(ws + o_cnt);
+    int32_t *wcnt = cnt + (K + 1);
+    if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_NUM, s) != cudaSuccess ||
+        cudaMemsetAsync(tr, 0, sizeof(cvx_node) * (size_t)n * NT, s) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 2 * (K + 1), s) != cudaSuccess)
+        return err(CVX_ERR_CUDA, "convexify_points_static: scratch clear failed");
+
+    InitArgs ia;
+    ia.n = n;
+    ia.F = F;
+    ia.beta = beta_k;
+    ia.tree = tr;
+    ia.NT = NT;
+    ia.depth = K;
+    ia.q_point = K ? (int32_t *)(ws + o_qp[0]) : nullptr;
+    ia.q_heap = K ? (int32_t *)(ws + o_qh[0]) : nullptr;
+    ia.q_count = cnt;
+    ia.status = status;
+    ia.mat = mat;
+    ia.m0 = ln.m0;
+    ia.counters = ctr;
+    if (launch_init(ia, s) != cudaSuccess) return err(CVX_ERR_CUDA, "convexify_points_static: init");
+
+    const float4 *d32 = (const float4 *)(ws + o_d32);
+    const double *d64 = (const double *)(ws + o_d64);
+    ItemCands *items = (ItemCands *)(ws + o_items);
+    NodeCands *cands = (NodeCands *)(ws + o_cands);
+    int2 *work = (int2 *)(ws + o_work);
+    RefineOut *refined = (RefineOut *)(ws + o_ref);
+    for (int l = 0; l < K; ++l) {
+        const int64_t max_nodes = (int64_t)n << l;
+        int32_t *qp = (int32_t *)(ws + o_qp[l]), *qh = (int32_t *)(ws + o_qh[l]);
+        ScanArgs sa;
+        sa.tree = tr;
+        sa.NT = NT;
+        sa.beta = beta_k;
+        sa.q_point = qp;
+        sa.q_heap = qh;
+        sa.q_count = cnt + l;
+        sa.dir32 = d32;
+        sa.D = D;
+        sa.chunks = chunks;
+        sa.dirs_per_item = dpi;
+        sa.mat = mat;
+        sa.line = ln;
+        sa.out = items;
+        sa.counters = ctr;
+        if (launch_scan(sa, warps, grid, s) != cudaSuccess)
+            return err(CVX_ERR_CUDA, "convexify_points_static: scan");
+        SelectArgs se;
+        se.q_count = cnt + l;
+        se.items = items;
+        se.chunks = chunks;
+        se.kappa = (float)line_kappa(mat);
+        se.cands = cands;
+        se.work = work;
+        se.work_count = wcnt + l;
+        se.counters = ctr;
+        if (launch_select(se, max_nodes, s) != cudaSuccess)
+            return err(CVX_ERR_CUDA, "convexify_points_static: select");
+        RefineArgs ra;
+        ra.tree = tr;
+        ra.NT = NT;
+        ra.beta = beta_k;
+        ra.q_point = qp;
+        ra.q_heap = qh;
+        ra.cands = cands;
+        ra.work = work;
+        ra.work_count = wcnt + l;
+        ra.dir64 = d64;
+        ra.mat = mat;
+        ra.line = ln;
+        ra.out = refined;
+        if (launch_refine(ra, max_nodes * kNodeCand, s) != cudaSuccess)
+            return err(CVX_ERR_CUDA, "convexify_points_static: refine");
+        CommitArgs ca;
+        ca.tree = tr;
+        ca.NT = NT;
+        ca.level = l;
+        ca.depth = K;
+        ca.beta = beta_k;
+        ca.q_point = qp;
+        ca.q_heap = qh;
+        ca.q_count = cnt + l;
+        ca.nq_point = l + 1 < K ? (int32_t *)(ws + o_qp[l + 1]) : nullptr;
+        ca.nq_heap = l + 1 < K ? (int32_t *)(ws + o_qh[l + 1]) : nullptr;
+        ca.nq_count = cnt + l + 1;
+        ca.cands = cands;
+        ca.refined = refined;
+        ca.dir64 = d64;
+        ca.kappa = line_kappa(mat);
+        ca.mat = mat;
+        ca.line = ln;
+        ca.counters = ctr;
+        if (launch_commit(ca, max_nodes, s) != cudaSuccess)
+            return err(CVX_ERR_CUDA, "convexify_points_static: commit");
+    }
+    LeafArgs la;
+    la.n = n;
+    la.tree = tr;
+    la.NT = NT;
+    la.beta = beta_k;
+    la.W_R = W_R;
+    la.P = P;
+    la.status = status;
+    la.root = nullptr;
+    la.mat = mat;
+    if (launch_leaf(la, s) != cudaSuccess) return err(CVX_ERR_CUDA, "convexify_points_static: leaf");
+    return CVX_OK;
+}
