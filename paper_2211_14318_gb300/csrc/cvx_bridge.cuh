@@ -44,10 +44,10 @@ struct LineGeom {
     int L, m0, nfull;  // samples, centre index, number of full 128-sample chunks
 };
 
+// Per-warp event counters in shared memory, written by lane 0 only.
+enum { HC_FP64W, HC_FP64R, HC_FP64C, HC_FULL, HC_RARE, HC_CAPS, HC_WSTEPS, HC_ROUNDS, HC_N };
 struct HullCounters {
-    unsigned fp64w, fp64r, fp64c;          // FP64 fallbacks: windows (per lane), rare (per lane), centre
-    unsigned full_passes, rare, caps;      // lane 0
-    unsigned wsteps, rounds;               // lane 0
+    unsigned *c;
 };
 
 struct BridgeOut {
@@ -133,7 +133,8 @@ __device__ __forceinline__ int win_lo_b(int b, int m0, int L) {
 // below the chord, or a collinear sample farther out).
 __device__ __noinline__ int rare_path(const float *sw, const LineGeom g, int lane, int &a, int &b,
                                       float wa, float wb, float s, float ns, float T, int loA,
-                                      int loB, unsigned &fp64) {
+                                      int loB, unsigned &fp64_total) {
+    unsigned fp64 = 0;
     int bestKeyL = 0x7fffffff, bestKL = -1, bestKeyR = 0x7fffffff, bestKR = -1;
     int outL = 0x7fffffff, outR = -1;
     for (int k0 = 0; k0 < g.L; k0 += 32) {
@@ -154,6 +155,7 @@ __device__ __noinline__ int rare_path(const float *sw, const LineGeom g, int lan
             if (sd == 0 && k > b && k > outR) outR = k;
         }
     }
+    fp64_total = __reduce_add_sync(kFull, fp64);
     int mL = __reduce_min_sync(kFull, bestKeyL), mR = __reduce_min_sync(kFull, bestKeyR);
     unsigned bl = __ballot_sync(kFull, bestKL >= 0 && bestKeyL == mL);
     unsigned br = __ballot_sync(kFull, bestKR >= 0 && bestKeyR == mR);
@@ -171,7 +173,7 @@ __device__ __noinline__ int rare_path(const float *sw, const LineGeom g, int lan
     return 0;
 }
 
-__device__ __forceinline__ BridgeOut warp_bridge(const float *sw, const LineGeom g, int lane,
+__device__ __forceinline__ BridgeOut warp_bridge(float *sw, const LineGeom g, int lane,
                                                  int warm_a, int warm_b, HullCounters &hc) {
     BridgeOut out;
     const int m0 = g.m0, L = g.L;
@@ -188,7 +190,7 @@ __device__ __forceinline__ BridgeOut warp_bridge(const float *sw, const LineGeom
         b = warm_b;
     } else {
         full_argmin(sw, g, lane, 0.0f, a, b);
-        if (lane == 0) ++hc.full_passes;
+        if (lane == 0) ++hc.c[HC_FULL];
         if (a < 0 || b < 0) return out;
     }
 
@@ -196,8 +198,9 @@ __device__ __forceinline__ BridgeOut warp_bridge(const float *sw, const LineGeom
     bool done = false;
     int round = 0;
     float wa = sw[a], wb = sw[b];
+    float s_fin = 0.0f;
     for (; round < kHullCap && !done; ++round) {
-        if (lane == 0) ++hc.rounds;
+        if (lane == 0) ++hc.c[HC_ROUNDS];
         int loA = win_lo_a(a, m0), loB = win_lo_b(b, m0, L);
         int kA = loA + lane, kB = loB + lane;
         float vA = kA < m0 ? nan_to_inf(sw[kA]) : INFINITY;
@@ -214,7 +217,7 @@ __device__ __forceinline__ BridgeOut warp_bridge(const float *sw, const LineGeom
                 const unsigned bB = __ballot_sync(kFull, keyB == mB);
                 const int na = ((bA >> (a - loA)) & 1u) ? a : loA + __ffs(bA) - 1;
                 const int nb = ((bB >> (b - loB)) & 1u) ? b : loB + __ffs(bB) - 1;
-                if (lane == 0) ++hc.wsteps;
+                if (lane == 0) ++hc.c[HC_WSTEPS];
                 if (na == a && nb == b) break;
                 wa = __shfl_sync(kFull, vA, na - loA);
                 wb = __shfl_sync(kFull, vB, nb - loB);
@@ -251,8 +254,13 @@ __device__ __forceinline__ BridgeOut warp_bridge(const float *sw, const LineGeom
         const float s = slope_exact(wa, a, wb, b);
 
         // ---- 3. exact check of the windows --------------------------------
-        const int sA = (inA && kA != a) ? side_exact(vA, kA, wa, a, wb, b, s, wa, a, hc.fp64w) : 1;
-        const int sB = (inB && kB != b) ? side_exact(vB, kB, wa, a, wb, b, s, wb, b, hc.fp64w) : 1;
+        unsigned uA = 0, uB = 0;
+        const int sA = (inA && kA != a) ? side_exact(vA, kA, wa, a, wb, b, s, wa, a, uA) : 1;
+        const int sB = (inB && kB != b) ? side_exact(vB, kB, wa, a, wb, b, s, wb, b, uB) : 1;
+        {
+            const unsigned n64 = __popc(__ballot_sync(kFull, uA != 0)) + __popc(__ballot_sync(kFull, uB != 0));
+            if (lane == 0) hc.c[HC_FP64W] += n64;
+        }
         const unsigned belowA = __ballot_sync(kFull, sA < 0), belowB = __ballot_sync(kFull, sB < 0);
         if (belowA | belowB) {
             // move to the violating sample with the lowest FP32 w - s x
@@ -281,48 +289,62 @@ __device__ __forceinline__ BridgeOut warp_bridge(const float *sw, const LineGeom
         }
 
         // ---- 4. certifying pass over the whole line ------------------------
+        // The window samples (checked exactly above) and the centre are
+        // masked with +inf; any other sample with w - s x < H + Delta is a
+        // candidate that needs the exact check of the rare path.
         const float ns = -s;
         const float Hp = __fmaf_rn(-s, (float)(a - m0), wa);
         const float Delta = 8.0f * kU32 * (fabsf(Hp) + 2.0f * fabsf(s) * (float)L) + 1e-30f;
         const float T = __fadd_rn(Hp, Delta);
+        if (inA) sw[kA] = INFINITY;
+        if (inB) sw[kB] = INFINITY;
+        if (lane == 0) sw[m0] = INFINITY;
+        __syncwarp();
         float Tl[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) Tl[i] = __fmaf_rn(s, (float)(4 * lane + i - m0), T);
-        int cnt = 0;
+        bool any = false;
         float fq = 0.0f;
-#pragma unroll 2
+#pragma unroll 4
         for (int q = 0; q < g.nfull; ++q, fq += 128.0f) {
             const float4 v = *reinterpret_cast<const float4 *>(sw + 128 * q + 4 * lane);
-            cnt += (__fmaf_rn(ns, fq, v.x) < Tl[0]) + (__fmaf_rn(ns, fq, v.y) < Tl[1]) +
-                   (__fmaf_rn(ns, fq, v.z) < Tl[2]) + (__fmaf_rn(ns, fq, v.w) < Tl[3]);
+            any |= __fmaf_rn(ns, fq, v.x) < Tl[0];
+            any |= __fmaf_rn(ns, fq, v.y) < Tl[1];
+            any |= __fmaf_rn(ns, fq, v.z) < Tl[2];
+            any |= __fmaf_rn(ns, fq, v.w) < Tl[3];
         }
-        for (int k = 128 * g.nfull + lane; k < L; k += 32) cnt += cand_pred(k, sw[k], ns, s, T, m0);
-        const int cw = (inA ? cand_pred(kA, vA, ns, s, T, m0) : 0) +
-                       (inB ? cand_pred(kB, vB, ns, s, T, m0) : 0) +
-                       (lane == 0 ? cand_pred(m0, out.w0, ns, s, T, m0) : 0);
-        const int C = __reduce_add_sync(kFull, cnt);
-        const int Cw = __reduce_add_sync(kFull, cw);
-        if (C == Cw) {
-            done = true;
-            break;
+        for (int k = 128 * g.nfull + lane; k < L; k += 32) any |= cand_pred(k, sw[k], ns, s, T, m0);
+        int moved = 0;
+        if (__any_sync(kFull, any)) {
+            // ---- rare path (windows and centre still masked) ----------------
+            unsigned r64 = 0;
+            moved = rare_path(sw, g, lane, a, b, wa, wb, s, ns, T, loA, loB, r64);
+            if (lane == 0) {
+                ++hc.c[HC_RARE];
+                hc.c[HC_FP64R] += r64;
+            }
         }
-        // ---- rare path ------------------------------------------------------
-        if (lane == 0) ++hc.rare;
-        if (rare_path(sw, g, lane, a, b, wa, wb, s, ns, T, loA, loB, hc.fp64r)) {
+        __syncwarp();
+        if (inA) sw[kA] = vA;  // excluded samples come back as +inf
+        if (inB) sw[kB] = vB;
+        if (lane == 0) sw[m0] = out.w0;
+        __syncwarp();
+        if (moved) {
             wa = sw[a];
             wb = sw[b];
             if (round >= 1) fp32_steps = false;
             continue;
         }
+        s_fin = s;
         done = true;  // every candidate lies exactly on or above the chord
     }
-    if (!done && lane == 0) ++hc.caps;
+    if (!done && lane == 0) ++hc.c[HC_CAPS];
 
     // ---- centre: strict vertex iff strictly below the bridge chord ---------
-    const float s = slope_exact(wa, a, wb, b);
+    const float s = done ? s_fin : slope_exact(wa, a, wb, b);
     unsigned c64 = 0;
     const int sc = side_exact(out.w0, m0, wa, a, wb, b, s, wa, a, c64);
-    if (lane == 0) hc.fp64c += c64;
+    if (lane == 0) hc.c[HC_FP64C] += c64;
     out.a = a;
     out.b = b;
     out.wa = wa;

@@ -37,7 +37,7 @@ __device__ __forceinline__ void sample_line(float *sw, const NodeLine &nl, const
                                             const LineSpec &ln, int lane, const float (&tl)[4]) {
     const float h128 = 128.0f * ln.h32;
     float fq = 0.0f;
-#pragma unroll 2
+#pragma unroll 1
     for (int q = 0; q < ln.nfull; ++q, fq += 1.0f) {
         float4 v;
         v.x = sample_w<EK>(nl, dl, __fmaf_rn(h128, fq, tl[0]));
@@ -53,7 +53,7 @@ __device__ __forceinline__ void sample_line(float *sw, const NodeLine &nl, const
 // Number of samples with J(t) > 0 on a line (the algorithmic work count).
 __device__ __forceinline__ int valid_samples(const DirLine &dl, const LineSpec &ln, int energy) {
     if (energy != CVX_ENERGY_NH_DAMAGE || dl.cJ == 0.0f) return ln.L;
-    const float xs = -dl.J0 / (dl.cJ * ln.h32);  // J = 0 at x = m - m0 = xs
+    const float xs = __fdividef(-dl.J0, dl.cJ * ln.h32);  // J = 0 at x = m - m0 = xs
     const float lim = (float)ln.L;
     if (dl.cJ > 0.0f) {  // valid for x > xs
         const float lo = fminf(fmaxf(floorf(xs) + 1.0f, -lim), lim);
@@ -94,8 +94,13 @@ __device__ __forceinline__ void top_insert(float (&q)[kWarpTop], int (&d)[kWarpT
 // scans a contiguous run of directions, warm-starting every hull search from
 // the previous direction's bridge, and keeps its best directions by q.
 // -------------------------------------------------------------------------
+// CTAs of 256 threads resident per SM that the register allocation targets
+#ifndef CVX_SCAN_MIN_BLOCKS
+#define CVX_SCAN_MIN_BLOCKS 3
+#endif
+
 template <int EK>
-__global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
+__global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const ScanArgs A) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const LineSpec ln = A.line;
@@ -106,6 +111,7 @@ __global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
     __shared__ float s_drop[16];
     __shared__ int s_fl[16];
     __shared__ float s_w0;
+    __shared__ unsigned s_hc[16][HC_N];
 
     const LineGeom g{ln.L, ln.m0, ln.nfull};
     float tl[4];
@@ -113,7 +119,10 @@ __global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
     for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
     const int n_nodes = *A.q_count;
     const long long n_items = (long long)n_nodes * A.chunks;
-    HullCounters hc{};
+    if (lane == 0)
+        for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
+    __syncwarp();
+    HullCounters hc{s_hc[warp]};
     unsigned long long n_valid = 0, n_lines = 0;
 
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -126,7 +135,15 @@ __global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
             s_nl = make_node_line(F, A.beta[p], A.mat);
         }
         __syncthreads();
-        const NodeLine nl = s_nl;
+        // the per-sample constants in registers; F and cof F stay in shared
+        // memory and are read once per direction
+        NodeLine nl;
+        nl.A0 = s_nl.A0;
+        nl.B1 = s_nl.B1;
+        nl.B2 = s_nl.B2;
+        nl.a1 = s_nl.a1;
+        nl.K1 = s_nl.K1;
+        nl.K2 = s_nl.K2;
         const int d0 = ch * A.dirs_per_item, d1 = min(A.D, d0 + A.dirs_per_item);
         const int per = (d1 - d0 + nw - 1) / nw;
         const int jb = d0 + warp * per, je = min(d1, jb + per);
@@ -142,16 +159,16 @@ __global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
         int fl = 0;
         int warm_a = -1, warm_b = -1;
         for (int dj = jb; dj < je; ++dj) {
-            const DirLine dl = make_dir_line<EK>(nl, A.dir32[dj]);
+            const DirLine dl = make_dir_line<EK>(s_nl, A.dir32[dj]);
             sample_line<EK>(sw, nl, dl, ln, lane, tl);
             __syncwarp();
-            const unsigned caps0 = hc.caps;
+            const unsigned caps0 = hc.c[HC_CAPS];
             const BridgeOut o = warp_bridge(sw, g, lane, warm_a, warm_b, hc);
             __syncwarp();
             if (lane == 0) {
                 ++n_lines;
                 n_valid += valid_samples(dl, ln, EK);
-                if (hc.caps != caps0) fl |= CVX_NODE_ITER_CAP;
+                if (hc.c[HC_CAPS] != caps0) fl |= CVX_NODE_ITER_CAP;
             }
             w0 = o.w0;
             float q = INFINITY;
@@ -213,20 +230,19 @@ __global__ void __launch_bounds__(256, 3) k_scan(const ScanArgs A) {
             A.out[item] = r;
         }
     }
-    const unsigned fp64w = __reduce_add_sync(kFull, hc.fp64w);
-    const unsigned fp64r = __reduce_add_sync(kFull, hc.fp64r);
     if (lane == 0) {
+        const unsigned *c = hc.c;
         add_counter(A.counters, C_LINES, n_lines);
         add_counter(A.counters, C_VALID, n_valid);
-        add_counter(A.counters, C_FP64, (unsigned long long)fp64w + fp64r + hc.fp64c);
-        add_counter(A.counters, C_FP64W, fp64w);
-        add_counter(A.counters, C_FP64R, fp64r);
-        add_counter(A.counters, C_FP64C, hc.fp64c);
-        add_counter(A.counters, C_FULL, hc.full_passes);
-        add_counter(A.counters, C_RARE, hc.rare);
-        add_counter(A.counters, C_CAPS, hc.caps);
-        add_counter(A.counters, C_WSTEPS, hc.wsteps);
-        add_counter(A.counters, C_ROUNDS, hc.rounds);
+        add_counter(A.counters, C_FP64, (unsigned long long)c[HC_FP64W] + c[HC_FP64R] + c[HC_FP64C]);
+        add_counter(A.counters, C_FP64W, c[HC_FP64W]);
+        add_counter(A.counters, C_FP64R, c[HC_FP64R]);
+        add_counter(A.counters, C_FP64C, c[HC_FP64C]);
+        add_counter(A.counters, C_FULL, c[HC_FULL]);
+        add_counter(A.counters, C_RARE, c[HC_RARE]);
+        add_counter(A.counters, C_CAPS, c[HC_CAPS]);
+        add_counter(A.counters, C_WSTEPS, c[HC_WSTEPS]);
+        add_counter(A.counters, C_ROUNDS, c[HC_ROUNDS]);
     }
 }
 
@@ -737,7 +753,11 @@ __global__ void __launch_bounds__(128) k_hull(int64_t n, int L, const float *w_i
     __syncwarp();
     const int m0 = (L - 1) / 2;
     const LineGeom g{L, m0, L >> 7};
-    HullCounters hc{};
+    __shared__ unsigned s_hc[4][HC_N];
+    if (lane == 0)
+        for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
+    __syncwarp();
+    HullCounters hc{s_hc[warp]};
     const BridgeOut o = warp_bridge(sw, g, lane, -1, -1, hc);
     if (lane == 0) {
         mm[line] = o.lam ? o.a : m0;
@@ -748,7 +768,7 @@ __global__ void __launch_bounds__(128) k_hull(int64_t n, int L, const float *w_i
         } else {
             hv[line] = (double)o.w0;
         }
-        if (hc.caps) atomicAdd(counters + C_CAPS, (unsigned long long)hc.caps);
+        if (hc.c[HC_CAPS]) atomicAdd(counters + C_CAPS, (unsigned long long)hc.c[HC_CAPS]);
     }
 }
 
