@@ -353,4 +353,133 @@ __device__ __forceinline__ BridgeOut warp_bridge(float *sw, const LineGeom g, in
     return out;
 }
 
+// -------------------------------------------------------------------------
+// Screening form (used by the line scan, whose decisions are taken later in
+// FP64): rigorous bounds on the value at 0 of the lower hull of the left and
+// right sets instead of the exact bridge.  For ANY slope s,
+//   hull(0) >= min_i (w_i - s x_i)                  (an affine minorant)
+// and for any pair a < 0 < b,
+//   hull(0) <= chord(a, b)(0).
+// The window iteration makes both sides meet up to rounding; the min pass
+// costs one FMA and one min per sample.
+// -------------------------------------------------------------------------
+struct ScreenOut {
+    int a, b;          // approximate bridge (for the next direction's warm start), -1 if none
+    float q_lo, q_hi;  // q_lo <= value at 0 of the hull of the FP32 left/right samples <= q_hi
+    float w0;          // FP32 centre sample
+};
+
+// Min over the line of w - s x, the centre excluded (set to +inf by the
+// caller); per lane four independent running minima per chunk component.
+__device__ __forceinline__ float min_pass(const float *sw, const LineGeom &g, int lane, float s) {
+    const float ns = -s;
+    float m[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+    float fq = 0.0f;
+#pragma unroll 4
+    for (int q = 0; q < g.nfull; ++q, fq += 128.0f) {
+        const float4 v = *reinterpret_cast<const float4 *>(sw + 128 * q + 4 * lane);
+        m[0] = fminf(m[0], __fmaf_rn(ns, fq, v.x));
+        m[1] = fminf(m[1], __fmaf_rn(ns, fq, v.y));
+        m[2] = fminf(m[2], __fmaf_rn(ns, fq, v.z));
+        m[3] = fminf(m[3], __fmaf_rn(ns, fq, v.w));
+    }
+    float e = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) e = fminf(e, __fmaf_rn(ns, (float)(4 * lane + i - g.m0), m[i]));
+    for (int k = 128 * g.nfull + lane; k < g.L; k += 32)
+        e = fminf(e, __fmaf_rn(ns, (float)(k - g.m0), sw[k]));
+    // warp minimum (keys order like floats; NaN never wins against +inf)
+    const int mk = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
+    return __int_as_float(f2key(__int_as_float(mk)));  // f2key is its own inverse
+}
+
+__device__ __forceinline__ ScreenOut warp_screen(float *sw, const LineGeom g, int lane,
+                                                 int warm_a, int warm_b, HullCounters &hc) {
+    ScreenOut out;
+    const int m0 = g.m0, L = g.L;
+    out.w0 = sw[m0];
+    out.a = out.b = -1;
+    out.q_lo = out.q_hi = INFINITY;
+    if (m0 < 1 || !(sw[m0 - 1] < INFINITY) || !(sw[m0 + 1] < INFINITY)) return out;
+
+    int a, b;
+    if (warm_a >= 0 && warm_a < m0 && warm_b > m0 && warm_b < L && sw[warm_a] < INFINITY &&
+        sw[warm_b] < INFINITY) {
+        a = warm_a;
+        b = warm_b;
+    } else {
+        full_argmin(sw, g, lane, 0.0f, a, b);
+        if (lane == 0) ++hc.c[HC_FULL];
+        if (a < 0 || b < 0) return out;
+    }
+    float wa = sw[a], wb = sw[b];
+    float s = 0.0f, emin = -INFINITY;
+    for (int round = 0; round < 2; ++round) {
+        if (lane == 0) ++hc.c[HC_ROUNDS];
+        // supporting-slope iteration inside 32-sample windows around a and b
+        int loA = win_lo_a(a, m0), loB = win_lo_b(b, m0, L);
+        int kA = loA + lane, kB = loB + lane;
+        float vA = kA < m0 ? nan_to_inf(sw[kA]) : INFINITY;
+        float vB = kB < L ? nan_to_inf(sw[kB]) : INFINITY;
+        float XA = (float)(kA - m0), XB = (float)(kB - m0);
+        for (int it = 0; it < 32; ++it) {
+            s = __fdividef(wb - wa, (float)(b - a));
+            const int keyA = f2key(__fmaf_rn(-s, XA, vA));
+            const int keyB = f2key(__fmaf_rn(-s, XB, vB));
+            const int mA = __reduce_min_sync(kFull, keyA), mB = __reduce_min_sync(kFull, keyB);
+            const unsigned bA = __ballot_sync(kFull, keyA == mA);
+            const unsigned bB = __ballot_sync(kFull, keyB == mB);
+            const int na = ((bA >> (a - loA)) & 1u) ? a : loA + __ffs(bA) - 1;
+            const int nb = ((bB >> (b - loB)) & 1u) ? b : loB + __ffs(bB) - 1;
+            if (lane == 0) ++hc.c[HC_WSTEPS];
+            if (na == a && nb == b) break;
+            wa = __shfl_sync(kFull, vA, na - loA);
+            wb = __shfl_sync(kFull, vB, nb - loB);
+            a = na;
+            b = nb;
+            const int nloA = win_lo_a(a, m0), nloB = win_lo_b(b, m0, L);
+            if (nloA != loA && (a - loA < 4 || a - loA > 27)) {
+                loA = nloA;
+                kA = loA + lane;
+                vA = kA < m0 ? nan_to_inf(sw[kA]) : INFINITY;
+                XA = (float)(kA - m0);
+            }
+            if (nloB != loB && (b - loB < 4 || b - loB > 27)) {
+                loB = nloB;
+                kB = loB + lane;
+                vB = kB < L ? nan_to_inf(sw[kB]) : INFINITY;
+                XB = (float)(kB - m0);
+            }
+        }
+        s = __fdividef(wb - wa, (float)(b - a));
+        // min pass with the centre masked
+        __syncwarp();
+        if (lane == 0) sw[m0] = INFINITY;
+        __syncwarp();
+        emin = min_pass(sw, g, lane, s);
+        __syncwarp();
+        if (lane == 0) sw[m0] = out.w0;
+        __syncwarp();
+        const float H = __fmaf_rn(-s, (float)(a - m0), wa);
+        const float M = fabsf(H) + fabsf(s) * (float)m0;
+        if (emin >= H - 4.0f * kU32 * M) break;  // the windows' pair is (nearly) global
+        // a sample lies clearly below the chord: restart from the global argmin
+        if (lane == 0) ++hc.c[HC_RARE];
+        full_argmin(sw, g, lane, s, a, b);
+        if (a < 0 || b < 0) return out;
+        wa = sw[a];
+        wb = sw[b];
+    }
+    // rigorous bounds (first-order rounding of each computed w - s x is at most
+    // 3u (|w - s x| + 2 |s| m0); the chord at 0 is within 4u (|wa|+|wb|+|q|))
+    const float xa = (float)(a - m0), xb = (float)(b - m0);
+    const float chord = wa + (wb - wa) * __fdividef(-xa, xb - xa);
+    out.q_lo = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(s) * (float)m0) - 1e-30f;
+    out.q_hi = chord + 4.0f * kU32 * (fabsf(wa) + fabsf(wb) + fabsf(chord)) + 1e-30f;
+    out.q_lo = fminf(out.q_lo, out.q_hi);
+    out.a = a;
+    out.b = b;
+    return out;
+}
+
 }  // namespace cvx

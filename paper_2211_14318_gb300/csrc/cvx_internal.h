@@ -20,14 +20,16 @@ constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
 constexpr float kEps32 = 1.1e-6f;
 
 // Best directions of one work item (a node and a block of its directions),
-// ranked by q = FP32 value at t = 0 of the chord between the left and right
-// sets' bridge (the hull value when the centre does not lie below it).
+// ranked by q = a rigorous lower bound on the value at t = 0 of the hull of the
+// FP32 samples of the left and right sets (the node's hull value when the
+// centre does not lie below it); qhi_min is the smallest upper bound seen.
 struct ItemCands {
     float q[kItemTop];
     int dir[kItemTop];
     float w0;       // FP32 centre sample
     float dropped;  // smallest q not kept
-    int n, flags;
+    float qhi_min;  // smallest upper bound over the item's directions
+    int n, flags, pad;
 };
 
 struct NodeCands {

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const ScanArg
     __shared__ NodeLine s_nl;
     __shared__ float s_q[16][kWarpTop];
     __shared__ int s_d[16][kWarpTop];
-    __shared__ float s_drop[16];
+    __shared__ float s_drop[16], s_qhi[16];
     __shared__ int s_fl[16];
     __shared__ float s_w0;
     __shared__ unsigned s_hc[16][HC_N];
@@ -155,30 +155,26 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const ScanArg
             tq[i] = INFINITY;
             td[i] = -1;
         }
-        float dropped = INFINITY, w0 = 0.0f;
+        float dropped = INFINITY, w0 = 0.0f, qhi_min = INFINITY;
         int fl = 0;
         int warm_a = -1, warm_b = -1;
         for (int dj = jb; dj < je; ++dj) {
             const DirLine dl = make_dir_line<EK>(s_nl, A.dir32[dj]);
             sample_line<EK>(sw, nl, dl, ln, lane, tl);
             __syncwarp();
-            const unsigned caps0 = hc.c[HC_CAPS];
-            const BridgeOut o = warp_bridge(sw, g, lane, warm_a, warm_b, hc);
+            const ScreenOut o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
             __syncwarp();
             if (lane == 0) {
                 ++n_lines;
                 n_valid += valid_samples(dl, ln, EK);
-                if (hc.c[HC_CAPS] != caps0) fl |= CVX_NODE_ITER_CAP;
             }
             w0 = o.w0;
-            float q = INFINITY;
             if (o.a >= 0) {
                 warm_a = o.a;
                 warm_b = o.b;
-                const float xa = (float)(o.a - ln.m0), xb = (float)(o.b - ln.m0);
-                q = o.wa + (o.wb - o.wa) * __fdividef(-xa, xb - xa);
             }
-            top_insert(tq, td, dropped, q, dj);
+            qhi_min = fminf(qhi_min, o.q_hi);
+            top_insert(tq, td, dropped, o.q_lo, dj);
         }
         if (lane == 0) {
 #pragma unroll
@@ -187,6 +183,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const ScanArg
                 s_d[warp][i] = td[i];
             }
             s_drop[warp] = dropped;
+            s_qhi[warp] = qhi_min;
             s_fl[warp] = fl;
             if (jb < je) s_w0 = w0;
         }
@@ -194,12 +191,15 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const ScanArg
         if (threadIdx.x == 0) {
             // merge the warps' lists (ties -> lower direction index)
             ItemCands r;
-            float drop = INFINITY;
+            float drop = INFINITY, qhi = INFINITY;
             int f = 0;
             for (int k = 0; k < nw; ++k) {
                 drop = fminf(drop, s_drop[k]);
+                qhi = fminf(qhi, s_qhi[k]);
                 f |= s_fl[k];
             }
+            r.qhi_min = qhi;
+            r.pad = 0;
             int taken[16];
             for (int k = 0; k < nw; ++k) taken[k] = 0;
             int n = 0;
@@ -285,22 +285,25 @@ int scan_max_blocks_per_sm(int energy, int warps, int stride) {
 // -------------------------------------------------------------------------
 // k_select: one thread per queued node.  q is the FP32 value at t = 0 of a
 // direction's left/right bridge chord and eps bounds |q_FP32 - q_FP64|
-// (1-Lipschitz in the samples).  The node's FP64 value is
-// min(W(F), min_R q_R^FP64), so a direction with q > Qmin + 2 eps cannot be the
-// FP64 minimiser and, if Qmin > w0 + 2 eps, no line splits.  The (at most
-// kNodeCand) directions with the smallest q inside that band are refined in
-// FP64; k_commit checks that no unrefined direction (q >= qcut) can win.
+// (1-Lipschitz in the samples), q_lo <= q_R^FP32 <= q_hi per direction.  The
+// node's FP64 value V = min(W(F), min_R q_R^FP64) is at most
+// min(w0, min_R q_hi) + eps, so a direction with q_lo > min(w0, U) + 2 eps
+// (U = min q_hi) can neither be the FP64 minimiser nor split the node, and if
+// min q_lo > w0 + 2 eps no line splits.  The (at most kNodeCand) directions
+// with the smallest q_lo inside that band are refined in FP64; k_commit checks
+// that no unrefined direction (q_lo >= qcut) can win.
 // -------------------------------------------------------------------------
 __global__ void k_select(const SelectArgs A) {
     const int qi = blockIdx.x * blockDim.x + threadIdx.x;
     if (qi >= *A.q_count) return;
     const ItemCands *r = A.items + (long long)qi * A.chunks;
-    float qmin = INFINITY, drop = INFINITY;
+    float qmin = INFINITY, drop = INFINITY, U = INFINITY;
     int fl = 0;
     const float w0 = r[0].w0;
     for (int c = 0; c < A.chunks; ++c) {
         qmin = fminf(qmin, r[c].q[0]);
         drop = fminf(drop, r[c].dropped);
+        U = fminf(U, r[c].qhi_min);
         fl |= r[c].flags;
     }
     NodeCands nc;
@@ -308,7 +311,7 @@ __global__ void k_select(const SelectArgs A) {
     nc.eps = kEps32 * fmaxf(A.kappa, fmaxf(fabsf(qmin), fabsf(w0)));
     float qcut = drop;
     if (qmin <= w0 + 2.0f * nc.eps) {
-        const float lim = qmin + 2.0f * nc.eps;
+        const float lim = fminf(w0, U) + 2.0f * nc.eps;
         // merge the items' sorted lists, smallest q first (ties: lower direction)
         int pos[64];
         const int nch = A.chunks < 64 ? A.chunks : 64;
