@@ -346,7 +346,7 @@ def run_ours(a):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "points/s",
                     "h2d_bytes_per_step": 2 * n * 4 * 8, "d2h_bytes_per_step": n * 8 + n * 4 * 8},
-            "gpu_launches": a.steps * (3 + 2 * DEPTH),
+            "gpu_launches": a.steps * (3 + 4 * DEPTH),  # history, init, 4 per level, leaf
             "clocks": ck,
             "stats": st,
         }

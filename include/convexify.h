@@ -192,11 +192,13 @@ int cvx_set_profiling(cvx_handle *h, int enable);
 int cvx_get_scan_timing(cvx_handle *h, double *ms, int64_t *launches, int reset);
 
 /* sizeof of the ABI structs, for bindings to check their layouts:
- * which = 0 cvx_params, 1 cvx_node, 2 cvx_laminate, 3 cvx_stats; -1 otherwise. */
+ * which = 0 cvx_params, 1 cvx_node, 2 cvx_laminate, 3 cvx_stats, 4 cvx_problem;
+ * -1 otherwise. */
 int cvx_struct_size(int which);
 
-/* Sets the launch shape of the line-scan kernel: warps per CTA (1..16) and
- * directions per work item (>= 1; 0 = automatic).  Used by the autotuner. */
+/* Sets the launch shape of the line-scan kernel of convexify_points: warps per
+ * CTA (1..8) and directions per work item (>= 1; 0 = automatic).
+ * convexify_batch chooses its own (see cvx_get_batch_tuning). */
 int cvx_set_tuning(cvx_handle *h, int warps_per_cta, int dirs_per_item);
 
 /* ----------------------------------------------------- steps of the method */
@@ -237,6 +239,43 @@ int cvx_hull_bridge(cvx_handle *h, int64_t n_lines, int32_t L, const float *w,
 int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double *F,
                      const double *beta_k, double *W_R, double *P, cvx_laminate *root,
                      cvx_node *tree, int32_t *status, cvx_stream s);
+
+/* ------------------------------------------------------------ batched form */
+
+/* One problem of a batch: its own parameters and caller-owned DEVICE arrays
+ * (as for convexify_points; root may be NULL). */
+typedef struct cvx_problem {
+    cvx_params params;
+    int64_t n;
+    const double *F;       /* n x 4 */
+    const double *beta_k;  /* n */
+    double *W_R;           /* n */
+    double *P;             /* n x 4 */
+    int32_t *status;       /* n */
+    cvx_laminate *root;    /* n, nullable */
+} cvx_problem;
+
+/* Many independent problems (meshes, load steps) of uneven sizes in one run:
+ * the points of all problems share the same per-level persistent kernels
+ * (work items handed out by an atomic counter, so uneven problems balance),
+ * and the whole multi-level run is a CUDA graph.  Results are those of
+ * convexify_points on each problem.  All problems must use the same energy
+ * kind; n_problems <= 65536; the problems array is a HOST array.
+ * The first call with a given set of problems (shapes, parameters and
+ * pointers) picks the launch shape with a short timed trial on a sample of the
+ * points (the autotuner; result cached in the handle, and in the JSON file
+ * named by the environment variable CVX_AUTOTUNE_CACHE if set), captures the
+ * graph and launches it; later calls with the same set replay the graph.
+ * The first call is therefore synchronous; later calls are asynchronous.
+ * The trial runs write their results into the leading points' outputs (later
+ * overwritten) and add to the handle's statistics counters.  A later
+ * convexify_points call that grows the handle's workspace makes the next
+ * batch call capture again. */
+int convexify_batch(cvx_handle *h, int n_problems, const cvx_problem *problems, cvx_stream s);
+
+/* The launch shape the autotuner chose for the last batch (0s before any). */
+int cvx_get_batch_tuning(cvx_handle *h, int *warps_per_cta, int *dirs_per_item_cap,
+                         int *from_cache);
 
 /* ------------------------------------------------ allocation-free variant */
 

@@ -57,6 +57,14 @@ class _Stats(ctypes.Structure):
         "fp64_rare", "fp64_center", "refined", "overflow")]
 
 
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("params", _Params), ("n", ctypes.c_int64),
+        ("F", ctypes.c_void_p), ("beta_k", ctypes.c_void_p), ("W_R", ctypes.c_void_p),
+        ("P", ctypes.c_void_p), ("status", ctypes.c_void_p), ("root", ctypes.c_void_p),
+    ]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -85,6 +93,9 @@ def lib() -> ctypes.CDLL:
         "cvx_hull_bridge": [vp, i64, i32, vp, vp, vp, vp, vp],
         "convexify_points": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp, vp, vp],
         "convexify_points_static": [ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp],
+        "convexify_batch": [vp, ctypes.c_int, ctypes.POINTER(_Problem), vp],
+        "cvx_get_batch_tuning": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -98,7 +109,8 @@ def exported_symbols() -> Sequence[str]:
     return ("cvx_create", "cvx_destroy", "cvx_last_error", "cvx_get_stats", "cvx_struct_size",
             "cvx_set_tuning", "cvx_set_profiling", "cvx_get_scan_timing",
             "cvx_energy", "cvx_history_update", "cvx_sample_lines", "cvx_hull_bridge",
-            "convexify_points", "convexify_points_static")
+            "convexify_points", "convexify_points_static", "convexify_batch",
+            "cvx_get_batch_tuning")
 
 
 def _check(rc: int, what: str):
@@ -291,6 +303,52 @@ class Convexifier:
                                       _ptr(P), _ptr(root), _ptr(tree), _ptr(st), _stream(stream)),
                "convexify_points")
         return dict(W_R=W_R, P=P, status=st, tree=tree, root=root)
+
+    def convexify_batch(self, problems, outs: Optional[list] = None, want_root: bool = False,
+                        stream=None):
+        """Several problems (a list of (Params, F, beta_k)) in one pipeline run.
+
+        The library captures the run as a CUDA graph and replays it while the
+        problems, parameters and tensors stay the same; pass ``outs`` (the list
+        this call returns) back in to keep the output tensors fixed."""
+        import torch
+
+        arr = (_Problem * len(problems))()
+        res = []
+        keep = []
+        for i, (p, F, beta) in enumerate(problems):
+            F = self._dev(F, torch.float64).reshape(-1, 4)
+            n = F.shape[0]
+            beta = self._dev(beta, torch.float64).reshape(n)
+            dev = F.device
+            o = dict(outs[i]) if outs else {}
+            if o.get("W_R") is None:
+                o["W_R"] = torch.empty(n, dtype=torch.float64, device=dev)
+            if o.get("P") is None:
+                o["P"] = torch.empty(n, 4, dtype=torch.float64, device=dev)
+            if o.get("status") is None:
+                o["status"] = torch.empty(n, dtype=torch.int32, device=dev)
+            if want_root and o.get("root") is None:
+                o["root"] = torch.empty(n * LAMINATE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            q = arr[i]
+            q.params = p.c()
+            keep.append((p, F, beta))
+            q.n = n
+            q.F, q.beta_k = _ptr(F), _ptr(beta)
+            q.W_R, q.P, q.status = _ptr(o["W_R"]), _ptr(o["P"]), _ptr(o["status"])
+            q.root = _ptr(o.get("root"))
+            res.append(o)
+        _check(lib().convexify_batch(self._h, len(problems), arr, _stream(stream)),
+               "convexify_batch")
+        return res
+
+    def batch_tuning(self):
+        """(warps per CTA, directions-per-item cap, taken from the cache) of the
+        last convexify_batch launch-shape choice."""
+        w, d, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().cvx_get_batch_tuning(self._h, ctypes.byref(w), ctypes.byref(d),
+                                          ctypes.byref(c)), "cvx_get_batch_tuning")
+        return w.value, d.value, bool(c.value)
 
 
 def tree_numpy(tree_bytes, n: int, tree_size: int) -> np.ndarray:

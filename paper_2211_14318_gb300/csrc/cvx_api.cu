@@ -1,6 +1,6 @@
 // cvx_api.cu -- host side of the C ABI declared in include/convexify.h:
 // argument validation, the handle (workspace, direction tables, counters),
-// and the enqueueing of the per-level kernels on the caller's stream.
+// the single steps and convexify_points (a pipeline run over one problem).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -11,35 +11,15 @@
 #include <string>
 #include <vector>
 
-#include "convexify.h"
-#include "cvx_internal.h"
+#include "cvx_handle.h"
 
 using namespace cvx;
 
-struct cvx_handle {
-    int device = 0;
-    int sm_count = 0;
-    // direction table cache
-    int dir_na = -1, dir_nb = -1;
-    bool dir_custom = false;
-    int D = 0;
-    size_t dir_cap = 0;
-    float4 *d_dir32 = nullptr;
-    double *d_dir64 = nullptr;
-    // workspace
-    char *ws = nullptr;
-    size_t ws_cap = 0;
-    unsigned long long *d_counters = nullptr;
-    int tune_warps = 8;
-    int tune_dpi = 0;
-    // optional CUDA-event timing of the scan launches
-    bool profiling = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_pool;
-};
-
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace cvx {
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -57,25 +37,8 @@ int cuda_fail(cudaError_t e, const char *where) {
     return fail(CVX_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-#define CK(call, where)                                 \
-    do {                                                \
-        cudaError_t e_ = (call);                        \
-        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-    } while (0)
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
+// Records the calling thread's last error for entry points in other files.
+int set_error_message(int code, const char *msg) { return fail(code, "%s", msg); }
 
 Material material_of(const cvx_params *p) {
     Material m;
@@ -104,7 +67,7 @@ int check_params(const cvx_params *p, bool need_line) {
                     p->line_points);
     if (!(p->t_half > 0.0) || !isfinite(p->t_half))
         return fail(CVX_ERR_INVALID_ARG, "t_half must be positive");
-    if (p->depth < 0 || p->depth > 8)
+    if (p->depth < 0 || p->depth > kMaxDepth)
         return fail(CVX_ERR_INVALID_ARG, "depth must be in [0, 8], got %d", p->depth);
     if (p->dirs) {
         if (p->n_dirs < 1 || p->n_dirs > (1 << 20))
@@ -117,45 +80,62 @@ int check_params(const cvx_params *p, bool need_line) {
     return CVX_OK;
 }
 
-LineSpec line_of(const cvx_params *p) {
-    LineSpec l;
-    l.L = p->line_points;
-    l.m0 = (p->line_points - 1) / 2;
-    l.h64 = 2.0 * p->t_half / (double)(p->line_points - 1);
-    l.h32 = (float)l.h64;
-    l.nfull = l.L >> 7;
-    l.stride = line_stride(l.L);
-    return l;
-}
-
 // Direction table: a_i = (cos pi i/Na, sin pi i/Na), b_j likewise, j_dir = i Nb + j,
 // or a copy of the caller's rows.
+void direction_rows(const cvx_params *p, std::vector<double> &d64) {
+    const int D = p->dirs ? p->n_dirs : p->n_theta_a * p->n_theta_b;
+    d64.resize((size_t)D * 4);
+    if (p->dirs) {
+        memcpy(d64.data(), p->dirs, sizeof(double) * 4 * (size_t)D);
+        return;
+    }
+    for (int i = 0; i < p->n_theta_a; ++i) {
+        const double ta = M_PI * (double)i / (double)p->n_theta_a;
+        for (int j = 0; j < p->n_theta_b; ++j) {
+            const double tb = M_PI * (double)j / (double)p->n_theta_b;
+            double *r = &d64[4 * ((size_t)i * p->n_theta_b + j)];
+            r[0] = cos(ta);
+            r[1] = sin(ta);
+            r[2] = cos(tb);
+            r[3] = sin(tb);
+        }
+    }
+}
+
+int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s) {
+    if (bytes <= h->ws_cap) return CVX_OK;
+    CK(cudaStreamSynchronize(s), "workspace");
+    CK(cudaDeviceSynchronize(), "workspace");
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_cap = 0;
+    ++h->ws_gen;
+    const size_t cap = std::max(bytes + bytes / 8, (size_t)1 << 20);
+    cudaError_t e = cudaMalloc(&h->ws, cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CVX_ERR_OOM, "workspace of %zu bytes: %s", cap, cudaGetErrorString(e));
+    }
+    h->ws_cap = cap;
+    return CVX_OK;
+}
+
+}  // namespace cvx
+
+namespace {
+
 int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s) {
     if (!p->dirs && !h->dir_custom && h->dir_na == p->n_theta_a && h->dir_nb == p->n_theta_b)
         return CVX_OK;
-    const int D = p->dirs ? p->n_dirs : p->n_theta_a * p->n_theta_b;
-    std::vector<double> d64((size_t)D * 4);
-    if (p->dirs) {
-        memcpy(d64.data(), p->dirs, sizeof(double) * 4 * (size_t)D);
-    } else {
-        for (int i = 0; i < p->n_theta_a; ++i) {
-            const double ta = M_PI * (double)i / (double)p->n_theta_a;
-            for (int j = 0; j < p->n_theta_b; ++j) {
-                const double tb = M_PI * (double)j / (double)p->n_theta_b;
-                double *r = &d64[4 * ((size_t)i * p->n_theta_b + j)];
-                r[0] = cos(ta);
-                r[1] = sin(ta);
-                r[2] = cos(tb);
-                r[3] = sin(tb);
-            }
-        }
-    }
+    std::vector<double> d64;
+    direction_rows(p, d64);
+    const int D = (int)(d64.size() / 4);
     std::vector<float4> d32(D);
     for (int k = 0; k < D; ++k)
         d32[k] = make_float4((float)d64[4 * k], (float)d64[4 * k + 1], (float)d64[4 * k + 2],
                              (float)d64[4 * k + 3]);
+    CK(cudaStreamSynchronize(s), "direction table");
     if ((size_t)D > h->dir_cap) {
-        CK(cudaStreamSynchronize(s), "direction table");
         cudaFree(h->d_dir32);
         cudaFree(h->d_dir64);
         h->d_dir32 = nullptr;
@@ -166,7 +146,6 @@ int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s) {
         h->dir_cap = D;
     }
     // synchronous copies: the host vectors die at return
-    CK(cudaStreamSynchronize(s), "direction table");
     CK(cudaMemcpy(h->d_dir32, d32.data(), sizeof(float4) * D, cudaMemcpyHostToDevice),
        "direction table");
     CK(cudaMemcpy(h->d_dir64, d64.data(), sizeof(double) * 4 * D, cudaMemcpyHostToDevice),
@@ -178,30 +157,9 @@ int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s) {
     return CVX_OK;
 }
 
-int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s) {
-    if (bytes <= h->ws_cap) return CVX_OK;
-    CK(cudaStreamSynchronize(s), "workspace");
-    cudaFree(h->ws);
-    h->ws = nullptr;
-    h->ws_cap = 0;
-    size_t cap = std::max(bytes, (size_t)1 << 20);
-    cudaError_t e = cudaMalloc(&h->ws, cap);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CVX_ERR_OOM, "workspace of %zu bytes: %s", cap, cudaGetErrorString(e));
-    }
-    h->ws_cap = cap;
-    return CVX_OK;
-}
-
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
-
-namespace cvx {
-// Records the calling thread's last error for entry points in other files.
-int set_error_message(int code, const char *msg) { return fail(code, "%s", msg); }
-}  // namespace cvx
 
 extern "C" {
 
@@ -239,6 +197,7 @@ int cvx_destroy(cvx_handle *h) {
     if (!h) return CVX_OK;
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
+    destroy_batch_plan(h);
     for (auto *v : {&h->ev_pending, &h->ev_pool})
         for (auto &e : *v) {
             cudaEventDestroy(e.first);
@@ -310,14 +269,15 @@ int cvx_struct_size(int which) {
     case 1: return (int)sizeof(cvx_node);
     case 2: return (int)sizeof(cvx_laminate);
     case 3: return (int)sizeof(cvx_stats);
+    case 4: return (int)sizeof(cvx_problem);
     default: return -1;
     }
 }
 
 int cvx_set_tuning(cvx_handle *h, int warps_per_cta, int dirs_per_item) {
     if (!h) return fail(CVX_ERR_INVALID_ARG, "handle is NULL");
-    if (warps_per_cta < 1 || warps_per_cta > 16)
-        return fail(CVX_ERR_INVALID_ARG, "warps_per_cta must be in [1, 16]");
+    if (warps_per_cta < 1 || warps_per_cta > 8)
+        return fail(CVX_ERR_INVALID_ARG, "warps_per_cta must be in [1, 8]");
     if (dirs_per_item < 0) return fail(CVX_ERR_INVALID_ARG, "dirs_per_item must be >= 0");
     h->tune_warps = warps_per_cta;
     h->tune_dpi = dirs_per_item;
@@ -359,7 +319,7 @@ int cvx_sample_lines(cvx_handle *h, const cvx_params *p, int64_t n_lines, const 
     DeviceGuard g(h->device);
     rc = ensure_dirs(h, p, (cudaStream_t)s);
     if (rc) return rc;
-    const LineSpec ln = line_of(p);
+    const LineSpec ln = make_line(p->line_points, p->t_half);
     CK(launch_sample_lines(n_lines, F, beta_k, dir, h->d_dir32, h->D, material_of(p), ln, w,
                            (cudaStream_t)s),
        "cvx_sample_lines");
@@ -375,8 +335,7 @@ int cvx_hull_bridge(cvx_handle *h, int64_t n_lines, int32_t L, const float *w, i
     if (n_lines > 0 && (!w || !m_minus || !m_plus || !hval))
         return fail(CVX_ERR_INVALID_ARG, "NULL array");
     DeviceGuard g(h->device);
-    CK(launch_hull(n_lines, L, w, m_minus, m_plus, hval, h->d_counters,
-                   (cudaStream_t)s),
+    CK(launch_hull(n_lines, L, w, m_minus, m_plus, hval, h->d_counters, (cudaStream_t)s),
        "cvx_hull_bridge");
     return CVX_OK;
 }
@@ -397,172 +356,69 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     rc = ensure_dirs(h, p, s);
     if (rc) return rc;
 
-    const LineSpec ln = line_of(p);
-    const int K = p->depth;
-    const int NT = (1 << (K + 1)) - 1;
-    const int D = h->D;
+    const Material mat = material_of(p);
     const int warps = h->tune_warps;
-    const int bpsm = scan_max_blocks_per_sm(p->energy, warps, ln.stride);
+    ProbDesc pd = {};
+    pd.line = make_line(p->line_points, p->t_half);
+    const int bpsm = scan_max_blocks_per_sm(p->energy, warps, pd.line.stride);
     if (bpsm < 1) return fail(CVX_ERR_UNSUPPORTED, "scan kernel cannot launch with %d warps", warps);
     const int grid = h->sm_count * bpsm;
-    // directions per work item: whole nodes when there are enough of them,
-    // otherwise split the directions so every SM gets work
-    int dpi = h->tune_dpi;
-    if (dpi <= 0) {
-        const int64_t want_items = (int64_t)grid * 4;
-        if (n >= want_items) dpi = D;
-        else {
-            const int64_t chunks = (want_items + n - 1) / n;
-            dpi = (int)std::max<int64_t>(warps * 2, (D + chunks - 1) / chunks);
-        }
-    }
-    dpi = std::min(dpi, D);
-    const int chunks = (D + dpi - 1) / dpi;
+    pd.mat = mat;
+    pd.kappa = line_kappa(mat);
+    pd.kappa_f = (float)pd.kappa;
+    pd.D = h->D;
+    pd.dir_off = 0;
+    pd.K = p->depth;
+    pd.NT = (1 << (p->depth + 1)) - 1;
+    pd.dpi = h->tune_dpi > 0 ? std::min(h->tune_dpi, pd.D)
+                             : dirs_per_item(n, pd.D, grid, warps, 0);
+    pd.chunks = (pd.D + pd.dpi - 1) / pd.dpi;
+    pd.point_off = 0;
+    pd.n = n;
+    pd.F = F;
+    pd.beta = beta_k;
+    pd.W_R = W_R;
+    pd.P = P;
+    pd.status = status;
+    pd.root = root;
 
-    // workspace layout (level l holds at most n 2^l nodes)
-    const size_t maxq = K > 0 ? ((size_t)n << (K - 1)) : 0;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        size_t o = off;
-        off = align_up(off + bytes);
-        return o;
-    };
-    const size_t o_tree = tree ? 0 : take(sizeof(cvx_node) * (size_t)n * NT);
-    std::vector<size_t> o_qp(K + 1), o_qh(K + 1);
-    for (int l = 0; l < K; ++l) {
-        o_qp[l] = take(sizeof(int32_t) * ((size_t)n << l));
-        o_qh[l] = take(sizeof(int32_t) * ((size_t)n << l));
-    }
-    const size_t o_cnt = take(sizeof(int32_t) * 2 * (K + 1));
-    const size_t o_items = take(sizeof(ItemCands) * maxq * chunks);
-    const size_t o_cands = take(sizeof(NodeCands) * maxq);
-    const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
-    const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
-    rc = ensure_ws(h, off, s);
+    Pipe pp = {};
+    pp.n_probs = 1;
+    pp.N = n;
+    pp.K = p->depth;
+    pp.C = pd.chunks;
+    pp.stride32 = pp.stride64 = pd.line.stride;
+    pp.energy = p->energy;
+    const size_t pipe_sz = align_up(pipe_bytes(pp.N, pp.K, pp.C, 1));
+    const size_t tree_sz = tree ? 0 : sizeof(cvx_node) * (size_t)n * pd.NT;
+    rc = ensure_ws(h, pipe_sz + tree_sz, s);
     if (rc) return rc;
-    char *ws = h->ws;
-    cvx_node *tr = tree ? tree : (cvx_node *)(ws + o_tree);
-    int32_t *cnt = (int32_t *)(ws + o_cnt);      // node counts per level
-    int32_t *wcnt = cnt + (K + 1);               // refine work counts per level
+    pipe_layout(pp, h->ws);
+    pd.tree = tree ? tree : (cvx_node *)(h->ws + pipe_sz);
+    pp.dir32 = h->d_dir32;
+    pp.dir64 = h->d_dir64;
+    pp.counters = h->d_counters;
+    // pageable source: returns once staged, so the stack copy may go away
+    CK(cudaMemcpyAsync((void *)pp.probs, &pd, sizeof pd, cudaMemcpyHostToDevice, s),
+       "convexify_points/table");
 
-    CK(cudaMemsetAsync(tr, 0, sizeof(cvx_node) * (size_t)n * NT, s), "convexify_points");
-    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 2 * (K + 1), s), "convexify_points");
-
-    const Material mat = material_of(p);
-    InitArgs ia;
-    ia.n = n;
-    ia.F = F;
-    ia.beta = beta_k;
-    ia.tree = tr;
-    ia.NT = NT;
-    ia.depth = K;
-    ia.q_point = K ? (int32_t *)(ws + o_qp[0]) : nullptr;
-    ia.q_heap = K ? (int32_t *)(ws + o_qh[0]) : nullptr;
-    ia.q_count = cnt;
-    ia.status = status;
-    ia.mat = mat;
-    ia.m0 = ln.m0;
-    ia.counters = h->d_counters;
-    CK(launch_init(ia, s), "convexify_points/init");
-
-    ItemCands *items = (ItemCands *)(ws + o_items);
-    NodeCands *cands = (NodeCands *)(ws + o_cands);
-    int2 *work = (int2 *)(ws + o_work);
-    RefineOut *refined = (RefineOut *)(ws + o_ref);
-    for (int l = 0; l < K; ++l) {
-        const int64_t max_nodes = (int64_t)n << l;
-        int32_t *qp = (int32_t *)(ws + o_qp[l]), *qh = (int32_t *)(ws + o_qh[l]);
-        ScanArgs sa;
-        sa.tree = tr;
-        sa.NT = NT;
-        sa.beta = beta_k;
-        sa.q_point = qp;
-        sa.q_heap = qh;
-        sa.q_count = cnt + l;
-        sa.dir32 = h->d_dir32;
-        sa.D = D;
-        sa.chunks = chunks;
-        sa.dirs_per_item = dpi;
-        sa.mat = mat;
-        sa.line = ln;
-        sa.out = items;
-        sa.counters = h->d_counters;
-        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-        if (h->profiling) {
+    std::vector<cudaEvent_t> ev;
+    if (h->profiling) {
+        for (int l = 0; l < pp.K; ++l) {
+            std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
             if (!h->ev_pool.empty()) {
-                ev = h->ev_pool.back();
+                e = h->ev_pool.back();
                 h->ev_pool.pop_back();
             } else {
-                CK(cudaEventCreate(&ev.first), "profiling");
-                CK(cudaEventCreate(&ev.second), "profiling");
+                CK(cudaEventCreate(&e.first), "profiling");
+                CK(cudaEventCreate(&e.second), "profiling");
             }
-            CK(cudaEventRecord(ev.first, s), "profiling");
+            ev.push_back(e.first);
+            ev.push_back(e.second);
+            h->ev_pending.push_back(e);
         }
-        CK(launch_scan(sa, warps, grid, s), "convexify_points/scan");
-        if (h->profiling) {
-            CK(cudaEventRecord(ev.second, s), "profiling");
-            h->ev_pending.push_back(ev);
-        }
-
-        SelectArgs se;
-        se.q_count = cnt + l;
-        se.items = items;
-        se.chunks = chunks;
-        se.kappa = (float)line_kappa(mat);
-        se.cands = cands;
-        se.work = work;
-        se.work_count = wcnt + l;
-        se.counters = h->d_counters;
-        CK(launch_select(se, max_nodes, s), "convexify_points/select");
-
-        RefineArgs ra;
-        ra.tree = tr;
-        ra.NT = NT;
-        ra.beta = beta_k;
-        ra.q_point = qp;
-        ra.q_heap = qh;
-        ra.cands = cands;
-        ra.work = work;
-        ra.work_count = wcnt + l;
-        ra.dir64 = h->d_dir64;
-        ra.mat = mat;
-        ra.line = ln;
-        ra.out = refined;
-        CK(launch_refine(ra, max_nodes * kNodeCand, s), "convexify_points/refine");
-
-        CommitArgs ca;
-        ca.tree = tr;
-        ca.NT = NT;
-        ca.level = l;
-        ca.depth = K;
-        ca.beta = beta_k;
-        ca.q_point = qp;
-        ca.q_heap = qh;
-        ca.q_count = cnt + l;
-        ca.nq_point = l + 1 < K ? (int32_t *)(ws + o_qp[l + 1]) : nullptr;
-        ca.nq_heap = l + 1 < K ? (int32_t *)(ws + o_qh[l + 1]) : nullptr;
-        ca.nq_count = cnt + l + 1;
-        ca.cands = cands;
-        ca.refined = refined;
-        ca.dir64 = h->d_dir64;
-        ca.kappa = line_kappa(mat);
-        ca.mat = mat;
-        ca.line = ln;
-        ca.counters = h->d_counters;
-        CK(launch_commit(ca, max_nodes, s), "convexify_points/commit");
     }
-
-    LeafArgs la;
-    la.n = n;
-    la.tree = tr;
-    la.NT = NT;
-    la.beta = beta_k;
-    la.W_R = W_R;
-    la.P = P;
-    la.status = status;
-    la.root = root;
-    la.mat = mat;
-    CK(launch_leaf(la, s), "convexify_points/leaf");
+    CK(pipe_enqueue(pp, warps, grid, s, ev.empty() ? nullptr : ev.data()), "convexify_points");
     return CVX_OK;
 }
 

@@ -98,7 +98,7 @@ __device__ __forceinline__ int cand_pred(int k, float v, float ns, float s, floa
 
 // Full pass over the line: argmin of w - s x over the left and right sets
 // (FP32, approximate; exactness comes from the later checks).
-__device__ __noinline__ void full_argmin(const float *sw, const LineGeom g, int lane, float s,
+static __device__ __noinline__ void full_argmin(const float *sw, const LineGeom g, int lane, float s,
                                          int &a, int &b) {
     float bl = INFINITY, br = INFINITY;
     int kl = -1, kr = -1;
@@ -131,7 +131,7 @@ __device__ __forceinline__ int win_lo_b(int b, int m0, int L) {
 // Rare path: exact check of every certifying-pass candidate outside the
 // windows and the centre.  Returns 1 if the pair changed (a sample strictly
 // below the chord, or a collinear sample farther out).
-__device__ __noinline__ int rare_path(const float *sw, const LineGeom g, int lane, int &a, int &b,
+static __device__ __noinline__ int rare_path(const float *sw, const LineGeom g, int lane, int &a, int &b,
                                       float wa, float wb, float s, float ns, float T, int loA,
                                       int loB, unsigned &fp64_total) {
     unsigned fp64 = 0;

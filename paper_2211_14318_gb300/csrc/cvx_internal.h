@@ -15,6 +15,7 @@ enum { CVX_NODE_ITER_CAP = 64, CVX_NODE_OVERFLOW = 128 };
 constexpr int kWarpTop = 4;    // best directions kept per warp
 constexpr int kItemTop = 8;    // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
+constexpr int kMaxDepth = 8;
 // Bound on the FP32 sampling error of kappa W (kappa-scaled units, relative to
 // max(kappa, |q|)): 3.5 times the largest error measured against FP64.
 constexpr float kEps32 = 1.1e-6f;
@@ -53,93 +54,65 @@ enum CounterIdx {
 struct LineSpec {
     int L, m0, nfull, stride;  // samples, centre, full 128-chunks, per-warp buffer floats
     float h32;                 // sample spacing, FP32
+    int pad;
     double h64;                // sample spacing, FP64
 };
 
-struct ScanArgs {
-    const cvx_node *tree;
-    int NT;
-    const double *beta;
-    const int32_t *q_point, *q_heap, *q_count;
-    const float4 *dir32;
-    int D, chunks, dirs_per_item;
-    Material mat;
+// One problem of a call (convexify_points is a batch of one).  Points of all
+// problems share one global index space [point_off, point_off + n).
+struct ProbDesc {
     LineSpec line;
-    ItemCands *out;
-    unsigned long long *counters;
-};
-
-struct SelectArgs {
-    const int32_t *q_count;
-    const ItemCands *items;
-    int chunks;
-    float kappa;
-    NodeCands *cands;
-    int2 *work;  // (queue index, candidate index)
-    int32_t *work_count;
-    unsigned long long *counters;
-};
-
-struct RefineArgs {
-    const cvx_node *tree;
-    int NT;
-    const double *beta;
-    const int32_t *q_point, *q_heap;
-    const NodeCands *cands;
-    const int2 *work;
-    const int32_t *work_count;
-    const double *dir64;
     Material mat;
-    LineSpec line;
-    RefineOut *out;
-};
-
-struct CommitArgs {
-    cvx_node *tree;
-    int NT, level, depth;
-    const double *beta;
-    const int32_t *q_point, *q_heap, *q_count;
-    int32_t *nq_point, *nq_heap, *nq_count;
-    const NodeCands *cands;
-    const RefineOut *refined;
-    const double *dir64;
     double kappa;
-    Material mat;
-    LineSpec line;
-    unsigned long long *counters;
-};
-
-struct InitArgs {
-    int64_t n;
+    float kappa_f;
+    int D, dir_off;  // directions [dir_off, dir_off + D) of the call's tables
+    int K, NT;       // depth, tree nodes per point
+    int chunks, dpi; // work items per node, directions per item
+    int pad;
+    long long point_off, n;
     const double *F, *beta;
-    cvx_node *tree;
-    int NT, depth;
-    int32_t *q_point, *q_heap, *q_count;
-    int32_t *status;
-    Material mat;
-    int m0;
-    unsigned long long *counters;
-};
-
-struct LeafArgs {
-    int64_t n;
-    const cvx_node *tree;
-    int NT;
-    const double *beta;
     double *W_R, *P;
     int32_t *status;
     cvx_laminate *root;
-    Material mat;
+    cvx_node *tree;  // n x NT nodes
 };
 
-// kernel launchers (cvx_kernels.cu)
-cudaError_t launch_init(const InitArgs &a, cudaStream_t s);
-cudaError_t launch_scan(const ScanArgs &a, int warps, int grid, cudaStream_t s);
+__device__ __forceinline__ cvx_node *node_ptr(const ProbDesc &pd, long long p, int hi) {
+    return pd.tree + (p - pd.point_off) * pd.NT + hi;
+}
+
+// Device buffers of one pipeline run (all in one workspace).
+struct Pipe {
+    const ProbDesc *probs;
+    int n_probs;
+    long long N;         // points of all problems
+    int K;               // largest depth
+    int C;               // item stride per node (largest chunks)
+    int stride32, stride64;
+    int energy;
+    int32_t *pid;        // problem of each global point
+    int32_t *qp[kMaxDepth], *qh[kMaxDepth];  // node queues per level
+    int32_t *cnt;        // node count per level (K + 1) and refine work count per level (K + 1)
+    unsigned long long *item_ctr;  // work-item counter per level
+    ItemCands *items;
+    NodeCands *cands;
+    int2 *work;
+    RefineOut *refined;
+    const float4 *dir32;
+    const double *dir64;
+    unsigned long long *counters;
+};
+
+// Bytes of the workspace part that depends on the shape (see pipe_layout).
+size_t pipe_bytes(long long N, int K, int C, int n_probs);
+// Carves the workspace into the Pipe's buffers.
+void pipe_layout(Pipe &p, char *ws);
+// Enqueues the whole pipeline (zeroing, init, K levels, leaves) on s.
+// ev (optional, 2*K events) brackets each line-scan launch.
+cudaError_t pipe_enqueue(const Pipe &p, int warps, int grid, cudaStream_t s, cudaEvent_t *ev);
 int scan_max_blocks_per_sm(int energy, int warps, int stride);
-cudaError_t launch_select(const SelectArgs &a, int64_t max_nodes, cudaStream_t s);
-cudaError_t launch_refine(const RefineArgs &a, int64_t max_work, cudaStream_t s);
-cudaError_t launch_commit(const CommitArgs &a, int64_t max_nodes, cudaStream_t s);
-cudaError_t launch_leaf(const LeafArgs &a, cudaStream_t s);
+
+// single steps
 cudaError_t launch_energy(int64_t n, const double *F, const double *beta, double *W, double *P,
                           Material m, cudaStream_t s);
 cudaError_t launch_history(int64_t n, const double *F, const double *bin, double *bout,
@@ -152,5 +125,17 @@ cudaError_t launch_hull(int64_t n, int L, const float *w, int32_t *mm, int32_t *
 
 // Per-warp shared-memory stride of a line of L samples (16-byte aligned).
 __host__ __device__ inline int line_stride(int L) { return (L + 3) & ~3; }
+
+inline LineSpec make_line(int L, double t_half) {
+    LineSpec l;
+    l.L = L;
+    l.m0 = (L - 1) / 2;
+    l.h64 = 2.0 * t_half / (double)(L - 1);
+    l.h32 = (float)l.h64;
+    l.nfull = L >> 7;
+    l.stride = line_stride(L);
+    l.pad = 0;
+    return l;
+}
 
 }  // namespace cvx

@@ -40,6 +40,7 @@ int g_sms[kMaxDevices];
 // host staging of the direction tables (static: no host heap either)
 float4 g_dir32[kStaticMaxDirs];
 double g_dir64[4 * kStaticMaxDirs];
+ProbDesc g_desc;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -95,16 +96,7 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
         return err(CVX_ERR_INVALID_ARG, "NULL array (F, beta_k, W_R, P, status are required)");
     if (n == 0) return CVX_OK;
 
-    const LineSpec ln = [&] {
-        LineSpec l;
-        l.L = p->line_points;
-        l.m0 = (l.L - 1) / 2;
-        l.h64 = 2.0 * p->t_half / (double)(l.L - 1);
-        l.h32 = (float)l.h64;
-        l.nfull = l.L >> 7;
-        l.stride = line_stride(l.L);
-        return l;
-    }();
+    const LineSpec ln = make_line(p->line_points, p->t_half);
     const int K = p->depth;
     const int NT = (1 << (K + 1)) - 1;
     const int warps = 8;
@@ -135,8 +127,8 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
     if (dpi > D) dpi = D;
     const int chunks = (D + dpi - 1) / dpi;
 
-    // scratch layout
-    const size_t maxq = K > 0 ? ((size_t)n << (K - 1)) : 0;
+    // scratch layout: counters, direction tables, tree, then the pipeline's
+    // own buffers (problem table first)
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -147,16 +139,7 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
     const size_t o_d32 = take(sizeof(float4) * D);
     const size_t o_d64 = take(sizeof(double) * 4 * D);
     const size_t o_tree = take(sizeof(cvx_node) * (size_t)n * NT);
-    size_t o_qp[9], o_qh[9];
-    for (int l = 0; l < K; ++l) {
-        o_qp[l] = take(sizeof(int32_t) * ((size_t)n << l));
-        o_qh[l] = take(sizeof(int32_t) * ((size_t)n << l));
-    }
-    const size_t o_cnt = take(sizeof(int32_t) * 2 * (K + 1));
-    const size_t o_items = take(sizeof(ItemCands) * maxq * chunks);
-    const size_t o_cands = take(sizeof(NodeCands) * maxq);
-    const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
-    const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
+    const size_t o_pipe = take(pipe_bytes(n, K, chunks, 1));
     if (off > kStaticScratchBytes)
         return err(CVX_ERR_INVALID_ARG,
                    "convexify_points_static: problem needs more than the 64 MiB static scratch "
@@ -183,123 +166,55 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
     for (int k = 0; k < D; ++k)
         g_dir32[k] = make_float4((float)g_dir64[4 * k], (float)g_dir64[4 * k + 1],
                                  (float)g_dir64[4 * k + 2], (float)g_dir64[4 * k + 3]);
-    // pageable source: cudaMemcpyAsync returns once the data is staged
+
+    ProbDesc &pd = g_desc;
+    pd = ProbDesc{};
+    pd.line = ln;
+    pd.mat = mat;
+    pd.kappa = line_kappa(mat);
+    pd.kappa_f = (float)pd.kappa;
+    pd.D = D;
+    pd.dir_off = 0;
+    pd.K = K;
+    pd.NT = NT;
+    pd.chunks = chunks;
+    pd.dpi = dpi;
+    pd.point_off = 0;
+    pd.n = n;
+    pd.F = F;
+    pd.beta = beta_k;
+    pd.W_R = W_R;
+    pd.P = P;
+    pd.status = status;
+    pd.root = nullptr;
+    pd.tree = (cvx_node *)(ws + o_tree);
+
+    Pipe pp = {};
+    pp.n_probs = 1;
+    pp.N = n;
+    pp.K = K;
+    pp.C = chunks;
+    pp.stride32 = pp.stride64 = ln.stride;
+    pp.energy = p->energy;
+    pipe_layout(pp, ws + o_pipe);
+    pp.dir32 = (const float4 *)(ws + o_d32);
+    pp.dir64 = (const double *)(ws + o_d64);
+    pp.counters = (unsigned long long *)(ws + o_ctr);
+
+    // pageable sources: cudaMemcpyAsync returns once the data is staged
     if (cudaMemcpyAsync(ws + o_d32, g_dir32, sizeof(float4) * D, cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemcpyAsync(ws + o_d64, g_dir64, sizeof(double) * 4 * D, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync((void *)pp.probs, &pd, sizeof pd, cudaMemcpyHostToDevice, s) !=
             cudaSuccess)
-        return err(CVX_ERR_CUDA, "convexify_points_static: direction table copy failed");
+        return err(CVX_ERR_CUDA, "convexify_points_static: table copy failed");
 
-    // everything that must start at zero: counters, tree flags, queue counts
-    unsigned long long *ctr = (unsigned long long *)(ws + o_ctr);
-    cvx_node *tr = (cvx_node *)(ws + o_tree);
-    int32_t *cnt = (int32_t *)(ws + o_cnt);
-    int32_t *wcnt = cnt + (K + 1);
-    if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * C_NUM, s) != cudaSuccess ||
-        cudaMemsetAsync(tr, 0, sizeof(cvx_node) * (size_t)n * NT, s) != cudaSuccess ||
-        cudaMemsetAsync(cnt, 0, sizeof(int32_t) * 2 * (K + 1), s) != cudaSuccess)
+    // What must start at zero: the counters here; the queue counts and work
+    // counters are cleared, and every tree node written, by the pipeline itself.
+    if (cudaMemsetAsync(pp.counters, 0, sizeof(unsigned long long) * C_NUM, s) != cudaSuccess)
         return err(CVX_ERR_CUDA, "convexify_points_static: scratch clear failed");
-
-    InitArgs ia;
-    ia.n = n;
-    ia.F = F;
-    ia.beta = beta_k;
-    ia.tree = tr;
-    ia.NT = NT;
-    ia.depth = K;
-    ia.q_point = K ? (int32_t *)(ws + o_qp[0]) : nullptr;
-    ia.q_heap = K ? (int32_t *)(ws + o_qh[0]) : nullptr;
-    ia.q_count = cnt;
-    ia.status = status;
-    ia.mat = mat;
-    ia.m0 = ln.m0;
-    ia.counters = ctr;
-    if (launch_init(ia, s) != cudaSuccess) return err(CVX_ERR_CUDA, "convexify_points_static: init");
-
-    const float4 *d32 = (const float4 *)(ws + o_d32);
-    const double *d64 = (const double *)(ws + o_d64);
-    ItemCands *items = (ItemCands *)(ws + o_items);
-    NodeCands *cands = (NodeCands *)(ws + o_cands);
-    int2 *work = (int2 *)(ws + o_work);
-    RefineOut *refined = (RefineOut *)(ws + o_ref);
-    for (int l = 0; l < K; ++l) {
-        const int64_t max_nodes = (int64_t)n << l;
-        int32_t *qp = (int32_t *)(ws + o_qp[l]), *qh = (int32_t *)(ws + o_qh[l]);
-        ScanArgs sa;
-        sa.tree = tr;
-        sa.NT = NT;
-        sa.beta = beta_k;
-        sa.q_point = qp;
-        sa.q_heap = qh;
-        sa.q_count = cnt + l;
-        sa.dir32 = d32;
-        sa.D = D;
-        sa.chunks = chunks;
-        sa.dirs_per_item = dpi;
-        sa.mat = mat;
-        sa.line = ln;
-        sa.out = items;
-        sa.counters = ctr;
-        if (launch_scan(sa, warps, grid, s) != cudaSuccess)
-            return err(CVX_ERR_CUDA, "convexify_points_static: scan");
-        SelectArgs se;
-        se.q_count = cnt + l;
-        se.items = items;
-        se.chunks = chunks;
-        se.kappa = (float)line_kappa(mat);
-        se.cands = cands;
-        se.work = work;
-        se.work_count = wcnt + l;
-        se.counters = ctr;
-        if (launch_select(se, max_nodes, s) != cudaSuccess)
-            return err(CVX_ERR_CUDA, "convexify_points_static: select");
-        RefineArgs ra;
-        ra.tree = tr;
-        ra.NT = NT;
-        ra.beta = beta_k;
-        ra.q_point = qp;
-        ra.q_heap = qh;
-        ra.cands = cands;
-        ra.work = work;
-        ra.work_count = wcnt + l;
-        ra.dir64 = d64;
-        ra.mat = mat;
-        ra.line = ln;
-        ra.out = refined;
-        if (launch_refine(ra, max_nodes * kNodeCand, s) != cudaSuccess)
-            return err(CVX_ERR_CUDA, "convexify_points_static: refine");
-        CommitArgs ca;
-        ca.tree = tr;
-        ca.NT = NT;
-        ca.level = l;
-        ca.depth = K;
-        ca.beta = beta_k;
-        ca.q_point = qp;
-        ca.q_heap = qh;
-        ca.q_count = cnt + l;
-        ca.nq_point = l + 1 < K ? (int32_t *)(ws + o_qp[l + 1]) : nullptr;
-        ca.nq_heap = l + 1 < K ? (int32_t *)(ws + o_qh[l + 1]) : nullptr;
-        ca.nq_count = cnt + l + 1;
-        ca.cands = cands;
-        ca.refined = refined;
-        ca.dir64 = d64;
-        ca.kappa = line_kappa(mat);
-        ca.mat = mat;
-        ca.line = ln;
-        ca.counters = ctr;
-        if (launch_commit(ca, max_nodes, s) != cudaSuccess)
-            return err(CVX_ERR_CUDA, "convexify_points_static: commit");
-    }
-    LeafArgs la;
-    la.n = n;
-    la.tree = tr;
-    la.NT = NT;
-    la.beta = beta_k;
-    la.W_R = W_R;
-    la.P = P;
-    la.status = status;
-    la.root = nullptr;
-    la.mat = mat;
-    if (launch_leaf(la, s) != cudaSuccess) return err(CVX_ERR_CUDA, "convexify_points_static: leaf");
+    if (pipe_enqueue(pp, warps, grid, s, nullptr) != cudaSuccess)
+        return err(CVX_ERR_CUDA, "convexify_points_static: pipeline launch failed");
     return CVX_OK;
 }

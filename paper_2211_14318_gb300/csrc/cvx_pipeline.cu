@@ -1,0 +1,698 @@
+// cvx_pipeline.cu -- the per-point convexification pipeline over any number
+// of problems (convexify_points is a batch of one).
+//
+// Per lamination level (Eq. 3.3, top-down):
+//   k_scan    FP32 screening: every direction's line is sampled (Eq. 4.4),
+//             bounds on its hull value at t = 0 (Algorithm 1 read at t = 0)
+//             are found and the best directions kept per work item -- the hot
+//             loop; work items are handed out by an atomic counter
+//   k_select  per node: the directions whose FP32 bound lies within the
+//             screening band of the best (any other direction provably loses
+//             in FP64), or none if the node provably does not split
+//   k_refine  per candidate: the line resampled in FP64 and its bridge found
+//             in FP64 -- the decisions whose stability needs it
+//   k_commit  per node: minimum over directions in FP64 (Eq. 4.3), split into
+//             F+- (Algorithm 2), next-level node queue
+// around them:
+//   k_init    problem of each point, roots of the lamination trees, level-0 queue
+//   k_leaf    W^R and P over the tree leaves (Eq. 5.2, Algorithm 3)
+#include <cuda_runtime.h>
+#include <limits.h>
+
+#include "cvx_line.cuh"
+
+namespace cvx {
+
+__device__ __forceinline__ void add_counter(unsigned long long *c, int idx, unsigned long long v) {
+    if (v) atomicAdd(c + idx, v);
+}
+
+// Sorted insertion into a warp's best list (uniform across the warp).
+__device__ __forceinline__ void top_insert(float (&q)[kWarpTop], int (&d)[kWarpTop],
+                                           float &dropped, float v, int dir) {
+    if (!(v < q[kWarpTop - 1])) {
+        dropped = fminf(dropped, v);
+        return;
+    }
+    dropped = fminf(dropped, q[kWarpTop - 1]);
+    int k = kWarpTop - 1;
+#pragma unroll
+    for (int i = kWarpTop - 1; i > 0; --i) {
+        if (v < q[i - 1]) {
+            q[i] = q[i - 1];
+            d[i] = d[i - 1];
+            k = i - 1;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kWarpTop; ++i)
+        if (i == k) {
+            q[i] = v;
+            d[i] = dir;
+        }
+}
+
+// -------------------------------------------------------------------------
+// k_init: one thread per point of any problem.
+// -------------------------------------------------------------------------
+__global__ void k_init(const Pipe P) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (threadIdx.x == 0) {
+        const long long left = P.N - (long long)blockIdx.x * blockDim.x;
+        atomicAdd(P.counters + C_POINTS,
+                  (unsigned long long)(left < (long long)blockDim.x ? left : blockDim.x));
+    }
+    if (p >= P.N) return;
+    int lo = 0, hi = P.n_probs - 1;  // problems are sorted by point_off
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.probs[mid].point_off <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    P.pid[p] = lo;
+    const ProbDesc &pd = P.probs[lo];
+    const long long lp = p - pd.point_off;
+    cvx_node *tr = node_ptr(pd, p, 0);
+    for (int i = 1; i < pd.NT; ++i) {  // unused nodes read as zero
+        cvx_node z = {};
+        tr[i] = z;
+    }
+    const double *Fp = pd.F + 4 * lp;
+    double F[4] = {Fp[0], Fp[1], Fp[2], Fp[3]};
+    const double J = F[0] * F[3] - F[1] * F[2];
+    const bool ok = pd.mat.energy == CVX_ENERGY_DOUBLE_WELL || J > 0.0;
+    cvx_node nd = {};
+    for (int k = 0; k < 4; ++k) nd.F[k] = F[k];
+    nd.weight = 1.0;
+    nd.dir = -1;
+    nd.m_minus = nd.m_plus = pd.line.m0;
+    if (!ok) {
+        nd.w = nan("");
+        nd.h = nd.w;
+        tr[0] = nd;
+        pd.status[lp] = CVX_PT_NONPOS_DET;
+        return;
+    }
+    nd.w = energy64(F, pd.beta[lp], pd.mat);
+    nd.h = nd.w;
+    pd.status[lp] = CVX_PT_OK;
+    if (pd.K == 0) {
+        nd.flags = CVX_NODE_EXISTS | CVX_NODE_LEAF;
+        tr[0] = nd;
+    } else {
+        nd.flags = CVX_NODE_EXISTS;
+        tr[0] = nd;
+        const int pos = atomicAdd(P.cnt, 1);
+        P.qp[0][pos] = (int32_t)p;
+        P.qh[0][pos] = 0;
+    }
+}
+
+// -------------------------------------------------------------------------
+// k_scan: persistent CTAs take work items (node, block of directions) from an
+// atomic counter.  Each warp scans a contiguous run of directions,
+// warm-starting every hull search from the previous direction's bridge, and
+// keeps its best directions by their lower bound.
+// -------------------------------------------------------------------------
+#ifndef CVX_SCAN_MIN_BLOCKS
+#define CVX_SCAN_MIN_BLOCKS 3  // CTAs of 256 threads per SM the registers target
+#endif
+
+template <int EK>
+__global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P, int level) {
+    extern __shared__ float4 smem4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float *sw = reinterpret_cast<float *>(smem4) + warp * P.stride32;
+    __shared__ NodeLine s_nl;
+    __shared__ ProbDesc s_pd;
+    __shared__ long long s_item;
+    __shared__ float s_q[16][kWarpTop];
+    __shared__ int s_d[16][kWarpTop];
+    __shared__ float s_drop[16], s_qhi[16];
+    __shared__ float s_w0;
+    __shared__ unsigned s_hc[16][HC_N];
+
+    const int n_nodes = P.cnt[level];
+    const long long n_items = (long long)n_nodes * P.C;
+    const int32_t *qp = P.qp[level], *qh = P.qh[level];
+    if (lane == 0)
+        for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
+    __syncwarp();
+    HullCounters hc{s_hc[warp]};
+    unsigned long long n_valid = 0, n_lines = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long item = (long long)atomicAdd(P.item_ctr + level, 1ull);
+            s_item = item;
+            if (item < n_items) {
+                const int qi = (int)(item / P.C), ch = (int)(item % P.C);
+                const int p = qp[qi], hi = qh[qi];
+                s_pd = P.probs[P.pid[p]];
+                if (ch < s_pd.chunks) {
+                    const cvx_node *nd = node_ptr(s_pd, p, hi);
+                    double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
+                    s_nl = make_node_line(F, s_pd.beta[p - s_pd.point_off], s_pd.mat);
+                }
+            }
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= n_items) break;
+        const int ch = (int)(item % P.C);
+        if (ch >= s_pd.chunks) continue;
+        const LineSpec ln = s_pd.line;
+        const LineGeom g{ln.L, ln.m0, ln.nfull};
+        float tl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
+        // the per-sample constants in registers; F and cof F stay in shared
+        // memory and are read once per direction
+        NodeLine nl;
+        nl.A0 = s_nl.A0;
+        nl.B1 = s_nl.B1;
+        nl.B2 = s_nl.B2;
+        nl.a1 = s_nl.a1;
+        nl.K1 = s_nl.K1;
+        nl.K2 = s_nl.K2;
+        const int D = s_pd.D, doff = s_pd.dir_off;
+        const int d0 = ch * s_pd.dpi, d1 = min(D, d0 + s_pd.dpi);
+        const int per = (d1 - d0 + nw - 1) / nw;
+        const int jb = d0 + warp * per, je = min(d1, jb + per);
+
+        float tq[kWarpTop];
+        int td[kWarpTop];
+#pragma unroll
+        for (int i = 0; i < kWarpTop; ++i) {
+            tq[i] = INFINITY;
+            td[i] = -1;
+        }
+        float dropped = INFINITY, w0 = 0.0f, qhi_min = INFINITY;
+        int warm_a = -1, warm_b = -1;
+        for (int dj = jb; dj < je; ++dj) {
+            const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + dj]);
+            sample_line<EK>(sw, nl, dl, ln, lane, tl);
+            __syncwarp();
+            const ScreenOut o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
+            __syncwarp();
+            if (lane == 0) {
+                ++n_lines;
+                n_valid += valid_samples(dl, ln, EK);
+            }
+            w0 = o.w0;
+            if (o.a >= 0) {
+                warm_a = o.a;
+                warm_b = o.b;
+            }
+            qhi_min = fminf(qhi_min, o.q_hi);
+            top_insert(tq, td, dropped, o.q_lo, dj);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < kWarpTop; ++i) {
+                s_q[warp][i] = tq[i];
+                s_d[warp][i] = td[i];
+            }
+            s_drop[warp] = dropped;
+            s_qhi[warp] = qhi_min;
+            if (jb < je) s_w0 = w0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // merge the warps' lists (ties -> lower direction index)
+            ItemCands r;
+            float drop = INFINITY, qhi = INFINITY;
+            for (int k = 0; k < nw; ++k) {
+                drop = fminf(drop, s_drop[k]);
+                qhi = fminf(qhi, s_qhi[k]);
+            }
+            int taken[16];
+            for (int k = 0; k < nw; ++k) taken[k] = 0;
+            int n = 0;
+            for (; n < kItemTop; ++n) {
+                int bk = -1;
+                for (int k = 0; k < nw; ++k) {
+                    if (taken[k] >= kWarpTop || s_d[k][taken[k]] < 0) continue;
+                    if (bk < 0 || s_q[k][taken[k]] < s_q[bk][taken[bk]] ||
+                        (s_q[k][taken[k]] == s_q[bk][taken[bk]] &&
+                         s_d[k][taken[k]] < s_d[bk][taken[bk]]))
+                        bk = k;
+                }
+                if (bk < 0) break;
+                r.q[n] = s_q[bk][taken[bk]];
+                r.dir[n] = s_d[bk][taken[bk]];
+                ++taken[bk];
+            }
+            for (int k = 0; k < nw; ++k)
+                if (taken[k] < kWarpTop && s_d[k][taken[k]] >= 0) drop = fminf(drop, s_q[k][taken[k]]);
+            for (int i = n; i < kItemTop; ++i) {
+                r.q[i] = INFINITY;
+                r.dir[i] = -1;
+            }
+            r.n = n;
+            r.w0 = s_w0;
+            r.dropped = drop;
+            r.qhi_min = qhi;
+            r.flags = 0;
+            r.pad = 0;
+            P.items[item] = r;
+        }
+    }
+    if (lane == 0) {
+        const unsigned *c = hc.c;
+        add_counter(P.counters, C_LINES, n_lines);
+        add_counter(P.counters, C_VALID, n_valid);
+        add_counter(P.counters, C_FULL, c[HC_FULL]);
+        add_counter(P.counters, C_RARE, c[HC_RARE]);
+        add_counter(P.counters, C_WSTEPS, c[HC_WSTEPS]);
+        add_counter(P.counters, C_ROUNDS, c[HC_ROUNDS]);
+    }
+}
+
+static size_t scan_smem(int warps, int stride) { return (size_t)warps * stride * sizeof(float); }
+
+template <int EK>
+static int occ_t(int warps, int stride) {
+    const size_t smem = scan_smem(warps, stride);
+    if (cudaFuncSetAttribute(k_scan<EK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_scan<EK>, warps * 32, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int scan_max_blocks_per_sm(int energy, int warps, int stride) {
+    return energy == CVX_ENERGY_NH_DAMAGE ? occ_t<CVX_ENERGY_NH_DAMAGE>(warps, stride)
+                                          : occ_t<CVX_ENERGY_DOUBLE_WELL>(warps, stride);
+}
+
+// -------------------------------------------------------------------------
+// k_select: one thread per queued node.  eps bounds |q_FP32 - q_FP64|
+// (1-Lipschitz in the samples), q_lo <= q_R^FP32 <= q_hi per direction.  The
+// node's FP64 value V = min(W(F), min_R q_R^FP64) is at most
+// min(w0, min_R q_hi) + eps, so a direction with q_lo > min(w0, U) + 2 eps
+// (U = min q_hi) can neither be the FP64 minimiser nor split the node, and if
+// min q_lo > w0 + 2 eps no line splits.  The (at most kNodeCand) directions
+// with the smallest q_lo inside that band are refined in FP64; k_commit checks
+// that no unrefined direction (q_lo >= qcut) can win.
+// -------------------------------------------------------------------------
+__global__ void k_select(const Pipe P, int level) {
+    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= P.cnt[level]) return;
+    const ProbDesc &pd = P.probs[P.pid[P.qp[level][qi]]];
+    const ItemCands *r = P.items + (long long)qi * P.C;
+    const int chunks = pd.chunks;
+    float qmin = INFINITY, drop = INFINITY, U = INFINITY;
+    int fl = 0;
+    const float w0 = r[0].w0;
+    for (int c = 0; c < chunks; ++c) {
+        qmin = fminf(qmin, r[c].q[0]);
+        drop = fminf(drop, r[c].dropped);
+        U = fminf(U, r[c].qhi_min);
+        fl |= r[c].flags;
+    }
+    NodeCands nc;
+    nc.n = 0;
+    nc.eps = kEps32 * fmaxf(pd.kappa_f, fmaxf(fabsf(qmin), fabsf(w0)));
+    float qcut = drop;
+    if (qmin <= w0 + 2.0f * nc.eps) {
+        const float lim = fminf(w0, U) + 2.0f * nc.eps;
+        // merge the items' sorted lists, smallest q first (ties: lower direction)
+        int pos[64];
+        const int nch = chunks < 64 ? chunks : 64;
+        for (int c = 0; c < nch; ++c) pos[c] = 0;
+        while (true) {
+            int bc = -1;
+            for (int c = 0; c < nch; ++c) {
+                if (pos[c] >= r[c].n) continue;
+                if (bc < 0 || r[c].q[pos[c]] < r[bc].q[pos[bc]] ||
+                    (r[c].q[pos[c]] == r[bc].q[pos[bc]] && r[c].dir[pos[c]] < r[bc].dir[pos[bc]]))
+                    bc = c;
+            }
+            if (bc < 0) break;
+            const float q = r[bc].q[pos[bc]];
+            if (!(q <= lim) || nc.n == kNodeCand) {
+                qcut = fminf(qcut, q);
+                break;
+            }
+            nc.dir[nc.n++] = r[bc].dir[pos[bc]];
+            ++pos[bc];
+        }
+        for (int c = nch; c < chunks; ++c) qcut = fminf(qcut, r[c].q[0]);
+    } else {
+        qcut = qmin;
+    }
+    nc.qcut = qcut;
+    nc.flags = fl;
+    P.cands[qi] = nc;
+    if (nc.n) {
+        const int pos = atomicAdd(P.cnt + (P.K + 1) + level, nc.n);
+        for (int c = 0; c < nc.n; ++c) P.work[pos + c] = make_int2(qi, c);
+        atomicAdd(P.counters + C_REFINED, (unsigned long long)nc.n);
+    }
+}
+
+// -------------------------------------------------------------------------
+// FP64 bridge of the left and right sets of one line held in shared memory:
+// supporting-slope iteration with full passes; ties go to the outermost sample
+// (Algorithm 1 keeps the outermost of collinear points).
+// -------------------------------------------------------------------------
+__device__ __forceinline__ void warp_min_dk(double &v, int &k, bool prefer_low) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double v2 = __shfl_xor_sync(kFull, v, o);
+        const int k2 = __shfl_xor_sync(kFull, k, o);
+        if (v2 < v || (v2 == v && (prefer_low ? k2 < k : k2 > k))) {
+            v = v2;
+            k = k2;
+        }
+    }
+}
+
+__device__ void bridge64(const double *sw, int L, int m0, int lane, int &a, int &b) {
+    double s = 0.0;
+    a = b = -1;
+    for (int it = 0; it < 128; ++it) {
+        double bl = INFINITY, br = INFINITY;
+        int kl = INT_MAX, kr = -1;
+        for (int k = lane; k < L; k += 32) {
+            if (k == m0) continue;
+            const double v = sw[k];
+            if (!(v < INFINITY)) continue;
+            const double e = v - s * (double)(k - m0);
+            if (k < m0) {
+                if (e < bl || (e == bl && k < kl)) {
+                    bl = e;
+                    kl = k;
+                }
+            } else if (e < br || (e == br && k > kr)) {
+                br = e;
+                kr = k;
+            }
+        }
+        warp_min_dk(bl, kl, true);
+        warp_min_dk(br, kr, false);
+        if (kl == INT_MAX || kr < 0) {
+            a = b = -1;
+            return;
+        }
+        if (kl == a && kr == b) return;
+        a = kl;
+        b = kr;
+        s = (sw[b] - sw[a]) / (double)(b - a);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
+    extern __shared__ double sm64[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *sw = sm64 + warp * P.stride64;
+    const int nwork = P.cnt[(P.K + 1) + level];
+    const int32_t *qp = P.qp[level], *qh = P.qh[level];
+    for (int w = blockIdx.x * (blockDim.x >> 5) + warp; w < nwork;
+         w += gridDim.x * (blockDim.x >> 5)) {
+        const int2 wk = P.work[w];
+        const int qi = wk.x, c = wk.y;
+        const int p = qp[qi], hi = qh[qi];
+        const ProbDesc &pd = P.probs[P.pid[p]];
+        const LineSpec ln = pd.line;
+        const int dir = P.cands[qi].dir[c];
+        const cvx_node *nd = node_ptr(pd, p, hi);
+        const double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
+        const double *d = P.dir64 + 4 * ((long long)pd.dir_off + dir);
+        const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
+                             __dmul_rn(d[1], d[3])};
+        const double beta = pd.beta[p - pd.point_off];
+        for (int k = lane; k < ln.L; k += 32) sw[k] = sample_w64(F, R, k, ln.m0, ln.h64, beta, pd.mat);
+        __syncwarp();
+        int a, b;
+        bridge64(sw, ln.L, ln.m0, lane, a, b);
+        if (lane == 0) {
+            RefineOut o;
+            o.a = a;
+            o.b = b;
+            o.pad = 0;
+            if (a >= 0) {
+                const double xa = (double)(a - ln.m0), xb = (double)(b - ln.m0);
+                o.q = (xb * sw[a] - xa * sw[b]) / (xb - xa);
+                o.ok = 1;
+            } else {
+                o.q = INFINITY;
+                o.ok = 0;
+            }
+            P.refined[(long long)qi * kNodeCand + c] = o;
+        }
+        __syncwarp();
+    }
+}
+
+// -------------------------------------------------------------------------
+// k_commit: one thread per queued node.  Split points in FP64 with explicit
+// rounding (no contraction): t = (m - m0) h, F+- = F + t R, xi = (m0-m-)/(m+-m-).
+// -------------------------------------------------------------------------
+__global__ void k_commit(const Pipe P, int level) {
+    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= P.cnt[level]) return;
+    const int p = P.qp[level][qi], hi = P.qh[level][qi];
+    const ProbDesc &pd = P.probs[P.pid[p]];
+    const NodeCands &nc = P.cands[qi];
+    cvx_node &nd = *node_ptr(pd, p, hi);
+    nd.flags |= CVX_NODE_SCANNED | (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW));
+    atomicAdd(P.counters + C_NODES, 1ull);
+    const RefineOut *ro = P.refined + (long long)qi * kNodeCand;
+    int bc = -1;
+    double second = INFINITY;
+    for (int c = 0; c < nc.n; ++c) {
+        if (!ro[c].ok) continue;
+        if (bc < 0 || ro[c].q < ro[bc].q || (ro[c].q == ro[bc].q && nc.dir[c] < nc.dir[bc])) {
+            if (bc >= 0) second = fmin(second, ro[bc].q);
+            bc = c;
+        } else {
+            second = fmin(second, ro[c].q);
+        }
+    }
+    const int m0 = pd.line.m0;
+    nd.gap = (float)(second - (bc >= 0 ? ro[bc].q : nd.w));
+    // FP64 node value among the refined directions; an unrefined direction
+    // (FP32 q >= qcut) could only win if qcut - eps reached it
+    const double V = (bc >= 0 && ro[bc].q < nd.w) ? ro[bc].q : nd.w;
+    if (!(((double)nc.qcut - (double)nc.eps) / pd.kappa > V)) {
+        nd.flags |= CVX_NODE_OVERFLOW;
+        atomicAdd(P.counters + C_OVERFLOW, 1ull);
+    }
+    // the centre splits off iff the chord lies strictly below W(F) (FP64)
+    if (bc < 0 || !(ro[bc].q < nd.w)) {
+        nd.dir = bc >= 0 ? nc.dir[bc] : -1;
+        nd.flags |= CVX_NODE_LEAF;
+        return;
+    }
+    const RefineOut b = ro[bc];
+    int fl = CVX_NODE_LAMINATED;
+    if (b.a == 0 || b.b == pd.line.L - 1) fl |= CVX_NODE_EDGE;
+    if (second == b.q) {
+        fl |= CVX_NODE_TIE;
+        atomicAdd(P.counters + C_TIES, 1ull);
+    }
+    nd.flags |= fl;
+    nd.dir = nc.dir[bc];
+    nd.m_minus = b.a;
+    nd.m_plus = b.b;
+    nd.h = b.q;
+    atomicAdd(P.counters + C_LAMINATED, 1ull);
+    const double xi = (double)(m0 - b.a) / (double)(b.b - b.a);
+    nd.xi = xi;
+    const double *d = P.dir64 + 4 * ((long long)pd.dir_off + nd.dir);
+    const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
+                         __dmul_rn(d[1], d[3])};
+    const double tm = __dmul_rn((double)(b.a - m0), pd.line.h64);
+    const double tp = __dmul_rn((double)(b.b - m0), pd.line.h64);
+    const bool leaf_children = level + 1 >= pd.K;
+    const double beta = pd.beta[p - pd.point_off];
+    for (int side = 0; side < 2; ++side) {
+        const int ci = 2 * hi + 1 + side;  // 2i+1: F-, 2i+2: F+
+        cvx_node &c = *node_ptr(pd, p, ci);
+        const double t = side ? tp : tm;
+        double F[4];
+        for (int k = 0; k < 4; ++k) F[k] = __dadd_rn(nd.F[k], __dmul_rn(t, R[k]));
+        for (int k = 0; k < 4; ++k) c.F[k] = F[k];
+        c.weight = side ? __dmul_rn(nd.weight, xi) : __dmul_rn(nd.weight, __dsub_rn(1.0, xi));
+        c.w = energy64(F, beta, pd.mat);
+        c.h = c.w;
+        c.xi = 0.0;
+        c.dir = -1;
+        c.m_minus = c.m_plus = m0;
+        c.gap = 0.0f;
+        c.pad = 0;
+        c.flags = CVX_NODE_EXISTS | (leaf_children ? CVX_NODE_LEAF : 0);
+    }
+    if (!leaf_children) {
+        const int pos = atomicAdd(P.cnt + level + 1, 2);
+        P.qp[level + 1][pos] = p;
+        P.qh[level + 1][pos] = 2 * hi + 1;
+        P.qp[level + 1][pos + 1] = p;
+        P.qh[level + 1][pos + 1] = 2 * hi + 2;
+    }
+}
+
+// -------------------------------------------------------------------------
+// k_leaf: W^R = sum over leaves of (path weight) W(F_leaf), same for P
+// (Algorithm 3 with the recursion unrolled over the heap).
+// -------------------------------------------------------------------------
+__global__ void k_leaf(const Pipe P) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.N) return;
+    const ProbDesc &pd = P.probs[P.pid[p]];
+    const long long lp = p - pd.point_off;
+    const cvx_node *tr = node_ptr(pd, p, 0);
+    int st = pd.status[lp];
+    if (st & CVX_PT_NONPOS_DET) {
+        pd.W_R[lp] = nan("");
+        for (int k = 0; k < 4; ++k) pd.P[4 * lp + k] = nan("");
+        if (pd.root) {
+            cvx_laminate z = {};
+            z.dir = -1;
+            pd.root[lp] = z;
+        }
+        return;
+    }
+    const double beta = pd.beta[lp];
+    double W = 0.0, Pv[4] = {0.0, 0.0, 0.0, 0.0};
+    int fl = 0;
+    for (int i = 0; i < pd.NT; ++i) {
+        const cvx_node &nd = tr[i];
+        if (!(nd.flags & CVX_NODE_EXISTS)) continue;
+        fl |= nd.flags;
+        if (nd.flags & CVX_NODE_LAMINATED) continue;
+        double F[4] = {nd.F[0], nd.F[1], nd.F[2], nd.F[3]};
+        double Pl[4];
+        stress64(F, beta, pd.mat, Pl);
+        W += nd.weight * energy64(F, beta, pd.mat);
+        for (int k = 0; k < 4; ++k) Pv[k] += nd.weight * Pl[k];
+    }
+    pd.W_R[lp] = W;
+    for (int k = 0; k < 4; ++k) pd.P[4 * lp + k] = Pv[k];
+    if (fl & CVX_NODE_TIE) st |= CVX_PT_TIE;
+    if (fl & CVX_NODE_EDGE) st |= CVX_PT_EDGE;
+    if (fl & CVX_NODE_ITER_CAP) st |= CVX_PT_ITER_CAP;
+    if (fl & CVX_NODE_OVERFLOW) st |= CVX_PT_OVERFLOW;
+    pd.status[lp] = st;
+    if (pd.root) {
+        cvx_laminate Lm;
+        const cvx_node &r0 = tr[0];
+        Lm.laminated = (r0.flags & CVX_NODE_LAMINATED) ? 1 : 0;
+        Lm.dir = r0.dir;
+        Lm.m_minus = r0.m_minus;
+        Lm.m_plus = r0.m_plus;
+        Lm.xi = r0.xi;
+        Lm.h = r0.h;
+        for (int k = 0; k < 4; ++k) {
+            Lm.F_plus[k] = Lm.laminated ? tr[2].F[k] : r0.F[k];
+            Lm.F_minus[k] = Lm.laminated ? tr[1].F[k] : r0.F[k];
+        }
+        pd.root[lp] = Lm;
+    }
+}
+
+// -------------------------------------------------------------------------
+// Workspace layout and the enqueueing of one run.
+// -------------------------------------------------------------------------
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_probs) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = up256(off + bytes);
+        return o;
+    };
+    const size_t maxq = K > 0 ? ((size_t)N << (K - 1)) : 0;
+    const size_t o_probs = take(sizeof(ProbDesc) * (size_t)n_probs);
+    const size_t o_pid = take(sizeof(int32_t) * (size_t)N);
+    size_t o_qp[kMaxDepth], o_qh[kMaxDepth];
+    for (int l = 0; l < K; ++l) {
+        o_qp[l] = take(sizeof(int32_t) * ((size_t)N << l));
+        o_qh[l] = take(sizeof(int32_t) * ((size_t)N << l));
+    }
+    const size_t o_cnt = take(sizeof(int32_t) * 2 * (K + 1));
+    const size_t o_ictr = take(sizeof(unsigned long long) * (K + 1));
+    const size_t o_items = take(sizeof(ItemCands) * maxq * C);
+    const size_t o_cands = take(sizeof(NodeCands) * maxq);
+    const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
+    const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
+    if (pp) {
+        Pipe &p = *pp;
+        p.probs = (const ProbDesc *)(ws + o_probs);
+        p.pid = (int32_t *)(ws + o_pid);
+        for (int l = 0; l < kMaxDepth; ++l) {
+            p.qp[l] = l < K ? (int32_t *)(ws + o_qp[l]) : nullptr;
+            p.qh[l] = l < K ? (int32_t *)(ws + o_qh[l]) : nullptr;
+        }
+        p.cnt = (int32_t *)(ws + o_cnt);
+        p.item_ctr = (unsigned long long *)(ws + o_ictr);
+        p.items = (ItemCands *)(ws + o_items);
+        p.cands = (NodeCands *)(ws + o_cands);
+        p.work = (int2 *)(ws + o_work);
+        p.refined = (RefineOut *)(ws + o_ref);
+    }
+    return off;
+}
+
+size_t pipe_bytes(long long N, int K, int C, int n_probs) {
+    return pipe_carve(nullptr, nullptr, N, K, C, n_probs);
+}
+
+void pipe_layout(Pipe &p, char *ws) { pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs); }
+
+template <int EK>
+static cudaError_t launch_scan_t(const Pipe &p, int level, int warps, int grid, cudaStream_t s) {
+    const size_t smem = scan_smem(warps, p.stride32);
+    cudaError_t e = cudaFuncSetAttribute(k_scan<EK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_scan<EK><<<grid, warps * 32, smem, s>>>(p, level);
+    return cudaGetLastError();
+}
+
+cudaError_t pipe_enqueue(const Pipe &p, int warps, int grid, cudaStream_t s, cudaEvent_t *ev) {
+    cudaError_t e;
+    if (p.N == 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * 2 * (p.K + 1), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.item_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
+        cudaSuccess)
+        return e;
+    k_init<<<(unsigned)((p.N + 255) / 256), 256, 0, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int l = 0; l < p.K; ++l) {
+        const long long max_nodes = p.N << l;
+        if (ev && (e = cudaEventRecord(ev[2 * l], s)) != cudaSuccess) return e;
+        e = p.energy == CVX_ENERGY_NH_DAMAGE
+                ? launch_scan_t<CVX_ENERGY_NH_DAMAGE>(p, l, warps, grid, s)
+                : launch_scan_t<CVX_ENERGY_DOUBLE_WELL>(p, l, warps, grid, s);
+        if (e != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecord(ev[2 * l + 1], s)) != cudaSuccess) return e;
+        const unsigned nb = (unsigned)((max_nodes + 127) / 128);
+        k_select<<<nb, 128, 0, s>>>(p, l);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const long long want = (max_nodes * kNodeCand + 3) / 4;
+        const unsigned rg = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+        const size_t rsm = (size_t)4 * p.stride64 * sizeof(double);
+        if ((e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)rsm)) != cudaSuccess)
+            return e;
+        k_refine<<<rg, 128, rsm, s>>>(p, l);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_commit<<<nb, 128, 0, s>>>(p, l);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_leaf<<<(unsigned)((p.N + 127) / 128), 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace cvx

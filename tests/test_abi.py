@@ -49,6 +49,7 @@ def test_struct_layouts_match_binding(cvxlib):
     assert cvxlib.cvx_struct_size(1) == api.NODE_DTYPE.itemsize
     assert cvxlib.cvx_struct_size(2) == api.LAMINATE_DTYPE.itemsize
     assert cvxlib.cvx_struct_size(3) == ctypes.sizeof(api._Stats)
+    assert cvxlib.cvx_struct_size(4) == ctypes.sizeof(api._Problem)
     assert cvxlib.cvx_struct_size(7) == -1
 
 
@@ -95,6 +96,37 @@ def test_null_handle_and_arrays_rejected(cvxlib):
     assert cvxlib.cvx_set_tuning(None, 8, 0) == -1
     assert cvxlib.cvx_energy(None, None, 1, None, None, None, None, None) == -1
     assert "params" in _err(cvxlib)
+
+
+def _problems(*params_and_n):
+    from paper_2211_14318_gb300 import api
+
+    arr = (api._Problem * len(params_and_n))()
+    for q, (p, n) in zip(arr, params_and_n):
+        q.params = p.c()
+        q.n = n
+    return arr
+
+
+def test_batch_validation_before_cuda(cvxlib):
+    from paper_2211_14318_gb300 import api
+
+    ok = api.Params(line_points=201, depth=2)
+    assert cvxlib.convexify_batch(None, 0, None, None) == -1
+    assert "problems" in _err(cvxlib)
+    bad = api.Params(line_points=200)
+    assert cvxlib.convexify_batch(None, 2, _problems((ok, 0), (bad, 0)), None) == -1
+    assert "line_points" in _err(cvxlib)
+    dw = api.Params(energy=api.ENERGY_DOUBLE_WELL)
+    assert cvxlib.convexify_batch(None, 2, _problems((ok, 0), (dw, 0)), None) == -1
+    assert "same energy" in _err(cvxlib)
+    assert cvxlib.convexify_batch(None, 1, _problems((ok, 5)), None) == -1
+    assert "NULL array" in _err(cvxlib)
+    assert cvxlib.convexify_batch(None, 1, _problems((ok, -1)), None) == -1
+    assert cvxlib.convexify_batch(None, 1, _problems((ok, 0)), None) == -1
+    assert "handle" in _err(cvxlib)
+    w, d, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert cvxlib.cvx_get_batch_tuning(None, ctypes.byref(w), ctypes.byref(d), ctypes.byref(c)) == -1
 
 
 def test_create_without_gpu_fails_cleanly(cvxlib):

@@ -1,0 +1,133 @@
+"""convexify_batch: several problems of uneven sizes and different parameters
+in one pipeline run (a CUDA graph), against the FP64 oracle per problem and
+against convexify_points; graph replay; the launch-shape autotuner."""
+import os
+
+import numpy as np
+import pytest
+
+from test_gpu_parity import MAT, TIE, _omat, _rel, cv  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+HARD = 2 | 16  # status bits TIE | OVERFLOW
+
+
+def _problems(orc):
+    from paper_2211_14318_gb300 import api, inputs
+
+    vecs = [(1, 0), (0, 1), (1, 1), (1, -1)]
+    r11 = np.array([[a[0], a[1], b[0], b[1]] for a in vecs for b in vecs], dtype=np.float64)
+    mat = _omat(orc)
+    specs = [
+        (api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT), 53, 0),
+        (api.Params(n_theta_a=7, n_theta_b=9, line_points=77, t_half=0.6, depth=3, **MAT), 29, 1),
+        (api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT), 0, 2),
+        (api.Params(line_points=101, t_half=0.4, depth=1, dirs=r11, **MAT), 17, 3),
+        (api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=0, **MAT), 5, 4),
+        (api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT), 31, 5),
+    ]
+    out = []
+    for p, n, seed in specs:
+        F, Fp = inputs.material_points(max(n, 1), seed=40 + seed, lam_hi=1.9)
+        F = F[:n]
+        beta = orc.history_update(mat, Fp)[:n]
+        out.append((p, F, beta))
+    return out
+
+
+def _oracle(orc, p, F, beta):
+    from paper_2211_14318_gb300 import api
+
+    mat = _omat(orc, energy=p.energy)
+    dirs = p.dirs if p.dirs is not None else orc.angle_directions(p.n_theta_a, p.n_theta_b)
+    sc = orc.Scan(dirs, p.line_points, p.t_half, p.depth, round32=False)
+    WRo, Po, tro, sto = orc.convexify(mat, sc, F, beta)
+    untied = np.array([all(tro[k, i]["margin"] > TIE for i in range(tro.shape[1])
+                           if tro[k, i]["flags"] & orc.SCANNED) for k in range(F.shape[0])],
+                      dtype=bool)
+    return WRo, Po, sto, untied
+
+
+def test_batch_matches_oracle_and_single_calls(cv, orc):
+    probs = _problems(orc)
+    res = cv.convexify_batch(probs)
+    for (p, F, beta), r in zip(probs, res):
+        n = F.shape[0]
+        WR, P, st = (r["W_R"].cpu().numpy(), r["P"].cpu().numpy(), r["status"].cpu().numpy())
+        assert WR.shape == (n,)
+        if n == 0:
+            continue
+        WRo, Po, sto, u = _oracle(orc, p, F, beta)
+        assert np.all((st & 1) == (sto & 1))
+        assert np.max(_rel(WR[u], WRo[u]), initial=0) < 1e-6
+        Pn = np.linalg.norm(Po, axis=1)
+        assert np.max(np.linalg.norm(P[u] - Po[u], axis=1) / (1e-8 + Pn[u]), initial=0) < 1e-5
+        one = cv.convexify_points(p, F, beta)
+        st1 = one["status"].cpu().numpy()
+        clean = ((st | st1) & HARD) == 0
+        np.testing.assert_array_equal(WR[clean], one["W_R"].cpu().numpy()[clean])
+        np.testing.assert_array_equal(P[clean], one["P"].cpu().numpy()[clean])
+        if p.depth == 0:
+            W0, P0 = cv.energy(p, F, beta)
+            np.testing.assert_allclose(WR, W0.cpu().numpy(), rtol=1e-11, atol=0)
+
+
+def test_graph_replay_reads_current_inputs(cv, orc):
+    """Second call with the same tensors replays the captured graph; the graph
+    reads F and beta_k at replay time, so new values in the same tensors give
+    the new results."""
+    import torch
+
+    from paper_2211_14318_gb300 import inputs
+
+    probs = _problems(orc)
+    dev = torch.device("cuda", 0)
+    tens = [(p, torch.as_tensor(F, device=dev), torch.as_tensor(b, device=dev)) for p, F, b in probs]
+    outs = cv.convexify_batch(tens)
+    first = [o["W_R"].clone() for o in outs]
+    cv.convexify_batch(tens, outs=outs)
+    for a, o in zip(first, outs):
+        assert torch.equal(a, o["W_R"])
+    mat = _omat(orc)
+    for k, (p, F, b) in enumerate(tens):
+        if F.shape[0] == 0:
+            continue
+        F2, Fp2 = inputs.material_points(F.shape[0], seed=90 + k, lam_hi=1.9)
+        F.copy_(torch.as_tensor(F2))
+        b.copy_(torch.as_tensor(orc.history_update(mat, Fp2)))
+    outs2 = cv.convexify_batch(tens, outs=outs)
+    assert all(o2["W_R"].data_ptr() == o["W_R"].data_ptr() for o, o2 in zip(outs, outs2))
+    for (p, F, b), o in zip(tens, outs2):
+        if F.shape[0] == 0:
+            continue
+        one = cv.convexify_points(p, F, b)
+        st, st1 = o["status"].cpu().numpy(), one["status"].cpu().numpy()
+        clean = ((st | st1) & HARD) == 0
+        assert clean.mean() > 0.5
+        np.testing.assert_array_equal(o["W_R"].cpu().numpy()[clean], one["W_R"].cpu().numpy()[clean])
+
+
+def test_autotuner_choice_and_cache_file(orc, tmp_path):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2211_14318_gb300 import api
+
+    path = tmp_path / "tune.json"
+    os.environ["CVX_AUTOTUNE_CACHE"] = str(path)
+    try:
+        probs = _problems(orc)
+        c1 = api.Convexifier(0)
+        c1.convexify_batch(probs)
+        w, cap, cached = c1.batch_tuning()
+        assert w in (4, 8) and cap in (0, 256, 1024) and not cached
+        c1.close()
+        assert path.exists() and f"[{w}, {cap}]" in path.read_text()
+        c2 = api.Convexifier(0)
+        c2.convexify_batch(probs)
+        assert c2.batch_tuning() == (w, cap, True)
+        c2.close()
+    finally:
+        del os.environ["CVX_AUTOTUNE_CACHE"]
