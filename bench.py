@@ -143,10 +143,17 @@ def fp32_peak_tflops(torch, dev):
     return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz, src
 
 
+SCAN_SOURCES = ("cvx_pipeline.cu", "cvx_bridge.cuh", "cvx_device.cuh", "cvx_line.cuh",
+                "cvx_internal.h")
+
+
 def scan_source_hash():
+    """Hash of the sources the line-scan kernel is compiled from."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2211_14318_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    c = os.path.join(ROOT, "paper_2211_14318_gb300", "csrc")
+    for f in SCAN_SOURCES:
+        h.update(open(os.path.join(c, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "convexify.h"), "rb").read())
     return h.hexdigest()[:16]
 
 

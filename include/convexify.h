@@ -101,18 +101,31 @@ typedef struct cvx_params {
     int32_t n_dirs;
     int32_t line_points; /* odd, 3 <= L <= 2079                          */
     int32_t depth;
-    int32_t flags; /* reserved, must be 0                                */
+    int32_t flags; /* CVX_FLAG_* bits (0: the plain grid method)        */
     int32_t reserved;
 } cvx_params;
+
+/* cvx_params.flags.
+ * CVX_FLAG_REFINE_NEWTON: after a node's split is decided on the grid, refine
+ * its ends t-, t+ by FP64 Newton on the common-tangent conditions
+ * g'(t-) = g'(t+) = (g(t+) - g(t-)) / (t+ - t-), g(t) = W(F + t R*), seeded by
+ * the grid bridge, at most 8 iterations.  The refinement is kept only if it
+ * converged with both ends inside the line window and its chord value at 0 is
+ * not above the grid bridge's; the node is then flagged CVX_NODE_NEWTON and
+ * its children, xi and h use the refined ends.  The paper takes laminates from
+ * its grids only; this is an addition (the direction is still the grid's). */
+enum cvx_param_flags { CVX_FLAG_REFINE_NEWTON = 1 };
 
 /* Node of the per-point lamination tree (Sec. 4.3, Algorithm 2), heap layout:
  * node i has children 2i+1 (F-) and 2i+2 (F+); 2^{K+1}-1 nodes per point. */
 typedef struct cvx_node {
     double F[4];     /* deformation gradient of this node                     */
     double w;        /* W(F), FP64                                            */
-    double h;        /* hull of the FP32 samples at t = 0 along the chosen
-                        direction (= W(F) sample if the node does not split)  */
-    double xi;       /* weight of F+ in this node's split, (m0-m-)/(m+-m-)    */
+    double h;        /* node value: FP64 bridge value at t = 0 along the chosen
+                        direction (the refined chord value if CVX_NODE_NEWTON);
+                        W(F) if the node does not split                       */
+    double xi;       /* weight of F+ in this node's split, (m0-m-)/(m+-m-)
+                        (-t-/(t+ - t-) with the refined ends)                 */
     double weight;   /* product of split weights from the root                */
     int32_t dir;     /* chosen direction index, -1 if the node was not scanned */
     int32_t m_minus; /* sample index of F- on the chosen line (0..L-1)         */
@@ -128,7 +141,10 @@ enum cvx_node_flags {
     CVX_NODE_LAMINATED = 4,
     CVX_NODE_LEAF = 8,
     CVX_NODE_TIE = 16,
-    CVX_NODE_EDGE = 32
+    CVX_NODE_EDGE = 32,
+    CVX_NODE_ITER_CAP = 64,  /* a hull search hit its iteration cap          */
+    CVX_NODE_OVERFLOW = 128, /* decision not certified against every direction */
+    CVX_NODE_NEWTON = 256    /* split refined by CVX_FLAG_REFINE_NEWTON        */
 };
 
 /* Root laminate of a point: direction a (x) b = dirs[dir], volume fraction xi

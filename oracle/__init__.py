@@ -36,7 +36,7 @@ NODE_DTYPE = np.dtype(
         ("flags", "<i4"),
     ]
 )
-EXISTS, SCANNED, LAMINATED, LEAF = 1, 2, 4, 8
+EXISTS, SCANNED, LAMINATED, LEAF, NEWTON = 1, 2, 4, 8, 16
 
 
 class _Material(ctypes.Structure):
@@ -58,6 +58,8 @@ class _Scan(ctypes.Structure):
         ("t_half", ctypes.c_double),
         ("depth", ctypes.c_int32),
         ("round32", ctypes.c_int32),
+        ("newton", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -96,6 +98,10 @@ def lib() -> ctypes.CDLL:
         L.orc_stress.restype = None
         L.orc_stress.argtypes = [vp, vp, d, vp]
         L.orc_psi0_F.restype = d
+        L.orc_tangent.argtypes = [vp, vp, d, vp]
+        L.orc_tangent.restype = None
+        L.orc_newton_tangent.argtypes = [vp, vp, d, vp, d, d, d, d, vp, vp, vp]
+        L.orc_newton_tangent.restype = i32
         L.orc_psi0_F.argtypes = [vp, vp]
         L.orc_history_update.restype = None
         L.orc_history_update.argtypes = [vp, i64, vp, vp, vp]
@@ -166,6 +172,26 @@ def stress(mat: Material, F, beta_k: float) -> np.ndarray:
     return P
 
 
+def tangent(mat: Material, F, beta_k: float) -> np.ndarray:
+    """A = d^2 W / dF dF as a 4 x 4 matrix over the row-major entries of F."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    A = np.zeros(16)
+    lib().orc_tangent(mat.ref, _p(F), beta_k, _p(A))
+    return A.reshape(4, 4)
+
+
+def newton_tangent(mat: Material, F, beta_k: float, R, t_half: float, tm: float, tp: float,
+                   h_grid: float):
+    """Common-tangent Newton refinement of a split; (t-, t+, chord value at 0)
+    or None when the refinement is not accepted."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(4)
+    out = np.zeros(3)
+    ok = lib().orc_newton_tangent(mat.ref, _p(F), beta_k, _p(R), t_half, tm, tp, h_grid,
+                                  _p(out[0:]), _p(out[1:]), _p(out[2:]))
+    return (out[0], out[1], out[2]) if ok else None
+
+
 def psi0_F(mat: Material, F) -> float:
     F = np.ascontiguousarray(F, dtype=np.float64).reshape(4)
     return lib().orc_psi0_F(mat.ref, _p(F))
@@ -193,13 +219,15 @@ def angle_directions(Na: int, Nb: int) -> np.ndarray:
 class Scan:
     """Direction set, line (L samples on [-t_half, t_half]) and depth K."""
 
-    def __init__(self, dirs: np.ndarray, L: int, t_half: float, depth: int, round32: bool = False):
+    def __init__(self, dirs: np.ndarray, L: int, t_half: float, depth: int, round32: bool = False,
+                 newton: bool = False):
         self.dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 4)
         self.L, self.t_half, self.depth, self.round32 = int(L), float(t_half), int(depth), bool(round32)
+        self.newton = bool(newton)
         self._c = _Scan(
             self.dirs.shape[0], self.L,
             self.dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-            self.t_half, self.depth, int(self.round32),
+            self.t_half, self.depth, int(self.round32), int(self.newton), 0,
         )
 
     @property

@@ -50,6 +50,8 @@ typedef struct {
     double t_half;      /* line covers t in [-t_half, t_half]            */
     int32_t depth;      /* lamination depth K                            */
     int32_t round32;    /* 1: hull decisions on samples rounded to FP32  */
+    int32_t newton;     /* 1: refine each split by common-tangent Newton */
+    int32_t pad;
 } orc_scan;
 
 /* One node of the per-point lamination tree in heap layout: node i has
@@ -67,7 +69,7 @@ typedef struct {
     int32_t flags;   /* bit0 exists, bit1 scanned, bit2 laminated, bit3 leaf */
 } orc_node;
 
-enum { ORC_EXISTS = 1, ORC_SCANNED = 2, ORC_LAMINATED = 4, ORC_LEAF = 8 };
+enum { ORC_EXISTS = 1, ORC_SCANNED = 2, ORC_LAMINATED = 4, ORC_LEAF = 8, ORC_NEWTON = 16 };
 enum { ORC_OK = 0, ORC_NONPOS_DET = 1 };
 
 /* ------------------------------------------------------------------------- */
@@ -174,6 +176,53 @@ void orc_stress(const orc_material *m, const double F[4], double beta_k, double 
     double lj = log(J);
     for (int i = 0; i < 4; ++i)
         P[i] = g * (m->mu * F[i] - m->mu * FiT[i] + m->lam * lj * FiT[i]);
+}
+
+/* Tangent A = d^2 W / dF dF (4 x 4, A[4 i + k] = d P_i / d F_k, F flattened
+ * row-major).  Differentiating P = g(s) dpsi0/dF with g = 1 - D(max(s, beta_k)):
+ *   A = g d^2 psi0/dF^2 + [s > beta_k] g'(s) dpsi0/dF (x) dpsi0/dF,
+ * g'(s) = -D'(s) = -(D_inf / D_0) exp(-s / D_0), and for Eq. (2.3)
+ *   d^2 psi0 / dF_iJ dF_kL = mu d_ik d_JL + (mu - lam ln J) Fit_iL Fit_kJ
+ *                           + lam Fit_iJ Fit_kL,     Fit = F^{-T},
+ * from d(F^{-T})_iJ / dF_kL = -Fit_iL Fit_kJ and d ln J / dF = F^{-T}. */
+void orc_tangent(const orc_material *m, const double F[4], double beta_k, double A[16])
+{
+    if (m->energy == 1) {
+        for (int i = 0; i < 16; ++i)
+            A[i] = 0.0;
+        A[0] = 12.0 * F[0] * F[0] - 4.0;
+        A[5] = 2.0;
+        A[10] = 2.0;
+        A[15] = 2.0;
+        return;
+    }
+    double I1, J;
+    nh_invariants(F, &I1, &J);
+    if (!(J > 0.0)) {
+        for (int i = 0; i < 16; ++i)
+            A[i] = NAN;
+        return;
+    }
+    double s = orc_psi0_nh(I1, J, m->mu, m->lam);
+    double beta = s > beta_k ? s : beta_k;
+    double g = 1.0 - orc_damage(beta, m->Dinf, m->D0);
+    double lj = log(J);
+    double Fit[2][2] = {{F[3] / J, -F[2] / J}, {-F[1] / J, F[0] / J}};
+    double dpsi[4];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            dpsi[2 * i + j] = m->mu * F[2 * i + j] - m->mu * Fit[i][j] + m->lam * lj * Fit[i][j];
+    double gp = s > beta_k ? -(m->Dinf / m->D0) * exp(-s / m->D0) : 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int J1 = 0; J1 < 2; ++J1)
+            for (int k = 0; k < 2; ++k)
+                for (int L1 = 0; L1 < 2; ++L1) {
+                    double d2 = (i == k && J1 == L1 ? m->mu : 0.0)
+                              + (m->mu - m->lam * lj) * Fit[i][L1] * Fit[k][J1]
+                              + m->lam * Fit[i][J1] * Fit[k][L1];
+                    A[4 * (2 * i + J1) + (2 * k + L1)] =
+                        g * d2 + gp * dpsi[2 * i + J1] * dpsi[2 * k + L1];
+                }
 }
 
 /* History update between load steps, Eq. (2.5): beta_new = max(beta_k, psi0(F)). */
@@ -430,6 +479,91 @@ int32_t orc_scan_node(const orc_material *mat, const orc_scan *sc, const double 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Optional refinement of a split: common tangent by Newton (a reading: the  */
+/* paper solves for laminates on grids only)                                 */
+/* ------------------------------------------------------------------------- */
+
+/* g(t) = W(F + t R) and its first two derivatives g' = P : R, g'' = R : A : R. */
+static void line_derivs(const orc_material *m, const double F[4], double beta_k,
+                        const double R[4], double t, double *g, double *g1, double *g2)
+{
+    double G[4], P[4], A[16];
+    for (int i = 0; i < 4; ++i)
+        G[i] = F[i] + t * R[i];
+    *g = orc_energy(m, G, beta_k);
+    orc_stress(m, G, beta_k, P);
+    orc_tangent(m, G, beta_k, A);
+    *g1 = 0.0;
+    *g2 = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        *g1 += P[i] * R[i];
+        for (int k = 0; k < 4; ++k)
+            *g2 += R[i] * A[4 * i + k] * R[k];
+    }
+}
+
+/* Chord value at t = 0 of the segment from (t-, g(t-)) to (t+, g(t+)). */
+static double chord_at_zero(double tm, double gm, double tp, double gp)
+{
+    return gm + (gp - gm) * (0.0 - tm) / (tp - tm);
+}
+
+/* Newton on the common-tangent conditions of the split (t-, t+) along R:
+ *   f1 = g'(t-) - g'(t+) = 0,
+ *   f2 = g'(t-) (t+ - t-) - (g(t+) - g(t-)) = 0,
+ * i.e. one line touches g at both ends (the stationarity conditions of the
+ * chord value at 0 over continuous t-, t+).  Seeded by the grid bridge, at
+ * most 8 iterations.  Accepted (returns 1) only if it converged with
+ * -t_half <= t- < 0 < t+ <= t_half, det F > 0 at both ends and a chord value
+ * at 0 not above the grid's; otherwise returns 0 and leaves the outputs. */
+int32_t orc_newton_tangent(const orc_material *m, const double F[4], double beta_k,
+                           const double R[4], double t_half, double tm0, double tp0,
+                           double h_grid, double *tm_out, double *tp_out, double *h_out)
+{
+    double tm = tm0, tp = tp0;
+    int converged = 0;
+    for (int it = 0; it < 8; ++it) {
+        double gm, gm1, gm2, gp, gp1, gp2;
+        line_derivs(m, F, beta_k, R, tm, &gm, &gm1, &gm2);
+        line_derivs(m, F, beta_k, R, tp, &gp, &gp1, &gp2);
+        double f1 = gm1 - gp1;
+        double f2 = gm1 * (tp - tm) - (gp - gm);
+        /* Jacobian d(f1, f2) / d(t-, t+) */
+        double j11 = gm2, j12 = -gp2;
+        double j21 = gm2 * (tp - tm), j22 = gm1 - gp1;
+        double det = j11 * j22 - j12 * j21;
+        if (!(fabs(det) > 0.0) || !isfinite(det))
+            return 0;
+        double dm = (-f1 * j22 + f2 * j12) / det;
+        double dp = (-f2 * j11 + f1 * j21) / det;
+        tm += dm;
+        tp += dp;
+        if (!isfinite(tm) || !isfinite(tp))
+            return 0;
+        if (fabs(dm) <= 1e-13 * (1.0 + fabs(tm)) && fabs(dp) <= 1e-13 * (1.0 + fabs(tp))) {
+            converged = 1;
+            break;
+        }
+    }
+    if (!converged)
+        return 0;
+    if (!(tm >= -t_half && tm < 0.0 && tp > 0.0 && tp <= t_half))
+        return 0;
+    double gm = 0.0, gp = 0.0, d1, d2;
+    line_derivs(m, F, beta_k, R, tm, &gm, &d1, &d2);
+    line_derivs(m, F, beta_k, R, tp, &gp, &d1, &d2);
+    if (!isfinite(gm) || !isfinite(gp))
+        return 0;
+    double h = chord_at_zero(tm, gm, tp, gp);
+    if (!(h <= h_grid))
+        return 0;
+    *tm_out = tm;
+    *tp_out = tp;
+    *h_out = h;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Lamination to depth K, Eq. (3.3), and derivative, Eq. (5.2)/Algorithm 3   */
 /* ------------------------------------------------------------------------- */
 
@@ -476,6 +610,15 @@ static void build_tree(const orc_material *mat, const orc_scan *sc, double beta_
     double tm = (double)(mm - m0) * hstep, tp = (double)(mp - m0) * hstep;
     /* Algorithm 2: xi = |F - F-|_1 / |F+ - F-|_1 = (m0 - m-)/(m+ - m-) */
     nd->xi = (double)(m0 - mm) / (double)(mp - mm);
+    double tmN, tpN, hN;
+    if (sc->newton &&
+        orc_newton_tangent(mat, nd->F, beta_k, R, sc->t_half, tm, tp, h, &tmN, &tpN, &hN)) {
+        tm = tmN;
+        tp = tpN;
+        nd->h = hN;
+        nd->xi = (0.0 - tm) / (tp - tm);
+        nd->flags |= ORC_NEWTON;
+    }
     orc_node *cm = &tree[2 * i + 1], *cp = &tree[2 * i + 2];
     for (int k = 0; k < 4; ++k) {
         cm->F[k] = nd->F[k] + tm * R[k];

@@ -23,6 +23,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NOT_TRAI
 ENERGY_NH_DAMAGE, ENERGY_DOUBLE_WELL = 0, 1
 PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP, PT_OVERFLOW = 1, 2, 4, 8, 16
 NODE_EXISTS, NODE_SCANNED, NODE_LAMINATED, NODE_LEAF, NODE_TIE, NODE_EDGE = 1, 2, 4, 8, 16, 32
+NODE_ITER_CAP, NODE_OVERFLOW, NODE_NEWTON = 64, 128, 256
+FLAG_REFINE_NEWTON = 1
 
 NODE_DTYPE = np.dtype([
     ("F", "<f8", (4,)), ("w", "<f8"), ("h", "<f8"), ("xi", "<f8"), ("weight", "<f8"),
@@ -134,13 +136,15 @@ class Params:
     depth: int = 2
     energy: int = ENERGY_NH_DAMAGE
     dirs: Optional[np.ndarray] = None  # custom (n, 4) rows (a1, a2, b1, b2)
+    newton: bool = False  # CVX_FLAG_REFINE_NEWTON
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
         p = _Params()
         p.mu, p.lambda_L, p.D_inf, p.D0, p.t_half = self.mu, self.lambda_L, self.D_inf, self.D0, self.t_half
         p.energy, p.n_theta_a, p.n_theta_b = self.energy, self.n_theta_a, self.n_theta_b
-        p.line_points, p.depth, p.flags, p.reserved = self.line_points, self.depth, 0, 0
+        p.line_points, p.depth, p.reserved = self.line_points, self.depth, 0
+        p.flags = FLAG_REFINE_NEWTON if self.newton else 0
         if self.dirs is not None:
             d = np.ascontiguousarray(self.dirs, dtype=np.float64).reshape(-1, 4)
             self._keep = [d]

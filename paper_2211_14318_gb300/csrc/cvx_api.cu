@@ -60,7 +60,7 @@ int check_params(const cvx_params *p, bool need_line) {
             return fail(CVX_ERR_INVALID_ARG,
                         "material out of range (mu > 0, lambda >= 0, 0 <= D_inf < 1, D0 > 0)");
     }
-    if (p->flags != 0) return fail(CVX_ERR_INVALID_ARG, "flags must be 0");
+    if (p->flags & ~CVX_FLAG_REFINE_NEWTON) return fail(CVX_ERR_INVALID_ARG, "unknown flags");
     if (!need_line) return CVX_OK;
     if (p->line_points < 3 || p->line_points > 2079 || (p->line_points % 2) == 0)
         return fail(CVX_ERR_INVALID_ARG, "line_points must be odd in [3, 2079], got %d",
@@ -368,6 +368,7 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     pd.kappa_f = (float)pd.kappa;
     pd.D = h->D;
     pd.dir_off = 0;
+    pd.flags = p->flags;
     pd.K = p->depth;
     pd.NT = (1 << (p->depth + 1)) - 1;
     pd.dpi = h->tune_dpi > 0 ? std::min(h->tune_dpi, pd.D)

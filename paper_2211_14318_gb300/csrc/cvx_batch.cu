@@ -146,6 +146,7 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
         pd.kappa_f = (float)pd.kappa;
         pd.D = p.dirs ? p.n_dirs : p.n_theta_a * p.n_theta_b;
         pd.dir_off = dir_off[i];
+        pd.flags = p.flags;
         pd.K = p.depth;
         pd.NT = (1 << (p.depth + 1)) - 1;
         pd.dpi = dirs_per_item(N, pd.D, lo.grid, warps, dpi_cap);

@@ -74,6 +74,99 @@ __host__ __device__ inline void stress64(const double F[4], double beta_k, const
 }
 
 // -------------------------------------------------------------------------
+// FP64 line function g(t) = W(F + t R) with g' and g'' in closed form, for the
+// common-tangent refinement of a split.  Along the line
+//   I1' = 2 G:R, I1'' = 2 |R|^2, J' = cof G : R, J'' = 2 det R,
+//   s'  = mu/2 I1' + (lam ln J - mu) J'/J,
+//   s'' = mu/2 I1'' + lam (J'/J)^2 + (lam ln J - mu)(J''/J - (J'/J)^2),
+// and with dW/ds = 1 - D(max(s, beta_k)), d^2W/ds^2 = -D'(s) [s > beta_k]:
+//   g' = W_s s',  g'' = W_ss s'^2 + W_s s''.
+// -------------------------------------------------------------------------
+__device__ inline void line_derivs64(const double F[4], const double R[4], double beta_k,
+                                     const Material &m, double t, double *g, double *g1,
+                                     double *g2) {
+    double G[4];
+    for (int k = 0; k < 4; ++k) G[k] = F[k] + t * R[k];
+    if (m.energy == CVX_ENERGY_DOUBLE_WELL) {
+        const double a = G[0] * G[0] - 1.0, d = G[3] - 1.0;
+        *g = a * a + G[1] * G[1] + G[2] * G[2] + d * d;
+        *g1 = 4.0 * G[0] * a * R[0] + 2.0 * (G[1] * R[1] + G[2] * R[2] + d * R[3]);
+        *g2 = (12.0 * G[0] * G[0] - 4.0) * R[0] * R[0] +
+              2.0 * (R[1] * R[1] + R[2] * R[2] + R[3] * R[3]);
+        return;
+    }
+    const double J = G[0] * G[3] - G[1] * G[2];
+    if (!(J > 0.0)) {
+        *g = *g1 = *g2 = nan("");
+        return;
+    }
+    const double lj = log(J);
+    const double I1 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2] + G[3] * G[3] + 1.0;
+    const double s = 0.5 * m.mu * (I1 - 3.0) - m.mu * lj + 0.5 * m.lam * lj * lj;
+    const double dI1 = 2.0 * (G[0] * R[0] + G[1] * R[1] + G[2] * R[2] + G[3] * R[3]);
+    const double ddI1 = 2.0 * (R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3]);
+    const double dJ = G[3] * R[0] - G[2] * R[1] - G[1] * R[2] + G[0] * R[3];
+    const double ddJ = 2.0 * (R[0] * R[3] - R[1] * R[2]);
+    const double q = dJ / J;
+    const double c = m.lam * lj - m.mu;
+    const double s1 = 0.5 * m.mu * dI1 + c * q;
+    const double s2 = 0.5 * m.mu * ddI1 + m.lam * q * q + c * (ddJ / J - q * q);
+    const double ek = exp(-beta_k / m.D0);
+    double Ws, Wss;
+    if (s <= beta_k) {
+        Ws = 1.0 - m.Dinf * (1.0 - ek);
+        Wss = 0.0;
+        *g = Ws * (s - beta_k);
+    } else {
+        const double es = exp(-s / m.D0);
+        Ws = 1.0 - m.Dinf * (1.0 - es);
+        Wss = -m.Dinf / m.D0 * es;
+        *g = (1.0 - m.Dinf) * (s - beta_k) + m.Dinf * m.D0 * (ek - es);
+    }
+    *g1 = Ws * s1;
+    *g2 = Wss * s1 * s1 + Ws * s2;
+}
+
+// Newton on the common-tangent conditions of a split (t-, t+) along R,
+//   g'(t-) = g'(t+) = (g(t+) - g(t-)) / (t+ - t-),
+// written as f1 = g'(t-) - g'(t+), f2 = g'(t-)(t+ - t-) - (g(t+) - g(t-)),
+// seeded by the grid bridge, at most 8 iterations.  Returns true, with the
+// refined ends and the chord value at 0, only if it converged inside the
+// line window, det > 0 at both ends and the chord value is not above h_grid.
+__device__ inline bool newton_tangent64(const double F[4], const double R[4], double beta_k,
+                                        const Material &m, double t_half, double h_grid,
+                                        double &tm, double &tp, double &h) {
+    double a = tm, b = tp;
+    bool conv = false;
+    for (int it = 0; it < 8 && !conv; ++it) {
+        double ga, ga1, ga2, gb, gb1, gb2;
+        line_derivs64(F, R, beta_k, m, a, &ga, &ga1, &ga2);
+        line_derivs64(F, R, beta_k, m, b, &gb, &gb1, &gb2);
+        const double f1 = ga1 - gb1, f2 = ga1 * (b - a) - (gb - ga);
+        const double j11 = ga2, j12 = -gb2, j21 = ga2 * (b - a), j22 = ga1 - gb1;
+        const double det = j11 * j22 - j12 * j21;
+        if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
+        const double da = (j12 * f2 - j22 * f1) / det;
+        const double db = (j21 * f1 - j11 * f2) / det;
+        a += da;
+        b += db;
+        if (!isfinite(a) || !isfinite(b)) return false;
+        conv = fabs(da) <= 1e-13 * (1.0 + fabs(a)) && fabs(db) <= 1e-13 * (1.0 + fabs(b));
+    }
+    if (!conv || !(a >= -t_half && a < 0.0 && b > 0.0 && b <= t_half)) return false;
+    double ga, gb, d1, d2;
+    line_derivs64(F, R, beta_k, m, a, &ga, &d1, &d2);
+    line_derivs64(F, R, beta_k, m, b, &gb, &d1, &d2);
+    if (!isfinite(ga) || !isfinite(gb)) return false;
+    const double hc = ga + (gb - ga) * (-a / (b - a));
+    if (!(hc <= h_grid)) return false;
+    tm = a;
+    tp = b;
+    h = hc;
+    return true;
+}
+
+// -------------------------------------------------------------------------
 // FP32 line form.  Along G(t) = F + t R with R = a (x) b rank one:
 //   I1(t) - 3 = |F|^2 - 2 + 2 t (F:R) + t^2 |R|^2,   J(t) = J0 + t (cof F : R).
 // With lg = log2 J(t) and d = psi0(t) - beta_k:

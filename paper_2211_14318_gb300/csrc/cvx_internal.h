@@ -10,8 +10,6 @@
 
 namespace cvx {
 
-enum { CVX_NODE_ITER_CAP = 64, CVX_NODE_OVERFLOW = 128 };
-
 constexpr int kWarpTop = 4;    // best directions kept per warp
 constexpr int kItemTop = 8;    // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
@@ -68,7 +66,7 @@ struct ProbDesc {
     int D, dir_off;  // directions [dir_off, dir_off + D) of the call's tables
     int K, NT;       // depth, tree nodes per point
     int chunks, dpi; // work items per node, directions per item
-    int pad;
+    int flags;       // cvx_params.flags
     long long point_off, n;
     const double *F, *beta;
     double *W_R, *P;

@@ -503,15 +503,23 @@ __global__ void k_commit(const Pipe P, int level) {
     nd.m_plus = b.b;
     nd.h = b.q;
     atomicAdd(P.counters + C_LAMINATED, 1ull);
-    const double xi = (double)(m0 - b.a) / (double)(b.b - b.a);
-    nd.xi = xi;
     const double *d = P.dir64 + 4 * ((long long)pd.dir_off + nd.dir);
     const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
                          __dmul_rn(d[1], d[3])};
-    const double tm = __dmul_rn((double)(b.a - m0), pd.line.h64);
-    const double tp = __dmul_rn((double)(b.b - m0), pd.line.h64);
+    double tm = __dmul_rn((double)(b.a - m0), pd.line.h64);
+    double tp = __dmul_rn((double)(b.b - m0), pd.line.h64);
     const bool leaf_children = level + 1 >= pd.K;
     const double beta = pd.beta[p - pd.point_off];
+    double xi = (double)(m0 - b.a) / (double)(b.b - b.a);
+    if (pd.flags & CVX_FLAG_REFINE_NEWTON) {
+        double hN;
+        if (newton_tangent64(nd.F, R, beta, pd.mat, pd.line.h64 * m0, b.q, tm, tp, hN)) {
+            xi = -tm / (tp - tm);
+            nd.h = hN;
+            nd.flags |= CVX_NODE_NEWTON;
+        }
+    }
+    nd.xi = xi;
     for (int side = 0; side < 2; ++side) {
         const int ci = 2 * hi + 1 + side;  // 2i+1: F-, 2i+2: F+
         cvx_node &c = *node_ptr(pd, p, ci);

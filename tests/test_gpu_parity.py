@@ -357,3 +357,65 @@ def test_stats_account_for_the_work(cv, orc):
     assert 0.9 * s["lines"] * 301 <= s["valid_samples"] <= s["lines"] * 301
     assert s["iter_caps"] == 0 and s["overflow"] <= 0.1 * s["nodes_scanned"]
     assert s["laminated"] <= s["refined"] <= 16 * s["nodes_scanned"]
+
+
+def test_newton_double_well_exact_tangent(cv, orc):
+    """CVX_FLAG_REFINE_NEWTON on the double well: the refined split of
+    F = diag(0.3, 1) is diag(+-1, 1) (off the line grid), W^R = 0, xi = 0.65."""
+    from paper_2211_14318_gb300 import api
+
+    p = api.Params(energy=api.ENERGY_DOUBLE_WELL, n_theta_a=8, n_theta_b=8, line_points=201,
+                   t_half=1.5, depth=1, newton=True)
+    out = cv.convexify_points(p, np.array([[0.3, 0, 0, 1.0]]), np.zeros(1), want_tree=True)
+    tr = api.tree_numpy(out["tree"], 1, p.tree_size)[0]
+    assert tr[0]["flags"] & api.NODE_NEWTON and tr[0]["dir"] == 0
+    np.testing.assert_allclose(tr[1]["F"], [-1, 0, 0, 1], atol=1e-12)
+    np.testing.assert_allclose(tr[2]["F"], [1, 0, 0, 1], atol=1e-12)
+    assert abs(tr[0]["xi"] - 0.65) < 1e-12
+    assert abs(out["W_R"].item()) < 1e-13
+
+
+def test_newton_refinement_matches_oracle(cv, orc):
+    """NH with damage, a window wide enough for interior splits (|t| <= 12),
+    depth 2: the GPU's refined splits against the oracle's (same grid
+    decision, refined ends to 1e-9, same acceptance), W^R and P to the bars."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    F, Fp = inputs.material_points(40, seed=12, lam_hi=1.8)
+    mat = _omat(orc)
+    beta = orc.history_update(mat, Fp)
+    p = api.Params(n_theta_a=12, n_theta_b=12, line_points=301, t_half=12.0, depth=2,
+                   newton=True, **MAT)
+    out = cv.convexify_points(p, F, beta, want_tree=True)
+    tg = api.tree_numpy(out["tree"], F.shape[0], p.tree_size)
+    sc = orc.Scan(orc.angle_directions(12, 12), 301, 12.0, 2, newton=True)
+    WRo, Po, to, sto = orc.convexify(mat, sc, F, beta)
+    WR, P = out["W_R"].cpu().numpy(), out["P"].cpu().numpy()
+    refined = 0
+    good = np.ones(F.shape[0], dtype=bool)
+    for q in range(F.shape[0]):
+        stack = [0]
+        while stack:
+            i = stack.pop()
+            o, g = to[q, i], tg[q, i]
+            if not o["flags"] & orc.SCANNED:
+                continue
+            if o["margin"] <= TIE:
+                good[q] = False
+                continue
+            lam = bool(o["flags"] & orc.LAMINATED)
+            assert bool(g["flags"] & api.NODE_LAMINATED) == lam, (q, i)
+            if lam:
+                assert (g["dir"], g["m_minus"], g["m_plus"]) == (o["dir"], o["m_minus"], o["m_plus"])
+            assert bool(g["flags"] & api.NODE_NEWTON) == bool(o["flags"] & orc.NEWTON), (q, i)
+            if o["flags"] & orc.NEWTON:
+                refined += 1
+                np.testing.assert_allclose(tg[q, 2 * i + 1]["F"], to[q, 2 * i + 1]["F"], atol=1e-9)
+                np.testing.assert_allclose(tg[q, 2 * i + 2]["F"], to[q, 2 * i + 2]["F"], atol=1e-9)
+                assert abs(g["xi"] - o["xi"]) < 1e-9
+            if o["flags"] & orc.LAMINATED:
+                stack += [2 * i + 1, 2 * i + 2]
+    assert refined >= 10
+    assert np.max(_rel(WR[good], WRo[good]), initial=0) < 1e-6
+    Pn = np.linalg.norm(Po, axis=1)
+    assert np.max(np.linalg.norm(P[good] - Po[good], axis=1) / (1e-8 + Pn[good]), initial=0) < 1e-5

@@ -230,6 +230,95 @@ def test_stress_is_gradient_of_energy(orc):
     assert np.max(np.abs(orc.stress(mat, [1, 0, 0, 1], 0.2))) < 1e-15
 
 
+def test_tangent_is_gradient_of_stress(orc):
+    """A = dP/dF against central differences of the (pinned) stress, on both
+    history branches; A is symmetric (a Hessian); double well exactly."""
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    rng = np.random.default_rng(5)
+    checked = 0
+    for trial in range(60):
+        F = np.array([1, 0, 0, 1.0]) + rng.normal(0, 0.25, 4)
+        if F[0] * F[3] - F[1] * F[2] < 0.3:
+            continue
+        beta = rng.choice([0.0, 0.05, 0.4, 3.0])
+        A = orc.tangent(mat, F, beta)
+        np.testing.assert_allclose(A, A.T, rtol=0, atol=1e-13 * max(1.0, np.max(np.abs(A))))
+        e = 1e-6
+        for k in range(4):
+            Fp, Fm = F.copy(), F.copy()
+            Fp[k] += e
+            Fm[k] -= e
+            if (orc.psi0_F(mat, Fp) - beta) * (orc.psi0_F(mat, Fm) - beta) < 0:
+                continue
+            fd = (orc.stress(mat, Fp, beta) - orc.stress(mat, Fm, beta)) / (2 * e)
+            assert np.max(np.abs(fd - A[:, k])) < 1e-6 * max(1.0, np.max(np.abs(A))), (F, beta, k)
+            checked += 1
+    assert checked > 100
+    dw = orc.Material(energy=1)
+    F = np.array([0.7, 0.2, -0.1, 1.3])
+    np.testing.assert_allclose(orc.tangent(dw, F, 0.0),
+                               np.diag([12 * 0.49 - 4, 2.0, 2.0, 2.0]), rtol=1e-15, atol=0)
+
+
+def test_newton_split_is_the_exact_common_tangent_of_the_double_well(orc):
+    """Double well along e1 (x) e1 from F = diag(0.3, 1): the common tangent of
+    (x^2 - 1)^2 touches at x = +-1, i.e. t- = -1.3, t+ = 0.7, neither on the
+    line grid (h = 0.015); the refined split lands there, W^R = 0 and
+    xi = 1.3 / 2."""
+    mat = orc.Material(energy=1)
+    F = np.array([[0.3, 0.0, 0.0, 1.0]])
+    grid = orc.Scan(orc.angle_directions(8, 8), 201, 1.5, 1)
+    WRg, _, trg, _ = orc.convexify(mat, grid, F, np.zeros(1))
+    assert WRg[0] > 1e-6 and not trg[0, 0]["flags"] & orc.NEWTON
+    sc = orc.Scan(orc.angle_directions(8, 8), 201, 1.5, 1, newton=True)
+    WR, P, tr, st = orc.convexify(mat, sc, F, np.zeros(1))
+    root = tr[0, 0]
+    assert root["dir"] == 0 and root["flags"] & orc.NEWTON
+    np.testing.assert_allclose(tr[0, 1]["F"], [-1, 0, 0, 1], atol=1e-12)
+    np.testing.assert_allclose(tr[0, 2]["F"], [1, 0, 0, 1], atol=1e-12)
+    assert abs(root["xi"] - 0.65) < 1e-12
+    assert abs(WR[0]) < 1e-13 and np.max(np.abs(P[0])) < 1e-11
+    assert WR[0] <= WRg[0]
+
+
+def test_newton_split_satisfies_tangency_by_differences(orc):
+    """NH with damage: at every refined split the line function's slope at
+    both ends (central differences of W alone) equals the chord slope, and the
+    refined chord value at 0 is not above the grid bridge's."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F, Fp = inputs.material_points(24, seed=11, lam_hi=1.8)
+    beta = orc.history_update(mat, Fp)
+    dirs = orc.angle_directions(12, 12)
+    # with this damage law the tangent points lie near |t| = 7..10, so the
+    # window must reach beyond them for a split to be interior
+    g = orc.Scan(dirs, 301, 12.0, 1)
+    sc = orc.Scan(dirs, 301, 12.0, 1, newton=True)
+    WRg, _, trg, _ = orc.convexify(mat, g, F, beta)
+    WR, _, tr, _ = orc.convexify(mat, sc, F, beta)
+    refined = 0
+    for p in range(F.shape[0]):
+        r = tr[p, 0]
+        if not r["flags"] & orc.NEWTON:
+            continue
+        refined += 1
+        R = np.outer(dirs[r["dir"], :2], dirs[r["dir"], 2:]).reshape(4)
+        k = np.argmax(np.abs(R))
+        tm = (tr[p, 1]["F"][k] - F[p, k]) / R[k]
+        tp = (tr[p, 2]["F"][k] - F[p, k]) / R[k]
+        gfun = lambda t: orc.energy(mat, F[p] + t * R, beta[p])  # noqa: E731
+        slope = (gfun(tp) - gfun(tm)) / (tp - tm)
+        e = 1e-6
+        for t in (tm, tp):
+            d = (gfun(t + e) - gfun(t - e)) / (2 * e)
+            assert abs(d - slope) < 1e-6 * max(1.0, abs(slope)), (p, t, d, slope)
+        assert r["h"] <= trg[p, 0]["h"] + 1e-15
+        assert WR[p] <= WRg[p] + 1e-15
+        assert abs(r["xi"] - (0 - tm) / (tp - tm)) < 1e-12
+    assert refined >= 5
+
+
 def test_undamaged_neo_hooke_is_not_relaxed(orc):
     """With D_inf = 0, W = psi0 - beta_k is convex along every rank-one line
     where ln J <= 1 + mu/lam (second derivative along the line is
