@@ -293,6 +293,65 @@ int convexify_batch(cvx_handle *h, int n_problems, const cvx_problem *problems, 
 int cvx_get_batch_tuning(cvx_handle *h, int *warps_per_cta, int *dirs_per_item_cap,
                          int *from_cache);
 
+/* ------------------------------------------- surrogate proposal network */
+
+/* A small network that proposes, per tree node, where the line scan should
+ * look (not in the paper: an addition; the full scan stays the judge and the
+ * fallback).  Inputs per node x = (F11, F12, F21, F22, beta_k, ln det F),
+ * standardised with a per-feature mean and std; 4 hidden layers of width 256
+ * with GELU; 7 outputs: the angles theta_a, theta_b of a (x) b (period pi),
+ * the logit of the volume fraction xi of F+, the four entries of the jump
+ * F+ - F- (row-major).  Training and inference run on the BF16 tensor cores
+ * (tcgen05, FP32 accumulation); the FP32 master weights and Adam state live
+ * in the handle.
+ *
+ * Parameters: one flat FP32 vector of CVX_SURROGATE_PARAMS values,
+ *   W0 (256 x 6), b0 (256), W1 (256 x 256), b1, W2, b2, W3, b3,
+ *   W4 (7 x 256), b4 (7), weights row-major as (out, in).
+ * Labels Y (n x 7): theta_a, theta_b, xi, jump (4); a node that does not
+ * split has NaN angles and xi (masked out of the loss) and a zero jump.
+ * Loss per sample: sum_i (1 - cos 2 (o_i - theta_i)) over the two angles
+ * + (sigmoid(o_2) - xi)^2 + |o_{3..6} - jump|^2, averaged over the batch. */
+#define CVX_SURROGATE_PARAMS 200967
+
+typedef struct cvx_train_cfg {
+    int32_t epochs; /* passes over the data                                  */
+    int32_t batch;  /* samples per Adam step, 16..65536                       */
+    float lr;       /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8)      */
+    int32_t init;   /* 1: standardise from X and draw fresh weights from seed */
+    uint64_t seed;  /* weight init and shuffling                             */
+} cvx_train_cfg;
+
+/* Sets / reads the FP32 weights (HOST arrays) and the input standardisation
+ * (mean[6], std[6], std > 0). */
+int surrogate_set_weights(cvx_handle *h, const float *params, const float *mean,
+                          const float *std);
+int surrogate_get_weights(cvx_handle *h, float *params, float *mean, float *std);
+
+/* Raw outputs (n x 7, DEVICE) of DEVICE inputs X (n x 6, unstandardised). */
+int surrogate_forward(cvx_handle *h, int64_t n, const float *X, float *out, cvx_stream s);
+
+/* Mean loss (DEVICE scalar) and its gradient (DEVICE, CVX_SURROGATE_PARAMS)
+ * over one batch of n <= 2^20 DEVICE samples, with the current weights. */
+int surrogate_loss_grad(cvx_handle *h, int64_t n, const float *X, const float *Y, float *loss,
+                        float *grad, cvx_stream s);
+
+/* Trains on n DEVICE samples (X n x 6, Y n x 7) with Adam; loss_log (HOST,
+ * cfg->epochs values, nullable) receives each epoch's mean batch loss.
+ * Synchronous. */
+int surrogate_train(cvx_handle *h, int64_t n, const float *X, const float *Y,
+                    const cvx_train_cfg *cfg, float *loss_log, cvx_stream s);
+
+/* Weights and standardisation to / from a file (little-endian FP32). */
+int surrogate_save(cvx_handle *h, const char *path);
+int surrogate_load(cvx_handle *h, const char *path);
+
+/* The tensor-core building block of the network: C (M x N, FP32, DEVICE) =
+ * A (M x K) B (N x K)^T with A, B bfloat16 (raw 16-bit patterns), DEVICE,
+ * row-major, 16-byte aligned; K a positive multiple of 16.  Synchronous. */
+int cvx_gemm_bf16(cvx_handle *h, int M, int N, int K, const uint16_t *A, const uint16_t *B,
+                  float *C, cvx_stream s);
+
 /* ------------------------------------------------ allocation-free variant */
 
 /* convexify_points for callers that may not allocate device memory — for

@@ -67,6 +67,13 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _TrainCfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("init", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+SURROGATE_PARAMS = 200967
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -96,6 +103,14 @@ def lib() -> ctypes.CDLL:
         "convexify_points": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp, vp, vp],
         "convexify_points_static": [ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp],
         "convexify_batch": [vp, ctypes.c_int, ctypes.POINTER(_Problem), vp],
+        "surrogate_set_weights": [vp, vp, vp, vp],
+        "surrogate_get_weights": [vp, vp, vp, vp],
+        "surrogate_forward": [vp, i64, vp, vp, vp],
+        "surrogate_loss_grad": [vp, i64, vp, vp, vp, vp, vp],
+        "surrogate_train": [vp, i64, vp, vp, ctypes.POINTER(_TrainCfg), vp, vp],
+        "surrogate_save": [vp, ctypes.c_char_p],
+        "surrogate_load": [vp, ctypes.c_char_p],
+        "cvx_gemm_bf16": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
         "cvx_get_batch_tuning": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)],
     }
@@ -112,7 +127,9 @@ def exported_symbols() -> Sequence[str]:
             "cvx_set_tuning", "cvx_set_profiling", "cvx_get_scan_timing",
             "cvx_energy", "cvx_history_update", "cvx_sample_lines", "cvx_hull_bridge",
             "convexify_points", "convexify_points_static", "convexify_batch",
-            "cvx_get_batch_tuning")
+            "cvx_get_batch_tuning", "surrogate_set_weights", "surrogate_get_weights",
+            "surrogate_forward", "surrogate_loss_grad", "surrogate_train", "surrogate_save",
+            "surrogate_load", "cvx_gemm_bf16")
 
 
 def _check(rc: int, what: str):
@@ -345,6 +362,73 @@ class Convexifier:
         _check(lib().convexify_batch(self._h, len(problems), arr, _stream(stream)),
                "convexify_batch")
         return res
+
+    # ----------------------------------------------------- surrogate network
+    def gemm_bf16(self, A, B, stream=None):
+        """C = A B^T (FP32) on the tensor cores; A (M x K), B (N x K) bf16."""
+        import torch
+
+        A = A.to(device=f"cuda:{self.device}", dtype=torch.bfloat16).contiguous()
+        B = B.to(device=f"cuda:{self.device}", dtype=torch.bfloat16).contiguous()
+        M, K = A.shape
+        N = B.shape[0]
+        C = torch.empty(M, N, dtype=torch.float32, device=A.device)
+        _check(lib().cvx_gemm_bf16(self._h, M, N, K, _ptr(A), _ptr(B), _ptr(C), _stream(stream)),
+               "cvx_gemm_bf16")
+        return C
+
+    def surrogate_set_weights(self, params, mean, std):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(SURROGATE_PARAMS)
+        m = np.ascontiguousarray(mean, dtype=np.float32).reshape(6)
+        sd = np.ascontiguousarray(std, dtype=np.float32).reshape(6)
+        _check(lib().surrogate_set_weights(self._h, p.ctypes.data, m.ctypes.data, sd.ctypes.data),
+               "surrogate_set_weights")
+
+    def surrogate_get_weights(self):
+        p = np.zeros(SURROGATE_PARAMS, dtype=np.float32)
+        m = np.zeros(6, dtype=np.float32)
+        sd = np.zeros(6, dtype=np.float32)
+        _check(lib().surrogate_get_weights(self._h, p.ctypes.data, m.ctypes.data, sd.ctypes.data),
+               "surrogate_get_weights")
+        return p, m, sd
+
+    def surrogate_forward(self, X, stream=None):
+        import torch
+
+        X = self._dev(X, torch.float32).reshape(-1, 6)
+        out = torch.empty(X.shape[0], 7, dtype=torch.float32, device=X.device)
+        _check(lib().surrogate_forward(self._h, X.shape[0], _ptr(X), _ptr(out), _stream(stream)),
+               "surrogate_forward")
+        return out
+
+    def surrogate_loss_grad(self, X, Y, stream=None):
+        import torch
+
+        X = self._dev(X, torch.float32).reshape(-1, 6)
+        Y = self._dev(Y, torch.float32).reshape(-1, 7)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        grad = torch.empty(SURROGATE_PARAMS, dtype=torch.float32, device=X.device)
+        _check(lib().surrogate_loss_grad(self._h, X.shape[0], _ptr(X), _ptr(Y), _ptr(loss),
+                                         _ptr(grad), _stream(stream)), "surrogate_loss_grad")
+        return loss, grad
+
+    def surrogate_train(self, X, Y, epochs: int, batch: int = 8192, lr: float = 1e-3,
+                        init: bool = True, seed: int = 0, stream=None):
+        import torch
+
+        X = self._dev(X, torch.float32).reshape(-1, 6)
+        Y = self._dev(Y, torch.float32).reshape(-1, 7)
+        cfg = _TrainCfg(epochs, batch, lr, 1 if init else 0, seed)
+        log = np.zeros(max(epochs, 1), dtype=np.float32)
+        _check(lib().surrogate_train(self._h, X.shape[0], _ptr(X), _ptr(Y), ctypes.byref(cfg),
+                                     log.ctypes.data, _stream(stream)), "surrogate_train")
+        return log[:epochs]
+
+    def surrogate_save(self, path: str):
+        _check(lib().surrogate_save(self._h, path.encode()), "surrogate_save")
+
+    def surrogate_load(self, path: str):
+        _check(lib().surrogate_load(self._h, path.encode()), "surrogate_load")
 
     def batch_tuning(self):
         """(warps per CTA, directions-per-item cap, taken from the cache) of the

@@ -198,6 +198,7 @@ int cvx_destroy(cvx_handle *h) {
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
     destroy_batch_plan(h);
+    destroy_surrogate(h);
     for (auto *v : {&h->ev_pending, &h->ev_pool})
         for (auto &e : *v) {
             cudaEventDestroy(e.first);

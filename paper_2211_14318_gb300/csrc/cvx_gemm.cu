@@ -1,0 +1,266 @@
+// cvx_gemm.cu -- the BF16 tensor-core GEMM of the surrogate network
+// (tcgen05, FP32 accumulation in TMEM, operands staged by TMA) with the
+// epilogues of the network's forward and backward passes fused in.
+//
+//   D[m][n] = sum_k A[m][k] B[n][k]       (A: M x K, B: N x K, both bf16,
+//                                          row-major with K contiguous)
+//
+// One CTA of 128 threads computes a 128 x BN tile over a K range (split-K for
+// the weight gradients).  Thread 0 issues the TMA loads (one box per k-block
+// of 8 elements, two stages of 64) and the MMAs (K = 16 each); every thread
+// then reads its own accumulator row (TMEM lane) and applies the epilogue.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "cvx_mlp.h"
+#include "cvx_tc.cuh"
+
+namespace cvx {
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kStages = 2;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait, then give up
+
+__device__ __forceinline__ float gelu(float z) {
+    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad(float z) {
+    const float Phi = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    return Phi + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *dst, const float (&v)[16]) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M,
+           int N, int K, int k_split, GemmEpi ep) {
+    constexpr int A_BYTES = kBM * kBK * 2;
+    constexpr int B_BYTES = BN * kBK * 2;
+    constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = smem;
+    unsigned char *sB = smem + kStages * A_BYTES;
+    __shared__ __align__(8) uint64_t bar_full[kStages], bar_mma[kStages], bar_done;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int kc0 = blockIdx.z * k_split;
+    const int kc1 = min(K, kc0 + k_split);
+    const int Mv = ep.M_dev ? min(*ep.M_dev, ep.M_valid) : ep.M_valid;
+    if (ep.mode != EPI_DW && m0 >= Mv) return;  // the whole tile is padding
+    if (kc0 >= kc1) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_mma[s], 1);
+        }
+        mbar_init(&bar_done, 1);
+        s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&s_tmem, TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    const int nchunks = (kc1 - kc0 + kBK - 1) / kBK;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = idesc_bf16(kBM, BN);
+        auto issue = [&](int c) {
+            const int s = c % kStages;
+            const int k0 = kc0 + c * kBK;
+            const int kbn = min(kBK, kc1 - k0) / 8;
+            mbar_expect_tx(&bar_full[s], (unsigned)(kbn * (kBM + BN) * 16));
+            for (int kb = 0; kb < kbn; ++kb) {
+                tma_load_2d(sA + s * A_BYTES + kb * kBM * 16, &tA, &bar_full[s], k0 + 8 * kb, m0);
+                tma_load_2d(sB + s * B_BYTES + kb * BN * 16, &tB, &bar_full[s], k0 + 8 * kb, n0);
+            }
+        };
+        bool ok = true;
+        issue(0);
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int s = c % kStages;
+            if (c + 1 < nchunks) {
+                const int c2 = c + 1, s2 = c2 % kStages;
+                if (c2 >= kStages) ok = mbar_wait(&bar_mma[s2], ((c2 - kStages) / kStages) & 1, kWaitNs);
+                if (!ok) break;
+                issue(c2);
+            }
+            ok = mbar_wait(&bar_full[s], (c / kStages) & 1, kWaitNs);
+            if (!ok) break;
+            tc_fence_after();
+            const int kbn = min(kBK, kc1 - (kc0 + c * kBK)) / 8;
+            const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+            for (int j = 0; j < kbn / 2; ++j) {
+                const uint64_t ad = smem_desc(a0 + 2 * j * kBM * 16, kBM * 16, 128);
+                const uint64_t bd = smem_desc(b0 + 2 * j * BN * 16, BN * 16, 128);
+                umma_bf16(tmem, ad, bd, idesc, (c > 0 || j > 0) ? 1u : 0u);
+            }
+            umma_commit(&bar_mma[s]);
+        }
+        if (ok) {
+            umma_commit(&bar_done);
+        } else {
+            s_fail = 1;
+            if (ep.err) atomicExch(ep.err, 1);
+        }
+    }
+    __syncwarp();
+    bool ok = mbar_wait(&bar_done, 0, kWaitNs);
+    if (!ok && ep.err) atomicExch(ep.err, 1);
+    tc_fence_after();
+
+    const int m = m0 + 32 * warp + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + c0, v);
+        if (!ok) continue;
+        const int n = n0 + c0;
+        switch (ep.mode) {
+        case EPI_F32:
+            if (m < Mv)
+                for (int i = 0; i < 16; ++i)
+                    if (n + i < N) ep.C[(long long)m * ep.ldc + n + i] = v[i];
+            break;
+        case EPI_HIDDEN: {
+            if (m >= Mv) break;
+            float a[16];
+            for (int i = 0; i < 16; ++i) {
+                const float z = v[i] + ep.bias[n + i];
+                if (ep.Z) ep.Z[(long long)m * ep.ldz + n + i] = z;
+                a[i] = gelu(z);
+            }
+            store_bf16x16(ep.A + (long long)m * ep.lda + n, a);
+            if (ep.AT)
+                for (int i = 0; i < 16; ++i)
+                    ep.AT[(long long)(n + i) * ep.ldat + m] = __float2bfloat16_rn(a[i]);
+            break;
+        }
+        case EPI_OUT:
+            if (m < Mv)
+                for (int i = 0; i < 16; ++i)
+                    if (n + i < ep.n_store)
+                        ep.C[(long long)m * ep.ldc + n + i] = v[i] + ep.bias[n + i];
+            break;
+        case EPI_DA: {
+            float dz[16];
+            const bool in = m < Mv;
+            for (int i = 0; i < 16; ++i)
+                dz[i] = in ? v[i] * gelu_grad(ep.Z[(long long)m * ep.ldz + n + i]) : 0.0f;
+            if (in) {
+                store_bf16x16(ep.A + (long long)m * ep.lda + n, dz);
+                if (ep.AT)
+                    for (int i = 0; i < 16; ++i)
+                        ep.AT[(long long)(n + i) * ep.ldat + m] = __float2bfloat16_rn(dz[i]);
+            }
+            if (ep.dbias) {
+                for (int i = 0; i < 16; ++i) {
+                    float s = dz[i];
+                    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (lane == 0) atomicAdd(ep.dbias + n + i, s);
+                }
+            }
+            break;
+        }
+        case EPI_DW:
+            if (m < ep.m_store)
+                for (int i = 0; i < 16; ++i)
+                    if (n + i < ep.n_store) atomicAdd(ep.C + (long long)m * ep.ldc + n + i, v[i]);
+            break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TCOLS);
+    }
+}
+
+template <int BN>
+constexpr size_t gemm_smem() {
+    return (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + 1024;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+}  // namespace
+
+bool make_tmap_bf16(CUtensorMap *map, const void *ptr, long long rows, long long cols,
+                    long long ld, int box_rows) {
+    EncodeTiled enc = encode_fn();
+    if (!enc) return false;
+    if (((uintptr_t)ptr & 15) || (ld * 2) % 16 || rows < 1 || cols < 1) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {8, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+               box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+cudaError_t launch_gemm(const CUtensorMap &tA, const CUtensorMap &tB, int M, int N, int K,
+                        int k_split, int BN, const GemmEpi &ep, cudaStream_t s) {
+    if (K % 16 || k_split % 16 || k_split < 16) return cudaErrorInvalidValue;
+    const dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, (K + k_split - 1) / k_split);
+    if (BN == 256) {
+        const size_t sm = gemm_smem<256>();
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_gemm<256><<<grid, 128, sm, s>>>(tA, tB, M, N, K, k_split, ep);
+    } else if (BN == 16) {
+        const size_t sm = gemm_smem<16>();
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_gemm<16><<<grid, 128, sm, s>>>(tA, tB, M, N, K, k_split, ep);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cvx

@@ -13,6 +13,9 @@
 #include "cvx_internal.h"
 
 struct cvx_batch_plan;  // cvx_batch.cu
+namespace cvx {
+struct Surrogate;  // cvx_surrogate.cu
+}
 
 struct cvx_handle {
     int device = 0;
@@ -38,6 +41,8 @@ struct cvx_handle {
     cvx_batch_plan *plan = nullptr;
     std::map<std::string, std::pair<int, int>> tune_cache;
     int last_tune_warps = 0, last_tune_dpi = 0, last_tune_cached = 0;
+    // surrogate proposal network (weights, optimiser state, batch buffers)
+    cvx::Surrogate *sur = nullptr;
 };
 
 namespace cvx {
@@ -50,6 +55,7 @@ int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s);
 // Direction rows (a1, a2, b1, b2) of a parameter set, FP64.
 void direction_rows(const cvx_params *p, std::vector<double> &rows);
 void destroy_batch_plan(cvx_handle *h);
+void destroy_surrogate(cvx_handle *h);
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
