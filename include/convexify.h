@@ -64,8 +64,10 @@ enum cvx_point_status {
                               the FP32 sampling error bound (warning only)     */
     CVX_PT_EDGE = 4,       /* some split point lies on the end of its line     */
     CVX_PT_ITER_CAP = 8,   /* a hull search hit its iteration cap (warning)    */
-    CVX_PT_OVERFLOW = 16   /* more directions passed the FP32 screen than the
-                              16 refined in FP64 at some node (warning)        */
+    CVX_PT_OVERFLOW = 16,  /* the decision at some node is not certified
+                              against every direction (warning)               */
+    CVX_PT_FALLBACK = 32   /* surrogate_propose: some node fell back to the
+                              full scan                                       */
 };
 
 /* energy kinds */
@@ -144,7 +146,8 @@ enum cvx_node_flags {
     CVX_NODE_EDGE = 32,
     CVX_NODE_ITER_CAP = 64,  /* a hull search hit its iteration cap          */
     CVX_NODE_OVERFLOW = 128, /* decision not certified against every direction */
-    CVX_NODE_NEWTON = 256    /* split refined by CVX_FLAG_REFINE_NEWTON        */
+    CVX_NODE_NEWTON = 256,   /* split refined by CVX_FLAG_REFINE_NEWTON        */
+    CVX_NODE_FALLBACK = 512  /* surrogate_propose: decided by the full scan     */
 };
 
 /* Root laminate of a point: direction a (x) b = dirs[dir], volume fraction xi
@@ -179,6 +182,8 @@ typedef struct cvx_stats {
     int64_t fp64_center;    /* FP64 fallbacks deciding the centre          */
     int64_t refined;        /* candidate lines resampled and decided in FP64 */
     int64_t overflow;       /* nodes with more screened candidates than kept */
+    int64_t window_nodes;   /* surrogate_propose: nodes scanned in a window */
+    int64_t fallbacks;      /* ... of which deferred to the full scan       */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */
@@ -341,6 +346,34 @@ int surrogate_loss_grad(cvx_handle *h, int64_t n, const float *X, const float *Y
  * Synchronous. */
 int surrogate_train(cvx_handle *h, int64_t n, const float *X, const float *Y,
                     const cvx_train_cfg *cfg, float *loss_log, cvx_stream s);
+
+/* Training samples from lamination trees (e.g. convexify_points with a tree
+ * output, angle-grid directions): one sample per scanned node, X = the node's
+ * inputs, Y = (pi i / Na, pi j / Nb) of its direction i Nb + j, its xi and
+ * jump F+ - F-; NaN angles and xi, zero jump for a node that does not split.
+ * X (n (2^{K+1} - 1) x 6) and Y (... x 7) are DEVICE arrays of that capacity;
+ * *count (HOST) receives the number written, in point then heap order.
+ * Synchronous. */
+int surrogate_labels(cvx_handle *h, const cvx_params *p, int64_t n, const double *beta_k,
+                     const cvx_node *tree, float *X, float *Y, int64_t *count, cvx_stream s);
+
+/* The surrogate-proposed form of convexify_points (same arguments and
+ * results; angle-grid directions only).  At every tree node the network
+ * proposes a direction; its nearest cell (ia, ib) of the Na x Nb grid centres
+ * a window of (2 window + 1)^2 directions (indices wrap), and only those lines
+ * are scanned.  The node falls back to the full scan of all Na Nb directions
+ * if (i) the window's best direction lies on its border, or (ii) the energy
+ * gap |E_pred - V| / (1e-8 + |V|) exceeds gap_tol, where V is the
+ * window's node value and E_pred = xi W(F+) + (1 - xi) W(F-) the proposed
+ * laminate evaluated exactly (F+ = F + (1 - xi) amp R, F- = F - xi amp R,
+ * R = a (x) b of the proposed angles, amp = jump : R).  fell_back (n, DEVICE,
+ * nullable) = 1 where some node of the point fell back (also status bit
+ * CVX_PT_FALLBACK; nodes flagged CVX_NODE_FALLBACK).  Requires weights
+ * (surrogate_train / set_weights / load); 0 <= 2 window + 1 <= min(Na, Nb). */
+int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const double *F,
+                      const double *beta_k, int window, double gap_tol, double *W_R, double *P,
+                      cvx_laminate *root, cvx_node *tree, uint8_t *fell_back, int32_t *status,
+                      cvx_stream s);
 
 /* Weights and standardisation to / from a file (little-endian FP32). */
 int surrogate_save(cvx_handle *h, const char *path);

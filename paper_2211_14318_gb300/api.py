@@ -21,9 +21,9 @@ CVX_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NOT_TRAINED",
           -6: "UNSUPPORTED"}
 ENERGY_NH_DAMAGE, ENERGY_DOUBLE_WELL = 0, 1
-PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP, PT_OVERFLOW = 1, 2, 4, 8, 16
+PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP, PT_OVERFLOW, PT_FALLBACK = 1, 2, 4, 8, 16, 32
 NODE_EXISTS, NODE_SCANNED, NODE_LAMINATED, NODE_LEAF, NODE_TIE, NODE_EDGE = 1, 2, 4, 8, 16, 32
-NODE_ITER_CAP, NODE_OVERFLOW, NODE_NEWTON = 64, 128, 256
+NODE_ITER_CAP, NODE_OVERFLOW, NODE_NEWTON, NODE_FALLBACK = 64, 128, 256, 512
 FLAG_REFINE_NEWTON = 1
 
 NODE_DTYPE = np.dtype([
@@ -56,7 +56,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
-        "fp64_rare", "fp64_center", "refined", "overflow")]
+        "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks")]
 
 
 class _Problem(ctypes.Structure):
@@ -111,6 +111,10 @@ def lib() -> ctypes.CDLL:
         "surrogate_save": [vp, ctypes.c_char_p],
         "surrogate_load": [vp, ctypes.c_char_p],
         "cvx_gemm_bf16": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
+        "surrogate_labels": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp,
+                             ctypes.POINTER(ctypes.c_int64), vp],
+        "surrogate_propose": [vp, ctypes.POINTER(_Params), i64, vp, vp, ctypes.c_int,
+                              ctypes.c_double, vp, vp, vp, vp, vp, vp, vp],
         "cvx_get_batch_tuning": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)],
     }
@@ -129,7 +133,7 @@ def exported_symbols() -> Sequence[str]:
             "convexify_points", "convexify_points_static", "convexify_batch",
             "cvx_get_batch_tuning", "surrogate_set_weights", "surrogate_get_weights",
             "surrogate_forward", "surrogate_loss_grad", "surrogate_train", "surrogate_save",
-            "surrogate_load", "cvx_gemm_bf16")
+            "surrogate_load", "cvx_gemm_bf16", "surrogate_labels", "surrogate_propose")
 
 
 def _check(rc: int, what: str):
@@ -423,6 +427,52 @@ class Convexifier:
         _check(lib().surrogate_train(self._h, X.shape[0], _ptr(X), _ptr(Y), ctypes.byref(cfg),
                                      log.ctypes.data, _stream(stream)), "surrogate_train")
         return log[:epochs]
+
+    def surrogate_labels(self, p: Params, beta, tree, n: int, stream=None):
+        """(X, Y) training samples from the scanned nodes of n trees."""
+        import torch
+
+        beta = self._dev(beta, torch.float64).reshape(n)
+        cap = max(1, n * p.tree_size)
+        X = torch.empty(cap, 6, dtype=torch.float32, device=beta.device)
+        Y = torch.empty(cap, 7, dtype=torch.float32, device=beta.device)
+        cnt = ctypes.c_int64()
+        c = p.c()
+        _check(lib().surrogate_labels(self._h, ctypes.byref(c), n, _ptr(beta), _ptr(tree), _ptr(X),
+                                      _ptr(Y), ctypes.byref(cnt), _stream(stream)),
+               "surrogate_labels")
+        return X[:cnt.value], Y[:cnt.value]
+
+    def surrogate_propose(self, p: Params, F, beta, window: int = 4, gap_tol: float = 1e-6,
+                          want_tree: bool = False, want_root: bool = False,
+                          out: Optional[dict] = None, stream=None):
+        """W^R, P, status and fell_back (uint8) by the surrogate-proposed form."""
+        import torch
+
+        F = self._dev(F, torch.float64).reshape(-1, 4)
+        n = F.shape[0]
+        beta = self._dev(beta, torch.float64).reshape(n)
+        dev = F.device
+        o = dict(out) if out else {}
+        W_R = o.get("W_R") if o.get("W_R") is not None else torch.empty(n, dtype=torch.float64, device=dev)
+        P = o.get("P") if o.get("P") is not None else torch.empty(n, 4, dtype=torch.float64, device=dev)
+        st = o.get("status") if o.get("status") is not None else torch.empty(n, dtype=torch.int32, device=dev)
+        fb = o.get("fell_back") if o.get("fell_back") is not None else torch.empty(n, dtype=torch.uint8, device=dev)
+        tree = None
+        if want_tree:
+            tree = o.get("tree")
+            if tree is None:
+                tree = torch.empty(n * p.tree_size * NODE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        root = None
+        if want_root:
+            root = o.get("root")
+            if root is None:
+                root = torch.empty(n * LAMINATE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        c = p.c()
+        _check(lib().surrogate_propose(self._h, ctypes.byref(c), n, _ptr(F), _ptr(beta), window,
+                                       gap_tol, _ptr(W_R), _ptr(P), _ptr(root), _ptr(tree),
+                                       _ptr(fb), _ptr(st), _stream(stream)), "surrogate_propose")
+        return dict(W_R=W_R, P=P, status=st, fell_back=fb, tree=tree, root=root)
 
     def surrogate_save(self, path: str):
         _check(lib().surrogate_save(self._h, path.encode()), "surrogate_save")

@@ -122,7 +122,7 @@ int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s) {
 
 }  // namespace cvx
 
-namespace {
+namespace cvx {
 
 int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s) {
     if (!p->dirs && !h->dir_custom && h->dir_na == p->n_theta_a && h->dir_nb == p->n_theta_b)
@@ -156,6 +156,10 @@ int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s) {
     h->dir_nb = p->dirs ? -1 : p->n_theta_b;
     return CVX_OK;
 }
+
+}  // namespace cvx
+
+namespace {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -235,6 +239,8 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->fp64_center = (int64_t)c[C_FP64C];
     out->refined = (int64_t)c[C_REFINED];
     out->overflow = (int64_t)c[C_OVERFLOW];
+    out->window_nodes = (int64_t)c[C_WNODES];
+    out->fallbacks = (int64_t)c[C_FALLBACK];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }

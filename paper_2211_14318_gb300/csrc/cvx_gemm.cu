@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128, 1)
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     const int kc0 = blockIdx.z * k_split;
     const int kc1 = min(K, kc0 + k_split);
-    const int Mv = ep.M_dev ? min(*ep.M_dev, ep.M_valid) : ep.M_valid;
+    const int Mv = ep.M_dev ? min(*ep.M_dev - ep.m_off, ep.M_valid) : ep.M_valid;
     if (ep.mode != EPI_DW && m0 >= Mv) return;  // the whole tile is padding
     if (kc0 >= kc1) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

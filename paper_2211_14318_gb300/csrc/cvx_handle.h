@@ -52,6 +52,8 @@ int cuda_fail(cudaError_t e, const char *where);
 Material material_of(const cvx_params *p);
 int check_params(const cvx_params *p, bool need_line);
 int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s);
+// Direction table of the handle for a parameter set (angle grid or custom).
+int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s);
 // Direction rows (a1, a2, b1, b2) of a parameter set, FP64.
 void direction_rows(const cvx_params *p, std::vector<double> &rows);
 void destroy_batch_plan(cvx_handle *h);

@@ -46,7 +46,15 @@ struct RefineOut {
 
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
-    C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_NUM
+    C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
+    C_FALLBACK, C_NUM
+};
+
+// Pipeline passes over one level's queue.
+enum PassKind {
+    PASS_FULL = 0,      // every direction of the problem
+    PASS_WINDOW = 1,    // the proposed angular window; failing nodes are deferred
+    PASS_FALLBACK = 2   // every direction, over the deferred nodes
 };
 
 struct LineSpec {
@@ -67,6 +75,11 @@ struct ProbDesc {
     int K, NT;       // depth, tree nodes per point
     int chunks, dpi; // work items per node, directions per item
     int flags;       // cvx_params.flags
+    // proposal window (surrogate_propose): half-width w on the Na x Nb angle
+    // grid, wD = (2w + 1)^2 directions in wchunks items of wdpi; gap_tol of
+    // the fallback test
+    int window, Na, Nb, wD, wchunks, wdpi;
+    double gap_tol;
     long long point_off, n;
     const double *F, *beta;
     double *W_R, *P;
@@ -99,15 +112,31 @@ struct Pipe {
     const float4 *dir32;
     const double *dir64;
     unsigned long long *counters;
+    // windowed passes (carved only when window != 0)
+    int window;
+    int pass;                             // PassKind of the launches this Pipe drives
+    int32_t *ncnt;                        // node counts the next level's queue uses
+    int32_t *fq_p[kMaxDepth], *fq_h[kMaxDepth];  // nodes deferred to the full scan
+    int32_t *fcnt;                        // their counts (as cnt)
+    unsigned long long *fitem_ctr;
+    int2 *center;                         // proposed window centre per queued node
+    double *e_pred;                       // energy of the proposed laminate per queued node
 };
 
 // Bytes of the workspace part that depends on the shape (see pipe_layout).
-size_t pipe_bytes(long long N, int K, int C, int n_probs);
-// Carves the workspace into the Pipe's buffers.
+size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window = false);
+// Carves the workspace into the Pipe's buffers (p.N, K, C, n_probs, window set).
 void pipe_layout(Pipe &p, char *ws);
 // Enqueues the whole pipeline (zeroing, init, K levels, leaves) on s.
 // ev (optional, 2*K events) brackets each line-scan launch.
 cudaError_t pipe_enqueue(const Pipe &p, int warps, int grid, cudaStream_t s, cudaEvent_t *ev);
+// The same in pieces: zeroing + init, one pass over one level, the leaves.
+cudaError_t pipe_begin(const Pipe &p, cudaStream_t s);
+cudaError_t pipe_level(const Pipe &p, int level, int warps, int grid, cudaStream_t s,
+                       cudaEvent_t *ev);
+cudaError_t pipe_end(const Pipe &p, cudaStream_t s);
+// The Pipe that runs the full scan over the nodes a window pass deferred.
+Pipe fallback_pipe(const Pipe &p, int level);
 int scan_max_blocks_per_sm(int energy, int warps, int stride);
 
 // single steps

@@ -20,7 +20,8 @@ enum GemmEpiMode {
 struct GemmEpi {
     int mode;
     int M_valid;       // rows holding data (EPI_F32/HIDDEN/OUT/DA)
-    const int *M_dev;  // optional device-side row count (min with M_valid)
+    const int *M_dev;  // optional device-side row count; rows valid = *M_dev - m_off
+    int m_off;
     float *C;
     int ldc;
     int m_store, n_store;

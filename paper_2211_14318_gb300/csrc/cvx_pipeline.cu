@@ -52,6 +52,21 @@ __device__ __forceinline__ void top_insert(float (&q)[kWarpTop], int (&d)[kWarpT
         }
 }
 
+// Global direction index of entry j of a node's proposal window: row-major
+// over (da, db) in [-w, w]^2 around the centre (ia, ib) of the Na x Nb grid.
+__device__ __forceinline__ int window_dir(const ProbDesc &pd, int2 c, int j) {
+    const int s = 2 * pd.window + 1;
+    int i = (c.x + j / s - pd.window) % pd.Na;
+    int k = (c.y + j % s - pd.window) % pd.Nb;
+    if (i < 0) i += pd.Na;
+    if (k < 0) k += pd.Nb;
+    return i * pd.Nb + k;
+}
+
+__device__ __forceinline__ int pass_chunks(const ProbDesc &pd, int pass) {
+    return pass == PASS_WINDOW ? pd.wchunks : pd.chunks;
+}
+
 // -------------------------------------------------------------------------
 // k_init: one thread per point of any problem.
 // -------------------------------------------------------------------------
@@ -130,7 +145,9 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
     __shared__ int s_d[16][kWarpTop];
     __shared__ float s_drop[16], s_qhi[16];
     __shared__ float s_w0;
+    __shared__ int2 s_c;
     __shared__ unsigned s_hc[16][HC_N];
+    const bool win = P.pass == PASS_WINDOW;
 
     const int n_nodes = P.cnt[level];
     const long long n_items = (long long)n_nodes * P.C;
@@ -150,7 +167,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                 const int qi = (int)(item / P.C), ch = (int)(item % P.C);
                 const int p = qp[qi], hi = qh[qi];
                 s_pd = P.probs[P.pid[p]];
-                if (ch < s_pd.chunks) {
+                if (win) s_c = P.center[qi];
+                if (ch < pass_chunks(s_pd, P.pass)) {
                     const cvx_node *nd = node_ptr(s_pd, p, hi);
                     double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
                     s_nl = make_node_line(F, s_pd.beta[p - s_pd.point_off], s_pd.mat);
@@ -161,7 +179,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         const long long item = s_item;
         if (item >= n_items) break;
         const int ch = (int)(item % P.C);
-        if (ch >= s_pd.chunks) continue;
+        if (ch >= pass_chunks(s_pd, P.pass)) continue;
         const LineSpec ln = s_pd.line;
         const LineGeom g{ln.L, ln.m0, ln.nfull};
         float tl[4];
@@ -176,8 +194,10 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         nl.a1 = s_nl.a1;
         nl.K1 = s_nl.K1;
         nl.K2 = s_nl.K2;
-        const int D = s_pd.D, doff = s_pd.dir_off;
-        const int d0 = ch * s_pd.dpi, d1 = min(D, d0 + s_pd.dpi);
+        const int D = win ? s_pd.wD : s_pd.D, doff = s_pd.dir_off;
+        const int dpi = win ? s_pd.wdpi : s_pd.dpi;
+        const int2 cen = s_c;
+        const int d0 = ch * dpi, d1 = min(D, d0 + dpi);
         const int per = (d1 - d0 + nw - 1) / nw;
         const int jb = d0 + warp * per, je = min(d1, jb + per);
 
@@ -191,7 +211,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         float dropped = INFINITY, w0 = 0.0f, qhi_min = INFINITY;
         int warm_a = -1, warm_b = -1;
         for (int dj = jb; dj < je; ++dj) {
-            const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + dj]);
+            const int gd = win ? window_dir(s_pd, cen, dj) : dj;
+            const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
             sample_line<EK>(sw, nl, dl, ln, lane, tl);
             __syncwarp();
             const ScreenOut o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
@@ -206,7 +227,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                 warm_b = o.b;
             }
             qhi_min = fminf(qhi_min, o.q_hi);
-            top_insert(tq, td, dropped, o.q_lo, dj);
+            top_insert(tq, td, dropped, o.q_lo, gd);
         }
         if (lane == 0) {
 #pragma unroll
@@ -305,7 +326,7 @@ __global__ void k_select(const Pipe P, int level) {
     if (qi >= P.cnt[level]) return;
     const ProbDesc &pd = P.probs[P.pid[P.qp[level][qi]]];
     const ItemCands *r = P.items + (long long)qi * P.C;
-    const int chunks = pd.chunks;
+    const int chunks = pass_chunks(pd, P.pass);
     float qmin = INFINITY, drop = INFINITY, U = INFINITY;
     int fl = 0;
     const float w0 = r[0].w0;
@@ -461,8 +482,6 @@ __global__ void k_commit(const Pipe P, int level) {
     const ProbDesc &pd = P.probs[P.pid[p]];
     const NodeCands &nc = P.cands[qi];
     cvx_node &nd = *node_ptr(pd, p, hi);
-    nd.flags |= CVX_NODE_SCANNED | (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW));
-    atomicAdd(P.counters + C_NODES, 1ull);
     const RefineOut *ro = P.refined + (long long)qi * kNodeCand;
     int bc = -1;
     double second = INFINITY;
@@ -476,11 +495,42 @@ __global__ void k_commit(const Pipe P, int level) {
         }
     }
     const int m0 = pd.line.m0;
-    nd.gap = (float)(second - (bc >= 0 ? ro[bc].q : nd.w));
     // FP64 node value among the refined directions; an unrefined direction
     // (FP32 q >= qcut) could only win if qcut - eps reached it
     const double V = (bc >= 0 && ro[bc].q < nd.w) ? ro[bc].q : nd.w;
-    if (!(((double)nc.qcut - (double)nc.eps) / pd.kappa > V)) {
+    const bool overflow = !(((double)nc.qcut - (double)nc.eps) / pd.kappa > V);
+    if (P.pass == PASS_WINDOW) {
+        // fallback test of a proposal window: the window's best direction on
+        // its border, or an energy gap |E_pred - V| / (1e-8 + |V|) above
+        // gap_tol between the proposed laminate and the window's value, defers
+        // the node to the full scan
+        atomicAdd(P.counters + C_WNODES, 1ull);
+        bool fb = false;
+        if (bc >= 0 && ro[bc].q < nd.w) {
+            const int gd = nc.dir[bc];
+            const int2 c = P.center[qi];
+            int di = (gd / pd.Nb - c.x) % pd.Na, dj = (gd % pd.Nb - c.y) % pd.Nb;
+            if (di < 0) di += pd.Na;
+            if (dj < 0) dj += pd.Nb;
+            if (di > pd.Na / 2) di -= pd.Na;
+            if (dj > pd.Nb / 2) dj -= pd.Nb;
+            fb |= abs(di) >= pd.window || abs(dj) >= pd.window;
+        }
+        const double gap = fabs(P.e_pred[qi] - V) / (1e-8 + fabs(V));
+        fb |= !(gap <= pd.gap_tol);
+        if (fb) {
+            const int pos = atomicAdd(P.fcnt + level, 1);
+            P.fq_p[level][pos] = p;
+            P.fq_h[level][pos] = hi;
+            atomicAdd(P.counters + C_FALLBACK, 1ull);
+            return;
+        }
+    }
+    nd.flags |= CVX_NODE_SCANNED | (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW));
+    if (P.pass == PASS_FALLBACK) nd.flags |= CVX_NODE_FALLBACK;
+    atomicAdd(P.counters + C_NODES, 1ull);
+    nd.gap = (float)(second - (bc >= 0 ? ro[bc].q : nd.w));
+    if (overflow) {
         nd.flags |= CVX_NODE_OVERFLOW;
         atomicAdd(P.counters + C_OVERFLOW, 1ull);
     }
@@ -538,7 +588,7 @@ __global__ void k_commit(const Pipe P, int level) {
         c.flags = CVX_NODE_EXISTS | (leaf_children ? CVX_NODE_LEAF : 0);
     }
     if (!leaf_children) {
-        const int pos = atomicAdd(P.cnt + level + 1, 2);
+        const int pos = atomicAdd(P.ncnt + level + 1, 2);
         P.qp[level + 1][pos] = p;
         P.qh[level + 1][pos] = 2 * hi + 1;
         P.qp[level + 1][pos + 1] = p;
@@ -587,6 +637,7 @@ __global__ void k_leaf(const Pipe P) {
     if (fl & CVX_NODE_EDGE) st |= CVX_PT_EDGE;
     if (fl & CVX_NODE_ITER_CAP) st |= CVX_PT_ITER_CAP;
     if (fl & CVX_NODE_OVERFLOW) st |= CVX_PT_OVERFLOW;
+    if (fl & CVX_NODE_FALLBACK) st |= CVX_PT_FALLBACK;
     pd.status[lp] = st;
     if (pd.root) {
         cvx_laminate Lm;
@@ -610,7 +661,8 @@ __global__ void k_leaf(const Pipe P) {
 // -------------------------------------------------------------------------
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_probs) {
+static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_probs,
+                         bool window) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -631,6 +683,17 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
     const size_t o_cands = take(sizeof(NodeCands) * maxq);
     const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
     const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
+    size_t o_fqp[kMaxDepth], o_fqh[kMaxDepth], o_fcnt = 0, o_fictr = 0, o_cen = 0, o_ep = 0;
+    if (window) {
+        for (int l = 0; l < K; ++l) {
+            o_fqp[l] = take(sizeof(int32_t) * ((size_t)N << l));
+            o_fqh[l] = take(sizeof(int32_t) * ((size_t)N << l));
+        }
+        o_fcnt = take(sizeof(int32_t) * 2 * (K + 1));
+        o_fictr = take(sizeof(unsigned long long) * (K + 1));
+        o_cen = take(sizeof(int2) * maxq);
+        o_ep = take(sizeof(double) * maxq);
+    }
     if (pp) {
         Pipe &p = *pp;
         p.probs = (const ProbDesc *)(ws + o_probs);
@@ -645,15 +708,38 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         p.cands = (NodeCands *)(ws + o_cands);
         p.work = (int2 *)(ws + o_work);
         p.refined = (RefineOut *)(ws + o_ref);
+        p.ncnt = p.cnt;
+        p.pass = window ? PASS_WINDOW : PASS_FULL;
+        for (int l = 0; l < kMaxDepth; ++l) {
+            p.fq_p[l] = window && l < K ? (int32_t *)(ws + o_fqp[l]) : nullptr;
+            p.fq_h[l] = window && l < K ? (int32_t *)(ws + o_fqh[l]) : nullptr;
+        }
+        p.fcnt = window ? (int32_t *)(ws + o_fcnt) : nullptr;
+        p.fitem_ctr = window ? (unsigned long long *)(ws + o_fictr) : nullptr;
+        p.center = window ? (int2 *)(ws + o_cen) : nullptr;
+        p.e_pred = window ? (double *)(ws + o_ep) : nullptr;
     }
     return off;
 }
 
-size_t pipe_bytes(long long N, int K, int C, int n_probs) {
-    return pipe_carve(nullptr, nullptr, N, K, C, n_probs);
+size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window) {
+    return pipe_carve(nullptr, nullptr, N, K, C, n_probs, window);
 }
 
-void pipe_layout(Pipe &p, char *ws) { pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs); }
+void pipe_layout(Pipe &p, char *ws) {
+    pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs, p.window != 0);
+}
+
+Pipe fallback_pipe(const Pipe &p, int level) {
+    Pipe q = p;
+    q.pass = PASS_FALLBACK;
+    q.cnt = p.fcnt;
+    q.item_ctr = p.fitem_ctr;
+    q.qp[level] = p.fq_p[level];
+    q.qh[level] = p.fq_h[level];
+    q.ncnt = p.cnt;
+    return q;
+}
 
 template <int EK>
 static cudaError_t launch_scan_t(const Pipe &p, int level, int warps, int grid, cudaStream_t s) {
@@ -665,42 +751,63 @@ static cudaError_t launch_scan_t(const Pipe &p, int level, int warps, int grid, 
     return cudaGetLastError();
 }
 
-cudaError_t pipe_enqueue(const Pipe &p, int warps, int grid, cudaStream_t s, cudaEvent_t *ev) {
+cudaError_t pipe_begin(const Pipe &p, cudaStream_t s) {
     cudaError_t e;
-    if (p.N == 0) return cudaSuccess;
     if ((e = cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * 2 * (p.K + 1), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.item_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
         cudaSuccess)
         return e;
+    if (p.window) {
+        if ((e = cudaMemsetAsync(p.fcnt, 0, sizeof(int32_t) * 2 * (p.K + 1), s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(p.fitem_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
+            cudaSuccess)
+            return e;
+    }
     k_init<<<(unsigned)((p.N + 255) / 256), 256, 0, s>>>(p);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t pipe_level(const Pipe &p, int l, int warps, int grid, cudaStream_t s,
+                       cudaEvent_t *ev) {
+    cudaError_t e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int l = 0; l < p.K; ++l) {
-        const long long max_nodes = p.N << l;
-        if (ev && (e = cudaEventRecord(ev[2 * l], s)) != cudaSuccess) return e;
-        e = p.energy == CVX_ENERGY_NH_DAMAGE
-                ? launch_scan_t<CVX_ENERGY_NH_DAMAGE>(p, l, warps, grid, s)
-                : launch_scan_t<CVX_ENERGY_DOUBLE_WELL>(p, l, warps, grid, s);
-        if (e != cudaSuccess) return e;
-        if (ev && (e = cudaEventRecord(ev[2 * l + 1], s)) != cudaSuccess) return e;
-        const unsigned nb = (unsigned)((max_nodes + 127) / 128);
-        k_select<<<nb, 128, 0, s>>>(p, l);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const long long want = (max_nodes * kNodeCand + 3) / 4;
-        const unsigned rg = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
-        const size_t rsm = (size_t)4 * p.stride64 * sizeof(double);
-        if ((e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)rsm)) != cudaSuccess)
-            return e;
-        k_refine<<<rg, 128, rsm, s>>>(p, l);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_commit<<<nb, 128, 0, s>>>(p, l);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    const long long max_nodes = p.N << l;
+    if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
+    e = p.energy == CVX_ENERGY_NH_DAMAGE ? launch_scan_t<CVX_ENERGY_NH_DAMAGE>(p, l, warps, grid, s)
+                                         : launch_scan_t<CVX_ENERGY_DOUBLE_WELL>(p, l, warps, grid, s);
+    if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+    const unsigned nb = (unsigned)((max_nodes + 127) / 128);
+    k_select<<<nb, 128, 0, s>>>(p, l);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long want = (max_nodes * kNodeCand + 3) / 4;
+    const unsigned rg = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    const size_t rsm = (size_t)4 * p.stride64 * sizeof(double);
+    if ((e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)rsm)) != cudaSuccess)
+        return e;
+    k_refine<<<rg, 128, rsm, s>>>(p, l);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_commit<<<nb, 128, 0, s>>>(p, l);
+    return cudaGetLastError();
+}
+
+cudaError_t pipe_end(const Pipe &p, cudaStream_t s) {
     k_leaf<<<(unsigned)((p.N + 127) / 128), 128, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t pipe_enqueue(const Pipe &p, int warps, int grid, cudaStream_t s, cudaEvent_t *ev) {
+    cudaError_t e;
+    if (p.N == 0) return cudaSuccess;
+    if ((e = pipe_begin(p, s)) != cudaSuccess) return e;
+    for (int l = 0; l < p.K; ++l)
+        if ((e = pipe_level(p, l, warps, grid, s, ev ? ev + 2 * l : nullptr)) != cudaSuccess)
+            return e;
+    return pipe_end(p, s);
 }
 
 }  // namespace cvx

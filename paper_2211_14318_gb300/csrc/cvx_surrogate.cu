@@ -137,23 +137,6 @@ cudaError_t alloc(T **p, size_t count) {
 
 }  // namespace
 
-// ----------------------------------------------------------------- state
-struct Surrogate {
-    bool has_weights = false;
-    float scale_h[12];  // mean (6), 1/std (6)
-    float *scale = nullptr;
-    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
-    bf16 *Wp[5] = {}, *Wt[5] = {};
-    long long adam_t = 0;
-    int cap = 0;
-    bf16 *X = nullptr, *XT = nullptr, *A[4] = {}, *AT[4] = {}, *dZo = nullptr, *dZoT = nullptr,
-         *dZ[2] = {}, *dZT[2] = {};
-    float *Z[4] = {}, *out = nullptr, *Yb = nullptr, *loss = nullptr;
-    int *err = nullptr;
-    int *idx = nullptr;
-    long long idx_cap = 0;
-};
-
 void destroy_surrogate(cvx_handle *h) {
     Surrogate *S = h->sur;
     if (!S) return;
@@ -176,8 +159,6 @@ void destroy_surrogate(cvx_handle *h) {
     delete S;
     h->sur = nullptr;
 }
-
-namespace {
 
 int sur_params(cvx_handle *h) {
     if (h->sur && h->sur->w) return CVX_OK;
@@ -242,6 +223,8 @@ int sur_batch(cvx_handle *h, int n) {
     return CVX_OK;
 }
 
+namespace {
+
 cudaError_t sur_pack(Surrogate &S, cudaStream_t s) {
     const int rp[5] = {256, 256, 256, 256, 16}, cp[5] = {16, 256, 256, 256, 256};
     for (int l = 0; l < 5; ++l) {
@@ -266,14 +249,20 @@ GemmEpi epi(int mode, int Mv, int *err) {
             return fail(CVX_ERR_CUDA, "tensor map for %s failed", #ptr);              \
     } while (0)
 
+}  // namespace
+
 // Forward pass of n <= cap standardised rows in S.X (and S.XT).  train: keep
-// Z, A^T for the backward pass.
-int sur_forward(cvx_handle *h, int n, bool train, cudaStream_t s) {
+// Z, A^T for the backward pass (otherwise the activations alternate between
+// two buffers).  M_dev (optional): device-side row count, of which rows
+// m_off .. m_off + n - 1 are these.
+int sur_forward(cvx_handle *h, int n, bool train, cudaStream_t s, const int *M_dev, int m_off) {
     Surrogate &S = *h->sur;
     CUtensorMap tX, tW, tA;
     TMAP(tX, S.X, n, 16, 16, 128);
     TMAP(tW, S.Wp[0], 256, 16, 16, 256);
     GemmEpi e = epi(EPI_HIDDEN, n, S.err);
+    e.M_dev = M_dev;
+    e.m_off = m_off;
     e.bias = S.w + kBOff[0];
     e.Z = train ? S.Z[0] : nullptr;
     e.ldz = 256;
@@ -283,17 +272,20 @@ int sur_forward(cvx_handle *h, int n, bool train, cudaStream_t s) {
     e.ldat = S.cap;
     CK(launch_gemm(tX, tW, n, 256, 16, 16, 256, e, s), "surrogate forward");
     for (int l = 1; l < 4; ++l) {
-        TMAP(tA, S.A[l - 1], n, 256, 256, 128);
+        bf16 *in = train ? S.A[l - 1] : S.A[(l - 1) & 1];
+        TMAP(tA, in, n, 256, 256, 128);
         TMAP(tW, S.Wp[l], 256, 256, 256, 256);
         e.bias = S.w + kBOff[l];
         e.Z = train ? S.Z[l] : nullptr;
-        e.A = S.A[l];
+        e.A = train ? S.A[l] : S.A[l & 1];
         e.AT = train ? S.AT[l] : nullptr;
         CK(launch_gemm(tA, tW, n, 256, 256, 256, 256, e, s), "surrogate forward");
     }
-    TMAP(tA, S.A[3], n, 256, 256, 128);
+    TMAP(tA, train ? S.A[3] : S.A[1], n, 256, 256, 128);
     TMAP(tW, S.Wp[4], 16, 256, 256, 16);
     GemmEpi o = epi(EPI_OUT, n, S.err);
+    o.M_dev = M_dev;
+    o.m_off = m_off;
     o.C = S.out;
     o.ldc = 7;
     o.n_store = 7;
@@ -301,6 +293,8 @@ int sur_forward(cvx_handle *h, int n, bool train, cudaStream_t s) {
     CK(launch_gemm(tA, tW, n, 16, 256, 256, 16, o, s), "surrogate forward");
     return CVX_OK;
 }
+
+namespace {
 
 // Loss and gradient (added to S.g) of the batch in S.X / S.Yb after
 // sur_forward(train = true).
@@ -406,9 +400,6 @@ int upload_weights(cvx_handle *h, const float *params, const float *mean, const 
 
 }  // namespace
 
-// Inference for the pipeline: raw outputs of n standardised input rows.
-int surrogate_outputs(cvx_handle *h, int n, cudaStream_t s) { return sur_forward(h, n, false, s); }
-
 }  // namespace cvx
 
 using namespace cvx;
@@ -477,7 +468,7 @@ int surrogate_forward(cvx_handle *h, int64_t n, const float *X, float *out, cvx_
         k_input<<<(m + 255) / 256, 256, 0, s>>>(m, nullptr, X + 6 * o, S.scale, S.X, nullptr, 0,
                                                 nullptr, nullptr);
         CK(cudaGetLastError(), "surrogate_forward");
-        rc = sur_forward(h, m, false, s);
+        rc = sur_forward(h, m, false, s, nullptr, 0);
         if (rc) return rc;
         CK(cudaMemcpyAsync(out + 7 * o, S.out, sizeof(float) * 7 * m, cudaMemcpyDeviceToDevice, s),
            "surrogate_forward");
@@ -501,7 +492,7 @@ int surrogate_loss_grad(cvx_handle *h, int64_t n, const float *X, const float *Y
     CK(cudaGetLastError(), "surrogate_loss_grad");
     CK(cudaMemsetAsync(S.g, 0, sizeof(float) * kSurParams, s), "surrogate_loss_grad");
     CK(cudaMemsetAsync(S.loss, 0, sizeof(float), s), "surrogate_loss_grad");
-    rc = sur_forward(h, (int)n, true, s);
+    rc = sur_forward(h, (int)n, true, s, nullptr, 0);
     if (rc) return rc;
     rc = sur_backward(h, (int)n, s);
     if (rc) return rc;
@@ -565,7 +556,7 @@ int surrogate_train(cvx_handle *h, int64_t n, const float *X, const float *Y,
             k_input<<<(m + 255) / 256, 256, 0, s>>>(m, S.idx + o, X, S.scale, S.X, S.XT, S.cap, Y, S.Yb);
             CK(cudaGetLastError(), "surrogate_train");
             CK(cudaMemsetAsync(S.g, 0, sizeof(float) * kSurParams, s), "surrogate_train");
-            rc = sur_forward(h, m, true, s);
+            rc = sur_forward(h, m, true, s, nullptr, 0);
             if (rc) return rc;
             rc = sur_backward(h, m, s);
             if (rc) return rc;

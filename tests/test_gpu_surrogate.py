@@ -125,3 +125,147 @@ def test_training_reduces_loss_and_save_load(cv, orc, tmp_path):
     out2 = c2.surrogate_forward(X[:64].astype(np.float32)).cpu().numpy()
     c2.close()
     np.testing.assert_array_equal(out1, out2)
+
+
+# ---------------------------------------------------------------- proposals
+TIE = 1e-11
+
+
+def _constant_net(theta_a, theta_b, xi, jump):
+    parts = [np.zeros(s) for s in mlp.SHAPES]
+    parts[9] = np.array([theta_a, theta_b, math.log(xi / (1 - xi)), *jump])
+    return mlp.flatten(parts).astype(np.float32).astype(np.float64)
+
+
+def test_labels_match_oracle_labels(cv, orc):
+    """surrogate_labels on the GPU's trees against oracle.mlp.labels_from_tree
+    on the oracle's trees of the same points (untied points only)."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    F, Fp = inputs.material_points(24, seed=33)
+    mat = _omat(orc)
+    beta = orc.history_update(mat, Fp)
+    p = api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT)
+    out = cv.convexify_points(p, F, beta, want_tree=True)
+    X, Y = cv.surrogate_labels(p, beta, out["tree"], 24)
+    X, Y = X.cpu().numpy(), Y.cpu().numpy()
+    sc = orc.Scan(orc.angle_directions(16, 16), 201, 0.5, 2)
+    _, _, tro, _ = orc.convexify(mat, sc, F, beta)
+    Xo, Yo = mlp.labels_from_tree(tro, F, beta, (16, 16), (orc.SCANNED, orc.LAMINATED))
+    tied = np.array([any(tro[q, i]["margin"] <= TIE for i in range(7) if tro[q, i]["flags"] & orc.SCANNED)
+                     for q in range(24)])
+    tg = api.tree_numpy(out["tree"], 24, 7)
+    per_g = [int(np.sum(tg[q]["flags"] & api.NODE_SCANNED > 0)) for q in range(24)]
+    per_o = [int(np.sum(tro[q]["flags"] & orc.SCANNED > 0)) for q in range(24)]
+    assert X.shape[0] == sum(per_g) and Xo.shape[0] == sum(per_o)
+    og = oo = 0
+    checked = 0
+    for q in range(24):
+        if not tied[q]:
+            assert per_g[q] == per_o[q]
+            sg, so = slice(og, og + per_g[q]), slice(oo, oo + per_o[q])
+            np.testing.assert_allclose(X[sg], Xo[so].astype(np.float32), rtol=1e-6, atol=1e-6)
+            np.testing.assert_allclose(Y[sg], Yo[so].astype(np.float32), rtol=1e-6, atol=1e-6)
+            checked += 1
+        og += per_g[q]
+        oo += per_o[q]
+    assert checked >= 12
+
+
+def test_propose_zero_tolerance_is_the_full_scan(cv, orc):
+    """gap_tol = 0: every node falls back, so the proposed form equals
+    convexify_points bit for bit (points without tie / overflow flags)."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    F, Fp = inputs.material_points(64, seed=34)
+    beta = orc.history_update(_omat(orc), Fp)
+    p = api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT)
+    cv.surrogate_set_weights(mlp.init_params(9), np.zeros(6), np.ones(6))
+    r = cv.surrogate_propose(p, F, beta, window=2, gap_tol=0.0)
+    q = cv.convexify_points(p, F, beta)
+    st, st1 = r["status"].cpu().numpy(), q["status"].cpu().numpy()
+    clean = ((st | st1) & (2 | 16)) == 0
+    assert clean.mean() > 0.5
+    np.testing.assert_array_equal(r["W_R"].cpu().numpy()[clean], q["W_R"].cpu().numpy()[clean])
+    np.testing.assert_array_equal(r["P"].cpu().numpy()[clean], q["P"].cpu().numpy()[clean])
+    assert np.all(r["fell_back"].cpu().numpy() == 1)
+
+
+def test_propose_constant_network_matches_oracle(cv, orc):
+    """A fixed network (biases only) proposing point 0's own full-scan
+    laminate: the GPU's window / fallback decisions and results against the
+    proposed-form oracle with the same network, depth 1 and 2."""
+    from oracle import surrogate as osur
+    from paper_2211_14318_gb300 import api, inputs
+
+    F, Fp = inputs.material_points(12, seed=35)
+    mat = _omat(orc)
+    beta = orc.history_update(mat, Fp)
+    Na = Nb = 12
+    sc = orc.Scan(orc.angle_directions(Na, Nb), 151, 0.5, 1)
+    _, _, tro, _ = orc.convexify(mat, sc, F, beta)
+    k = next(q for q in range(12) if tro[q, 0]["flags"] & orc.LAMINATED)
+    r0 = tro[k, 0]
+    d = int(r0["dir"])
+    flat = _constant_net(math.pi * (d // Nb) / Na, math.pi * (d % Nb) / Nb, r0["xi"],
+                         tro[k, 2]["F"] - tro[k, 1]["F"])
+    cv.surrogate_set_weights(flat, np.zeros(6), np.ones(6))
+    for depth in (1, 2):
+        p = api.Params(n_theta_a=Na, n_theta_b=Nb, line_points=151, depth=depth, **MAT)
+        r = cv.surrogate_propose(p, F, beta, window=2, gap_tol=1e-5, want_tree=True)
+        WRo, Po, trees = osur.propose_convexify(orc, mat, Na, Nb, 151, 0.5, depth, 2, 1e-5, flat,
+                                                np.zeros(6), np.ones(6), F, beta)
+        tg = api.tree_numpy(r["tree"], 12, p.tree_size)
+        WR = r["W_R"].cpu().numpy()
+        fb = r["fell_back"].cpu().numpy()
+        assert fb[k] == 0 or depth > 1
+        for q in range(12):
+            clear = all(rec.get("margin", np.inf) > TIE and rec.get("window_margin", np.inf) > TIE
+                        and abs(rec.get("gap", 0.0) - 1e-5) > 1e-6
+                        for rec in trees[q].values() if rec["flags"] & orc.SCANNED)
+            if not clear:
+                continue
+            ofb = any(rec["flags"] & osur.FALLBACK for rec in trees[q].values())
+            assert bool(fb[q]) == ofb, (depth, q)
+            for i, rec in trees[q].items():
+                if rec["flags"] & orc.LAMINATED:
+                    assert tg[q, i]["dir"] == rec["dir"], (depth, q, i)
+                    assert bool(tg[q, i]["flags"] & api.NODE_FALLBACK) == bool(rec["flags"] & osur.FALLBACK)
+            assert abs(WR[q] - WRo[q]) <= 1e-6 * (1e-8 + abs(WRo[q]))
+        if depth == 1:
+            assert fb[k] == 0 and abs(WR[k] - WRo[k]) <= 1e-12 * abs(WRo[k])
+
+
+def test_trained_network_gains_over_untrained(cv, orc):
+    """Train on labels from the GPU's own full scans (points drawn like the
+    16 x 16, L = 201 material-point workload with lambda in [1, 2]), then on
+    held-out points compare the window-only form (window 2, fallback on the
+    border only) with a trained and an untrained network: the trained one
+    falls back less and its W^R is closer to the full scan's."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    mat = _omat(orc)
+    p = api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT)
+    F, Fp = inputs.material_points(6000, seed=40, lam_hi=2.0)
+    beta = orc.history_update(mat, Fp)
+    out = cv.convexify_points(p, F, beta, want_tree=True)
+    X, Y = cv.surrogate_labels(p, beta, out["tree"], F.shape[0])
+    log = cv.surrogate_train(X, Y, epochs=40, batch=1024, lr=2e-3, init=True, seed=1)
+    assert log[-1] < 0.5 * log[0]
+    Ft, Fpt = inputs.material_points(512, seed=41, lam_hi=2.0)
+    bt = orc.history_update(mat, Fpt)
+    ref = cv.convexify_points(p, Ft, bt)["W_R"].cpu().numpy()
+
+    def run():
+        cv.stats(reset=True)
+        r = cv.surrogate_propose(p, Ft, bt, window=2, gap_tol=1e30)
+        s = cv.stats(reset=True)
+        err = np.abs(r["W_R"].cpu().numpy() - ref) / (1e-8 + np.abs(ref))
+        return r["fell_back"].cpu().numpy().mean(), np.quantile(err, 0.9), s
+
+    fb_t, e_t, s_t = run()
+    w, m, sd = cv.surrogate_get_weights()
+    cv.surrogate_set_weights(mlp.init_params(123), m, sd)
+    fb_u, e_u, s_u = run()
+    assert fb_t < fb_u and e_t <= e_u, (fb_t, fb_u, e_t, e_u)
+    assert s_t["lines"] < 0.5 * s_u["lines"] + 1, (s_t["lines"], s_u["lines"])

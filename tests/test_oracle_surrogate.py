@@ -1,0 +1,83 @@
+"""Pins of the surrogate-proposed oracle (oracle/surrogate.py) against the
+plain oracle (oracle.c): when every node falls back, or when a fixed network
+proposes the full scan's own direction, the proposed form must reproduce the
+plain method; the window enumerates (2w + 1)^2 wrapped grid cells."""
+import math
+
+import numpy as np
+
+from oracle import mlp
+from oracle import surrogate as osur
+
+MAT = (1.0, 5.0, 0.99, 0.5)
+
+
+def _points(orc, n, seed):
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(*MAT)
+    F, Fp = inputs.material_points(n, seed=seed)
+    return mat, F, orc.history_update(mat, Fp)
+
+
+def test_window_indices_wrap():
+    idx = osur.window_indices(0, 7, 1, 8, 8)
+    assert len(idx) == 9 and len(set(idx.tolist())) == 9
+    rows = sorted({int(i) // 8 for i in idx})
+    cols = sorted({int(i) % 8 for i in idx})
+    assert rows == [0, 1, 7] and cols == [0, 6, 7]
+    assert len(set(osur.window_indices(3, 3, 3, 7, 7).tolist())) == 49
+
+
+def test_zero_tolerance_falls_back_everywhere_and_equals_plain(orc):
+    """gap_tol = 0: every scanned node falls back, so the proposed form is the
+    plain method node for node (W^R and P bit-identical)."""
+    mat, F, beta = _points(orc, 10, 31)
+    flat = mlp.init_params(2)
+    mean, std = np.zeros(6), np.ones(6)
+    WR, P, trees = osur.propose_convexify(orc, mat, 8, 8, 101, 0.5, 2, 1, 0.0, flat, mean, std,
+                                          F, beta)
+    sc = orc.Scan(orc.angle_directions(8, 8), 101, 0.5, 2)
+    WRo, Po, tro, _ = orc.convexify(mat, sc, F, beta)
+    np.testing.assert_allclose(WR, WRo, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(P, Po, rtol=1e-12, atol=1e-14)
+    for t in trees:
+        for rec in t.values():
+            if rec["flags"] & orc.SCANNED:
+                assert rec["flags"] & osur.FALLBACK
+
+
+def _constant_net(theta_a, theta_b, xi, jump):
+    parts = [np.zeros(s) for s in mlp.SHAPES]
+    parts[9] = np.array([theta_a, theta_b, math.log(xi / (1 - xi)), *jump])
+    return mlp.flatten(parts)
+
+
+def test_window_around_the_true_direction_reproduces_the_full_scan(orc):
+    """Depth 1: a network that outputs exactly the full scan's own laminate
+    (angles of its direction, its xi and jump) centres the window on that
+    direction, which is then the window's best and not on its border; the
+    energy gap is zero, nothing falls back, and the result is the plain one."""
+    mat, F, beta = _points(orc, 8, 32)
+    Na = Nb = 12
+    dirs = orc.angle_directions(Na, Nb)
+    sc = orc.Scan(dirs, 151, 0.5, 1)
+    WRo, Po, tro, _ = orc.convexify(mat, sc, F, beta)
+    checked = 0
+    for p in range(F.shape[0]):
+        r = tro[p, 0]
+        if not r["flags"] & orc.LAMINATED:
+            continue
+        d = int(r["dir"])
+        jump = tro[p, 2]["F"] - tro[p, 1]["F"]
+        flat = _constant_net(math.pi * (d // Nb) / Na, math.pi * (d % Nb) / Nb, r["xi"], jump)
+        WR, P, trees = osur.propose_convexify(orc, mat, Na, Nb, 151, 0.5, 1, 2, 1e-9, flat,
+                                              np.zeros(6), np.ones(6), F[p:p + 1], beta[p:p + 1])
+        rec = trees[0][0]
+        assert rec["center"] == (d // Nb, d % Nb)
+        assert not rec["flags"] & osur.FALLBACK
+        assert rec["dir"] == d and rec["gap"] < 1e-9
+        assert WR[0] == WRo[p]
+        np.testing.assert_array_equal(P[0], Po[p])
+        checked += 1
+    assert checked >= 4
