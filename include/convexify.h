@@ -184,6 +184,8 @@ typedef struct cvx_stats {
     int64_t overflow;       /* nodes with more screened candidates than kept */
     int64_t window_nodes;   /* surrogate_propose: nodes scanned in a window */
     int64_t fallbacks;      /* ... of which deferred to the full scan       */
+    int64_t refine_full;    /* FP64 refinements that resampled the whole line
+                               (the windowed FP64 bridge was not certified) */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */

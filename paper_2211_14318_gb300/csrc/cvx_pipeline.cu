@@ -428,12 +428,51 @@ __device__ void bridge64(const double *sw, int L, int m0, int lane, int &a, int 
     }
 }
 
+// Windowed FP64 bridge: supporting-slope iteration over two 32-sample
+// windows of FP64 samples (vA at kA = loA + lane left of the centre, vB at
+// kB = loB + lane right of it), seeded with (a, b).  Ties go to the outermost
+// sample, as in bridge64.  false if it does not settle.
+__device__ bool window_bridge64(double vA, double vB, int kA, int kB, int m0, int &a, int &b,
+                                double &wa, double &wb, int lane, int loA, int loB) {
+    for (int it = 0; it < 64; ++it) {
+        const double s = (wb - wa) / (double)(b - a);
+        double eA = vA < INFINITY ? vA - s * (double)(kA - m0) : INFINITY;
+        double eB = vB < INFINITY ? vB - s * (double)(kB - m0) : INFINITY;
+        int ka = vA < INFINITY ? kA : INT_MAX, kb = vB < INFINITY ? kB : -1;
+        warp_min_dk(eA, ka, true);
+        warp_min_dk(eB, kb, false);
+        if (ka == INT_MAX || kb < 0) return false;
+        if (ka == a && kb == b) return true;
+        a = ka;
+        b = kb;
+        wa = __shfl_sync(kFull, vA, a - loA);
+        wb = __shfl_sync(kFull, vB, b - loB);
+    }
+    return false;
+}
+
+// k_refine: one warp per screened (node, direction).  The FP64 bridge of the
+// left and right sample sets is searched in two 32-sample FP64 windows around
+// the FP32 bridge and certified against the whole line with the FP32 samples:
+// every sample m outside the windows must satisfy
+//   (kappa w32_m - kEps32 max(kappa, |kappa w32_m|)) / kappa > the FP64 bridge line at m,
+// i.e. its FP64 value lies strictly above the line, so the windows' bridge is
+// the bridge of all samples.  Otherwise (and where the FP32 samples are not
+// finite) the whole line is resampled in FP64 (bridge64).
+template <int EK>
 __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
     extern __shared__ double sm64[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double *sw = sm64 + warp * P.stride64;
+    float *sw32 = reinterpret_cast<float *>(sw);
+    __shared__ unsigned s_hc[4][HC_N];  // the screen's event counters (not reported here)
+    if (lane == 0)
+        for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
+    __syncwarp();
+    HullCounters hc{s_hc[warp]};
     const int nwork = P.cnt[(P.K + 1) + level];
     const int32_t *qp = P.qp[level], *qh = P.qh[level];
+    unsigned long long n_full = 0;
     for (int w = blockIdx.x * (blockDim.x >> 5) + warp; w < nwork;
          w += gridDim.x * (blockDim.x >> 5)) {
         const int2 wk = P.work[w];
@@ -441,6 +480,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         const int p = qp[qi], hi = qh[qi];
         const ProbDesc &pd = P.probs[P.pid[p]];
         const LineSpec ln = pd.line;
+        const int m0 = ln.m0;
         const int dir = P.cands[qi].dir[c];
         const cvx_node *nd = node_ptr(pd, p, hi);
         const double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
@@ -448,18 +488,80 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
                              __dmul_rn(d[1], d[3])};
         const double beta = pd.beta[p - pd.point_off];
-        for (int k = lane; k < ln.L; k += 32) sw[k] = sample_w64(F, R, k, ln.m0, ln.h64, beta, pd.mat);
+        // FP32 line and its approximate bridge
+        const NodeLine nl = make_node_line(F, beta, pd.mat);
+        const DirLine dl = make_dir_line<EK>(nl, P.dir32[pd.dir_off + dir]);
+        float tl[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - m0) * ln.h32;
+        sample_line<EK>(sw32, nl, dl, ln, lane, tl);
         __syncwarp();
-        int a, b;
-        bridge64(sw, ln.L, ln.m0, lane, a, b);
+        const LineGeom g{ln.L, m0, ln.nfull};
+        const ScreenOut so = warp_screen(sw32, g, lane, -1, -1, hc);
+        int a = so.a, b = so.b;
+        bool ok = a >= 0 && b >= 0;
+        double wa = 0.0, wb = 0.0;
+        int loA = 0, loB = 0;
+        if (ok) {
+            loA = max(0, min(a - 16, m0 - 32));
+            loB = min(max(m0 + 1, b - 15), ln.L - 32);
+            loB = max(loB, m0 + 1);
+            const int kA = loA + lane, kB = loB + lane;
+            double vA = INFINITY, vB = INFINITY;
+            if (kA < m0) {
+                const double v = sample_w64(F, R, kA, m0, ln.h64, beta, pd.mat);
+                vA = v == v ? v : INFINITY;
+            }
+            if (kB < ln.L) {
+                const double v = sample_w64(F, R, kB, m0, ln.h64, beta, pd.mat);
+                vB = v == v ? v : INFINITY;
+            }
+            wa = __shfl_sync(kFull, vA, a - loA);
+            wb = __shfl_sync(kFull, vB, b - loB);
+            ok = wa < INFINITY && wb < INFINITY &&
+                 window_bridge64(vA, vB, kA, kB, m0, a, b, wa, wb, lane, loA, loB);
+        }
+        if (ok) {
+            // certificate over the samples outside the windows
+            const double s = (wb - wa) / (double)(b - a);
+            const double kap = pd.kappa;
+            bool good = true;
+            for (int k = lane; k < ln.L && good; k += 32) {
+                if (k == m0 || (k >= loA && k < loA + 32 && k < m0) || (k >= loB && k < loB + 32))
+                    continue;
+                const double line = wa + s * (double)(k - a);
+                const float v32 = sw32[k];
+                if (v32 < INFINITY && v32 > -INFINITY) {
+                    const double e = (double)kEps32 * fmax(kap, fabs((double)v32));
+                    const double lb = ((double)v32 - e) / kap;
+                    good = lb > line + 1e-14 * (fabs(line) + fabs(lb));
+                } else {
+                    const double v = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
+                    good = !(v == v) || v > line + 1e-14 * fabs(line);
+                }
+            }
+            ok = __all_sync(kFull, good);
+        }
+        __syncwarp();
+        if (!ok) {
+            // resample the whole line in FP64
+            ++n_full;
+            for (int k = lane; k < ln.L; k += 32) sw[k] = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
+            __syncwarp();
+            bridge64(sw, ln.L, m0, lane, a, b);
+            if (a >= 0) {
+                wa = sw[a];
+                wb = sw[b];
+            }
+        }
         if (lane == 0) {
             RefineOut o;
             o.a = a;
             o.b = b;
             o.pad = 0;
             if (a >= 0) {
-                const double xa = (double)(a - ln.m0), xb = (double)(b - ln.m0);
-                o.q = (xb * sw[a] - xa * sw[b]) / (xb - xa);
+                const double xa = (double)(a - m0), xb = (double)(b - m0);
+                o.q = (xb * wa - xa * wb) / (xb - xa);
                 o.ok = 1;
             } else {
                 o.q = INFINITY;
@@ -469,6 +571,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         }
         __syncwarp();
     }
+    if (lane == 0) add_counter(P.counters, C_REFFULL, n_full);
 }
 
 // -------------------------------------------------------------------------
@@ -786,10 +889,12 @@ cudaError_t pipe_level(const Pipe &p, int l, int warps, int grid, cudaStream_t s
     const long long want = (max_nodes * kNodeCand + 3) / 4;
     const unsigned rg = (unsigned)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     const size_t rsm = (size_t)4 * p.stride64 * sizeof(double);
-    if ((e = cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)rsm)) != cudaSuccess)
+    auto kr = p.energy == CVX_ENERGY_NH_DAMAGE ? k_refine<CVX_ENERGY_NH_DAMAGE>
+                                               : k_refine<CVX_ENERGY_DOUBLE_WELL>;
+    if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm)) !=
+        cudaSuccess)
         return e;
-    k_refine<<<rg, 128, rsm, s>>>(p, l);
+    kr<<<rg, 128, rsm, s>>>(p, l);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_commit<<<nb, 128, 0, s>>>(p, l);
     return cudaGetLastError();
