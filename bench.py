@@ -49,6 +49,13 @@ def args_parse():
     ap.add_argument("--nx", type=int, default=NX, help="mesh size (default 128 -> 65,536 points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
+    ap.add_argument("--form", default="full-scan", choices=["full-scan", "surrogate"],
+                    help="surrogate: the learned-proposal form over a load path (its own line)")
+    ap.add_argument("--gap-tol", type=float, default=1e-6, help="surrogate fallback tolerance")
+    ap.add_argument("--window", type=int, default=4, help="surrogate window half-width (cells)")
+    ap.add_argument("--load-steps", type=int, default=20)
+    ap.add_argument("--check-points", type=int, default=1024,
+                    help="surrogate: subsample checked against the full scan")
     return ap.parse_args()
 
 
@@ -363,10 +370,136 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- surrogate form
+S_ANGLES, S_LINE, S_DEPTH = 128, 2049, 3
+
+
+def run_surrogate(a):
+    """The learned-proposal form over a load path (stretch 1.0 -> 1.8, history
+    updated every step): 128 x 128 angles, window +-w cells, L = 2049, depth 3,
+    fallback per gap_tol.  The network is first trained on labels from the
+    GPU's own full scans (material points with lambda in [1, 2] and points of
+    the load path; labels on the 128^2 grid, L = 513, depth 2).  Reported: the
+    proposed form's points/s over the whole path, its fallback rate, its W^R
+    error against the full scan on a subsample at three steps, and the plain
+    full scan's points/s on the same mesh and on coarser angle grids with their
+    own errors (the plain form's curve of points/s against error)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api, inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    cv = api.Convexifier(0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(f):
+        e0, e1 = ev(), ev()
+        e0.record()
+        r = f()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    # ---- training data and training
+    pl = api.Params(n_theta_a=S_ANGLES, n_theta_b=S_ANGLES, line_points=513, depth=2, **MAT)
+    path = inputs.load_path(a.nx, n_steps=a.load_steps, stretch_end=1.8, seed=7)
+    F1, Fp1 = inputs.surrogate_inputs(131072, seed=100)
+    b1 = cv.history_update(pl, Fp1)
+    Xs, Ys, t_label = [], [], 0.0
+    out, dt = timed(lambda: cv.convexify_points(pl, F1, b1, want_tree=True))
+    t_label += dt
+    X, Y = cv.surrogate_labels(pl, b1, out["tree"], F1.shape[0])
+    Xs.append(X)
+    Ys.append(Y)
+    for k in (3, 7, 11, 15, 19):
+        k = min(k, a.load_steps - 1)
+        Fk = path[k]
+        bk = cv.history_update(pl, path[k - 1]).cpu().numpy()
+        idx = np.random.default_rng(k).choice(Fk.shape[0], min(16384, Fk.shape[0]), replace=False)
+        out, dt = timed(lambda: cv.convexify_points(pl, Fk[idx], bk[idx], want_tree=True))
+        t_label += dt
+        X, Y = cv.surrogate_labels(pl, bk[idx], out["tree"], len(idx))
+        Xs.append(X)
+        Ys.append(Y)
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    t0 = time.perf_counter()
+    log = cv.surrogate_train(X, Y, epochs=30, batch=8192, lr=1e-3, init=True, seed=0)
+    t_train = time.perf_counter() - t0
+
+    # ---- load path
+    p = api.Params(n_theta_a=S_ANGLES, n_theta_b=S_ANGLES, line_points=S_LINE, depth=S_DEPTH, **MAT)
+    n = path[0].shape[0]
+    sub = np.linspace(0, n - 1, min(a.check_points, n)).astype(int)
+    beta = torch.zeros(n, dtype=torch.float64, device=dev)
+    out = dict(W_R=torch.empty(n, dtype=torch.float64, device=dev),
+               P=torch.empty(n, 4, dtype=torch.float64, device=dev),
+               status=torch.empty(n, dtype=torch.int32, device=dev),
+               fell_back=torch.empty(n, dtype=torch.uint8, device=dev))
+    checks = {max(1, a.load_steps // 4), max(1, a.load_steps // 2), a.load_steps}
+    t_sur, fell, rows = 0.0, 0.0, []
+    cv.stats(reset=True)
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None else "0")
+    clocks.start()
+    for k in range(1, a.load_steps + 1):
+        Fk = torch.from_numpy(path[k - 1]).to(dev)
+
+        def step():
+            return cv.surrogate_propose(p, Fk, beta, window=a.window, gap_tol=a.gap_tol, out=out)
+
+        r, dt = timed(step)
+        t_sur += dt
+        fell += float(r["fell_back"].float().mean())
+        if k in checks:
+            ref, dt_ref = timed(lambda: cv.convexify_points(p, Fk, beta))
+            W = r["W_R"].cpu().numpy()[sub]
+            refW = ref["W_R"].cpu().numpy()[sub]
+            e = np.abs(W - refW) / (1e-8 + np.abs(refW))
+            row = {"step": k, "surrogate_pts_per_s": n / dt, "full_scan_pts_per_s": n / dt_ref,
+                   "err_p50": float(np.quantile(e, 0.5)), "err_p99": float(np.quantile(e, 0.99)),
+                   "fell_back": float(r["fell_back"].float().mean())}
+            for na in (16, 32, 64):
+                q = api.Params(n_theta_a=na, n_theta_b=na, line_points=S_LINE, depth=S_DEPTH, **MAT)
+                rq, dtq = timed(lambda: cv.convexify_points(q, Fk, beta))
+                eq = np.abs(rq["W_R"].cpu().numpy()[sub] - refW) / (1e-8 + np.abs(refW))
+                row[f"plain_{na}x{na}"] = {"pts_per_s": n / dtq, "err_p50": float(np.quantile(eq, 0.5)),
+                                           "err_p99": float(np.quantile(eq, 0.99))}
+            rows.append(row)
+        beta = cv.history_update(p, Fk, beta)
+    ck = clocks.stop()
+    st = cv.stats(reset=True)
+    line = {
+        "metric": METRIC, "value": n * a.load_steps / t_sur, "unit": "points/s", "n_gpus": 1,
+        "steps": a.load_steps, "warmup": 0, "ms_per_step": 1e3 * t_sur / a.load_steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32/f64",
+        "data": "synthetic",
+        "config": {"workload": f"load path, mesh {a.nx}x{a.nx} Q1 x 4 Gauss points = {n} points, "
+                               f"stretch 1.0 -> 1.8 in {a.load_steps} steps, {S_ANGLES}x{S_ANGLES} "
+                               f"angles, window +-{a.window}, L={S_LINE}, depth {S_DEPTH}",
+                   "form": "surrogate", "gap_tol": a.gap_tol, "window": a.window,
+                   "timed": "surrogate_propose per step (CUDA events); history update excluded"},
+        "surrogate": {"fell_back_points_mean": fell / a.load_steps,
+                      "window_nodes": st["window_nodes"], "fallback_nodes": st["fallbacks"],
+                      "train": {"samples": int(X.shape[0]), "label_s": t_label, "train_s": t_train,
+                                "loss_first": float(log[0]), "loss_last": float(log[-1])},
+                      "checks": rows},
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    cv.close()
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.form == "surrogate":
+        run_surrogate(a)
     else:
         run_ours(a)
 

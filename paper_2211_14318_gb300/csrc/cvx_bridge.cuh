@@ -373,15 +373,20 @@ struct ScreenOut {
 // caller); per lane four independent running minima per chunk component.
 __device__ __forceinline__ float min_pass(const float *sw, const LineGeom &g, int lane, float s) {
     const float ns = -s;
+    const f32x2 NS = pk2(ns, ns);
     float m[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
     float fq = 0.0f;
 #pragma unroll 4
     for (int q = 0; q < g.nfull; ++q, fq += 128.0f) {
         const float4 v = *reinterpret_cast<const float4 *>(sw + 128 * q + 4 * lane);
-        m[0] = fminf(m[0], __fmaf_rn(ns, fq, v.x));
-        m[1] = fminf(m[1], __fmaf_rn(ns, fq, v.y));
-        m[2] = fminf(m[2], __fmaf_rn(ns, fq, v.z));
-        m[3] = fminf(m[3], __fmaf_rn(ns, fq, v.w));
+        const f32x2 FQ = pk2(fq, fq);
+        float e0, e1, e2, e3;
+        upk2(fma2(NS, FQ, pk2(v.x, v.y)), e0, e1);
+        upk2(fma2(NS, FQ, pk2(v.z, v.w)), e2, e3);
+        m[0] = fminf(m[0], e0);
+        m[1] = fminf(m[1], e1);
+        m[2] = fminf(m[2], e2);
+        m[3] = fminf(m[3], e3);
     }
     float e = INFINITY;
 #pragma unroll

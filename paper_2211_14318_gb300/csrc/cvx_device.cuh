@@ -178,13 +178,17 @@ __device__ inline bool newton_tangent64(const double F[4], const double R[4], do
 //   K1 = D_inf D_0 e_k, K2 = D_inf e_k
 // (d <= 0 gives (1 - D_inf + D_inf e_k) d = (1 - D(beta_k)) d; d > 0 gives
 // (1 - D_inf)(s - beta_k) + D_inf D_0 (e_k - e^{-s/D_0})).  The kernels sample
-// kappa W with kappa = log2(e)/D_0 > 0, so that the exponential is one ex2 of
-// -max(kappa d, 0): all coefficients carry the factor kappa, which changes no
-// hull or direction decision.  J <= 0 yields +inf or NaN, which the hull
-// search ignores.
+//   v = kappa' W - C,  kappa' = kappa / (1 - D_inf),  kappa = log2(e) / D_0,
+//   C = kappa D_inf D_0 e_k / (1 - D_inf)          (per point),
+// i.e. with d scaled by kappa (so that the exponential is one ex2 of
+// -max(d, 0)) and the whole divided by 1 - D_inf:
+//   v = d + K2' min(d, 0) - K1' 2^{-max(d, 0)},  K1' = C,  K2' = K2 / (1 - D_inf).
+// A positive factor and a per-point constant change no hull or direction
+// decision; values are mapped back by W = (v + C) / kappa'.  J <= 0 yields
+// +inf or NaN, which the hull search ignores.
 // -------------------------------------------------------------------------
 struct NodeLine {
-    float A0, B1, B2, a1, K1, K2, mu;  // kappa-scaled (K2 and a1 are ratios)
+    float A0, B1, B2, K1, K2, mu;  // kappa-scaled (K2 is a ratio)
     float J0;
     float F[4];
     float cof[4];
@@ -206,23 +210,50 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Sample scale kappa: log2(e)/D_0 for the damage energy, 1 for the test energy.
-__host__ __device__ inline double line_kappa(const Material &m) {
-    return m.energy == CVX_ENERGY_NH_DAMAGE ? kLog2e / m.D0 : 1.0;
+// Paired FP32 arithmetic: two independent FP32 values in a 64-bit register
+// pair, one fma.rn.f32x2 computing both (each an IEEE fma with round to
+// nearest, so results equal the scalar __fmaf_rn ones).  Used by the
+// certification pass of the hull search; the sampler stays scalar (measured
+// faster inside the full line scan).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float x, float y) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(r));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
-// Node constants from F (FP64) and beta_k, rounded to FP32 (kappa-scaled).
+// Sample scale kappa' (v = kappa' W - C): log2(e) / (D_0 (1 - D_inf)) for the
+// damage energy, 1 for the test energy.
+__host__ __device__ inline double line_kappa(const Material &m) {
+    return m.energy == CVX_ENERGY_NH_DAMAGE ? kLog2e / (m.D0 * (1.0 - m.Dinf)) : 1.0;
+}
+
+// Sample shift C of a point with history beta_k (0 for the test energy).
+__host__ __device__ inline double line_shift(const Material &m, double beta_k) {
+    if (m.energy != CVX_ENERGY_NH_DAMAGE) return 0.0;
+    return kLog2e * m.Dinf * exp(-beta_k / m.D0) / (1.0 - m.Dinf);
+}
+
+// Node constants from F (FP64) and beta_k, rounded to FP32.
 __device__ inline NodeLine make_node_line(const double F[4], double beta_k, const Material &m) {
     NodeLine nl;
-    const double kap = line_kappa(m);
+    const double kap = m.energy == CVX_ENERGY_NH_DAMAGE ? kLog2e / m.D0 : 1.0;
+    const double a1 = 1.0 - m.Dinf;
     double fsq = F[0] * F[0] + F[1] * F[1] + F[2] * F[2] + F[3] * F[3];
     double ek = exp(-beta_k / m.D0);
     nl.A0 = (float)(kap * (0.5 * m.mu * (fsq - 2.0) - beta_k));
     nl.B1 = (float)(kap * (-m.mu * kLn2d));
     nl.B2 = (float)(kap * (0.5 * m.lam * kLn2d * kLn2d));
-    nl.a1 = (float)(1.0 - m.Dinf);
-    nl.K1 = (float)(kap * m.Dinf * m.D0 * ek);
-    nl.K2 = (float)(m.Dinf * ek);
+    nl.K1 = (float)line_shift(m, beta_k);
+    nl.K2 = (float)(m.Dinf * ek / a1);
     nl.mu = (float)(kap * m.mu);
     nl.J0 = (float)(F[0] * F[3] - F[1] * F[2]);
     for (int k = 0; k < 4; ++k) nl.F[k] = (float)F[k];
@@ -259,8 +290,8 @@ __device__ __forceinline__ DirLine make_dir_line(const NodeLine &nl, float4 d) {
     return dl;
 }
 
-// One FP32 sample of kappa W at parameter t: 11 FP32-pipe instructions and
-// 2 MUFU for the damage energy.
+// One FP32 sample of v = kappa' W - C at parameter t: 9 FP32-pipe
+// instructions and 2 MUFU for the damage energy.
 template <int EK>
 __device__ __forceinline__ float sample_w(const NodeLine &nl, const DirLine &dl, float t) {
     if (EK == CVX_ENERGY_NH_DAMAGE) {
@@ -269,9 +300,8 @@ __device__ __forceinline__ float sample_w(const NodeLine &nl, const DirLine &dl,
         const float lg = lg2_approx(J);
         const float d = __fmaf_rn(lg, __fmaf_rn(lg, nl.B2, nl.B1), p);
         const float e = ex2_approx(-fmaxf(d, 0.0f));
-        float w = __fmaf_rn(d, nl.a1, nl.K1);
-        w = __fmaf_rn(-nl.K1, e, w);
-        return __fmaf_rn(nl.K2, fminf(d, 0.0f), w);
+        const float w = __fmaf_rn(nl.K2, fminf(d, 0.0f), d);
+        return __fmaf_rn(-nl.K1, e, w);
     } else {
         float w = __fmaf_rn(dl.c[4], t, dl.c[3]);
         w = __fmaf_rn(w, t, dl.c[2]);

@@ -14,8 +14,9 @@ constexpr int kWarpTop = 4;    // best directions kept per warp
 constexpr int kItemTop = 8;    // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
 constexpr int kMaxDepth = 8;
-// Bound on the FP32 sampling error of kappa W (kappa-scaled units, relative to
-// max(kappa, |q|)): 3.5 times the largest error measured against FP64.
+// Bound on the FP32 sampling error of v = kappa' W - C in sample units,
+// relative to max(kappa', |v| + C) (>= kappa' max(1, |W|)): 3.5 times the
+// largest error measured against FP64.
 constexpr float kEps32 = 1.1e-6f;
 
 // Best directions of one work item (a node and a block of its directions),
@@ -34,8 +35,8 @@ struct ItemCands {
 struct NodeCands {
     int dir[kNodeCand];
     int n, flags;
-    float qcut;  // smallest FP32 q of a direction not refined (kappa-scaled)
-    float eps;   // FP32 error bound used at this node (kappa-scaled)
+    float qcut;  // smallest FP32 q of a direction not refined (sample units)
+    float eps;   // FP32 error bound used at this node (sample units)
 };
 
 struct RefineOut {

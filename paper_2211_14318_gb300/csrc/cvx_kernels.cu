@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(128) k_sample_lines(int64_t n, const double *F
     for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
     sample_line<EK>(sw, nl, dl, ln, lane, tl);
     __syncwarp();
-    const double kap = line_kappa(m);
-    for (int k = lane; k < ln.L; k += 32) out[line * ln.L + k] = (float)((double)sw[k] / kap);
+    const double kap = line_kappa(m), shift = line_shift(m, beta[line]);
+    for (int k = lane; k < ln.L; k += 32)
+        out[line * ln.L + k] = (float)(((double)sw[k] + shift) / kap);
 }
 
 cudaError_t launch_sample_lines(int64_t n, const double *F, const double *beta,

@@ -191,7 +191,6 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         nl.A0 = s_nl.A0;
         nl.B1 = s_nl.B1;
         nl.B2 = s_nl.B2;
-        nl.a1 = s_nl.a1;
         nl.K1 = s_nl.K1;
         nl.K2 = s_nl.K2;
         const int D = win ? s_pd.wD : s_pd.D, doff = s_pd.dir_off;
@@ -338,7 +337,8 @@ __global__ void k_select(const Pipe P, int level) {
     }
     NodeCands nc;
     nc.n = 0;
-    nc.eps = kEps32 * fmaxf(pd.kappa_f, fmaxf(fabsf(qmin), fabsf(w0)));
+    const float shift = (float)line_shift(pd.mat, pd.beta[P.qp[level][qi] - pd.point_off]);
+    nc.eps = kEps32 * fmaxf(pd.kappa_f, fmaxf(fabsf(qmin), fabsf(w0)) + shift);
     float qcut = drop;
     if (qmin <= w0 + 2.0f * nc.eps) {
         const float lim = fminf(w0, U) + 2.0f * nc.eps;
@@ -455,7 +455,7 @@ __device__ bool window_bridge64(double vA, double vB, int kA, int kB, int m0, in
 // left and right sample sets is searched in two 32-sample FP64 windows around
 // the FP32 bridge and certified against the whole line with the FP32 samples:
 // every sample m outside the windows must satisfy
-//   (kappa w32_m - kEps32 max(kappa, |kappa w32_m|)) / kappa > the FP64 bridge line at m,
+//   (v32_m - kEps32 max(kappa', |v32_m| + C) + C) / kappa' > the FP64 bridge line at m,
 // i.e. its FP64 value lies strictly above the line, so the windows' bridge is
 // the bridge of all samples.  Otherwise (and where the FP32 samples are not
 // finite) the whole line is resampled in FP64 (bridge64).
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         if (ok) {
             // certificate over the samples outside the windows
             const double s = (wb - wa) / (double)(b - a);
-            const double kap = pd.kappa;
+            const double kap = pd.kappa, shift = line_shift(pd.mat, beta);
             bool good = true;
             for (int k = lane; k < ln.L && good; k += 32) {
                 if (k == m0 || (k >= loA && k < loA + 32 && k < m0) || (k >= loB && k < loB + 32))
@@ -532,8 +532,8 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
                 const double line = wa + s * (double)(k - a);
                 const float v32 = sw32[k];
                 if (v32 < INFINITY && v32 > -INFINITY) {
-                    const double e = (double)kEps32 * fmax(kap, fabs((double)v32));
-                    const double lb = ((double)v32 - e) / kap;
+                    const double e = (double)kEps32 * fmax(kap, fabs((double)v32) + shift);
+                    const double lb = ((double)v32 - e + shift) / kap;
                     good = lb > line + 1e-14 * (fabs(line) + fabs(lb));
                 } else {
                     const double v = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
@@ -601,7 +601,8 @@ __global__ void k_commit(const Pipe P, int level) {
     // FP64 node value among the refined directions; an unrefined direction
     // (FP32 q >= qcut) could only win if qcut - eps reached it
     const double V = (bc >= 0 && ro[bc].q < nd.w) ? ro[bc].q : nd.w;
-    const bool overflow = !(((double)nc.qcut - (double)nc.eps) / pd.kappa > V);
+    const double shift = line_shift(pd.mat, pd.beta[p - pd.point_off]);
+    const bool overflow = !(((double)nc.qcut - (double)nc.eps + shift) / pd.kappa > V);
     if (P.pass == PASS_WINDOW) {
         // fallback test of a proposal window: the window's best direction on
         // its border, or an energy gap |E_pred - V| / (1e-8 + |V|) above
