@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         }
         float dropped = INFINITY, w0 = 0.0f, qhi_min = INFINITY;
         int warm_a = -1, warm_b = -1;
+        float my_cJ = 0.0f;  // lane k keeps the k-th line of each run of 32 for the work count
         for (int dj = jb; dj < je; ++dj) {
             const int gd = win ? window_dir(s_pd, cen, dj) : dj;
             const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
@@ -216,10 +217,16 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             __syncwarp();
             const ScreenOut o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
             __syncwarp();
-            if (lane == 0) {
-                ++n_lines;
-                n_valid += valid_samples(dl, ln, EK);
+            const int r = (dj - jb) & 31;
+            if (lane == r) my_cJ = dl.cJ;
+            if (r == 31 || dj == je - 1) {
+                if (lane <= r) {
+                    DirLine vl = dl;
+                    vl.cJ = my_cJ;
+                    n_valid += valid_samples(vl, ln, EK);
+                }
             }
+            if (lane == 0) ++n_lines;
             w0 = o.w0;
             if (o.a >= 0) {
                 warm_a = o.a;
@@ -279,6 +286,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             P.items[item] = r;
         }
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) n_valid += __shfl_xor_sync(kFull, n_valid, o);
     if (lane == 0) {
         const unsigned *c = hc.c;
         add_counter(P.counters, C_LINES, n_lines);

@@ -131,3 +131,51 @@ def test_autotuner_choice_and_cache_file(orc, tmp_path):
         c2.close()
     finally:
         del os.environ["CVX_AUTOTUNE_CACHE"]
+
+
+def test_full_size_batch_sampled_against_oracle(cv, orc):
+    """The batched workload at full size: 256 meshes with log-uniform point
+    counts in [1e3, 1e5] (about 5.5 M points), per-problem stretch in
+    [1.1, 1.8], angle grid 32^2 or 64^2, line 513 or 1025, depth 2 or 3, in one
+    autotuned, graph-captured run; the oracle recomputes two sampled points
+    of each of 12 problems one by one."""
+    import torch
+
+    from paper_2211_14318_gb300 import api, inputs
+
+    probs = inputs.batch_problems(256, seed=0)
+    mat = _omat(orc)
+    dev = torch.device("cuda", 0)
+    items, total = [], 0
+    for pr in probs:
+        p = api.Params(n_theta_a=pr.n_angle, n_theta_b=pr.n_angle, line_points=pr.L,
+                       depth=pr.depth, **MAT)
+        beta = cv.history_update(p, pr.F_prev)
+        items.append((p, torch.as_tensor(pr.F, device=dev), beta))
+        total += pr.F.shape[0]
+    assert 3_000_000 < total < 9_000_000
+    res = cv.convexify_batch(items)
+    torch.cuda.synchronize()
+    w, cap, cached = cv.batch_tuning()
+    assert w in (4, 8)
+    rng = np.random.default_rng(1)
+    checked = 0
+    for k in rng.choice(256, 12, replace=False):
+        p, F, beta = items[k]
+        n = F.shape[0]
+        idx = rng.choice(n, 2, replace=False)
+        Fh = F.cpu().numpy()[idx]
+        bh = beta.cpu().numpy()[idx]
+        sc = orc.Scan(orc.angle_directions(p.n_theta_a, p.n_theta_b), p.line_points, p.t_half,
+                      p.depth, round32=False)
+        WRo, Po, tro, sto = orc.convexify(mat, sc, Fh, bh)
+        WR = res[k]["W_R"].cpu().numpy()[idx]
+        P = res[k]["P"].cpu().numpy()[idx]
+        for j in range(2):
+            sc_nodes = tro[j]["flags"] & orc.SCANNED > 0
+            if np.any(tro[j]["margin"][sc_nodes] <= TIE):
+                continue
+            assert _rel(np.array([WR[j]]), np.array([WRo[j]]))[0] < 1e-6, (k, j)
+            assert np.linalg.norm(P[j] - Po[j]) / (1e-8 + np.linalg.norm(Po[j])) < 1e-5
+            checked += 1
+    assert checked >= 16
