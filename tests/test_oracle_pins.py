@@ -126,6 +126,36 @@ def test_alg1_matches_brute_force_vertices(orc, seed):
     assert list(orc.lower_hull(x, w)) == _brute_vertices(x, w)
 
 
+def test_hull_arrays_are_convex_minorants(orc):
+    """Every hull array of Algorithm 1 on sampled NH lines, interpolated on the
+    whole grid: below the samples, equal to them at its vertices, with
+    nonnegative second differences (a convex minorant)."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F, Fp = inputs.material_points(20, seed=12, lam_hi=1.8)
+    beta = orc.history_update(mat, Fp)
+    dirs = orc.angle_directions(6, 6)
+    rng = np.random.default_rng(4)
+    lines = 0
+    for p in range(20):
+        for j in rng.choice(36, 6, replace=False):
+            w, v = orc.sample_line(mat, F[p], beta[p], orc.rank_one(dirs[j]), 161, 0.6)
+            idx = np.nonzero(v)[0]
+            x = idx.astype(np.float64)
+            wv = w[idx]
+            vt = orc.lower_hull(x, wv)
+            hull = np.interp(x, x[vt], wv[vt])
+            scale = np.max(np.abs(wv))
+            assert np.all(hull <= wv + 1e-13 * scale)
+            np.testing.assert_array_equal(hull[vt], wv[vt])
+            d2 = hull[2:] - 2 * hull[1:-1] + hull[:-2]
+            assert np.all(d2 >= -1e-13 * scale), d2.min()
+            assert vt[0] == 0 and vt[-1] == len(x) - 1
+            lines += 1
+    assert lines == 120
+
+
 @pytest.mark.parametrize("seed", range(40))
 def test_bridge_is_min_over_pairs(orc, seed):
     """Value of the hull at x = 0 equals min(w_0, min over pairs a < 0 < b of
