@@ -186,6 +186,8 @@ typedef struct cvx_stats {
     int64_t fallbacks;      /* ... of which deferred to the full scan       */
     int64_t refine_full;    /* FP64 refinements that resampled the whole line
                                (the windowed FP64 bridge was not certified) */
+    int64_t lines_bounded;  /* lines excluded by their sampling-pass bound,
+                               without a hull search                        */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */

@@ -19,6 +19,11 @@ constexpr int kMaxDepth = 8;
 // largest error measured against FP64.
 constexpr float kEps32 = 1.1e-6f;
 
+// The FP32 error bound at sample value x (C = the point's sample shift).
+__device__ __forceinline__ float eps32_at(float x, float kappa, float C) {
+    return kEps32 * fmaxf(kappa, fabsf(x) + C);
+}
+
 // Best directions of one work item (a node and a block of its directions),
 // ranked by q = a rigorous lower bound on the value at t = 0 of the hull of the
 // FP32 samples of the left and right sets (the node's hull value when the
@@ -48,7 +53,7 @@ struct RefineOut {
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
     C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
-    C_FALLBACK, C_REFFULL, C_NUM
+    C_FALLBACK, C_REFFULL, C_BOUNDED, C_NUM
 };
 
 // Pipeline passes over one level's queue.

@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
     __shared__ int s_d[16][kWarpTop];
     __shared__ float s_drop[16], s_qhi[16];
     __shared__ float s_w0;
+    __shared__ float s_shift;  // the point's sample shift C
+    __shared__ int s_ukey;     // smallest q_hi screened so far in this item (f2key order)
     __shared__ int2 s_c;
     __shared__ unsigned s_hc[16][HC_N];
     const bool win = P.pass == PASS_WINDOW;
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
     __syncwarp();
     HullCounters hc{s_hc[warp]};
-    unsigned long long n_valid = 0, n_lines = 0;
+    unsigned long long n_valid = 0, n_lines = 0, n_bounded = 0;
 
     for (;;) {
         __syncthreads();
@@ -171,7 +173,10 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                 if (ch < pass_chunks(s_pd, P.pass)) {
                     const cvx_node *nd = node_ptr(s_pd, p, hi);
                     double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
-                    s_nl = make_node_line(F, s_pd.beta[p - s_pd.point_off], s_pd.mat);
+                    const double beta = s_pd.beta[p - s_pd.point_off];
+                    s_nl = make_node_line(F, beta, s_pd.mat);
+                    s_shift = (float)line_shift(s_pd.mat, beta);
+                    s_ukey = f2key(INFINITY);
                 }
             }
         }
@@ -209,13 +214,41 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         }
         float dropped = INFINITY, w0 = 0.0f, qhi_min = INFINITY;
         int warm_a = -1, warm_b = -1;
-        float my_cJ = 0.0f;  // lane k keeps the k-th line of each run of 32 for the work count
+        float s_warm = 0.0f;  // slope of the last searched bridge
+        float my_cJ = 0.0f;   // lane k keeps the k-th line of each run of 32 for the work count
+        const float kap = s_pd.kappa_f, C = s_shift;
         for (int dj = jb; dj < je; ++dj) {
             const int gd = win ? window_dir(s_pd, cen, dj) : dj;
             const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
-            sample_line<EK>(sw, nl, dl, ln, lane, tl);
+            // sampling, with min over the line of v - s x at the last slope:
+            // a lower bound qb of this line's hull value at 0
+            const float e = sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -s_warm);
+            const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
+            const float emin = __int_as_float(f2key(__int_as_float(ek)));
+            const float qb = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(s_warm) * (float)ln.m0) -
+                             1e-30f;
             __syncwarp();
-            const ScreenOut o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
+            // a line whose bound already exceeds m + eps(m), m = min(W(F), the
+            // smallest upper bound seen in this item), can neither win nor split
+            // (the node-level test in k_select uses the same monotone rule)
+            const float wc = sw[ln.m0];
+            const int ukey = *(volatile int *)&s_ukey;
+            const float mref = fminf(wc, __int_as_float(f2key(__int_as_float(ukey))));
+            const bool bounded = qb - eps32_at(qb, kap, C) > mref + eps32_at(mref, kap, C);
+            ScreenOut o;
+            if (bounded) {
+                o.a = o.b = -1;
+                o.q_lo = qb;
+                o.q_hi = INFINITY;
+                o.w0 = wc;
+            } else {
+                o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
+                if (o.a >= 0) {
+                    s_warm = __fdividef(sw[o.b] - sw[o.a], (float)(o.b - o.a));
+                    if (lane == 0) atomicMin(&s_ukey, f2key(o.q_hi));
+                }
+            }
+            if (lane == 0 && bounded) ++n_bounded;
             __syncwarp();
             const int r = (dj - jb) & 31;
             if (lane == r) my_cJ = dl.cJ;
@@ -233,7 +266,10 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                 warm_b = o.b;
             }
             qhi_min = fminf(qhi_min, o.q_hi);
-            top_insert(tq, td, dropped, o.q_lo, gd);
+            if (bounded)
+                dropped = fminf(dropped, qb);
+            else
+                top_insert(tq, td, dropped, o.q_lo, gd);
         }
         if (lane == 0) {
 #pragma unroll
@@ -291,6 +327,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
     if (lane == 0) {
         const unsigned *c = hc.c;
         add_counter(P.counters, C_LINES, n_lines);
+        add_counter(P.counters, C_BOUNDED, n_bounded);
         add_counter(P.counters, C_VALID, n_valid);
         add_counter(P.counters, C_FULL, c[HC_FULL]);
         add_counter(P.counters, C_RARE, c[HC_RARE]);
@@ -347,10 +384,12 @@ __global__ void k_select(const Pipe P, int level) {
     NodeCands nc;
     nc.n = 0;
     const float shift = (float)line_shift(pd.mat, pd.beta[P.qp[level][qi] - pd.point_off]);
-    nc.eps = kEps32 * fmaxf(pd.kappa_f, fmaxf(fabsf(qmin), fabsf(w0)) + shift);
+    const float kap = pd.kappa_f;
+    // a direction is a candidate iff q - eps(q) <= m + eps(m), m = min(W(F), U)
+    const float mref = fminf(w0, U);
+    const float R = mref + eps32_at(mref, kap, shift);
     float qcut = drop;
-    if (qmin <= w0 + 2.0f * nc.eps) {
-        const float lim = fminf(w0, U) + 2.0f * nc.eps;
+    if (qmin - eps32_at(qmin, kap, shift) <= R) {
         // merge the items' sorted lists, smallest q first (ties: lower direction)
         int pos[64];
         const int nch = chunks < 64 ? chunks : 64;
@@ -365,7 +404,7 @@ __global__ void k_select(const Pipe P, int level) {
             }
             if (bc < 0) break;
             const float q = r[bc].q[pos[bc]];
-            if (!(q <= lim) || nc.n == kNodeCand) {
+            if (!(q - eps32_at(q, kap, shift) <= R) || nc.n == kNodeCand) {
                 qcut = fminf(qcut, q);
                 break;
             }
@@ -374,9 +413,10 @@ __global__ void k_select(const Pipe P, int level) {
         }
         for (int c = nch; c < chunks; ++c) qcut = fminf(qcut, r[c].q[0]);
     } else {
-        qcut = qmin;
+        qcut = fminf(qcut, qmin);
     }
     nc.qcut = qcut;
+    nc.eps = qcut < INFINITY ? eps32_at(qcut, kap, shift) : 0.0f;
     nc.flags = fl;
     P.cands[qi] = nc;
     if (nc.n) {
