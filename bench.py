@@ -49,8 +49,10 @@ def args_parse():
     ap.add_argument("--nx", type=int, default=NX, help="mesh size (default 128 -> 65,536 points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
-    ap.add_argument("--form", default="full-scan", choices=["full-scan", "surrogate"],
-                    help="surrogate: the learned-proposal form over a load path (its own line)")
+    ap.add_argument("--form", default="full-scan", choices=["full-scan", "surrogate", "train"],
+                    help="surrogate: the learned-proposal form over a load path; train: "
+                         "training and inference of the proposal network (own lines)")
+    ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--gap-tol", type=float, default=1e-6, help="surrogate fallback tolerance")
     ap.add_argument("--window", type=int, default=4, help="surrogate window half-width (cells)")
     ap.add_argument("--load-steps", type=int, default=20)
@@ -511,12 +513,115 @@ def run_surrogate(a):
     cv.close()
 
 
+def run_train(a):
+    """The proposal network's training and inference on the tensor cores:
+    labels from the full scan of material points (16 x 16 angles, L = 201,
+    t in [-0.5, 0.5], depth 2, lambda in [1, 2]), 2 M training samples, Adam
+    with batch 8,192; then inference on 1 M held-out points.  Throughput in
+    samples/s and algorithmic TFLOP/s of the GEMMs (forward 2 x 200,192 FLOP
+    per sample, training 3 x that less the unused input gradient) against the
+    measured BF16 peak; held-out quality: the proposed cell of the 16 x 16
+    grid against the full scan's direction on laminated points."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api, inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    cv = api.Convexifier(0)
+
+    def timed(f):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = f()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    p = api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT)
+    F, Fp = inputs.surrogate_inputs(1_000_000, seed=200)
+    beta = cv.history_update(p, Fp)
+    Fd = torch.from_numpy(F).to(dev)
+    out, t_label = timed(lambda: cv.convexify_points(p, Fd, beta, want_tree=True))
+    X, Y = cv.surrogate_labels(p, beta, out["tree"], F.shape[0])
+    n_train = min(2_000_000, X.shape[0])
+    X, Y = X[:n_train].contiguous(), Y[:n_train].contiguous()
+    log, t_train = timed(lambda: cv.surrogate_train(X, Y, epochs=a.train_epochs, batch=8192,
+                                                    lr=1e-3, init=True, seed=0))
+    fwd_flop = 2.0 * (256 * 6 + 3 * 256 * 256 + 7 * 256)
+    train_flop = 3.0 * fwd_flop - 2.0 * 256 * 6
+    steps = a.train_epochs * (n_train // 8192)
+    train_rate = steps * 8192 / t_train
+
+    Fh, Fph = inputs.surrogate_inputs(1_000_000, seed=201)
+    bh = cv.history_update(p, Fph)
+    Fhd = torch.from_numpy(Fh).to(dev)
+    J = Fhd[:, 0] * Fhd[:, 3] - Fhd[:, 1] * Fhd[:, 2]
+    Xh = torch.cat([Fhd, bh[:, None], torch.log(J)[:, None]], dim=1).float().contiguous()
+    cv.surrogate_forward(Xh[:8192])  # warm
+    o, t_inf = timed(lambda: cv.surrogate_forward(Xh))
+    inf_rate = Xh.shape[0] / t_inf
+    # held-out quality: root decisions of the full scan (depth 1)
+    p1 = api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=1, **MAT)
+    r1 = cv.convexify_points(p1, Fhd, bh, want_root=True)
+    root = api.root_numpy(r1["root"], Fh.shape[0])
+    lam = root["laminated"] == 1
+    oh = o.cpu().numpy()
+    ia = np.mod(np.floor(np.mod(oh[:, 0], math.pi) * 16 / math.pi + 0.5), 16).astype(int)
+    ib = np.mod(np.floor(np.mod(oh[:, 1], math.pi) * 16 / math.pi + 0.5), 16).astype(int)
+    la, lb = root["dir"] // 16, root["dir"] % 16
+
+    def cdist(x, y):
+        d = np.abs(x - y) % 16
+        return np.minimum(d, 16 - d)
+
+    da, db = cdist(ia, la)[lam], cdist(ib, lb)[lam]
+    peak = None
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    except (OSError, ValueError, KeyError):
+        pass
+    ach_inf = fwd_flop * inf_rate / 1e12
+    line = {
+        "metric": "proposal-network samples/s (training, BF16 tensor cores)",
+        "value": train_rate, "unit": "samples/s", "n_gpus": 1, "steps": steps, "warmup": 0,
+        "ms_per_step": 1e3 * t_train / max(1, steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32", "data": "synthetic",
+        "config": {"workload": "network 6 -> 256 x 4 -> 7 GELU; labels from the full scan of 1 M "
+                               "material points (16x16 angles, L=201, depth 2, lambda in [1,2])",
+                   "form": "train", "train_samples": int(n_train), "batch": 8192,
+                   "epochs": a.train_epochs, "held_out": int(Xh.shape[0])},
+        "roofline": {"bound": "tensor", "kernel": "k_gemm (forward, inference)",
+                     "achieved": ach_inf, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach_inf / peak if peak else None,
+                     "training_tflops": train_flop * train_rate / 1e12,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS burst), of measured"},
+        "inference": {"value": inf_rate, "unit": "points/s", "points": int(Xh.shape[0])},
+        "labels": {"points": int(F.shape[0]), "samples": int(X.shape[0]), "seconds": t_label,
+                   "points_per_s": F.shape[0] / t_label},
+        "loss": {"first": float(log[0]), "last": float(log[-1])},
+        "held_out_quality": {"laminated_points": int(lam.sum()),
+                             "cell_exact": float(np.mean((da == 0) & (db == 0))),
+                             "within_one_cell": float(np.mean((da <= 1) & (db <= 1)))},
+    }
+    print(json.dumps(line), flush=True)
+    cv.close()
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.form == "surrogate":
         run_surrogate(a)
+    elif a.form == "train":
+        run_train(a)
     else:
         run_ours(a)
 

@@ -179,3 +179,23 @@ def test_full_size_batch_sampled_against_oracle(cv, orc):
             assert np.linalg.norm(P[j] - Po[j]) / (1e-8 + np.linalg.norm(Po[j])) < 1e-5
             checked += 1
     assert checked >= 16
+
+
+def test_newton_flag_through_batch_and_static_entry(cv, orc):
+    """CVX_FLAG_REFINE_NEWTON reaches the kernels through convexify_batch and
+    convexify_points_static: the double well's refined split (exact
+    common tangent at x = +-1, off the line grid) comes out of every entry."""
+    from paper_2211_14318_gb300 import api
+
+    p = api.Params(energy=api.ENERGY_DOUBLE_WELL, n_theta_a=8, n_theta_b=8, line_points=201,
+                   t_half=1.5, depth=1, newton=True)
+    F = np.array([[0.3, 0, 0, 1.0], [-0.2, 0, 0, 1.0]])
+    one = cv.convexify_points(p, F, np.zeros(2))
+    bat = cv.convexify_batch([(p, F, np.zeros(2))], want_root=True)[0]
+    sta = api.convexify_points_static(p, F, np.zeros(2))
+    for r in (one, bat, sta):
+        np.testing.assert_allclose(r["W_R"].cpu().numpy(), [0.0, 0.0], atol=1e-13)
+    root = api.root_numpy(bat["root"], 2)
+    np.testing.assert_allclose(root["F_plus"][:, 0], [1.0, 1.0], atol=1e-12)
+    np.testing.assert_allclose(root["F_minus"][:, 0], [-1.0, -1.0], atol=1e-12)
+    np.testing.assert_allclose(root["xi"], [0.65, 0.4], atol=1e-12)
