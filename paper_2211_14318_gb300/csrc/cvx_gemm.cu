@@ -5,10 +5,11 @@
 //   D[m][n] = sum_k A[m][k] B[n][k]       (A: M x K, B: N x K, both bf16,
 //                                          row-major with K contiguous)
 //
-// One CTA of 128 threads computes a 128 x BN tile over a K range (split-K for
+// One CTA of 256 threads computes a 128 x BN tile over a K range (split-K for
 // the weight gradients).  Thread 0 issues the TMA loads (one box per k-block
-// of 8 elements, two stages of 64) and the MMAs (K = 16 each); every thread
-// then reads its own accumulator row (TMEM lane) and applies the epilogue.
+// of 8 elements, two stages of 64) and the MMAs (K = 16 each); then warps w
+// and w + 4 read the TMEM lanes of rows 32 (w % 4) .. +31 (one accumulator
+// row per thread), each half of the columns, and apply the epilogue.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -26,12 +27,32 @@ namespace {
 constexpr int kBM = 128, kBK = 64, kStages = 2;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait, then give up
 
+// Normal CDF Phi(z) and density phi(z) with erf from Abramowitz & Stegun,
+// Handbook of Mathematical Functions, formula 7.1.26:
+//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
+//   t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7
+// (one exponential shared by Phi and phi).
+__device__ __forceinline__ void normal_cdf_pdf(float z, float &Phi, float &phi) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f),
+                         -0.284496736f),
+                 0.254829592f);
+    const float ex = __expf(-x * x);
+    const float erfx = 1.0f - poly * ex;
+    Phi = 0.5f * (1.0f + (z < 0.0f ? -erfx : erfx));
+    phi = 0.39894228040143268f * ex;
+}
 __device__ __forceinline__ float gelu(float z) {
-    return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+    float Phi, phi;
+    normal_cdf_pdf(z, Phi, phi);
+    return z * Phi;
 }
 __device__ __forceinline__ float gelu_grad(float z) {
-    const float Phi = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-    return Phi + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    float Phi, phi;
+    normal_cdf_pdf(z, Phi, phi);
+    return Phi + z * phi;
 }
 
 __device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *dst, const float (&v)[16]) {
@@ -47,7 +68,7 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *dst, const float (&
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     k_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M,
            int N, int K, int k_split, GemmEpi ep) {
     constexpr int A_BYTES = kBM * kBK * 2;
@@ -132,9 +153,14 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok && ep.err) atomicExch(ep.err, 1);
     tc_fence_after();
 
-    const int m = m0 + 32 * warp + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    const int quarter = warp & 3;
+    const int m = m0 + 32 * quarter + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+    // columns of this warp: halves of the tile (BN = 16: warps 0-3 only)
+    constexpr int CW = BN >= 32 ? BN / 2 : BN;
+    const int cbeg = (warp >> 2) * CW;
+    const int cend = BN >= 32 ? cbeg + CW : (warp < 4 ? BN : 0);
+    for (int c0 = cbeg; c0 < cend; c0 += 16) {
         float v[16];
         tmem_ld16(trow + c0, v);
         if (!ok) continue;
@@ -251,12 +277,12 @@ cudaError_t launch_gemm(const CUtensorMap &tA, const CUtensorMap &tB, int M, int
         const size_t sm = gemm_smem<256>();
         cudaError_t e = cudaFuncSetAttribute(k_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_gemm<256><<<grid, 128, sm, s>>>(tA, tB, M, N, K, k_split, ep);
+        k_gemm<256><<<grid, 256, sm, s>>>(tA, tB, M, N, K, k_split, ep);
     } else if (BN == 16) {
         const size_t sm = gemm_smem<16>();
         cudaError_t e = cudaFuncSetAttribute(k_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_gemm<16><<<grid, 128, sm, s>>>(tA, tB, M, N, K, k_split, ep);
+        k_gemm<16><<<grid, 256, sm, s>>>(tA, tB, M, N, K, k_split, ep);
     } else {
         return cudaErrorInvalidValue;
     }
