@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "cvx_mlp.h"
@@ -65,6 +66,63 @@ __device__ __forceinline__ void store_bf16x16(__nv_bfloat16 *dst, const float (&
     uint4 *d = reinterpret_cast<uint4 *>(dst);
     d[0] = make_uint4(w[0], w[1], w[2], w[3]);
     d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// The epilogue of 16 accumulator columns n .. n + 15 of row m (one thread).
+__device__ __forceinline__ void gemm_epilogue(const GemmEpi &ep, int m, int n, const float (&v)[16],
+                                              int Mv, int N, int lane) {
+    switch (ep.mode) {
+    case EPI_F32:
+        if (m < Mv)
+            for (int i = 0; i < 16; ++i)
+                if (n + i < N) ep.C[(long long)m * ep.ldc + n + i] = v[i];
+        break;
+    case EPI_HIDDEN: {
+        if (m >= Mv) break;
+        float a[16];
+        for (int i = 0; i < 16; ++i) {
+            const float z = v[i] + ep.bias[n + i];
+            if (ep.Z) ep.Z[(long long)m * ep.ldz + n + i] = z;
+            a[i] = gelu(z);
+        }
+        store_bf16x16(ep.A + (long long)m * ep.lda + n, a);
+        if (ep.AT)
+            for (int i = 0; i < 16; ++i)
+                ep.AT[(long long)(n + i) * ep.ldat + m] = __float2bfloat16_rn(a[i]);
+        break;
+    }
+    case EPI_OUT:
+        if (m < Mv)
+            for (int i = 0; i < 16; ++i)
+                if (n + i < ep.n_store)
+                    ep.C[(long long)m * ep.ldc + n + i] = v[i] + ep.bias[n + i];
+        break;
+    case EPI_DA: {
+        float dz[16];
+        const bool in = m < Mv;
+        for (int i = 0; i < 16; ++i)
+            dz[i] = in ? v[i] * gelu_grad(ep.Z[(long long)m * ep.ldz + n + i]) : 0.0f;
+        if (in) {
+            store_bf16x16(ep.A + (long long)m * ep.lda + n, dz);
+            if (ep.AT)
+                for (int i = 0; i < 16; ++i)
+                    ep.AT[(long long)(n + i) * ep.ldat + m] = __float2bfloat16_rn(dz[i]);
+        }
+        if (ep.dbias) {
+            for (int i = 0; i < 16; ++i) {
+                float s = dz[i];
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) atomicAdd(ep.dbias + n + i, s);
+            }
+        }
+        break;
+    }
+    case EPI_DW:
+        if (m < ep.m_store)
+            for (int i = 0; i < 16; ++i)
+                if (n + i < ep.n_store) atomicAdd(ep.C + (long long)m * ep.ldc + n + i, v[i]);
+        break;
+    }
 }
 
 template <int BN>
@@ -163,64 +221,147 @@ __global__ void __launch_bounds__(256, 1)
     for (int c0 = cbeg; c0 < cend; c0 += 16) {
         float v[16];
         tmem_ld16(trow + c0, v);
-        if (!ok) continue;
-        const int n = n0 + c0;
-        switch (ep.mode) {
-        case EPI_F32:
-            if (m < Mv)
-                for (int i = 0; i < 16; ++i)
-                    if (n + i < N) ep.C[(long long)m * ep.ldc + n + i] = v[i];
-            break;
-        case EPI_HIDDEN: {
-            if (m >= Mv) break;
-            float a[16];
-            for (int i = 0; i < 16; ++i) {
-                const float z = v[i] + ep.bias[n + i];
-                if (ep.Z) ep.Z[(long long)m * ep.ldz + n + i] = z;
-                a[i] = gelu(z);
-            }
-            store_bf16x16(ep.A + (long long)m * ep.lda + n, a);
-            if (ep.AT)
-                for (int i = 0; i < 16; ++i)
-                    ep.AT[(long long)(n + i) * ep.ldat + m] = __float2bfloat16_rn(a[i]);
-            break;
+        if (ok) gemm_epilogue(ep, m, n0 + c0, v, Mv, N, lane);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TCOLS);
+    }
+}
+
+// Persistent, warp-specialised form for K <= 256 (all forward layers and
+// the input-gradient products): the B operand (the weights, BN x K) stays in
+// shared memory for the whole kernel; A tiles (128 x 64) stream through a
+// four-stage ring; two TMEM accumulators let the epilogue of one tile run
+// while the MMAs of the next are in flight.  Warp 0 (lane 0) issues the TMA
+// loads, warp 1 (lane 0) the MMAs, warps 4..11 run the epilogue (two per
+// TMEM lane quarter, each half of the columns); every wait is bounded.
+constexpr int kWsStages = 4;
+constexpr int kWsThreads = 384;
+
+template <int BN>
+constexpr size_t gemm_ws_smem(int K) {
+    return (size_t)BN * K * 2 + (size_t)kWsStages * kBM * kBK * 2 + 1024;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_gemm_ws(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+              int M, int N, int K, GemmEpi ep) {
+    constexpr int A_STAGE = kBM * kBK * 2;
+    constexpr uint32_t TC = BN < 32 ? 32 : BN;  // columns per accumulator
+    constexpr uint32_t TCOLS = 2 * TC;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sB = smem;
+    unsigned char *sA = smem + (size_t)BN * K * 2;
+    __shared__ __align__(8) uint64_t full[kWsStages], empty[kWsStages], bfull, accf[2], acce[2];
+    __shared__ uint32_t s_tmem;
+
+    const int Mv = ep.M_dev ? min(*ep.M_dev - ep.m_off, ep.M_valid) : ep.M_valid;
+    const int ntiles = Mv > 0 ? (Mv + kBM - 1) / kBM : 0;
+    if ((int)blockIdx.x >= ntiles) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkc = (K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWsStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
         }
-        case EPI_OUT:
-            if (m < Mv)
-                for (int i = 0; i < 16; ++i)
-                    if (n + i < ep.n_store)
-                        ep.C[(long long)m * ep.ldc + n + i] = v[i] + ep.bias[n + i];
-            break;
-        case EPI_DA: {
-            float dz[16];
-            const bool in = m < Mv;
-            for (int i = 0; i < 16; ++i)
-                dz[i] = in ? v[i] * gelu_grad(ep.Z[(long long)m * ep.ldz + n + i]) : 0.0f;
-            if (in) {
-                store_bf16x16(ep.A + (long long)m * ep.lda + n, dz);
-                if (ep.AT)
-                    for (int i = 0; i < 16; ++i)
-                        ep.AT[(long long)(n + i) * ep.ldat + m] = __float2bfloat16_rn(dz[i]);
-            }
-            if (ep.dbias) {
-                for (int i = 0; i < 16; ++i) {
-                    float s = dz[i];
-                    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) atomicAdd(ep.dbias + n + i, s);
+        mbar_init(&bfull, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 8);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&s_tmem, TCOLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            bool ok = true;
+            mbar_expect_tx(&bfull, (unsigned)((K / 8) * BN * 16));
+            for (int kb = 0; kb < K / 8; ++kb) tma_load_2d(sB + kb * BN * 16, &tB, &bfull, 8 * kb, 0);
+            int u = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int kc = 0; kc < nkc; ++kc, ++u) {
+                    const int st = u % kWsStages, use = u / kWsStages;
+                    if (use > 0 && !(ok = mbar_wait(&empty[st], (use - 1) & 1, kWaitNs))) break;
+                    const int k0 = kc * kBK, kbn = min(kBK, K - k0) / 8;
+                    mbar_expect_tx(&full[st], (unsigned)(kbn * kBM * 16));
+                    for (int kb = 0; kb < kbn; ++kb)
+                        tma_load_2d(sA + st * A_STAGE + kb * kBM * 16, &tA, &full[st], k0 + 8 * kb,
+                                    t * kBM);
                 }
             }
-            break;
+            if (!ok && ep.err) atomicExch(ep.err, 1);
         }
-        case EPI_DW:
-            if (m < ep.m_store)
-                for (int i = 0; i < 16; ++i)
-                    if (n + i < ep.n_store) atomicAdd(ep.C + (long long)m * ep.ldc + n + i, v[i]);
-            break;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(kBM, BN);
+            bool ok = mbar_wait(&bfull, 0, kWaitNs);
+            int u = 0, v = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++v) {
+                const int acc = v & 1, vu = v >> 1;
+                if (vu > 0 && !(ok = mbar_wait(&acce[acc], (vu - 1) & 1, kWaitNs))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + acc * TC;
+                for (int kc = 0; kc < nkc; ++kc, ++u) {
+                    const int st = u % kWsStages, use = u / kWsStages;
+                    if (!(ok = mbar_wait(&full[st], use & 1, kWaitNs))) break;
+                    tc_fence_after();
+                    const int kbn = min(kBK, K - kc * kBK) / 8;
+                    const uint32_t a0 = smem_u32(sA + st * A_STAGE);
+                    const uint32_t b0 = smem_u32(sB + (size_t)kc * 8 * BN * 16);
+                    for (int j = 0; j < kbn / 2; ++j) {
+                        const uint64_t ad = smem_desc(a0 + 2 * j * kBM * 16, kBM * 16, 128);
+                        const uint64_t bd = smem_desc(b0 + 2 * j * BN * 16, BN * 16, 128);
+                        umma_bf16(d, ad, bd, idesc, (kc > 0 || j > 0) ? 1u : 0u);
+                    }
+                    umma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                umma_commit(&accf[acc]);
+            }
+            if (!ok && ep.err) atomicExch(ep.err, 1);
+        }
+    } else if (warp >= 4) {
+        const int ew = warp - 4, quarter = ew & 3, half = ew >> 2;
+        constexpr int CW = BN >= 32 ? BN / 2 : BN;
+        const int cbeg = half * CW;
+        const int cend = BN >= 32 ? cbeg + CW : (half == 0 ? BN : 0);
+        int v = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++v) {
+            const int acc = v & 1, vu = v >> 1;
+            if (!mbar_wait(&accf[acc], vu & 1, kWaitNs)) {
+                if (ep.err) atomicExch(ep.err, 1);
+                break;
+            }
+            tc_fence_after();
+            const int m = t * kBM + 32 * quarter + lane;
+            const uint32_t trow = tmem + acc * TC + ((uint32_t)(32 * quarter) << 16);
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                float r[16];
+                tmem_ld16(trow + c0, r);
+                gemm_epilogue(ep, m, c0, r, Mv, N, lane);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[acc]);
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
+        __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem, TCOLS);
     }
@@ -272,6 +413,30 @@ bool make_tmap_bf16(CUtensorMap *map, const void *ptr, long long rows, long long
 cudaError_t launch_gemm(const CUtensorMap &tA, const CUtensorMap &tB, int M, int N, int K,
                         int k_split, int BN, const GemmEpi &ep, cudaStream_t s) {
     if (K % 16 || k_split % 16 || k_split < 16) return cudaErrorInvalidValue;
+    if (ep.mode != EPI_DW && K <= 256 && k_split >= K && N <= BN) {
+        // one tile column, the whole K: the persistent warp-specialised form
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const unsigned grid = (unsigned)std::max(1, std::min((M + kBM - 1) / kBM, sms));
+        cudaError_t e;
+        if (BN == 256) {
+            const size_t sm = gemm_ws_smem<256>(K);
+            if ((e = cudaFuncSetAttribute(k_gemm_ws<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm)) != cudaSuccess)
+                return e;
+            k_gemm_ws<256><<<grid, kWsThreads, sm, s>>>(tA, tB, M, N, K, ep);
+        } else if (BN == 16) {
+            const size_t sm = gemm_ws_smem<16>(K);
+            if ((e = cudaFuncSetAttribute(k_gemm_ws<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm)) != cudaSuccess)
+                return e;
+            k_gemm_ws<16><<<grid, kWsThreads, sm, s>>>(tA, tB, M, N, K, ep);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, (K + k_split - 1) / k_split);
     if (BN == 256) {
         const size_t sm = gemm_smem<256>();
