@@ -55,6 +55,8 @@ def args_parse():
     ap.add_argument("--train-epochs", type=int, default=10)
     ap.add_argument("--gap-tol", type=float, default=1e-6, help="surrogate fallback tolerance")
     ap.add_argument("--window", type=int, default=4, help="surrogate window half-width (cells)")
+    ap.add_argument("--gap-one-sided", action="store_true",
+                    help="surrogate: fall back only when the proposed laminate beats the window")
     ap.add_argument("--load-steps", type=int, default=20)
     ap.add_argument("--check-points", type=int, default=4096,
                     help="surrogate: subsample checked against the full scan")
@@ -443,7 +445,8 @@ def run_surrogate(a):
     t_train = time.perf_counter() - t0
 
     # ---- load path
-    p = api.Params(n_theta_a=S_ANGLES, n_theta_b=S_ANGLES, line_points=S_LINE, depth=S_DEPTH, **MAT)
+    p = api.Params(n_theta_a=S_ANGLES, n_theta_b=S_ANGLES, line_points=S_LINE, depth=S_DEPTH,
+                   gap_one_sided=a.gap_one_sided, **MAT)
     n = path[0].shape[0]
     sub = np.linspace(0, n - 1, min(a.check_points, n)).astype(int)
     sub_t = torch.from_numpy(sub).to(dev)
@@ -501,6 +504,7 @@ def run_surrogate(a):
                                f"stretch 1.0 -> 1.8 in {a.load_steps} steps, {S_ANGLES}x{S_ANGLES} "
                                f"angles, window +-{a.window}, L={S_LINE}, depth {S_DEPTH}",
                    "form": "surrogate", "gap_tol": a.gap_tol, "window": a.window,
+                   "gap_test": "one-sided" if a.gap_one_sided else "two-sided",
                    "timed": "surrogate_propose per step (CUDA events); history update excluded"},
         "surrogate": {"fell_back_points_mean": fell / a.load_steps,
                       "window_nodes": st["window_nodes"], "fallback_nodes": st["fallbacks"],

@@ -116,7 +116,10 @@ typedef struct cvx_params {
  * not above the grid bridge's; the node is then flagged CVX_NODE_NEWTON and
  * its children, xi and h use the refined ends.  The paper takes laminates from
  * its grids only; this is an addition (the direction is still the grid's). */
-enum cvx_param_flags { CVX_FLAG_REFINE_NEWTON = 1 };
+/* CVX_FLAG_GAP_ONE_SIDED (surrogate_propose only): the energy-gap fallback
+ * test becomes (V - E_pred) / (1e-8 + |V|) > gap_tol, i.e. a node falls back
+ * only when the proposed laminate is better than what its window found. */
+enum cvx_param_flags { CVX_FLAG_REFINE_NEWTON = 1, CVX_FLAG_GAP_ONE_SIDED = 2 };
 
 /* Node of the per-point lamination tree (Sec. 4.3, Algorithm 2), heap layout:
  * node i has children 2i+1 (F-) and 2i+2 (F+); 2^{K+1}-1 nodes per point. */

@@ -13,7 +13,8 @@ Per tree node, top-down as the plain method (Eq. 3.3 per point):
   3. the node falls back to the scan of all directions if the window's best
      direction lies on the window border or the energy gap
      |E_pred - V| / (1e-8 + |V|) exceeds gap_tol, with V the window's node
-     value and E_pred = xi W(F+) + (1 - xi) W(F-) of the proposed laminate;
+     value and E_pred = xi W(F+) + (1 - xi) W(F-) of the proposed laminate
+     (one_sided: (V - E_pred) / (1e-8 + |V|), only a better proposal counts);
   4. the split and the recursion are those of the plain method.
 Every integer decision comes with its margin: the distance of the scaled
 angles to a rounding boundary (in cells), the scan's certified margin, and
@@ -42,7 +43,8 @@ def _offset(i, c, N):
     return d - N if d > N // 2 else d
 
 
-def propose_convexify(orc, mat, Na, Nb, L, t_half, K, w, gap_tol, flat, mean, std, F, beta):
+def propose_convexify(orc, mat, Na, Nb, L, t_half, K, w, gap_tol, flat, mean, std, F, beta,
+                      one_sided=False):
     """Returns (W_R, P, nodes) with nodes[p] = {heap index: record}."""
     dirs_all = orc.angle_directions(Na, Nb)
     full = orc.Scan(dirs_all, L, t_half, 1)
@@ -74,7 +76,7 @@ def propose_convexify(orc, mat, Na, Nb, L, t_half, K, w, gap_tol, flat, mean, st
             lam = info["m_minus"] != m0
             V = info["h"] if lam else rec["w"]
             border = lam and (abs(_offset(gd // Nb, ia, Na)) >= w or abs(_offset(gd % Nb, ib, Nb)) >= w)
-            gap = abs(E_pred - V) / (1e-8 + abs(V))
+            gap = ((V - E_pred) if one_sided else abs(E_pred - V)) / (1e-8 + abs(V))
             rec.update(center=(ia, ib), center_margin=float(dist[0]), gap=gap, E_pred=E_pred,
                        window_margin=info["margin"], window_dir=gd, window_lam=lam, V=V)
             if border or not gap <= gap_tol:

@@ -158,6 +158,7 @@ class Params:
     energy: int = ENERGY_NH_DAMAGE
     dirs: Optional[np.ndarray] = None  # custom (n, 4) rows (a1, a2, b1, b2)
     newton: bool = False  # CVX_FLAG_REFINE_NEWTON
+    gap_one_sided: bool = False  # CVX_FLAG_GAP_ONE_SIDED (surrogate_propose)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
@@ -165,7 +166,7 @@ class Params:
         p.mu, p.lambda_L, p.D_inf, p.D0, p.t_half = self.mu, self.lambda_L, self.D_inf, self.D0, self.t_half
         p.energy, p.n_theta_a, p.n_theta_b = self.energy, self.n_theta_a, self.n_theta_b
         p.line_points, p.depth, p.reserved = self.line_points, self.depth, 0
-        p.flags = FLAG_REFINE_NEWTON if self.newton else 0
+        p.flags = (FLAG_REFINE_NEWTON if self.newton else 0) | (2 if self.gap_one_sided else 0)
         if self.dirs is not None:
             d = np.ascontiguousarray(self.dirs, dtype=np.float64).reshape(-1, 4)
             self._keep = [d]

@@ -60,7 +60,8 @@ int check_params(const cvx_params *p, bool need_line) {
             return fail(CVX_ERR_INVALID_ARG,
                         "material out of range (mu > 0, lambda >= 0, 0 <= D_inf < 1, D0 > 0)");
     }
-    if (p->flags & ~CVX_FLAG_REFINE_NEWTON) return fail(CVX_ERR_INVALID_ARG, "unknown flags");
+    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED))
+        return fail(CVX_ERR_INVALID_ARG, "unknown flags");
     if (!need_line) return CVX_OK;
     if (p->line_points < 3 || p->line_points > 2079 || (p->line_points % 2) == 0)
         return fail(CVX_ERR_INVALID_ARG, "line_points must be odd in [3, 2079], got %d",

@@ -80,7 +80,8 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
         (!(p->mu > 0.0) || !(p->lambda_L >= 0.0) || !(p->D_inf >= 0.0 && p->D_inf < 1.0) ||
          !(p->D0 > 0.0)))
         return err(CVX_ERR_INVALID_ARG, "material out of range");
-    if (p->flags & ~CVX_FLAG_REFINE_NEWTON) return err(CVX_ERR_INVALID_ARG, "unknown flags");
+    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED))
+        return err(CVX_ERR_INVALID_ARG, "unknown flags");
     if (p->line_points < 3 || p->line_points > 2079 || (p->line_points % 2) == 0)
         return err(CVX_ERR_INVALID_ARG, "line_points must be odd in [3, 2079]");
     if (!(p->t_half > 0.0) || !isfinite(p->t_half)) return err(CVX_ERR_INVALID_ARG, "t_half must be positive");

@@ -669,7 +669,9 @@ __global__ void k_commit(const Pipe P, int level) {
             if (dj > pd.Nb / 2) dj -= pd.Nb;
             fb |= abs(di) >= pd.window || abs(dj) >= pd.window;
         }
-        const double gap = fabs(P.e_pred[qi] - V) / (1e-8 + fabs(V));
+        const double gap = ((pd.flags & CVX_FLAG_GAP_ONE_SIDED) ? V - P.e_pred[qi]
+                                                                : fabs(P.e_pred[qi] - V)) /
+                           (1e-8 + fabs(V));
         fb |= !(gap <= pd.gap_tol);
         if (fb) {
             const int pos = atomicAdd(P.fcnt + level, 1);

@@ -210,18 +210,20 @@ def test_propose_constant_network_matches_oracle(cv, orc):
     flat = _constant_net(math.pi * (d // Nb) / Na, math.pi * (d % Nb) / Nb, r0["xi"],
                          tro[k, 2]["F"] - tro[k, 1]["F"])
     cv.surrogate_set_weights(flat, np.zeros(6), np.ones(6))
-    for depth in (1, 2):
-        p = api.Params(n_theta_a=Na, n_theta_b=Nb, line_points=151, depth=depth, **MAT)
+    for depth, one_sided in ((1, False), (2, False), (2, True)):
+        p = api.Params(n_theta_a=Na, n_theta_b=Nb, line_points=151, depth=depth,
+                       gap_one_sided=one_sided, **MAT)
         r = cv.surrogate_propose(p, F, beta, window=2, gap_tol=1e-5, want_tree=True)
         WRo, Po, trees = osur.propose_convexify(orc, mat, Na, Nb, 151, 0.5, depth, 2, 1e-5, flat,
-                                                np.zeros(6), np.ones(6), F, beta)
+                                                np.zeros(6), np.ones(6), F, beta,
+                                                one_sided=one_sided)
         tg = api.tree_numpy(r["tree"], 12, p.tree_size)
         WR = r["W_R"].cpu().numpy()
         fb = r["fell_back"].cpu().numpy()
         assert fb[k] == 0 or depth > 1
         for q in range(12):
             clear = all(rec.get("margin", np.inf) > TIE and rec.get("window_margin", np.inf) > TIE
-                        and abs(rec.get("gap", 0.0) - 1e-5) > 1e-6
+                        and abs(rec.get("gap", 0.0) - 1e-5) > 1e-6 and np.isfinite(rec.get("gap", 0.0))
                         for rec in trees[q].values() if rec["flags"] & orc.SCANNED)
             if not clear:
                 continue

@@ -81,3 +81,34 @@ def test_window_around_the_true_direction_reproduces_the_full_scan(orc):
         np.testing.assert_array_equal(P[0], Po[p])
         checked += 1
     assert checked >= 4
+
+
+def test_one_sided_gap_falls_back_on_a_subset(orc):
+    """One-sided gap test: a node falls back on the border or when
+    V - E_pred > gap_tol (1e-8 + |V|); its fallbacks are a subset of the
+    two-sided test's, and a proposal that is worse than the window's value
+    never falls back through the gap (a fixed network with a small jump;
+    NaN proposals fall back in both modes)."""
+    mat, F, beta = _points(orc, 8, 33)
+    parts = [np.zeros(s) for s in mlp.SHAPES]
+    parts[9] = np.array([0.3, 0.2, 0.0, 0.05, -0.04, 0.03, 0.02])
+    flat = mlp.flatten(parts)
+    kw = dict(Na=8, Nb=8, L=101, t_half=0.5, K=2, w=1, gap_tol=1e-6, flat=flat,
+              mean=np.zeros(6), std=np.ones(6), F=F, beta=beta)
+    _, _, t1 = osur.propose_convexify(orc, mat, one_sided=True, **kw)
+    _, _, t2 = osur.propose_convexify(orc, mat, one_sided=False, **kw)
+    seen = 0
+    for a, b in zip(t1, t2):
+        r1, r2 = a[0], b[0]  # the roots see the same proposal in both modes
+        fb1, fb2 = bool(r1["flags"] & osur.FALLBACK), bool(r2["flags"] & osur.FALLBACK)
+        assert not fb1 or fb2
+        g = r1["gap"]
+        gd, (ia, ib) = r1["window_dir"], r1["center"]
+        border = bool(r1["window_lam"]) and (abs(osur._offset(gd // 8, ia, 8)) >= 1 or
+                                             abs(osur._offset(gd % 8, ib, 8)) >= 1)
+        if np.isfinite(g):
+            assert fb1 == (g > 1e-6 or border)
+            if g < 0:
+                assert fb1 == border
+                seen += 1
+    assert seen >= 1
