@@ -199,3 +199,32 @@ def test_newton_flag_through_batch_and_static_entry(cv, orc):
     np.testing.assert_allclose(root["F_plus"][:, 0], [1.0, 1.0], atol=1e-12)
     np.testing.assert_allclose(root["F_minus"][:, 0], [-1.0, -1.0], atol=1e-12)
     np.testing.assert_allclose(root["xi"], [0.65, 0.4], atol=1e-12)
+
+
+def test_many_tiny_problems(cv, orc):
+    """400 problems of 0 to 3 points with alternating parameters in one batch:
+    every point's W^R, P and status equal the single-problem call's (the
+    problem table's point offsets, empty problems and per-problem depth)."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    rng = np.random.default_rng(7)
+    F, Fp = inputs.material_points(1200, seed=70)
+    beta = orc.history_update(_omat(orc), Fp)
+    items, off = [], 0
+    for k in range(400):
+        m = int(rng.integers(0, 4))
+        p = api.Params(n_theta_a=8 + 4 * (k % 2), n_theta_b=8, line_points=61 + 40 * (k % 3),
+                       depth=k % 3, **MAT)
+        items.append((p, F[off:off + m], beta[off:off + m]))
+        off += m
+    res = cv.convexify_batch(items)
+    for (p, Fk, bk), r in zip(items, res):
+        if Fk.shape[0] == 0:
+            assert r["W_R"].numel() == 0
+            continue
+        one = cv.convexify_points(p, Fk, bk)
+        st, st1 = r["status"].cpu().numpy(), one["status"].cpu().numpy()
+        clean = ((st | st1) & HARD) == 0
+        np.testing.assert_array_equal(st[clean], st1[clean])
+        np.testing.assert_array_equal(r["W_R"].cpu().numpy()[clean], one["W_R"].cpu().numpy()[clean])
+        np.testing.assert_array_equal(r["P"].cpu().numpy()[clean], one["P"].cpu().numpy()[clean])
