@@ -191,6 +191,9 @@ typedef struct cvx_stats {
                                (the windowed FP64 bridge was not certified) */
     int64_t lines_bounded;  /* lines excluded by their sampling-pass bound,
                                without a hull search                        */
+    int64_t lines_flat;     /* lines whose sampling-pass bound is within the
+                               FP32 sample error of the centre value: no
+                               hull search, the bound is their lower bound  */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */

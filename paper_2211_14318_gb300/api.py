@@ -56,7 +56,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
-        "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks", "refine_full", "lines_bounded")]
+        "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks", "refine_full", "lines_bounded",
+        "lines_flat")]
 
 
 class _Problem(ctypes.Structure):

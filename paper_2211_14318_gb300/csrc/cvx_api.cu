@@ -244,6 +244,7 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->fallbacks = (int64_t)c[C_FALLBACK];
     out->refine_full = (int64_t)c[C_REFFULL];
     out->lines_bounded = (int64_t)c[C_BOUNDED];
+    out->lines_flat = (int64_t)c[C_FLAT];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }

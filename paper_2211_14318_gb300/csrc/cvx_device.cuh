@@ -187,11 +187,11 @@ __device__ inline bool newton_tangent64(const double F[4], const double R[4], do
 // decision; values are mapped back by W = (v + C) / kappa'.  J <= 0 yields
 // +inf or NaN, which the hull search ignores.
 // -------------------------------------------------------------------------
-struct NodeLine {
+struct __align__(16) NodeLine {
+    float F[4];  // first, so that F and cof F are two 16-byte loads
+    float cof[4];
     float A0, B1, B2, K1, K2, mu;  // kappa-scaled (K2 is a ratio)
     float J0;
-    float F[4];
-    float cof[4];
 };
 
 struct DirLine {
@@ -227,6 +227,18 @@ __device__ __forceinline__ void upk2(f32x2 r, float &x, float &y) {
 __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
     f32x2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// min of three FP32 values (a NaN operand is ignored, as by fminf)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
 }
 
@@ -308,6 +320,54 @@ __device__ __forceinline__ float sample_w(const NodeLine &nl, const DirLine &dl,
         w = __fmaf_rn(w, t, dl.c[1]);
         return __fmaf_rn(w, t, dl.c[0]);
     }
+}
+
+// Slope of v along a line at t = 0, per sample step: sl = sa (A1 + cb cJ)
+// with, at the node (d0 = d(0), lg0 = log2 J0),
+//   dd/dt(0) = A1 + cJ (B1 + 2 B2 lg0) / (J0 ln 2),
+//   dv/dd(d0) = 1 + K2' (d0 < 0),  1 + K1' ln 2 2^{-d0} (d0 >= 0),
+//   sa = h dv/dd(d0),  cb = (B1 + 2 B2 lg0) / (J0 ln 2).
+// Used only to pick the slope of a rigorous lower bound (any slope gives
+// one), so its own rounding does not matter.
+__device__ inline void center_slope_consts(const NodeLine &nl, double h, float &sa, float &cb) {
+    const double J0 = nl.J0, lg0 = J0 > 0.0 ? log2(J0) : 0.0;
+    const double d0 = (double)nl.A0 + lg0 * ((double)nl.B1 + (double)nl.B2 * lg0);
+    const double dv = d0 < 0.0 ? 1.0 + (double)nl.K2 : 1.0 + (double)nl.K1 * kLn2d * exp2(-d0);
+    sa = (float)(h * dv);
+    cb = J0 > 0.0 ? (float)(((double)nl.B1 + 2.0 * (double)nl.B2 * lg0) / (J0 * kLn2d)) : 0.0f;
+}
+
+// The constants of sample_w<NH> duplicated into register pairs, and two
+// samples at the parameters in T: every FMA of sample_w is one half of a
+// fma.rn.f32x2 (so each component is rounded exactly as sample_w rounds it);
+// the MUFU operations and the clamps stay scalar.
+struct NHPair {
+    f32x2 A0, A1, A2, B1, B2, K2, NK1, CJ, J0;
+};
+__device__ __forceinline__ NHPair nh_pair(const NodeLine &nl, const DirLine &dl) {
+    NHPair c;
+    c.A0 = pk2(nl.A0, nl.A0);
+    c.A1 = pk2(dl.A1, dl.A1);
+    c.A2 = pk2(dl.A2, dl.A2);
+    c.B1 = pk2(nl.B1, nl.B1);
+    c.B2 = pk2(nl.B2, nl.B2);
+    c.K2 = pk2(nl.K2, nl.K2);
+    c.NK1 = pk2(-nl.K1, -nl.K1);
+    c.CJ = pk2(dl.cJ, dl.cJ);
+    c.J0 = pk2(dl.J0, dl.J0);
+    return c;
+}
+__device__ __forceinline__ f32x2 sample_nh2(const NHPair &c, f32x2 T) {
+    const f32x2 P = fma2(T, fma2(T, c.A2, c.A1), c.A0);
+    float j0, j1;
+    upk2(fma2(T, c.CJ, c.J0), j0, j1);
+    const f32x2 LG = pk2(lg2_approx(j0), lg2_approx(j1));
+    const f32x2 D = fma2(LG, fma2(LG, c.B2, c.B1), P);
+    float d0, d1;
+    upk2(D, d0, d1);
+    const f32x2 E = pk2(ex2_approx(-fmaxf(d0, 0.0f)), ex2_approx(-fmaxf(d1, 0.0f)));
+    const f32x2 W = fma2(c.K2, pk2(fminf(d0, 0.0f), fminf(d1, 0.0f)), D);
+    return fma2(c.NK1, E, W);
 }
 
 // FP64 sample of W along the line: G = F + t R with t = (m - m0) h and R, G

@@ -53,7 +53,7 @@ struct RefineOut {
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
     C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
-    C_FALLBACK, C_REFFULL, C_BOUNDED, C_NUM
+    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_NUM
 };
 
 // Pipeline passes over one level's queue.

@@ -62,6 +62,62 @@ __device__ __forceinline__ float sample_line_min(float *sw, const NodeLine &nl, 
     return e;
 }
 
+// sample_line_min for the damage energy on paired FP32 arithmetic: the same
+// samples bit for bit.  The bound takes v - s x with the sample's own
+// abscissa in one FMA (x exact), so each term has a single rounding, and it
+// leaves the centre out: the result bounds from below the value at 0 of the
+// hull of the left and right sets, which is the quantity the hull search
+// bounds.  The chunk holding the centre is peeled so that only it pays for
+// the mask.
+__device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &nl,
+                                                    const DirLine &dl, const LineSpec &ln,
+                                                    int lane, const float (&tl)[4], float ns) {
+    const NHPair c = nh_pair(nl, dl);
+    const float h128 = 128.0f * ln.h32;
+    const f32x2 H = pk2(h128, h128), TL01 = pk2(tl[0], tl[1]), TL23 = pk2(tl[2], tl[3]);
+    const f32x2 NS = pk2(ns, ns), ONE = pk2(1.0f, 1.0f), STEP = pk2(128.0f, 128.0f);
+    const float x0 = (float)(4 * lane - ln.m0);
+    f32x2 FQ = pk2(0.0f, 0.0f), X01 = pk2(x0, x0 + 1.0f), X23 = pk2(x0 + 2.0f, x0 + 3.0f);
+    float e = INFINITY;
+    auto chunk = [&](int q, bool centre) {
+        const f32x2 V01 = sample_nh2(c, fma2(H, FQ, TL01));
+        const f32x2 V23 = sample_nh2(c, fma2(H, FQ, TL23));
+        float4 v;
+        upk2(V01, v.x, v.y);
+        upk2(V23, v.z, v.w);
+        *reinterpret_cast<float4 *>(sw + 128 * q + 4 * lane) = v;
+        float b0, b1, b2, b3;
+        upk2(fma2(NS, X01, V01), b0, b1);
+        upk2(fma2(NS, X23, V23), b2, b3);
+        if (centre) {
+            const int ic = ln.m0 - 128 * q - 4 * lane;  // in [0, 4) on the lane holding m0
+            b0 = ic == 0 ? INFINITY : b0;
+            b1 = ic == 1 ? INFINITY : b1;
+            b2 = ic == 2 ? INFINITY : b2;
+            b3 = ic == 3 ? INFINITY : b3;
+        }
+        e = fmin3(e, b0, b1);
+        e = fmin3(e, b2, b3);
+        FQ = add2(FQ, ONE);
+        X01 = add2(X01, STEP);
+        X23 = add2(X23, STEP);
+    };
+    const int qc = min(ln.m0 >> 7, ln.nfull);  // chunk of the centre (nfull: in the tail)
+#pragma unroll 1
+    for (int q = 0; q < qc; ++q) chunk(q, false);
+    if (qc < ln.nfull) {
+        chunk(qc, true);
+#pragma unroll 1
+        for (int q = qc + 1; q < ln.nfull; ++q) chunk(q, false);
+    }
+    for (int k = 128 * ln.nfull + lane; k < ln.L; k += 32) {
+        const float v = sample_w<CVX_ENERGY_NH_DAMAGE>(nl, dl, (float)(k - ln.m0) * ln.h32);
+        sw[k] = v;
+        if (k != ln.m0) e = fminf(e, __fmaf_rn(ns, (float)(k - ln.m0), v));
+    }
+    return e;
+}
+
 // Number of samples with J(t) > 0 on a line (the algorithmic work count).
 __device__ __forceinline__ int valid_samples(const DirLine &dl, const LineSpec &ln, int energy) {
     if (energy != CVX_ENERGY_NH_DAMAGE || dl.cJ == 0.0f) return ln.L;

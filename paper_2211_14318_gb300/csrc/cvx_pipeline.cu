@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
     __shared__ float s_drop[16], s_qhi[16];
     __shared__ float s_w0;
     __shared__ float s_shift;  // the point's sample shift C
+    __shared__ float s_sa, s_cb;  // centre-slope constants of the node (damage energy)
     __shared__ int s_ukey;     // smallest q_hi screened so far in this item (f2key order)
     __shared__ int2 s_c;
     __shared__ unsigned s_hc[16][HC_N];
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
     __syncwarp();
     HullCounters hc{s_hc[warp]};
-    unsigned long long n_valid = 0, n_lines = 0, n_bounded = 0;
+    unsigned long long n_valid = 0, n_lines = 0, n_bounded = 0, n_flat = 0;
 
     for (;;) {
         __syncthreads();
@@ -177,6 +178,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                     s_nl = make_node_line(F, beta, s_pd.mat);
                     s_shift = (float)line_shift(s_pd.mat, beta);
                     s_ukey = f2key(INFINITY);
+                    if (EK == CVX_ENERGY_NH_DAMAGE)
+                        center_slope_consts(s_nl, s_pd.line.h64, s_sa, s_cb);
                 }
             }
         }
@@ -215,17 +218,27 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         float dropped = INFINITY, w0 = 0.0f, qhi_min = INFINITY;
         int warm_a = -1, warm_b = -1;
         float s_warm = 0.0f;  // slope of the last searched bridge
+        // slope of the sampling-pass bound: the line's own tangent at t = 0
+        // (damage energy) until a search finds a bridge clearly below the
+        // centre, then that bridge's slope until a line is flat again
+        bool cmode = EK == CVX_ENERGY_NH_DAMAGE;
+        const float sa = s_sa, cb = s_cb;
         float my_cJ = 0.0f;   // lane k keeps the k-th line of each run of 32 for the work count
         const float kap = s_pd.kappa_f, C = s_shift;
         for (int dj = jb; dj < je; ++dj) {
             const int gd = win ? window_dir(s_pd, cen, dj) : dj;
             const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
-            // sampling, with min over the line of v - s x at the last slope:
-            // a lower bound qb of this line's hull value at 0
-            const float e = sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -s_warm);
+            // sampling, with min over the line of v - s x at slope sl: a lower
+            // bound qb of the value at 0 of the hull of the left and right sets
+            // (any slope gives one; the damage-energy sampler leaves the centre
+            // out of the min, the test energy's keeps it, which only lowers qb)
+            const float sl = cmode ? sa * __fmaf_rn(cb, dl.cJ, dl.A1) : s_warm;
+            const float e = EK == CVX_ENERGY_NH_DAMAGE
+                                ? sample_line_min_nh(sw, nl, dl, ln, lane, tl, -sl)
+                                : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
             const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
             const float emin = __int_as_float(f2key(__int_as_float(ek)));
-            const float qb = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(s_warm) * (float)ln.m0) -
+            const float qb = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(sl) * (float)ln.m0) -
                              1e-30f;
             __syncwarp();
             // a line whose bound already exceeds m + eps(m), m = min(W(F), the
@@ -235,20 +248,31 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             const int ukey = *(volatile int *)&s_ukey;
             const float mref = fminf(wc, __int_as_float(f2key(__int_as_float(ukey))));
             const bool bounded = qb - eps32_at(qb, kap, C) > mref + eps32_at(mref, kap, C);
+            // a flat line: its bound is within the sample error of the centre
+            // value, so no bridge of it lies clearly below the centre; the
+            // search is skipped and qb stands as its lower bound (its upper
+            // bound stays unknown).  Such lines only matter at nodes whose
+            // split, if any, is within the FP32 error, where the FP64
+            // refinement of the best candidates decides.
+            const float epsc = eps32_at(wc, kap, C);
+            const bool flat = EK == CVX_ENERGY_NH_DAMAGE && !bounded && qb >= wc - epsc;
             ScreenOut o;
-            if (bounded) {
+            if (bounded || flat) {
                 o.a = o.b = -1;
                 o.q_lo = qb;
                 o.q_hi = INFINITY;
                 o.w0 = wc;
+                if (flat) cmode = true;
             } else {
                 o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
                 if (o.a >= 0) {
                     s_warm = __fdividef(sw[o.b] - sw[o.a], (float)(o.b - o.a));
                     if (lane == 0) atomicMin(&s_ukey, f2key(o.q_hi));
                 }
+                cmode = EK == CVX_ENERGY_NH_DAMAGE && !(o.a >= 0 && o.q_hi < wc - epsc);
             }
             if (lane == 0 && bounded) ++n_bounded;
+            if (lane == 0 && flat) ++n_flat;
             __syncwarp();
             const int r = (dj - jb) & 31;
             if (lane == r) my_cJ = dl.cJ;
@@ -328,6 +352,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         const unsigned *c = hc.c;
         add_counter(P.counters, C_LINES, n_lines);
         add_counter(P.counters, C_BOUNDED, n_bounded);
+        add_counter(P.counters, C_FLAT, n_flat);
         add_counter(P.counters, C_VALID, n_valid);
         add_counter(P.counters, C_FULL, c[HC_FULL]);
         add_counter(P.counters, C_RARE, c[HC_RARE]);
