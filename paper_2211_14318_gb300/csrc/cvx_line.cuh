@@ -68,10 +68,12 @@ __device__ __forceinline__ float sample_line_min(float *sw, const NodeLine &nl, 
 // leaves the centre out: the result bounds from below the value at 0 of the
 // hull of the left and right sets, which is the quantity the hull search
 // bounds.  The chunk holding the centre is peeled so that only it pays for
-// the mask.
+// the mask.  With tail1 the line has one sample past its full chunks (the
+// right end, L = 128 nfull + 1), computed beforehand by the caller (tv).
 __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &nl,
                                                     const DirLine &dl, const LineSpec &ln,
-                                                    int lane, const float (&tl)[4], float ns) {
+                                                    int lane, const float (&tl)[4], float ns,
+                                                    bool tail1, float tv) {
     const NHPair c = nh_pair(nl, dl);
     const float h128 = 128.0f * ln.h32;
     const f32x2 H = pk2(h128, h128), TL01 = pk2(tl[0], tl[1]), TL23 = pk2(tl[2], tl[3]);
@@ -109,6 +111,10 @@ __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &n
         chunk(qc, true);
 #pragma unroll 1
         for (int q = qc + 1; q < ln.nfull; ++q) chunk(q, false);
+    }
+    if (tail1) {
+        if (lane == 0) sw[ln.L - 1] = tv;
+        return fminf(e, __fmaf_rn(ns, (float)(ln.L - 1 - ln.m0), tv));
     }
     for (int k = 128 * ln.nfull + lane; k < ln.L; k += 32) {
         const float v = sample_w<CVX_ENERGY_NH_DAMAGE>(nl, dl, (float)(k - ln.m0) * ln.h32);

@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
     __shared__ int s_ukey;     // smallest q_hi screened so far in this item (f2key order)
     __shared__ int2 s_c;
     __shared__ unsigned s_hc[16][HC_N];
+    __shared__ float s_tail[16][32];  // right-end samples of a warp's next 32 lines
     const bool win = P.pass == PASS_WINDOW;
 
     const int n_nodes = P.cnt[level];
@@ -225,8 +226,25 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         const float sa = s_sa, cb = s_cb;
         float my_cJ = 0.0f;   // lane k keeps the k-th line of each run of 32 for the work count
         const float kap = s_pd.kappa_f, C = s_shift;
+        // damage energy with L = 128 nfull + 1: every 32 lines, lane k samples
+        // the right end of the k-th next line (and counts its valid samples),
+        // instead of the whole warp sampling one tail sample per line
+        const bool tail1 = EK == CVX_ENERGY_NH_DAMAGE && ln.nfull > 0 && ln.L == 128 * ln.nfull + 1;
         for (int dj = jb; dj < je; ++dj) {
             const int gd = win ? window_dir(s_pd, cen, dj) : dj;
+            const int r = (dj - jb) & 31;
+            if (tail1 && r == 0) {
+                const int dd = dj + lane;
+                float tv = INFINITY;
+                if (dd < je) {
+                    const int gd2 = win ? window_dir(s_pd, cen, dd) : dd;
+                    const DirLine d2 = make_dir_line<EK>(s_nl, P.dir32[doff + gd2]);
+                    tv = sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32);
+                    n_valid += valid_samples(d2, ln, EK);
+                }
+                s_tail[warp][lane] = tv;
+                __syncwarp();
+            }
             const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
             // sampling, with min over the line of v - s x at slope sl: a lower
             // bound qb of the value at 0 of the hull of the left and right sets
@@ -234,7 +252,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             // out of the min, the test energy's keeps it, which only lowers qb)
             const float sl = cmode ? sa * __fmaf_rn(cb, dl.cJ, dl.A1) : s_warm;
             const float e = EK == CVX_ENERGY_NH_DAMAGE
-                                ? sample_line_min_nh(sw, nl, dl, ln, lane, tl, -sl)
+                                ? sample_line_min_nh(sw, nl, dl, ln, lane, tl, -sl, tail1,
+                                                     s_tail[warp][r])
                                 : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
             const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
             const float emin = __int_as_float(f2key(__int_as_float(ek)));
@@ -274,9 +293,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             if (lane == 0 && bounded) ++n_bounded;
             if (lane == 0 && flat) ++n_flat;
             __syncwarp();
-            const int r = (dj - jb) & 31;
-            if (lane == r) my_cJ = dl.cJ;
-            if (r == 31 || dj == je - 1) {
+            if (!tail1 && lane == r) my_cJ = dl.cJ;
+            if (!tail1 && (r == 31 || dj == je - 1)) {
                 if (lane <= r) {
                     DirLine vl = dl;
                     vl.cJ = my_cJ;
