@@ -206,8 +206,11 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         const int dpi = win ? s_pd.wdpi : s_pd.dpi;
         const int2 cen = s_c;
         const int d0 = ch * dpi, d1 = min(D, d0 + dpi);
-        const int per = (d1 - d0 + nw - 1) / nw;
-        const int jb = d0 + warp * per, je = min(d1, jb + per);
+        // the item's directions in segments of up to 64 contiguous ones, dealt
+        // to the warps in turn: the lines that need a hull search cluster
+        // around the split direction, and this spreads them over the warps
+        const int seg = max(1, min(64, (d1 - d0 + nw - 1) / nw));
+        const int nseg = (d1 - d0 + seg - 1) / seg;
 
         float tq[kWarpTop];
         int td[kWarpTop];
@@ -230,88 +233,92 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         // the right end of the k-th next line (and counts its valid samples),
         // instead of the whole warp sampling one tail sample per line
         const bool tail1 = EK == CVX_ENERGY_NH_DAMAGE && ln.nfull > 0 && ln.L == 128 * ln.nfull + 1;
-        for (int dj = jb; dj < je; ++dj) {
-            const int gd = win ? window_dir(s_pd, cen, dj) : dj;
-            const int r = (dj - jb) & 31;
-            if (tail1 && r == 0) {
-                const int dd = dj + lane;
-                float tv = INFINITY;
-                if (dd < je) {
-                    const int gd2 = win ? window_dir(s_pd, cen, dd) : dd;
-                    const DirLine d2 = make_dir_line<EK>(s_nl, P.dir32[doff + gd2]);
-                    tv = sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32);
-                    n_valid += valid_samples(d2, ln, EK);
+        for (int sg = warp; sg < nseg; sg += nw) {
+            const int jb = d0 + sg * seg, je = min(d1, jb + seg);
+            if (EK == CVX_ENERGY_NH_DAMAGE) cmode = true;
+            for (int dj = jb; dj < je; ++dj) {
+                const int gd = win ? window_dir(s_pd, cen, dj) : dj;
+                const int r = (dj - jb) & 31;
+                if (tail1 && r == 0) {
+                    const int dd = dj + lane;
+                    float tv = INFINITY;
+                    if (dd < je) {
+                        const int gd2 = win ? window_dir(s_pd, cen, dd) : dd;
+                        const DirLine d2 = make_dir_line<EK>(s_nl, P.dir32[doff + gd2]);
+                        tv = sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32);
+                        n_valid += valid_samples(d2, ln, EK);
+                    }
+                    s_tail[warp][lane] = tv;
+                    __syncwarp();
                 }
-                s_tail[warp][lane] = tv;
+                const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
+                // sampling, with min over the line of v - s x at slope sl: a lower
+                // bound qb of the value at 0 of the hull of the left and right sets
+                // (any slope gives one; the damage-energy sampler leaves the centre
+                // out of the min, the test energy's keeps it, which only lowers qb)
+                const float sl = cmode ? sa * __fmaf_rn(cb, dl.cJ, dl.A1) : s_warm;
+                const float e = EK == CVX_ENERGY_NH_DAMAGE
+                                    ? sample_line_min_nh(sw, nl, dl, ln, lane, tl, -sl, tail1,
+                                                         s_tail[warp][r])
+                                    : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
+                const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
+                const float emin = __int_as_float(f2key(__int_as_float(ek)));
+                const float qb = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(sl) * (float)ln.m0) -
+                                 1e-30f;
                 __syncwarp();
-            }
-            const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
-            // sampling, with min over the line of v - s x at slope sl: a lower
-            // bound qb of the value at 0 of the hull of the left and right sets
-            // (any slope gives one; the damage-energy sampler leaves the centre
-            // out of the min, the test energy's keeps it, which only lowers qb)
-            const float sl = cmode ? sa * __fmaf_rn(cb, dl.cJ, dl.A1) : s_warm;
-            const float e = EK == CVX_ENERGY_NH_DAMAGE
-                                ? sample_line_min_nh(sw, nl, dl, ln, lane, tl, -sl, tail1,
-                                                     s_tail[warp][r])
-                                : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
-            const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
-            const float emin = __int_as_float(f2key(__int_as_float(ek)));
-            const float qb = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(sl) * (float)ln.m0) -
-                             1e-30f;
-            __syncwarp();
-            // a line whose bound already exceeds m + eps(m), m = min(W(F), the
-            // smallest upper bound seen in this item), can neither win nor split
-            // (the node-level test in k_select uses the same monotone rule)
-            const float wc = sw[ln.m0];
-            const int ukey = *(volatile int *)&s_ukey;
-            const float mref = fminf(wc, __int_as_float(f2key(__int_as_float(ukey))));
-            const bool bounded = qb - eps32_at(qb, kap, C) > mref + eps32_at(mref, kap, C);
-            // a flat line: its bound is within the sample error of the centre
-            // value, so no bridge of it lies clearly below the centre; the
-            // search is skipped and qb stands as its lower bound (its upper
-            // bound stays unknown).  Such lines only matter at nodes whose
-            // split, if any, is within the FP32 error, where the FP64
-            // refinement of the best candidates decides.
-            const float epsc = eps32_at(wc, kap, C);
-            const bool flat = EK == CVX_ENERGY_NH_DAMAGE && !bounded && qb >= wc - epsc;
-            ScreenOut o;
-            if (bounded || flat) {
-                o.a = o.b = -1;
-                o.q_lo = qb;
-                o.q_hi = INFINITY;
-                o.w0 = wc;
-                if (flat) cmode = true;
-            } else {
-                o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
+                // a line whose bound already exceeds m + eps(m), m = min(W(F), the
+                // smallest upper bound seen in this item), can neither win nor split
+                // (the node-level test in k_select uses the same monotone rule)
+                const float wc = sw[ln.m0];
+                const int ukey = *(volatile int *)&s_ukey;
+                const float mref = fminf(wc, __int_as_float(f2key(__int_as_float(ukey))));
+                const bool bounded = qb - eps32_at(qb, kap, C) > mref + eps32_at(mref, kap, C);
+                // a flat line: its bound is within the sample error of the centre
+                // value, so no bridge of it lies clearly below the centre; the
+                // search is skipped and qb stands as its lower bound (its upper
+                // bound stays unknown).  Such lines only matter at nodes whose
+                // split, if any, is within the FP32 error, where the FP64
+                // refinement of the best candidates decides.
+                const float epsc = eps32_at(wc, kap, C);
+                const bool flat = EK == CVX_ENERGY_NH_DAMAGE && !bounded && qb >= wc - epsc;
+                ScreenOut o;
+                if (bounded || flat) {
+                    o.a = o.b = -1;
+                    o.q_lo = qb;
+                    o.q_hi = INFINITY;
+                    o.w0 = wc;
+                    if (flat) cmode = true;
+                } else {
+                    o = warp_screen(sw, g, lane, warm_a, warm_b, hc);
+                    if (o.a >= 0) {
+                        s_warm = __fdividef(sw[o.b] - sw[o.a], (float)(o.b - o.a));
+                        if (lane == 0) atomicMin(&s_ukey, f2key(o.q_hi));
+                    }
+                    cmode = EK == CVX_ENERGY_NH_DAMAGE && !(o.a >= 0 && o.q_hi < wc - epsc);
+                }
+                if (lane == 0 && bounded) ++n_bounded;
+                if (lane == 0 && flat) ++n_flat;
+                __syncwarp();
+                if (!tail1 && lane == r) my_cJ = dl.cJ;
+                if (!tail1 && (r == 31 || dj == je - 1)) {
+                    if (lane <= r) {
+                        DirLine vl = dl;
+                        vl.cJ = my_cJ;
+                        n_valid += valid_samples(vl, ln, EK);
+                    }
+                }
+                if (lane == 0) ++n_lines;
+                w0 = o.w0;
                 if (o.a >= 0) {
-                    s_warm = __fdividef(sw[o.b] - sw[o.a], (float)(o.b - o.a));
-                    if (lane == 0) atomicMin(&s_ukey, f2key(o.q_hi));
+                    warm_a = o.a;
+                    warm_b = o.b;
                 }
-                cmode = EK == CVX_ENERGY_NH_DAMAGE && !(o.a >= 0 && o.q_hi < wc - epsc);
+                qhi_min = fminf(qhi_min, o.q_hi);
+                if (bounded)
+                    dropped = fminf(dropped, qb);
+                else
+                    top_insert(tq, td, dropped, o.q_lo, gd);
             }
-            if (lane == 0 && bounded) ++n_bounded;
-            if (lane == 0 && flat) ++n_flat;
-            __syncwarp();
-            if (!tail1 && lane == r) my_cJ = dl.cJ;
-            if (!tail1 && (r == 31 || dj == je - 1)) {
-                if (lane <= r) {
-                    DirLine vl = dl;
-                    vl.cJ = my_cJ;
-                    n_valid += valid_samples(vl, ln, EK);
-                }
-            }
-            if (lane == 0) ++n_lines;
-            w0 = o.w0;
-            if (o.a >= 0) {
-                warm_a = o.a;
-                warm_b = o.b;
-            }
-            qhi_min = fminf(qhi_min, o.q_hi);
-            if (bounded)
-                dropped = fminf(dropped, qb);
-            else
-                top_insert(tq, td, dropped, o.q_lo, gd);
         }
         if (lane == 0) {
 #pragma unroll
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             }
             s_drop[warp] = dropped;
             s_qhi[warp] = qhi_min;
-            if (jb < je) s_w0 = w0;
+            if (warp < nseg) s_w0 = w0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
