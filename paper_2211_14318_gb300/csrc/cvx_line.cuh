@@ -1,6 +1,8 @@
 // cvx_line.cuh -- sampling one rank-one line into a warp's shared buffer.
 #pragma once
 
+#include <type_traits>
+
 #include "cvx_bridge.cuh"
 #include "cvx_internal.h"
 
@@ -104,13 +106,26 @@ __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &n
         X01 = add2(X01, STEP);
         X23 = add2(X23, STEP);
     };
-    const int qc = min(ln.m0 >> 7, ln.nfull);  // chunk of the centre (nfull: in the tail)
+    // L = 1025 and 2049 (centre in chunk nfull / 2): chunks unrolled at compile
+    // time, so no loop counter, branch or address arithmetic per chunk
+    auto unrolled = [&](auto nf) {
+        constexpr int NF = decltype(nf)::value;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) chunk(q, q == NF / 2);
+    };
+    if (tail1 && ln.nfull == 8) {
+        unrolled(std::integral_constant<int, 8>());
+    } else if (tail1 && ln.nfull == 16) {
+        unrolled(std::integral_constant<int, 16>());
+    } else {
+        const int qc = min(ln.m0 >> 7, ln.nfull);  // chunk of the centre (nfull: in the tail)
 #pragma unroll 1
-    for (int q = 0; q < qc; ++q) chunk(q, false);
-    if (qc < ln.nfull) {
-        chunk(qc, true);
+        for (int q = 0; q < qc; ++q) chunk(q, false);
+        if (qc < ln.nfull) {
+            chunk(qc, true);
 #pragma unroll 1
-        for (int q = qc + 1; q < ln.nfull; ++q) chunk(q, false);
+            for (int q = qc + 1; q < ln.nfull; ++q) chunk(q, false);
+        }
     }
     if (tail1) {
         if (lane == 0) sw[ln.L - 1] = tv;

@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
     __syncwarp();
     HullCounters hc{s_hc[warp]};
-    unsigned long long n_valid = 0, n_lines = 0, n_bounded = 0, n_flat = 0;
+    unsigned long long n_valid = 0, n_lines = 0;
+    unsigned n_bounded = 0, n_flat = 0;  // warp-uniform, reported by lane 0
 
     for (;;) {
         __syncthreads();
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         for (int sg = warp; sg < nseg; sg += nw) {
             const int jb = d0 + sg * seg, je = min(d1, jb + seg);
             if (EK == CVX_ENERGY_NH_DAMAGE) cmode = true;
+            n_lines += (unsigned long long)(je - jb);
             for (int dj = jb; dj < je; ++dj) {
                 const int gd = win ? window_dir(s_pd, cen, dj) : dj;
                 const int r = (dj - jb) & 31;
@@ -296,8 +298,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                     }
                     cmode = EK == CVX_ENERGY_NH_DAMAGE && !(o.a >= 0 && o.q_hi < wc - epsc);
                 }
-                if (lane == 0 && bounded) ++n_bounded;
-                if (lane == 0 && flat) ++n_flat;
+                n_bounded += bounded ? 1u : 0u;
+                n_flat += flat ? 1u : 0u;
                 __syncwarp();
                 if (!tail1 && lane == r) my_cJ = dl.cJ;
                 if (!tail1 && (r == 31 || dj == je - 1)) {
@@ -307,7 +309,6 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                         n_valid += valid_samples(vl, ln, EK);
                     }
                 }
-                if (lane == 0) ++n_lines;
                 w0 = o.w0;
                 if (o.a >= 0) {
                     warm_a = o.a;
