@@ -344,6 +344,16 @@ __device__ inline void center_slope_consts(const NodeLine &nl, double h, float &
 struct NHPair {
     f32x2 A0, A1, A2, B1, B2, K2, NK1, CJ, J0;
 };
+__device__ __forceinline__ NHPair nh_pair_node(const NodeLine &nl) {
+    NHPair c;
+    c.A0 = pk2(nl.A0, nl.A0);
+    c.B1 = pk2(nl.B1, nl.B1);
+    c.B2 = pk2(nl.B2, nl.B2);
+    c.K2 = pk2(nl.K2, nl.K2);
+    c.NK1 = pk2(-nl.K1, -nl.K1);
+    c.A1 = c.A2 = c.CJ = c.J0 = c.A0;
+    return c;
+}
 __device__ __forceinline__ NHPair nh_pair(const NodeLine &nl, const DirLine &dl) {
     NHPair c;
     c.A0 = pk2(nl.A0, nl.A0);

@@ -72,11 +72,13 @@ __device__ __forceinline__ float sample_line_min(float *sw, const NodeLine &nl, 
 // bounds.  The chunk holding the centre is peeled so that only it pays for
 // the mask.  With tail1 the line has one sample past its full chunks (the
 // right end, L = 128 nfull + 1), computed beforehand by the caller (tv).
+// c holds the line's constants in register pairs (nh_pair); nl and dl serve
+// the scalar samples past the full chunks.
 __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &nl,
-                                                    const DirLine &dl, const LineSpec &ln,
-                                                    int lane, const float (&tl)[4], float ns,
-                                                    bool tail1, float tv) {
-    const NHPair c = nh_pair(nl, dl);
+                                                    const NHPair &c, const DirLine &dl,
+                                                    const LineSpec &ln, int lane,
+                                                    const float (&tl)[4], float ns, bool tail1,
+                                                    float tv) {
     const float h128 = 128.0f * ln.h32;
     const f32x2 H = pk2(h128, h128), TL01 = pk2(tl[0], tl[1]), TL23 = pk2(tl[2], tl[3]);
     const f32x2 NS = pk2(ns, ns), ONE = pk2(1.0f, 1.0f), STEP = pk2(128.0f, 128.0f);

@@ -150,7 +150,11 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
     __shared__ int s_ukey;     // smallest q_hi screened so far in this item (f2key order)
     __shared__ int2 s_c;
     __shared__ unsigned s_hc[16][HC_N];
-    __shared__ float s_tail[16][32];  // right-end samples of a warp's next 32 lines
+    __shared__ float s_tail[8][32];   // right-end samples of a warp's next 32 lines
+    // damage energy: the next 32 lines' constants (A1, A2, cof F : R, J0), each
+    // duplicated into a register pair, and their tangent slopes at t = 0
+    __shared__ float4 s_dir[8][32][2];
+    __shared__ float s_slc[8][32];
     const bool win = P.pass == PASS_WINDOW;
 
     const int n_nodes = P.cnt[level];
@@ -207,10 +211,9 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         const int dpi = win ? s_pd.wdpi : s_pd.dpi;
         const int2 cen = s_c;
         const int d0 = ch * dpi, d1 = min(D, d0 + dpi);
-        // the item's directions in segments of up to 64 contiguous ones, dealt
-        // to the warps in turn: the lines that need a hull search cluster
-        // around the split direction, and this spreads them over the warps
-        const int seg = max(1, min(64, (d1 - d0 + nw - 1) / nw));
+        // one contiguous run of directions per warp: every line warm-starts
+        // its hull search from a neighbouring direction's bridge
+        const int seg = max(1, (d1 - d0 + nw - 1) / nw);
         const int nseg = (d1 - d0 + seg - 1) / seg;
 
         float tq[kWarpTop];
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         // centre, then that bridge's slope until a line is flat again
         bool cmode = EK == CVX_ENERGY_NH_DAMAGE;
         const float sa = s_sa, cb = s_cb;
+        const NHPair npair = nh_pair_node(nl);
         float my_cJ = 0.0f;   // lane k keeps the k-th line of each run of 32 for the work count
         const float kap = s_pd.kappa_f, C = s_shift;
         // damage energy with L = 128 nfull + 1: every 32 lines, lane k samples
@@ -241,26 +245,47 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
             for (int dj = jb; dj < je; ++dj) {
                 const int gd = win ? window_dir(s_pd, cen, dj) : dj;
                 const int r = (dj - jb) & 31;
-                if (tail1 && r == 0) {
+                // damage energy: every 32 lines, lane k sets up the k-th next line
+                // (its constants, tangent slope, valid-sample count and, with
+                // L = 128 nfull + 1, its right-end sample) for the whole warp
+                if (EK == CVX_ENERGY_NH_DAMAGE && r == 0) {
                     const int dd = dj + lane;
-                    float tv = INFINITY;
                     if (dd < je) {
                         const int gd2 = win ? window_dir(s_pd, cen, dd) : dd;
                         const DirLine d2 = make_dir_line<EK>(s_nl, P.dir32[doff + gd2]);
-                        tv = sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32);
+                        if (tail1) s_tail[warp][lane] = sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32);
+                        s_dir[warp][lane][0] = make_float4(d2.A1, d2.A1, d2.A2, d2.A2);
+                        s_dir[warp][lane][1] = make_float4(d2.cJ, d2.cJ, d2.J0, d2.J0);
+                        s_slc[warp][lane] = sa * __fmaf_rn(cb, d2.cJ, d2.A1);
                         n_valid += valid_samples(d2, ln, EK);
                     }
-                    s_tail[warp][lane] = tv;
                     __syncwarp();
                 }
-                const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
+                DirLine dl;
+                NHPair c;
+                float sl;
+                if (EK == CVX_ENERGY_NH_DAMAGE) {
+                    const float4 q0 = s_dir[warp][r][0], q1 = s_dir[warp][r][1];
+                    c = npair;
+                    c.A1 = pk2(q0.x, q0.y);
+                    c.A2 = pk2(q0.z, q0.w);
+                    c.CJ = pk2(q1.x, q1.y);
+                    c.J0 = pk2(q1.z, q1.w);
+                    dl.A1 = q0.x;
+                    dl.A2 = q0.z;
+                    dl.cJ = q1.x;
+                    dl.J0 = q1.z;
+                    sl = cmode ? s_slc[warp][r] : s_warm;
+                } else {
+                    dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
+                    sl = s_warm;
+                }
                 // sampling, with min over the line of v - s x at slope sl: a lower
                 // bound qb of the value at 0 of the hull of the left and right sets
                 // (any slope gives one; the damage-energy sampler leaves the centre
                 // out of the min, the test energy's keeps it, which only lowers qb)
-                const float sl = cmode ? sa * __fmaf_rn(cb, dl.cJ, dl.A1) : s_warm;
                 const float e = EK == CVX_ENERGY_NH_DAMAGE
-                                    ? sample_line_min_nh(sw, nl, dl, ln, lane, tl, -sl, tail1,
+                                    ? sample_line_min_nh(sw, nl, c, dl, ln, lane, tl, -sl, tail1,
                                                          s_tail[warp][r])
                                     : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
                 const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
@@ -301,8 +326,8 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                 n_bounded += bounded ? 1u : 0u;
                 n_flat += flat ? 1u : 0u;
                 __syncwarp();
-                if (!tail1 && lane == r) my_cJ = dl.cJ;
-                if (!tail1 && (r == 31 || dj == je - 1)) {
+                if (EK != CVX_ENERGY_NH_DAMAGE && lane == r) my_cJ = dl.cJ;
+                if (EK != CVX_ENERGY_NH_DAMAGE && (r == 31 || dj == je - 1)) {
                     if (lane <= r) {
                         DirLine vl = dl;
                         vl.cJ = my_cJ;
