@@ -30,8 +30,9 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    # CVX_NVCC_FLAGS: extra nvcc options (e.g. -DCVX_SCAN_MIN_BLOCKS=4 to trade
-    # registers for occupancy); a change of options needs build(force=True)
+    # CVX_NVCC_FLAGS: extra nvcc options (e.g. -DCVX_SCAN_MIN_BLOCKS=3: fewer
+    # resident line-scan CTAs, more registers per thread); a change of options
+    # needs build(force=True)
     env = os.environ.get("CVX_NVCC_FLAGS", "").split()
     return ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE,
             "-I", CSRC, "--expt-relaxed-constexpr", *env, *extra]

@@ -39,6 +39,10 @@ namespace cvx {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kHullCap = 96;  // rounds of the search before it gives up (flagged)
+// rounds of the screening search: a search that stops before its pair is
+// global leaves a rigorous but loose lower bound, and loose bounds can push
+// the best directions out of the FP64 refinement
+constexpr int kScreenRounds = 4;
 
 struct LineGeom {
     int L, m0, nfull;  // samples, centre index, number of full 128-sample chunks
@@ -419,7 +423,7 @@ __device__ __forceinline__ ScreenOut warp_screen(float *sw, const LineGeom g, in
     }
     float wa = sw[a], wb = sw[b];
     float s = 0.0f, emin = -INFINITY;
-    for (int round = 0; round < 2; ++round) {
+    for (int round = 0; round < kScreenRounds; ++round) {
         if (lane == 0) ++hc.c[HC_ROUNDS];
         // supporting-slope iteration inside 32-sample windows around a and b
         int loA = win_lo_a(a, m0), loB = win_lo_b(b, m0, L);
@@ -468,6 +472,7 @@ __device__ __forceinline__ ScreenOut warp_screen(float *sw, const LineGeom g, in
         const float H = __fmaf_rn(-s, (float)(a - m0), wa);
         const float M = fabsf(H) + fabsf(s) * (float)m0;
         if (emin >= H - 4.0f * kU32 * M) break;  // the windows' pair is (nearly) global
+        if (round == kScreenRounds - 1) break;     // bounds stay rigorous, only looser
         // a sample lies clearly below the chord: restart from the global argmin
         if (lane == 0) ++hc.c[HC_RARE];
         full_argmin(sw, g, lane, s, a, b);

@@ -130,7 +130,7 @@ __global__ void k_init(const Pipe P) {
 // keeps its best directions by their lower bound.
 // -------------------------------------------------------------------------
 #ifndef CVX_SCAN_MIN_BLOCKS
-#define CVX_SCAN_MIN_BLOCKS 3  // CTAs of 256 threads per SM the registers target
+#define CVX_SCAN_MIN_BLOCKS 4  // CTAs of 256 threads per SM the registers target
 #endif
 
 template <int EK>
@@ -211,9 +211,12 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         const int dpi = win ? s_pd.wdpi : s_pd.dpi;
         const int2 cen = s_c;
         const int d0 = ch * dpi, d1 = min(D, d0 + dpi);
-        // one contiguous run of directions per warp: every line warm-starts
-        // its hull search from a neighbouring direction's bridge
-        const int seg = max(1, (d1 - d0 + nw - 1) / nw);
+        // the item's directions in segments of up to 64 contiguous ones, dealt
+        // to the warps in turn: the lines that need a hull search cluster
+        // around the split direction, and this spreads them over the warps
+        // (the first search of a segment starts far from its bridge; the
+        // search runs until its pair is certified, kScreenRounds)
+        const int seg = max(1, min(64, (d1 - d0 + nw - 1) / nw));
         const int nseg = (d1 - d0 + seg - 1) / seg;
 
         float tq[kWarpTop];

@@ -342,9 +342,11 @@ def test_full_size_sampled_parity(cv, orc):
     assert compared >= 16 and frac >= 0.9
 
 
-def test_load_path_fine_grid_parity(cv, orc):
+@pytest.mark.parametrize("step", [5, 10])
+def test_load_path_fine_grid_parity(cv, orc, step):
     """The configuration the proposed form is judged against (128 x 128
-    angles, L = 2049, depth 3) on 4,096 points of the load path at step 10:
+    angles, L = 2049, depth 3) on 4,096 points of the load path at a low and
+    a medium load:
     enough points that every node is a single work item of 16,384 directions,
     as in bench.py's surrogate checks.  The oracle recomputes 8 sampled
     points."""
@@ -353,10 +355,10 @@ def test_load_path_fine_grid_parity(cv, orc):
     mat = _omat(orc)
     path = inputs.load_path(128, n_steps=20, stretch_end=1.8, seed=7)
     beta = np.zeros(path[0].shape[0])
-    for k in range(9):  # history of load steps 1..9
+    for k in range(step - 1):  # history of the earlier load steps
         beta = orc.history_update(mat, path[k], beta)
-    sub = np.linspace(0, path[9].shape[0] - 1, 4096).astype(int)
-    F, b = path[9][sub], beta[sub]
+    sub = np.linspace(0, path[0].shape[0] - 1, 4096).astype(int)
+    F, b = path[step - 1][sub], beta[sub]
     p = api.Params(n_theta_a=128, n_theta_b=128, line_points=2049, t_half=0.5, depth=3, **MAT)
     idx = np.linspace(0, F.shape[0] - 1, 8).astype(int)
     compared, frac = _parity(cv, orc, F, b, p, orc.angle_directions(128, 128), sample_idx=idx)
