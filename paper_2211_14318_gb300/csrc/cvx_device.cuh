@@ -242,6 +242,14 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     return d;
 }
 
+// Warp-wide minimum of FP32 values (one redux.sync; NaN operands are ignored,
+// -0 < +0 as for min.f32).
+__device__ __forceinline__ float warp_min_f32(float x) {
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Sample scale kappa' (v = kappa' W - C): log2(e) / (D_0 (1 - D_inf)) for the
 // damage energy, 1 for the test energy.
 __host__ __device__ inline double line_kappa(const Material &m) {

@@ -85,7 +85,7 @@ __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &n
     const float x0 = (float)(4 * lane - ln.m0);
     f32x2 FQ = pk2(0.0f, 0.0f), X01 = pk2(x0, x0 + 1.0f), X23 = pk2(x0 + 2.0f, x0 + 3.0f);
     float e = INFINITY;
-    auto chunk = [&](int q, bool centre) {
+    auto chunk = [&](int q, bool centre, bool lane0 = false) {
         const f32x2 V01 = sample_nh2(c, fma2(H, FQ, TL01));
         const f32x2 V23 = sample_nh2(c, fma2(H, FQ, TL23));
         float4 v;
@@ -95,7 +95,9 @@ __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &n
         float b0, b1, b2, b3;
         upk2(fma2(NS, X01, V01), b0, b1);
         upk2(fma2(NS, X23, V23), b2, b3);
-        if (centre) {
+        if (centre && lane0) {  // m0 = 128 q: the first sample of lane 0
+            b0 = lane == 0 ? INFINITY : b0;
+        } else if (centre) {
             const int ic = ln.m0 - 128 * q - 4 * lane;  // in [0, 4) on the lane holding m0
             b0 = ic == 0 ? INFINITY : b0;
             b1 = ic == 1 ? INFINITY : b1;
@@ -113,7 +115,7 @@ __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &n
     auto unrolled = [&](auto nf) {
         constexpr int NF = decltype(nf)::value;
 #pragma unroll
-        for (int q = 0; q < NF; ++q) chunk(q, q == NF / 2);
+        for (int q = 0; q < NF; ++q) chunk(q, q == NF / 2, true);  // m0 = 64 NF
     };
     if (tail1 && ln.nfull == 8) {
         unrolled(std::integral_constant<int, 8>());

@@ -291,8 +291,15 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                                     ? sample_line_min_nh(sw, nl, c, dl, ln, lane, tl, -sl, tail1,
                                                          s_tail[warp][r])
                                     : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
-                const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
-                const float emin = __int_as_float(f2key(__int_as_float(ek)));
+                // (the damage-energy bound starts at +inf and its mins skip NaN,
+                // so it is never NaN: a float reduction gives the key order's min)
+                float emin;
+                if (EK == CVX_ENERGY_NH_DAMAGE) {
+                    emin = warp_min_f32(e);
+                } else {
+                    const int ek = __reduce_min_sync(kFull, f2key(nan_to_inf(e)));
+                    emin = __int_as_float(f2key(__int_as_float(ek)));
+                }
                 const float qb = emin - 3.2f * kU32 * (fabsf(emin) + 2.0f * fabsf(sl) * (float)ln.m0) -
                                  1e-30f;
                 __syncwarp();
