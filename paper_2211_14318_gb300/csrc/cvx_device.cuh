@@ -345,8 +345,9 @@ __device__ inline void center_slope_consts(const NodeLine &nl, double h, float &
     cb = J0 > 0.0 ? (float)(((double)nl.B1 + 2.0 * (double)nl.B2 * lg0) / (J0 * kLn2d)) : 0.0f;
 }
 
-// The constants of sample_w<NH> duplicated into register pairs, and two
-// samples at the parameters in T: every FMA of sample_w is one half of a
+// The constants of sample_w<NH> duplicated into register pairs (the node's
+// from nh_pair_node, the direction's from the line scan's shared table), and
+// two samples at the parameters in T: every FMA of sample_w is one half of a
 // fma.rn.f32x2 (so each component is rounded exactly as sample_w rounds it);
 // the MUFU operations and the clamps stay scalar.
 struct NHPair {
@@ -360,19 +361,6 @@ __device__ __forceinline__ NHPair nh_pair_node(const NodeLine &nl) {
     c.K2 = pk2(nl.K2, nl.K2);
     c.NK1 = pk2(-nl.K1, -nl.K1);
     c.A1 = c.A2 = c.CJ = c.J0 = c.A0;
-    return c;
-}
-__device__ __forceinline__ NHPair nh_pair(const NodeLine &nl, const DirLine &dl) {
-    NHPair c;
-    c.A0 = pk2(nl.A0, nl.A0);
-    c.A1 = pk2(dl.A1, dl.A1);
-    c.A2 = pk2(dl.A2, dl.A2);
-    c.B1 = pk2(nl.B1, nl.B1);
-    c.B2 = pk2(nl.B2, nl.B2);
-    c.K2 = pk2(nl.K2, nl.K2);
-    c.NK1 = pk2(-nl.K1, -nl.K1);
-    c.CJ = pk2(dl.cJ, dl.cJ);
-    c.J0 = pk2(dl.J0, dl.J0);
     return c;
 }
 __device__ __forceinline__ f32x2 sample_nh2(const NHPair &c, f32x2 T) {

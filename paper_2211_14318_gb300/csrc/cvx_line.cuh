@@ -72,7 +72,7 @@ __device__ __forceinline__ float sample_line_min(float *sw, const NodeLine &nl, 
 // bounds.  The chunk holding the centre is peeled so that only it pays for
 // the mask.  With tail1 the line has one sample past its full chunks (the
 // right end, L = 128 nfull + 1), computed beforehand by the caller (tv).
-// c holds the line's constants in register pairs (nh_pair); nl and dl serve
+// c holds the line's constants in register pairs; nl and dl serve
 // the scalar samples past the full chunks.
 __device__ __forceinline__ float sample_line_min_nh(float *sw, const NodeLine &nl,
                                                     const NHPair &c, const DirLine &dl,

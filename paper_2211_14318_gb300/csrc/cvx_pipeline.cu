@@ -133,28 +133,29 @@ __global__ void k_init(const Pipe P) {
 #define CVX_SCAN_MIN_BLOCKS 4  // CTAs of 256 threads per SM the registers target
 #endif
 
+constexpr int kScanWarps = 8;  // warps per line-scan CTA at most (256 threads)
+
 template <int EK>
-__global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P, int level) {
+__global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P, int level) {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float *sw = reinterpret_cast<float *>(smem4) + warp * P.stride32;
     __shared__ NodeLine s_nl;
     __shared__ ProbDesc s_pd;
     __shared__ long long s_item;
-    __shared__ float s_q[16][kWarpTop];
-    __shared__ int s_d[16][kWarpTop];
-    __shared__ float s_drop[16], s_qhi[16];
+    // per-warp arrays: at most kScanWarps warps (the launch bound)
+    __shared__ float s_q[kScanWarps][kWarpTop];
+    __shared__ int s_d[kScanWarps][kWarpTop];
+    __shared__ float s_drop[kScanWarps], s_qhi[kScanWarps];
     __shared__ float s_w0;
     __shared__ float s_shift;  // the point's sample shift C
     __shared__ float s_sa, s_cb;  // centre-slope constants of the node (damage energy)
     __shared__ int s_ukey;     // smallest q_hi screened so far in this item (f2key order)
     __shared__ int2 s_c;
-    __shared__ unsigned s_hc[16][HC_N];
-    __shared__ float s_tail[8][32];   // right-end samples of a warp's next 32 lines
-    // damage energy: the next 32 lines' constants (A1, A2, cof F : R, J0), each
-    // duplicated into a register pair, and their tangent slopes at t = 0
-    __shared__ float4 s_dir[8][32][2];
-    __shared__ float s_slc[8][32];
+    __shared__ unsigned s_hc[kScanWarps][HC_N];
+    // damage energy, a warp's next 32 lines: (A1, A1, A2, A2) and
+    // (cof F : R, cof F : R, tangent slope at t = 0, right-end sample)
+    __shared__ float4 s_dir[kScanWarps][32][2];
     const bool win = P.pass == PASS_WINDOW;
 
     const int n_nodes = P.cnt[level];
@@ -234,12 +235,12 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
         // centre, then that bridge's slope until a line is flat again
         bool cmode = EK == CVX_ENERGY_NH_DAMAGE;
         const float sa = s_sa, cb = s_cb;
-        const NHPair npair = nh_pair_node(nl);
+        NHPair npair = nh_pair_node(nl);
+        npair.J0 = pk2(s_nl.J0, s_nl.J0);  // J(0) = det F of the node, every line
         float my_cJ = 0.0f;   // lane k keeps the k-th line of each run of 32 for the work count
         const float kap = s_pd.kappa_f, C = s_shift;
-        // damage energy with L = 128 nfull + 1: every 32 lines, lane k samples
-        // the right end of the k-th next line (and counts its valid samples),
-        // instead of the whole warp sampling one tail sample per line
+        // L = 128 nfull + 1: the one sample past the full chunks (the right
+        // end) is taken in the 32-line setup below, one lane per line
         const bool tail1 = EK == CVX_ENERGY_NH_DAMAGE && ln.nfull > 0 && ln.L == 128 * ln.nfull + 1;
         for (int sg = warp; sg < nseg; sg += nw) {
             const int jb = d0 + sg * seg, je = min(d1, jb + seg);
@@ -256,29 +257,30 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                     if (dd < je) {
                         const int gd2 = win ? window_dir(s_pd, cen, dd) : dd;
                         const DirLine d2 = make_dir_line<EK>(s_nl, P.dir32[doff + gd2]);
-                        if (tail1) s_tail[warp][lane] = sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32);
+                        const float tv =
+                            tail1 ? sample_w<EK>(nl, d2, (float)(ln.L - 1 - ln.m0) * ln.h32) : 0.0f;
                         s_dir[warp][lane][0] = make_float4(d2.A1, d2.A1, d2.A2, d2.A2);
-                        s_dir[warp][lane][1] = make_float4(d2.cJ, d2.cJ, d2.J0, d2.J0);
-                        s_slc[warp][lane] = sa * __fmaf_rn(cb, d2.cJ, d2.A1);
+                        s_dir[warp][lane][1] =
+                            make_float4(d2.cJ, d2.cJ, sa * __fmaf_rn(cb, d2.cJ, d2.A1), tv);
                         n_valid += valid_samples(d2, ln, EK);
                     }
                     __syncwarp();
                 }
                 DirLine dl;
                 NHPair c;
-                float sl;
+                float sl, tvr = 0.0f;
                 if (EK == CVX_ENERGY_NH_DAMAGE) {
                     const float4 q0 = s_dir[warp][r][0], q1 = s_dir[warp][r][1];
                     c = npair;
                     c.A1 = pk2(q0.x, q0.y);
                     c.A2 = pk2(q0.z, q0.w);
                     c.CJ = pk2(q1.x, q1.y);
-                    c.J0 = pk2(q1.z, q1.w);
                     dl.A1 = q0.x;
                     dl.A2 = q0.z;
                     dl.cJ = q1.x;
-                    dl.J0 = q1.z;
-                    sl = cmode ? s_slc[warp][r] : s_warm;
+                    dl.J0 = s_nl.J0;
+                    sl = cmode ? q1.z : s_warm;
+                    tvr = q1.w;
                 } else {
                     dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
                     sl = s_warm;
@@ -288,8 +290,7 @@ __global__ void __launch_bounds__(256, CVX_SCAN_MIN_BLOCKS) k_scan(const Pipe P,
                 // (any slope gives one; the damage-energy sampler leaves the centre
                 // out of the min, the test energy's keeps it, which only lowers qb)
                 const float e = EK == CVX_ENERGY_NH_DAMAGE
-                                    ? sample_line_min_nh(sw, nl, c, dl, ln, lane, tl, -sl, tail1,
-                                                         s_tail[warp][r])
+                                    ? sample_line_min_nh(sw, nl, c, dl, ln, lane, tl, -sl, tail1, tvr)
                                     : sample_line_min<EK>(sw, nl, dl, ln, lane, tl, -sl);
                 // (the damage-energy bound starts at +inf and its mins skip NaN,
                 // so it is never NaN: a float reduction gives the key order's min)
