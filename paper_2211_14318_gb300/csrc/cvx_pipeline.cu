@@ -242,6 +242,26 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
         // L = 128 nfull + 1: the one sample past the full chunks (the right
         // end) is taken in the 32-line setup below, one lane per line
         const bool tail1 = EK == CVX_ENERGY_NH_DAMAGE && ln.nfull > 0 && ln.L == 128 * ln.nfull + 1;
+        if (EK == CVX_ENERGY_NH_DAMAGE && d1 - d0 >= 64 * nw) {
+            // seed: one line per warp, spread over the item, searched outright,
+            // so that the item's smallest upper bound starts near the best value
+            // and the bound test drops more lines from the start (the seed lines
+            // are scanned again below)
+            const int span = (d1 - d0) / nw;
+            const int dj = d0 + warp * span + span / 2;
+            const int gd = win ? window_dir(s_pd, cen, dj) : dj;
+            const DirLine dl = make_dir_line<EK>(s_nl, P.dir32[doff + gd]);
+            NHPair c = npair;
+            c.A1 = pk2(dl.A1, dl.A1);
+            c.A2 = pk2(dl.A2, dl.A2);
+            c.CJ = pk2(dl.cJ, dl.cJ);
+            const float tv = tail1 ? sample_w<EK>(nl, dl, (float)(ln.L - 1 - ln.m0) * ln.h32) : 0.0f;
+            sample_line_min_nh(sw, nl, c, dl, ln, lane, tl, 0.0f, tail1, tv);
+            __syncwarp();
+            const ScreenOut o = warp_screen(sw, g, lane, -1, -1, hc);
+            if (o.a >= 0 && lane == 0) atomicMin(&s_ukey, f2key(o.q_hi));
+            __syncthreads();
+        }
         for (int sg = warp; sg < nseg; sg += nw) {
             const int jb = d0 + sg * seg, je = min(d1, jb + seg);
             if (EK == CVX_ENERGY_NH_DAMAGE) cmode = true;
