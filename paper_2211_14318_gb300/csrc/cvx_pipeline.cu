@@ -212,12 +212,12 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
         const int dpi = win ? s_pd.wdpi : s_pd.dpi;
         const int2 cen = s_c;
         const int d0 = ch * dpi, d1 = min(D, d0 + dpi);
-        // the item's directions in segments of up to 64 contiguous ones, dealt
+        // the item's directions in segments of up to 16 contiguous ones, dealt
         // to the warps in turn: the lines that need a hull search cluster
         // around the split direction, and this spreads them over the warps
         // (the first search of a segment starts far from its bridge; the
         // search runs until its pair is certified, kScreenRounds)
-        const int seg = max(1, min(64, (d1 - d0 + nw - 1) / nw));
+        const int seg = max(1, min(16, (d1 - d0 + nw - 1) / nw));
         const int nseg = (d1 - d0 + seg - 1) / seg;
 
         float tq[kWarpTop];
