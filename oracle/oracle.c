@@ -16,8 +16,8 @@
  *                  (lamination tree of Sec. 4.3 / Algorithm 2);
  *   - derivative:  Sec. 5.3, Eq. (5.2) and Algorithm 3.
  *
- * Readings of the paper (where it is silent or garbled) are listed in
- * the design doc; the ones used here are named at the point of use.
+ * Readings of the paper (where it is silent or garbled) are named at the
+ * point of use, each with the reading taken.
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off (no FMA contraction,
  * so x86_64 and aarch64 hosts give identical results).
