@@ -27,13 +27,13 @@
  *  - The library owns the handle's workspace (grown on demand with cudaMalloc)
  *    and its direction tables.  A handle may be used by one host thread at a
  *    time; work of one handle is serialised on the streams it is given.
- *  - Arithmetic: every line is first sampled in FP32 on the CUDA cores and its
- *    lower hull found exactly for those FP32 values (FP32 filter with an exact
- *    FP64 fallback).  That FP32 pass screens the directions: only those whose
- *    FP32 hull value lies within a tolerance of the best (several times the
- *    FP32 sampling error) are resampled in FP64, and the node's direction,
- *    split and value are decided on those FP64 samples.  Split points, W^R
- *    and P are evaluated in FP64.
+ *  - Arithmetic: every line is first sampled in FP32 on the CUDA cores, and
+ *    that pass bounds the value at t = 0 of its lower hull from below and
+ *    above (rigorously, for the FP32 samples).  It screens the directions:
+ *    only those whose lower bound lies within a tolerance of the best upper
+ *    bound (several times the FP32 sampling error) are resampled in FP64, and
+ *    the node's direction, split and value are decided on those FP64
+ *    samples.  Split points, W^R and P are evaluated in FP64.
  */
 #ifndef CONVEXIFY_H
 #define CONVEXIFY_H
@@ -228,7 +228,10 @@ int cvx_get_scan_timing(cvx_handle *h, double *ms, int64_t *launches, int reset)
 int cvx_struct_size(int which);
 
 /* Sets the launch shape of the line-scan kernel of convexify_points: warps per
- * CTA (1..8) and directions per work item (>= 1; 0 = automatic).
+ * CTA (1..8) and directions per work item (>= 1; 0 = automatic).  For the
+ * damage energy the line scan runs one line per lane (the environment
+ * variable CVX_SCAN_KERNEL=warp selects the warp-per-line scan instead); it
+ * ignores warps_per_cta and caps the directions per item at 256.
  * convexify_batch chooses its own (see cvx_get_batch_tuning). */
 int cvx_set_tuning(cvx_handle *h, int warps_per_cta, int dirs_per_item);
 
@@ -304,7 +307,9 @@ typedef struct cvx_problem {
  * batch call capture again. */
 int convexify_batch(cvx_handle *h, int n_problems, const cvx_problem *problems, cvx_stream s);
 
-/* The launch shape the autotuner chose for the last batch (0s before any). */
+/* The launch shape the autotuner chose for the last batch (0s before any):
+ * warps_per_cta 4 or 8 for the warp-per-line scan, 0 for the lane-per-line
+ * scan (damage energy); dirs_per_item_cap 0 = no cap. */
 int cvx_get_batch_tuning(cvx_handle *h, int *warps_per_cta, int *dirs_per_item_cap,
                          int *from_cache);
 

@@ -382,8 +382,13 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     pd.flags = p->flags;
     pd.K = p->depth;
     pd.NT = (1 << (p->depth + 1)) - 1;
-    pd.dpi = h->tune_dpi > 0 ? std::min(h->tune_dpi, pd.D)
-                             : dirs_per_item(n, pd.D, grid, warps, 0);
+    const bool lanes = lane_scan_enabled(p->energy);
+    if (lanes)
+        pd.dpi = lane_dirs_per_item(n, pd.D, (long long)h->sm_count * lane_scan_blocks_per_sm() * 8,
+                                    h->tune_dpi);
+    else
+        pd.dpi = h->tune_dpi > 0 ? std::min(h->tune_dpi, pd.D)
+                                 : dirs_per_item(n, pd.D, grid, warps, 0);
     pd.chunks = (pd.D + pd.dpi - 1) / pd.dpi;
     pd.point_off = 0;
     pd.n = n;
@@ -401,6 +406,7 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     pp.C = pd.chunks;
     pp.stride32 = pp.stride64 = pd.line.stride;
     pp.energy = p->energy;
+    pp.lanes = lanes ? 1 : 0;
     const size_t pipe_sz = align_up(pipe_bytes(pp.N, pp.K, pp.C, 1));
     const size_t tree_sz = tree ? 0 : sizeof(cvx_node) * (size_t)n * pd.NT;
     rc = ensure_ws(h, pipe_sz + tree_sz, s);

@@ -89,7 +89,8 @@ void load_tune_file(cvx_handle *h) {
     while (fgets(line, sizeof line, f)) {
         char key[3000];
         int w = 0, d = 0;
-        if (sscanf(line, " \"%2999[^\"]\": [%d, %d]", key, &w, &d) == 3 && w > 0)
+        // warps 0: the lane-per-line scan; 1..8: the warp-per-line scan
+        if (sscanf(line, " \"%2999[^\"]\": [%d, %d]", key, &w, &d) == 3 && w >= 0 && w <= 8)
             h->tune_cache[key] = {w, d};
     }
     fclose(f);
@@ -129,9 +130,14 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
         N += n_use[i];
     }
     const int energy = pr[0].params.energy;
-    const int bpsm = scan_max_blocks_per_sm(energy, warps, stride);
+    const int bpsm = scan_max_blocks_per_sm(energy, warps > 0 ? warps : 8, stride);
     if (bpsm < 1) return fail(CVX_ERR_UNSUPPORTED, "scan kernel cannot launch with %d warps", warps);
     lo.grid = h->sm_count * bpsm;
+    // warps == 0: the lane-per-line scan (damage energy)
+    const bool lanes = warps == 0;
+    if (lanes && !lane_scan_enabled(energy))
+        return fail(CVX_ERR_UNSUPPORTED, "lane-per-line scan not available for this energy");
+    const long long lane_warps = (long long)h->sm_count * lane_scan_blocks_per_sm() * 8;
     lo.table.assign(np, ProbDesc{});
     int C = 1;
     long long off = 0;
@@ -149,7 +155,8 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
         pd.flags = p.flags;
         pd.K = p.depth;
         pd.NT = (1 << (p.depth + 1)) - 1;
-        pd.dpi = dirs_per_item(N, pd.D, lo.grid, warps, dpi_cap);
+        pd.dpi = lanes ? lane_dirs_per_item(N, pd.D, lane_warps, dpi_cap)
+                       : dirs_per_item(N, pd.D, lo.grid, warps, dpi_cap);
         pd.chunks = (pd.D + pd.dpi - 1) / pd.dpi;
         C = std::max(C, pd.chunks);
         pd.point_off = off;
@@ -172,6 +179,7 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
     pp.C = C;
     pp.stride32 = pp.stride64 = stride;
     pp.energy = energy;
+    pp.lanes = lanes ? 1 : 0;
     const size_t pipe_sz = (pipe_bytes(N, K, C, np) + 255) & ~(size_t)255;
     int rc = ensure_ws(h, pipe_sz + tree_bytes, s);
     if (rc) return rc;
@@ -281,8 +289,17 @@ int convexify_batch(cvx_handle *h, int np, const cvx_problem *pr, cvx_stream sv)
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0), "autotune");
         CK(cudaEventCreate(&e1), "autotune");
-        for (int w : {4, 8}) {  // k_scan is compiled for at most 256 threads
-            for (int cap : {256, 1024, 0}) {
+        // launch shapes: the warp-per-line scan with 4 or 8 warps per CTA (it is
+        // compiled for at most 256 threads) and three item caps, and (damage
+        // energy) the lane-per-line scan (warps 0) with three item caps
+        std::vector<std::pair<int, int>> shapes;
+        for (int w : {4, 8})
+            for (int cap : {256, 1024, 0}) shapes.push_back({w, cap});
+        if (lane_scan_enabled(pr[0].params.energy))
+            for (int cap : {64, 128, 0}) shapes.push_back({0, cap});
+        for (const auto &sh : shapes) {
+            const int w = sh.first, cap = sh.second;
+            {
                 Layout lo;
                 int rc = build_layout(h, np, pr, n_s, dir_off, plan->d_dir32, plan->d_dir64, w,
                                       cap, s, lo);

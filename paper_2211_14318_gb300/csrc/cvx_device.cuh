@@ -235,6 +235,11 @@ __device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 // min of three FP32 values (a NaN operand is ignored, as by fminf)
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
     float d;
@@ -376,6 +381,17 @@ __device__ __forceinline__ f32x2 sample_nh2(const NHPair &c, f32x2 T) {
     return fma2(c.NK1, E, W);
 }
 
+// energy64 of the damage energy with the node's e_k = exp(-beta_k / D_0)
+// precomputed (the same operations on the same values: bit-identical).
+__device__ inline double energy64_ek(const double F[4], double beta_k, double ek,
+                                     const Material &m) {
+    double lj, J;
+    double s = psi0_nh64(F, m, &lj, &J);
+    if (!(J > 0.0)) return nan("");
+    if (s <= beta_k) return (1.0 - m.Dinf * (1.0 - ek)) * (s - beta_k);
+    return (1.0 - m.Dinf) * (s - beta_k) + m.Dinf * m.D0 * (ek - exp(-s / m.D0));
+}
+
 // FP64 sample of W along the line: G = F + t R with t = (m - m0) h and R, G
 // rounded exactly as the split points are (no contraction).
 __device__ __forceinline__ double sample_w64(const double F[4], const double R[4], int m, int m0,
@@ -384,6 +400,16 @@ __device__ __forceinline__ double sample_w64(const double F[4], const double R[4
     double G[4];
     for (int k = 0; k < 4; ++k) G[k] = __dadd_rn(F[k], __dmul_rn(t, R[k]));
     return energy64(G, beta_k, mat);
+}
+
+// sample_w64 of the damage energy with e_k precomputed (bit-identical).
+__device__ __forceinline__ double sample_w64_ek(const double F[4], const double R[4], int m, int m0,
+                                                double h, double beta_k, double ek,
+                                                const Material &mat) {
+    const double t = __dmul_rn((double)(m - m0), h);
+    double G[4];
+    for (int k = 0; k < 4; ++k) G[k] = __dadd_rn(F[k], __dmul_rn(t, R[k]));
+    return energy64_ek(G, beta_k, ek, mat);
 }
 
 }  // namespace cvx

@@ -13,6 +13,7 @@ namespace cvx {
 constexpr int kWarpTop = 4;    // best directions kept per warp
 constexpr int kItemTop = 8;    // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
+constexpr int kLaneItemMax = 256;  // directions per work item of the lane-per-line scan
 constexpr int kMaxDepth = 8;
 // Bound on the FP32 sampling error of v = kappa' W - C in sample units,
 // relative to max(kappa', |v| + C) (>= kappa' max(1, |W|)): 3.5 times the
@@ -31,6 +32,7 @@ __device__ __forceinline__ float eps32_at(float x, float kappa, float C) {
 struct ItemCands {
     float q[kItemTop];
     int dir[kItemTop];
+    int ab[kItemTop];  // FP32 bridge pair a | b << 16 of each kept direction, -1 if unknown
     float w0;       // FP32 centre sample
     float dropped;  // smallest q not kept
     float qhi_min;  // smallest upper bound over the item's directions
@@ -39,9 +41,14 @@ struct ItemCands {
 
 struct NodeCands {
     int dir[kNodeCand];
+    int ab[kNodeCand];  // FP32 bridge pair hint per candidate (as in ItemCands), -1 if unknown
     int n, flags;
     float qcut;  // smallest FP32 q of a direction not refined (sample units)
     float eps;   // FP32 error bound used at this node (sample units)
+    // node constants for the FP64 refinement, computed once per node
+    NodeLine nl;  // FP32 line constants (make_node_line)
+    double ek;    // exp(-beta_k / D_0)
+    double shift; // sample shift C in FP64 (line_shift)
 };
 
 struct RefineOut {
@@ -127,6 +134,9 @@ struct Pipe {
     unsigned long long *fitem_ctr;
     int2 *center;                         // proposed window centre per queued node
     double *e_pred;                       // energy of the proposed laminate per queued node
+    // lane-per-line scan (damage energy): 1 selects it for this run's levels
+    int lanes;
+    int *node_u;                          // per queued node: smallest FP32 upper bound (f2key)
 };
 
 // Bytes of the workspace part that depends on the shape (see pipe_layout).
@@ -144,6 +154,27 @@ cudaError_t pipe_end(const Pipe &p, cudaStream_t s);
 // The Pipe that runs the full scan over the nodes a window pass deferred.
 Pipe fallback_pipe(const Pipe &p, int level);
 int scan_max_blocks_per_sm(int energy, int warps, int stride);
+// Lane-per-line scan (cvx_scan_lanes.cu): whether it serves this energy (the
+// damage energy, unless the environment variable CVX_SCAN_KERNEL is "warp"),
+// its resident CTAs per SM, and its launch (node-bound reset included).
+bool lane_scan_enabled(int energy);
+int lane_scan_blocks_per_sm();
+cudaError_t launch_scan_lanes(const Pipe &p, int level, int sms, cudaStream_t s);
+// Directions per work item of the lane-per-line scan: whole nodes up to
+// kLaneItemMax directions, smaller items (multiples of 32) when the nodes are
+// too few for every warp of the grid to get two items.
+inline int lane_dirs_per_item(long long n_nodes, int D, long long total_warps, int cap) {
+    int dpi = D < kLaneItemMax ? D : kLaneItemMax;
+    if (cap > 0 && cap < dpi) dpi = cap;
+    const long long want = total_warps * 2;
+    if (n_nodes * ((D + dpi - 1) / dpi) < want) {
+        const long long chunks = (want + n_nodes - 1) / n_nodes;
+        long long d = (D + chunks - 1) / chunks;
+        d = (d + 31) / 32 * 32;
+        if (d < dpi) dpi = (int)d;
+    }
+    return dpi < D ? dpi : D;
+}
 
 // single steps
 cudaError_t launch_energy(int64_t n, const double *F, const double *beta, double *W, double *P,

@@ -68,9 +68,15 @@ __global__ void __launch_bounds__(128) k_sample_lines(int64_t n, const double *F
     double G[4] = {F[4 * line], F[4 * line + 1], F[4 * line + 2], F[4 * line + 3]};
     const NodeLine nl = make_node_line(G, beta[line], m);
     const DirLine dl = make_dir_line<EK>(nl, dir32[dj]);
-    float tl[4];
-    for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
-    sample_line<EK>(sw, nl, dl, ln, lane, tl);
+    if (EK == CVX_ENERGY_NH_DAMAGE) {
+        // the lane-per-line scan's samples: t = fl((m - m0) h)
+        for (int k = lane; k < ln.L; k += 32)
+            sw[k] = sample_w<EK>(nl, dl, __fmul_rn((float)(k - ln.m0), ln.h32));
+    } else {
+        float tl[4];
+        for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - ln.m0) * ln.h32;
+        sample_line<EK>(sw, nl, dl, ln, lane, tl);
+    }
     __syncwarp();
     const double kap = line_kappa(m), shift = line_shift(m, beta[line]);
     for (int k = lane; k < ln.L; k += 32)

@@ -20,6 +20,7 @@
 
 namespace cvx {
 int set_error_message(int code, const char *msg);  // cvx_api.cu
+int check_params(const cvx_params *p, bool need_line);  // cvx_api.cu
 }
 
 using namespace cvx;
@@ -73,25 +74,16 @@ int setup(int dev, void **addr, int *sms) {
 extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const double *F,
                                        const double *beta_k, double *W_R, double *P,
                                        int32_t *status, cvx_stream sv) {
-    if (!p) return err(CVX_ERR_INVALID_ARG, "params is NULL");
-    if (p->energy != CVX_ENERGY_NH_DAMAGE && p->energy != CVX_ENERGY_DOUBLE_WELL)
-        return err(CVX_ERR_INVALID_ARG, "unknown energy kind");
-    if (p->energy == CVX_ENERGY_NH_DAMAGE &&
-        (!(p->mu > 0.0) || !(p->lambda_L >= 0.0) || !(p->D_inf >= 0.0 && p->D_inf < 1.0) ||
-         !(p->D0 > 0.0)))
-        return err(CVX_ERR_INVALID_ARG, "material out of range");
-    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED))
-        return err(CVX_ERR_INVALID_ARG, "unknown flags");
-    if (p->line_points < 3 || p->line_points > 2079 || (p->line_points % 2) == 0)
-        return err(CVX_ERR_INVALID_ARG, "line_points must be odd in [3, 2079]");
-    if (!(p->t_half > 0.0) || !isfinite(p->t_half)) return err(CVX_ERR_INVALID_ARG, "t_half must be positive");
-    if (p->depth < 0 || p->depth > 8) return err(CVX_ERR_INVALID_ARG, "depth must be in [0, 8]");
-    const int D = p->dirs ? p->n_dirs : p->n_theta_a * p->n_theta_b;
-    if ((p->dirs && p->n_dirs < 1) || (!p->dirs && (p->n_theta_a < 1 || p->n_theta_b < 1)))
-        return err(CVX_ERR_INVALID_ARG, "empty direction set");
-    if (D > kStaticMaxDirs)
+    // the same parameter checks as convexify_points (material, flags, line,
+    // depth, direction count in [1, 2^20] computed in 64 bits), then the
+    // static limit
+    int rc = check_params(p, true);
+    if (rc) return rc;
+    const int64_t D64 = p->dirs ? (int64_t)p->n_dirs : (int64_t)p->n_theta_a * p->n_theta_b;
+    if (D64 < 1 || D64 > kStaticMaxDirs)
         return err(CVX_ERR_INVALID_ARG,
                    "convexify_points_static: more than 16384 directions (use convexify_points)");
+    const int D = (int)D64;
     if (n < 0) return err(CVX_ERR_INVALID_ARG, "n < 0");
     if (n > 0 && (!F || !beta_k || !W_R || !P || !status))
         return err(CVX_ERR_INVALID_ARG, "NULL array (F, beta_k, W_R, P, status are required)");
@@ -113,19 +105,24 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
     if (cudaGetDevice(&dev) != cudaSuccess) return err(CVX_ERR_CUDA, "no current device");
     void *base = nullptr;
     int sms = 0;
-    int rc = setup(dev, &base, &sms);
+    rc = setup(dev, &base, &sms);
     if (rc) return rc;
     const int bpsm = scan_max_blocks_per_sm(p->energy, warps, ln.stride);
     if (bpsm < 1) return err(CVX_ERR_UNSUPPORTED, "scan kernel cannot launch");
     const int grid = sms * bpsm;
+    const bool lanes = lane_scan_enabled(p->energy);
     int dpi = D;
-    const int64_t want_items = (int64_t)grid * 4;
-    if (n < want_items) {
-        const int64_t chunks = (want_items + n - 1) / n;
-        const int64_t d = (D + chunks - 1) / chunks;
-        dpi = (int)(d > warps * 2 ? d : warps * 2);
+    if (lanes) {
+        dpi = lane_dirs_per_item(n, D, (long long)sms * lane_scan_blocks_per_sm() * 8, 0);
+    } else {
+        const int64_t want_items = (int64_t)grid * 4;
+        if (n < want_items) {
+            const int64_t chunks = (want_items + n - 1) / n;
+            const int64_t d = (D + chunks - 1) / chunks;
+            dpi = (int)(d > warps * 2 ? d : warps * 2);
+        }
+        if (dpi > D) dpi = D;
     }
-    if (dpi > D) dpi = D;
     const int chunks = (D + dpi - 1) / dpi;
 
     // scratch layout: counters, direction tables, tree, then the pipeline's
@@ -198,6 +195,7 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
     pp.C = chunks;
     pp.stride32 = pp.stride64 = ln.stride;
     pp.energy = p->energy;
+    pp.lanes = lanes ? 1 : 0;
     pipe_layout(pp, ws + o_pipe);
     pp.dir32 = (const float4 *)(ws + o_d32);
     pp.dir64 = (const double *)(ws + o_d64);

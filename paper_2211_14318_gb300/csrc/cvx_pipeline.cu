@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
                 if (bk < 0) break;
                 r.q[n] = s_q[bk][taken[bk]];
                 r.dir[n] = s_d[bk][taken[bk]];
+                r.ab[n] = -1;
                 ++taken[bk];
             }
             for (int k = 0; k < nw; ++k)
@@ -418,6 +419,7 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
             for (int i = n; i < kItemTop; ++i) {
                 r.q[i] = INFINITY;
                 r.dir[i] = -1;
+                r.ab[i] = -1;
             }
             r.n = n;
             r.w0 = s_w0;
@@ -515,7 +517,8 @@ __global__ void k_select(const Pipe P, int level) {
                 qcut = fminf(qcut, q);
                 break;
             }
-            nc.dir[nc.n++] = r[bc].dir[pos[bc]];
+            nc.dir[nc.n] = r[bc].dir[pos[bc]];
+            nc.ab[nc.n++] = r[bc].ab[pos[bc]];
             ++pos[bc];
         }
         for (int c = nch; c < chunks; ++c) qcut = fminf(qcut, r[c].q[0]);
@@ -525,6 +528,15 @@ __global__ void k_select(const Pipe P, int level) {
     nc.qcut = qcut;
     nc.eps = qcut < INFINITY ? eps32_at(qcut, kap, shift) : 0.0f;
     nc.flags = fl;
+    if (nc.n) {
+        // node constants of the FP64 refinement, once per node
+        const cvx_node *nd = node_ptr(pd, P.qp[level][qi], P.qh[level][qi]);
+        const double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
+        const double beta = pd.beta[P.qp[level][qi] - pd.point_off];
+        nc.nl = make_node_line(F, beta, pd.mat);
+        nc.ek = exp(-beta / pd.mat.D0);
+        nc.shift = line_shift(pd.mat, beta);
+    }
     P.cands[qi] = nc;
     if (nc.n) {
         const int pos = atomicAdd(P.cnt + (P.K + 1) + level, nc.n);
@@ -607,6 +619,119 @@ __device__ bool window_bridge64(double vA, double vB, int kA, int kB, int m0, in
     return false;
 }
 
+// Half-warp minimum with the sample index (lanes 0-15 and 16-31 reduce
+// separately); ties to the lower index if prefer_low, else to the higher.
+__device__ __forceinline__ void half_min_dk(double &v, int &k, bool prefer_low) {
+#pragma unroll
+    for (int o = 8; o; o >>= 1) {
+        const double v2 = __shfl_xor_sync(kFull, v, o);
+        const int k2 = __shfl_xor_sync(kFull, k, o);
+        if (v2 < v || (v2 == v && (prefer_low ? k2 < k : k2 > k))) {
+            v = v2;
+            k = k2;
+        }
+    }
+}
+
+// FP64 bridge from the line scan's FP32 pair (a, b) (damage energy): the
+// supporting-slope iteration over FP64 samples in two windows around a and
+// b (16 samples each, one per lane, for L <= 513; 32 each, two per lane,
+// above), then a certificate over the whole line that every sample outside
+// the windows lies strictly above the FP64 chord: its FP32 sample, computed
+// on the fly, less the FP32 error bound kEps32 max(kappa', |v| + C) and the
+// rounding bound of the chord evaluated in FP32 sample units, lies above
+// the chord.  Samples whose FP32 value is not finite (near det = 0) are
+// checked in FP64.  Returns false where the windows' pair does not settle
+// or the certificate fails (the caller resamples the whole line in FP64).
+__device__ bool refine_hinted(const double F[4], const double R[4], double beta, const NodeCands &nc,
+                              const ProbDesc &pd, float4 d32, int hab, int lane, int &a, int &b,
+                              double &wa, double &wb) {
+    const LineSpec ln = pd.line;
+    const int m0 = ln.m0, L = ln.L;
+    const double ek = nc.ek;
+    a = hab & 0xffff;
+    b = hab >> 16;
+    if (!(a >= 0 && a < m0 && b > m0 && b < L)) return false;
+    const bool narrow = L <= 513;
+    const int W = narrow ? 16 : 32;
+    const int loA = max(0, min(a - W / 2, m0 - W));
+    const int loB = max(m0 + 1, min(b - (W / 2 - 1), L - W));
+    // window samples: narrow, lane l < 16 holds left loA + l and lane l >= 16
+    // right loB + l - 16; wide, every lane holds left loA + l and right loB + l
+    const int kA = narrow ? loA + (lane & 15) : loA + lane;
+    const int kB = narrow ? loB + (lane & 15) : loB + lane;
+    const bool hasA = narrow ? lane < 16 : true, hasB = narrow ? lane >= 16 : true;
+    double vA = INFINITY, vB = INFINITY;
+    if (hasA && kA < m0) {
+        const double v = sample_w64_ek(F, R, kA, m0, ln.h64, beta, ek, pd.mat);
+        vA = v == v ? v : INFINITY;
+    }
+    if (hasB && kB < L) {
+        const double v = sample_w64_ek(F, R, kB, m0, ln.h64, beta, ek, pd.mat);
+        vB = v == v ? v : INFINITY;
+    }
+    auto valA = [&](int k) { return __shfl_sync(kFull, vA, narrow ? k - loA : k - loA); };
+    auto valB = [&](int k) { return __shfl_sync(kFull, vB, narrow ? 16 + k - loB : k - loB); };
+    wa = valA(a);
+    wb = valB(b);
+    if (!(wa < INFINITY && wb < INFINITY)) return false;
+    bool settled = false;
+    for (int it = 0; it < 64 && !settled; ++it) {
+        const double s = (wb - wa) / (double)(b - a);
+        int na, nb;
+        if (narrow) {
+            const bool left = lane < 16;
+            const double v = left ? vA : vB;
+            const int k = left ? kA : kB;
+            double e = v < INFINITY ? v - s * (double)(k - m0) : INFINITY;
+            int kk = v < INFINITY ? k : (left ? INT_MAX : -1);
+            half_min_dk(e, kk, left);
+            na = __shfl_sync(kFull, kk, 0);
+            nb = __shfl_sync(kFull, kk, 16);
+        } else {
+            double eA = vA < INFINITY ? vA - s * (double)(kA - m0) : INFINITY;
+            double eB = vB < INFINITY ? vB - s * (double)(kB - m0) : INFINITY;
+            int ka = vA < INFINITY ? kA : INT_MAX, kb = vB < INFINITY ? kB : -1;
+            warp_min_dk(eA, ka, true);
+            warp_min_dk(eB, kb, false);
+            na = ka;
+            nb = kb;
+        }
+        if (na == INT_MAX || nb < 0) return false;
+        settled = na == a && nb == b;
+        a = na;
+        b = nb;
+        wa = valA(a);
+        wb = valB(b);
+    }
+    if (!settled) return false;
+    // certificate over the samples outside the windows and the centre
+    const double s = (wb - wa) / (double)(b - a);
+    const double kap = pd.kappa, C = nc.shift;
+    const float la = (float)(kap * wa - C), ls = (float)(kap * s);
+    const float kapf = pd.kappa_f, Cf = (float)C;
+    const DirLine dl = make_dir_line<CVX_ENERGY_NH_DAMAGE>(nc.nl, d32);
+    const int hiA = min(loA + W, m0), hiB = min(loB + W, L);
+    bool good = true;
+    for (int k = lane; k < L && good; k += 32) {
+        if (k == m0 || (k >= loA && k < hiA) || (k >= loB && k < hiB)) continue;
+        const float v32 =
+            sample_w<CVX_ENERGY_NH_DAMAGE>(nc.nl, dl, __fmul_rn((float)(k - m0), ln.h32));
+        if (v32 < INFINITY && v32 > -INFINITY) {
+            const float x = (float)(k - a);
+            const float Lv = __fmaf_rn(ls, x, la);
+            const float err = 2.0f * kU32 * (fabsf(la) + fabsf(ls * x) + fabsf(Lv)) +
+                              kEps32 * fmaxf(kapf, fabsf(v32) + Cf) + 1e-30f;
+            good = __fsub_rn(v32, Lv) > 1.001f * err;
+        } else {
+            const double v = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
+            const double line = wa + s * (double)(k - a);
+            good = !(v == v) || v > line + 1e-14 * fabs(line);
+        }
+    }
+    return __all_sync(kFull, good);
+}
+
 // k_refine: one warp per screened (node, direction).  The FP64 bridge of the
 // left and right sample sets is searched in two 32-sample FP64 windows around
 // the FP32 bridge and certified against the whole line with the FP32 samples:
@@ -644,8 +769,45 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
                              __dmul_rn(d[1], d[3])};
         const double beta = pd.beta[p - pd.point_off];
+        const int hab = P.cands[qi].ab[c];
+        if (EK == CVX_ENERGY_NH_DAMAGE && hab >= 0) {
+            // the scan's FP32 pair as the start, windows in FP64, FP32 certificate
+            int a, b;
+            double wa = 0.0, wb = 0.0;
+            bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, P.dir32[pd.dir_off + dir], hab,
+                                    lane, a, b, wa, wb);
+            if (!ok) {
+                ++n_full;
+                const double ek = P.cands[qi].ek;
+                for (int k = lane; k < ln.L; k += 32)
+                    sw[k] = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
+                __syncwarp();
+                bridge64(sw, ln.L, m0, lane, a, b);
+                if (a >= 0) {
+                    wa = sw[a];
+                    wb = sw[b];
+                }
+            }
+            if (lane == 0) {
+                RefineOut o;
+                o.a = a;
+                o.b = b;
+                o.pad = 0;
+                if (a >= 0) {
+                    const double xa = (double)(a - m0), xb = (double)(b - m0);
+                    o.q = (xb * wa - xa * wb) / (xb - xa);
+                    o.ok = 1;
+                } else {
+                    o.q = INFINITY;
+                    o.ok = 0;
+                }
+                P.refined[(long long)qi * kNodeCand + c] = o;
+            }
+            __syncwarp();
+            continue;
+        }
         // FP32 line and its approximate bridge
-        const NodeLine nl = make_node_line(F, beta, pd.mat);
+        const NodeLine nl = P.cands[qi].nl;
         const DirLine dl = make_dir_line<EK>(nl, P.dir32[pd.dir_off + dir]);
         float tl[4];
 #pragma unroll
@@ -680,7 +842,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         if (ok) {
             // certificate over the samples outside the windows
             const double s = (wb - wa) / (double)(b - a);
-            const double kap = pd.kappa, shift = line_shift(pd.mat, beta);
+            const double kap = pd.kappa, shift = P.cands[qi].shift;
             bool good = true;
             for (int k = lane; k < ln.L && good; k += 32) {
                 if (k == m0 || (k >= loA && k < loA + 32 && k < m0) || (k >= loB && k < loB + 32))
@@ -945,6 +1107,7 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
     const size_t o_cands = take(sizeof(NodeCands) * maxq);
     const size_t o_work = take(sizeof(int2) * maxq * kNodeCand);
     const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
+    const size_t o_nu = take(sizeof(int) * maxq);
     size_t o_fqp[kMaxDepth], o_fqh[kMaxDepth], o_fcnt = 0, o_fictr = 0, o_cen = 0, o_ep = 0;
     if (window) {
         for (int l = 0; l < K; ++l) {
@@ -970,6 +1133,7 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         p.cands = (NodeCands *)(ws + o_cands);
         p.work = (int2 *)(ws + o_work);
         p.refined = (RefineOut *)(ws + o_ref);
+        p.node_u = (int *)(ws + o_nu);
         p.ncnt = p.cnt;
         p.pass = window ? PASS_WINDOW : PASS_FULL;
         for (int l = 0; l < kMaxDepth; ++l) {
@@ -1037,9 +1201,18 @@ cudaError_t pipe_level(const Pipe &p, int l, int warps, int grid, cudaStream_t s
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long max_nodes = p.N << l;
+    if (p.lanes) {
+        // the node bounds start at +inf (a huge finite key); reset outside the timed region
+        if ((e = cudaMemsetAsync(p.node_u, 0x7f, sizeof(int) * (size_t)max_nodes, s)) != cudaSuccess)
+            return e;
+    }
     if (ev && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) return e;
-    e = p.energy == CVX_ENERGY_NH_DAMAGE ? launch_scan_t<CVX_ENERGY_NH_DAMAGE>(p, l, warps, grid, s)
-                                         : launch_scan_t<CVX_ENERGY_DOUBLE_WELL>(p, l, warps, grid, s);
+    if (p.lanes)
+        e = launch_scan_lanes(p, l, sms, s);
+    else
+        e = p.energy == CVX_ENERGY_NH_DAMAGE
+                ? launch_scan_t<CVX_ENERGY_NH_DAMAGE>(p, l, warps, grid, s)
+                : launch_scan_t<CVX_ENERGY_DOUBLE_WELL>(p, l, warps, grid, s);
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
     const unsigned nb = (unsigned)((max_nodes + 127) / 128);

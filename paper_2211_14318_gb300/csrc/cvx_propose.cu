@@ -202,13 +202,17 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     pd.flags = p->flags;
     pd.K = p->depth;
     pd.NT = (1 << (p->depth + 1)) - 1;
-    pd.dpi = dirs_per_item(n, pd.D, grid, warps, 0);
+    const bool lanes = lane_scan_enabled(p->energy);
+    const long long lane_warps = (long long)h->sm_count * lane_scan_blocks_per_sm() * 8;
+    pd.dpi = lanes ? lane_dirs_per_item(n, pd.D, lane_warps, 0)
+                   : dirs_per_item(n, pd.D, grid, warps, 0);
     pd.chunks = (pd.D + pd.dpi - 1) / pd.dpi;
     pd.window = window;
     pd.Na = p->n_theta_a;
     pd.Nb = p->n_theta_b;
     pd.wD = (2 * window + 1) * (2 * window + 1);
-    pd.wdpi = dirs_per_item(n, pd.wD, grid, warps, 0);
+    pd.wdpi = lanes ? lane_dirs_per_item(n, pd.wD, lane_warps, 0)
+                    : dirs_per_item(n, pd.wD, grid, warps, 0);
     pd.wchunks = (pd.wD + pd.wdpi - 1) / pd.wdpi;
     pd.gap_tol = gap_tol;
     pd.point_off = 0;
@@ -228,6 +232,7 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     pp.stride32 = pp.stride64 = pd.line.stride;
     pp.energy = p->energy;
     pp.window = 1;
+    pp.lanes = lanes ? 1 : 0;
     const size_t pipe_sz = up256(pipe_bytes(pp.N, pp.K, pp.C, 1, true));
     const size_t tree_sz = tree ? 0 : sizeof(cvx_node) * (size_t)n * pd.NT;
     rc = ensure_ws(h, pipe_sz + tree_sz, s);

@@ -1,0 +1,120 @@
+"""Writes the oracle-only expected values of the full-size parity tests.
+
+Every value stored here comes from the FP64 CPU oracle (``oracle/``) run on
+seeded inputs from ``paper_2211_14318_gb300.inputs``; nothing is read from the
+CUDA path.  Each file holds a fixed subsample of 4,096 points of one workload:
+the inputs themselves (F, beta_k, so that the GPU side convexifies exactly the
+same numbers on any host), and the oracle's W^R, P, status and lamination
+tree (per node: flags, decision margin, direction, bridge indices, F).
+
+Workloads (the sizes the benchmark runs, subsampled evenly):
+
+* ``mesh128``: 128 x 128 Q1 mesh x 4 Gauss points (65,536 points), stretch
+  1.3, seed 0, history from the previous load step (0.9 x the displacement);
+  64 x 64 angles, L = 1025, t in [-0.5, 0.5], depth 3.
+* ``material1m_l201``: 1,048,576 material points (F = Q diag(lam, lam^-0.3)
+  Q^T + N(0, 0.02^2), lam ~ U[1, 2], seed 201, history from one prior step);
+  16 x 16 angles, L = 201, t in [-0.5, 0.5], depth 2.
+* ``loadpath512_sKK``: 512 x 512 Q1 mesh x 4 Gauss points (1,048,576
+  points), load path stretch 1.0 -> 1.8 in 20 steps (seed 7), load step KK
+  in {1, 10, 20} with the history of the earlier steps (Eq. 2.5);
+  128 x 128 angles, L = 2049, t in [-0.5, 0.5], depth 3.
+
+Usage: python tests/golden/make_goldens.py [--only NAME ...] [--threads N]
+The load-path files take hours of CPU time (the oracle is plain FP64 C).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_2211_14318_gb300 import inputs  # noqa: E402
+
+N_SUB = 4096
+MAT = dict(mu=1.0, lam=5.0, Dinf=0.99, D0=0.5)
+LOAD_STEPS = (1, 10, 20)
+
+
+def subsample(n: int) -> np.ndarray:
+    return np.linspace(0, n - 1, N_SUB).astype(np.int64)
+
+
+def workloads():
+    """name -> (description, angles, L, t_half, depth, thunk returning (idx, F, beta))."""
+    mat = oracle.Material(**MAT)
+    out = {}
+
+    def mesh128():
+        F, Fp = inputs.mesh_points(128, stretch=1.3, seed=0)
+        idx = subsample(F.shape[0])
+        return idx, F[idx], oracle.history_update(mat, Fp[idx])
+
+    out["mesh128"] = ("128x128 Q1 mesh x 4 Gauss points, stretch 1.3, seed 0", 64, 1025, 0.5, 3,
+                      mesh128)
+
+    def material():
+        F, Fp = inputs.surrogate_inputs(1 << 20, seed=201)
+        idx = subsample(F.shape[0])
+        return idx, F[idx], oracle.history_update(mat, Fp[idx])
+
+    out["material1m_l201"] = ("1,048,576 material points, lam ~ U[1, 2], seed 201", 16, 201, 0.5,
+                              2, material)
+
+    for k in LOAD_STEPS:
+        def lp(k=k):
+            path = inputs.load_path(512, n_steps=20, stretch_end=1.8, seed=7)
+            idx = subsample(path[0].shape[0])
+            beta = np.zeros(N_SUB)
+            for j in range(k - 1):  # history of the earlier load steps
+                beta = oracle.history_update(mat, path[j][idx], beta)
+            return idx, path[k - 1][idx], beta
+
+        out[f"loadpath512_s{k:02d}"] = (
+            f"512x512 Q1 mesh x 4 Gauss points, load path 1.0 -> 1.8 in 20 steps (seed 7), step {k}",
+            128, 2049, 0.5, 3, lp)
+    return out
+
+
+def write(name, desc, na, L, t_half, depth, thunk, threads):
+    mat = oracle.Material(**MAT)
+    idx, F, beta = thunk()
+    sc = oracle.Scan(oracle.angle_directions(na, na), L, t_half, depth)
+    t0 = time.perf_counter()
+    WR, P, tree, st = oracle.convexify(mat, sc, F, beta, nthreads=threads)
+    dt = time.perf_counter() - t0
+    meta = dict(workload=desc, angles=[na, na], line_points=L, t_half=t_half, depth=depth,
+                material=MAT, points=N_SUB, oracle_seconds=dt, threads=threads)
+    path = os.path.join(HERE, f"{name}.npz")
+    np.savez_compressed(
+        path, meta=np.array(json.dumps(meta)), idx=idx, F=F, beta=beta, W_R=WR, P=P, status=st,
+        flags=tree["flags"].astype(np.int8), margin=tree["margin"], dir=tree["dir"].astype(np.int16),
+        m_minus=tree["m_minus"].astype(np.int16), m_plus=tree["m_plus"].astype(np.int16),
+        node_F=tree["F"])
+    print(f"{name}: {N_SUB} points in {dt:.0f} s -> {path}", flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", nargs="*", default=None)
+    ap.add_argument("--threads", type=int, default=0)
+    a = ap.parse_args()
+    oracle.build()
+    for name, (desc, na, L, t_half, depth, thunk) in workloads().items():
+        if a.only and name not in a.only:
+            continue
+        write(name, desc, na, L, t_half, depth, thunk, a.threads or oracle.cores())
+
+
+if __name__ == "__main__":
+    main()

@@ -148,3 +148,17 @@ def test_binding_refuses_cpu_fallback():
         pytest.skip("a GPU is present")
     with pytest.raises(api.CvxError):
         api.Convexifier(0)
+
+
+@pytest.mark.parametrize("na,nb,msg", [
+    (65536, 65536, "angle grid"),   # 2^32 directions: wraps to 0 in 32-bit arithmetic
+    (46341, 46341, "angle grid"),   # wraps to a negative count in 32-bit arithmetic
+    (200, 200, "16384"),            # valid grid, above the static limit
+])
+def test_static_entry_rejects_direction_counts_before_cuda(cvxlib, na, nb, msg):
+    from paper_2211_14318_gb300 import api
+
+    c = api.Params(n_theta_a=na, n_theta_b=nb, line_points=201, depth=2).c()
+    rc = cvxlib.convexify_points_static(ctypes.byref(c), 4, None, None, None, None, None, None)
+    assert rc == -1
+    assert msg in _err(cvxlib)

@@ -1,0 +1,175 @@
+"""GPU parity at full size against stored oracle results.
+
+tests/golden/*.npz hold, for a fixed subsample of 4,096 points of each
+benchmark workload, the inputs (F, beta_k) and the FP64 oracle's W^R, P,
+status and lamination tree, written by tests/golden/make_goldens.py (which
+calls only oracle/).  Here the CUDA path convexifies the whole workload in
+the launch configuration the benchmark uses -- all 1,048,576 material points,
+all 65,536 mesh points -- with the stored inputs placed at the subsample's
+rows, and the subsample is compared element by element:
+
+* on every node whose oracle decision margin exceeds TIE (a perturbation of
+  the FP64 samples smaller than that cannot change it): the split decision,
+  the direction and bridge indices bit-exact and the children's F bit-exact;
+* on every point whose nodes are all untied: W^R within 1e-6 relative and P
+  within 1e-5 relative (gamma = 1e-8, the paper's error measure of Sec. 6.2);
+* on tied points: W^R equals the oracle's energy summed over the GPU's own
+  tree leaves (the GPU's laminate is a valid one).
+
+The load-path workload (128 x 128 angles, L = 2049, depth 3) runs the full
+scan on the 4,096 subsample points at three load steps, as the benchmark's
+accuracy check does.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-11
+MAT = dict(mu=1.0, lambda_L=5.0, D_inf=0.99, D0=0.5)
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def cv():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api
+
+    c = api.Convexifier(0)
+    yield c
+    c.close()
+
+
+def load(name):
+    g = dict(np.load(os.path.join(HERE, "golden", f"{name}.npz")))
+    g["meta"] = json.loads(str(g["meta"]))
+    return g
+
+
+def params(g):
+    from paper_2211_14318_gb300 import api
+
+    m = g["meta"]
+    return api.Params(n_theta_a=m["angles"][0], n_theta_b=m["angles"][1],
+                      line_points=m["line_points"], t_half=m["t_half"], depth=m["depth"], **MAT)
+
+
+def compare(orc, api, g, WR, P, st, tree):
+    """Element-by-element comparison of the subsample; returns (untied
+    fraction, compared nodes)."""
+    n = g["F"].shape[0]
+    SC, LM = orc.SCANNED, orc.LAMINATED
+    assert np.all((st & api.PT_NONPOS_DET) == (g["status"] & 1))
+    untied = np.ones(n, dtype=bool)
+    compared = 0
+    for p in range(n):
+        stack = [0]
+        while stack:
+            i = stack.pop()
+            fo = int(g["flags"][p, i])
+            if not fo & SC:
+                continue
+            if g["margin"][p, i] <= TIE:
+                untied[p] = False
+                continue
+            compared += 1
+            t = tree[p, i]
+            assert t["flags"] & api.NODE_SCANNED, (p, i)
+            lam = bool(fo & LM)
+            assert bool(t["flags"] & api.NODE_LAMINATED) == lam, (p, i)
+            if lam:
+                assert (t["dir"], t["m_minus"], t["m_plus"]) == (
+                    int(g["dir"][p, i]), int(g["m_minus"][p, i]), int(g["m_plus"][p, i])), (p, i)
+                for c in (2 * i + 1, 2 * i + 2):
+                    np.testing.assert_array_equal(tree[p, c]["F"], g["node_F"][p, c])
+                stack += [2 * i + 1, 2 * i + 2]
+    u = untied
+    rel = np.abs(WR[u] - g["W_R"][u]) / (1e-8 + np.abs(g["W_R"][u]))
+    assert rel.max(initial=0) < 1e-6, rel.max()
+    Pn = np.linalg.norm(g["P"][u], axis=1)
+    assert np.max(np.linalg.norm(P[u] - g["P"][u], axis=1) / (1e-8 + Pn), initial=0) < 1e-5
+    mat = orc.Material(MAT["mu"], MAT["lambda_L"], MAT["D_inf"], MAT["D0"])
+    for p in np.nonzero(~u)[0]:
+        tr = tree[p]
+        leaf = (tr["flags"] & api.NODE_EXISTS > 0) & (tr["flags"] & api.NODE_LAMINATED == 0)
+        Wl = sum(tr[i]["weight"] * orc.energy(mat, tr[i]["F"], g["beta"][p])
+                 for i in np.nonzero(leaf)[0])
+        assert abs(WR[p] - Wl) <= 1e-11 * (1 + abs(Wl)), p
+    return u.mean(), compared
+
+
+def run_full(cv, g, F_all, beta_all):
+    """The whole workload with the stored inputs at the subsample's rows;
+    returns the subsample's outputs and tree."""
+    import torch
+
+    from paper_2211_14318_gb300 import api
+
+    p = params(g)
+    idx = g["idx"]
+    F_all = F_all.copy()
+    beta_all = beta_all.copy()
+    F_all[idx] = g["F"]
+    beta_all[idx] = g["beta"]
+    out = cv.convexify_points(p, F_all, beta_all, want_tree=True)
+    n = F_all.shape[0]
+    it = torch.from_numpy(idx).to(out["W_R"].device)
+    tr = out["tree"].view(n, -1)[it]
+    tree = api.tree_numpy(tr.reshape(-1), len(idx), p.tree_size)
+    return (out["W_R"][it].cpu().numpy(), out["P"][it].cpu().numpy(),
+            out["status"][it].cpu().numpy(), tree)
+
+
+def test_golden_material_points_1m_l201(cv, orc):
+    """1,048,576 material points, 16 x 16 angles, L = 201, depth 2: the
+    spec resolution; 4,096 points against the oracle."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    g = load("material1m_l201")
+    F, Fp = inputs.surrogate_inputs(1 << 20, seed=201)
+    beta = cv.history_update(params(g), Fp).cpu().numpy()
+    WR, P, st, tree = run_full(cv, g, F, beta)
+    frac, compared = compare(orc, api, g, WR, P, st, tree)
+    assert frac >= 0.95 and compared >= 4096
+
+
+def test_golden_mesh128(cv, orc):
+    """128 x 128 Q1 mesh x 4 Gauss points (65,536 points), 64 x 64 angles,
+    L = 1025, depth 3; 4,096 points against the oracle."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    g = load("mesh128")
+    F, Fp = inputs.mesh_points(128, stretch=1.3, seed=0)
+    beta = cv.history_update(params(g), Fp).cpu().numpy()
+    WR, P, st, tree = run_full(cv, g, F, beta)
+    frac, compared = compare(orc, api, g, WR, P, st, tree)
+    assert frac >= 0.9 and compared >= 4096
+
+
+@pytest.mark.parametrize("step", [1, 10, 20])
+def test_golden_load_path(cv, orc, step):
+    """Load path on the 512 x 512 mesh (1,048,576 points), 128 x 128 angles,
+    L = 2049, depth 3, history of the earlier steps: the full scan on the
+    4,096 subsample points against the oracle."""
+    from paper_2211_14318_gb300 import api
+
+    name = f"loadpath512_s{step:02d}"
+    if not os.path.exists(os.path.join(HERE, "golden", f"{name}.npz")):
+        pytest.fail(f"missing tests/golden/{name}.npz (run tests/golden/make_goldens.py)")
+    g = load(name)
+    p = params(g)
+    out = cv.convexify_points(p, g["F"], g["beta"], want_tree=True)
+    n = g["F"].shape[0]
+    tree = api.tree_numpy(out["tree"], n, p.tree_size)
+    frac, compared = compare(orc, api, g, out["W_R"].cpu().numpy(), out["P"].cpu().numpy(),
+                             out["status"].cpu().numpy(), tree)
+    assert frac >= 0.9 and compared >= 4096

@@ -68,6 +68,48 @@ def test_static_entry_matches_convexify_points_twice(cv):
     _check_same(ref1, got3)
 
 
+def test_static_entry_leaves_device_memory_unchanged(cv):
+    """The defining property: with inputs and outputs already on the device,
+    calls of different shapes take no device memory (cudaMemGetInfo's free
+    bytes are the same before and after)."""
+    import ctypes
+
+    import torch
+
+    import oracle
+    from paper_2211_14318_gb300 import api, inputs
+
+    mat = oracle.Material(MAT["mu"], MAT["lambda_L"], MAT["D_inf"], MAT["D0"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shapes = [(64, api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT)),
+              (37, api.Params(n_theta_a=7, n_theta_b=9, line_points=77, t_half=0.6, depth=3, **MAT)),
+              (500, api.Params(n_theta_a=32, n_theta_b=32, line_points=513, depth=2, **MAT))]
+    bufs = []
+    for n, p in shapes:
+        F, Fp = inputs.material_points(n, seed=n)
+        b = oracle.history_update(mat, Fp)
+        bufs.append((p, n, torch.from_numpy(F).to(dev), torch.from_numpy(b).to(dev),
+                     torch.empty(n, dtype=torch.float64, device=dev),
+                     torch.empty(n, 4, dtype=torch.float64, device=dev),
+                     torch.empty(n, dtype=torch.int32, device=dev)))
+
+    def call(p, n, F, b, W, P, st):
+        c = p.c()
+        rc = api.lib().convexify_points_static(ctypes.byref(c), n, F.data_ptr(), b.data_ptr(),
+                                               W.data_ptr(), P.data_ptr(), st.data_ptr(), None)
+        assert rc == 0
+
+    call(*bufs[0])  # warm: the first call on a device looks up the scratch address
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        for args in bufs:
+            call(*args)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+
+
 def test_static_entry_rejects_oversized_problems(cv):
     from paper_2211_14318_gb300 import api
 
