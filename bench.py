@@ -1,17 +1,27 @@
 """Throughput of per-point rank-one convexification on GB300.
 
-Workload (one GPU): a 128 x 128 Q1 mesh x 4 Gauss points = 65,536 quadrature
-points, F from a seeded synthetic displacement (affine stretch 1.3 + 8 Fourier
-modes + a 45 degree shear band), history from the previous load step; NH with
-exponential damage (mu=1, lambda=5, D_inf=0.99, D_0=0.5); 64 x 64 angle grid
-(4096 rank-one directions), 1025 samples per line on t in [-0.5, 0.5],
-lamination depth 3.  A step is the whole path: history update (Eq. 2.5) and
-the convexification with W^R and P (Secs. 4-5).
+Default workload (the metric's): a load path on a 512 x 512 Q1 mesh x 4
+Gauss points = 1,048,576 quadrature points, 20 load steps (stretch 1.0 ->
+1.8, seeded smooth field and shear band), history updated after every step
+(Eq. 2.5); NH with exponential damage (mu=1, lambda=5, D_inf=0.99, D_0=0.5);
+128 x 128 angle grid (16,384 rank-one directions), 2049 samples per line on
+t in [-0.5, 0.5], lamination depth 3.  A step is one load step of the
+surrogate-proposed form: the network proposes a direction per tree node, a
++-4-cell angular window around it is scanned (re-centred on its border
+minimum up to 4 times), nodes whose window minimum stays on its border fall
+back to the full scan of all 16,384 directions; then W^R and P (Secs. 4-5).
+Beside it, in the same JSON line: the plain full scan on the same steps, its
+accuracy and the coarser plain grids (points/s against W^R error), the
+accuracy of the proposed form against the FP64 oracle on 4,096 points at
+steps 1, 10 and 20 (stored oracle results under tests/golden), the 1 M-point
+full scan at 16 x 16 angles, L = 201, depth 2 with its own roofline, and the
+65,536-point mesh at 64 x 64 angles, L = 1025, depth 3.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--form loadpath|full-scan|train]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank convexifies
-its own mesh (weak scaling, no collective in the data path).
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+load path (weak scaling, no collective in the data path).
 """
 from __future__ import annotations
 
@@ -44,18 +54,25 @@ def workload_desc(n):
 def args_parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=NX, help="mesh size (default 128 -> 65,536 points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
-    ap.add_argument("--form", default="full-scan", choices=["full-scan", "surrogate", "train"],
-                    help="surrogate: the learned-proposal form over a load path; train: "
+    ap.add_argument("--form", default="loadpath",
+                    choices=["loadpath", "full-scan", "surrogate", "train"],
+                    help="loadpath: the metric's workload (default); full-scan: the 65,536-point "
+                         "mesh alone; surrogate: the load path with the older report; train: "
                          "training and inference of the proposal network (own lines)")
     ap.add_argument("--train-epochs", type=int, default=10)
-    ap.add_argument("--gap-tol", type=float, default=1e-6, help="surrogate fallback tolerance")
+    ap.add_argument("--gap-tol", type=float, default=1e30,
+                    help="surrogate energy-gap fallback tolerance (1e30: border test only)")
     ap.add_argument("--window", type=int, default=4, help="surrogate window half-width (cells)")
+    ap.add_argument("--recentre", type=int, default=4, help="surrogate window re-centrings")
+    ap.add_argument("--lp-nx", type=int, default=512, help="load-path mesh size (512: 1,048,576 points)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="loadpath: skip the 1M-point L = 201 and the 65,536-point mesh lines")
     ap.add_argument("--gap-one-sided", action="store_true",
                     help="surrogate: fall back only when the proposed laminate beats the window")
     ap.add_argument("--load-steps", type=int, default=20)
@@ -174,7 +191,7 @@ def fp32_peak_tflops(torch, dev):
 
 
 SCAN_SOURCES = ("cvx_pipeline.cu", "cvx_bridge.cuh", "cvx_device.cuh", "cvx_line.cuh",
-                "cvx_internal.h")
+                "cvx_internal.h", "cvx_scan_lanes.cu")
 
 
 def scan_source_hash():
@@ -187,10 +204,10 @@ def scan_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(valid_per_launch):
+def traffic_per_launch(valid_per_launch, name="k_scan_traffic.json"):
     """DRAM bytes per scan launch from the committed ncu summary, scaled to
     this launch's work; None if the kernel changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "k_scan_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         t = json.load(open(path))
     except (OSError, ValueError):
@@ -218,31 +235,41 @@ def oracle_rate(F, F_prev, npts, cores):
 
 
 def run_reference(a):
+    """The FP64 CPU oracle on the default workload (the load path), each step
+    a bounded sample: `cpu_points` (default 8) evenly spaced points of load
+    step k (k = 1, 2, ... cycling over the path), with their history."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     import oracle
+    from paper_2211_14318_gb300 import inputs
 
     oracle.build()
     cores = host_cores()
-    F, F_prev = make_inputs(a.nx, 0)
-    npts = a.cpu_points or max(cores, 2 * cores)
-    for _ in range(a.warmup):
-        oracle_rate(F, F_prev, max(1, cores // 4), cores)
-    rates, times = [], []
-    for _ in range(a.steps):
-        r, dt = oracle_rate(F, F_prev, npts, cores)
-        rates.append(r)
-        times.append(dt)
+    path = inputs.load_path(a.lp_nx, n_steps=LP_STEPS, stretch_end=LP_STRETCH, seed=LP_SEED)
+    npts = a.cpu_points or 8
+    for i in range(a.warmup):
+        loadpath_oracle_rate(path, 1 + i % LP_STEPS, cores, 1)
+    times = []
+    for i in range(a.steps):
+        r = loadpath_oracle_rate(path, 1 + i % LP_STEPS, cores, npts)
+        times.append(npts / r["value"])
     value = npts * a.steps / sum(times)
+    n = path[0].shape[0]
+    sample = (f"{npts} evenly spaced points of load step k per step (k = 1, 2, ... cycling over "
+              f"the {LP_STEPS} steps), with their history")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * sum(times) / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(F.shape[0]), "form": "full-scan"},
+        "config": {"workload": (f"load path, {a.lp_nx}x{a.lp_nx} Q1 mesh x 4 Gauss points = {n} "
+                                f"points, {LP_STEPS} load steps (stretch 1.0 -> {LP_STRETCH}), "
+                                f"history updated, {LP_ANGLES}x{LP_ANGLES} angles, L={LP_LINE}, "
+                                f"t in [-0.5,0.5], depth {LP_DEPTH}"),
+                   "form": "full scan (the oracle has no proposal network)"},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{npts} evenly spaced points of the workload per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -384,6 +411,388 @@ def run_ours(a):
     cv.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------- load path (the metric)
+LP_STEPS, LP_ANGLES, LP_LINE, LP_DEPTH, LP_SEED, LP_STRETCH = 20, 128, 2049, 3, 7, 1.8
+NS_ANGLES, NS_LINE, NS_DEPTH, NS_POINTS, NS_SEED = 16, 201, 2, 1 << 20, 201
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+CHECK_STEPS = (1, 10, 20)
+
+
+def load_golden(name):
+    """Stored FP64 oracle results of 4,096 points of a workload (or None)."""
+    import numpy as np
+
+    path = os.path.join(GOLDEN, f"{name}.npz")
+    if not os.path.exists(path):
+        return None
+    g = dict(np.load(path))
+    g["meta"] = json.loads(str(g["meta"]))
+    return g
+
+
+def err_stats(W, Wo, P=None, Po=None):
+    """Relative W^R and P errors (gamma = 1e-8, Sec. 6.2): p50 / p99 / max."""
+    import numpy as np
+
+    e = np.abs(W - Wo) / (1e-8 + np.abs(Wo))
+    out = {"points": int(e.size), "W_R_p50": float(np.quantile(e, 0.5)),
+           "W_R_p99": float(np.quantile(e, 0.99)), "W_R_max": float(e.max())}
+    if P is not None:
+        ep = np.linalg.norm(P - Po, axis=1) / (1e-8 + np.linalg.norm(Po, axis=1))
+        out.update(P_p50=float(np.quantile(ep, 0.5)), P_p99=float(np.quantile(ep, 0.99)),
+                   P_max=float(ep.max()))
+    return out
+
+
+def train_proposal(cv, api, inputs, path, dev):
+    """The proposal network, trained on the GPU: labels from the GPU's own full
+    scans (131,072 material points with lambda in [1, 2], and 16,384 points
+    of the load path at five steps; 128^2 grid, L = 513, depth 2), then 30
+    epochs of Adam (batch 8,192) on the tensor cores."""
+    import numpy as np
+    import torch
+
+    pl = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=513, depth=2, **MAT)
+    F1, Fp1 = inputs.surrogate_inputs(131072, seed=100)
+    b1 = cv.history_update(pl, Fp1)
+    t0 = time.perf_counter()
+    out = cv.convexify_points(pl, F1, b1, want_tree=True)
+    X, Y = cv.surrogate_labels(pl, b1, out["tree"], F1.shape[0])
+    Xs, Ys = [X], [Y]
+    steps = len(path)
+    for k in (3, 7, 11, 15, 19):
+        k = min(k, steps - 1)
+        Fk = path[k]
+        bk = cv.history_update(pl, path[k - 1]).cpu().numpy()
+        idx = np.random.default_rng(k).choice(Fk.shape[0], min(16384, Fk.shape[0]), replace=False)
+        out = cv.convexify_points(pl, Fk[idx], bk[idx], want_tree=True)
+        X, Y = cv.surrogate_labels(pl, bk[idx], out["tree"], len(idx))
+        Xs.append(X)
+        Ys.append(Y)
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    log = cv.surrogate_train(X, Y, epochs=30, batch=8192, lr=1e-3, init=True, seed=0)
+    return {"samples": int(X.shape[0]), "label_s": t_label, "train_s": time.perf_counter() - t0,
+            "loss_first": float(log[0]), "loss_last": float(log[-1])}
+
+
+def propose_launches(n, K, R):
+    """Kernels of this library one surrogate_propose call and its history
+    update launch: k_init; per level and 65,536-node chunk the features, five
+    tensor-core GEMMs and the decoding; per level R + 1 window passes and the
+    fallback pass (line scan, select, refine, commit each); k_leaf,
+    k_fell_back; k_history."""
+    chunks = sum(-(-(n << l) // 65536) for l in range(K))
+    return 1 + 7 * chunks + 4 * (R + 2) * K + 3
+
+
+def timed_full_scan(cv, p, F, beta, steps, torch):
+    """CUDA-event time of `steps` plain convexify_points calls (after two
+    warm calls), the line-scan launches' own time and the counters."""
+    import numpy as np
+
+    for _ in range(2):
+        cv.convexify_points(p, F, beta)
+    torch.cuda.synchronize()
+    cv.stats(reset=True)
+    cv.set_profiling(True)
+    cv.scan_timing(reset=True)
+    ms = 0.0
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = cv.convexify_points(p, F, beta)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    scan_ms, launches = cv.scan_timing(reset=True)
+    cv.set_profiling(False)
+    st = cv.stats(reset=True)
+    return ms, scan_ms, launches, st, out
+
+
+def roofline_obj(st, scan_ms, launches, step_ms, peak, sms, mhz, peak_src, traffic_name=None):
+    flop = FLOP_PER_SAMPLE * st["valid_samples"]
+    achieved = flop / (scan_ms / 1e3) / 1e12 if scan_ms > 0 else None
+    traffic = (traffic_per_launch(st["valid_samples"] / max(1, launches), traffic_name)
+               if traffic_name else None)
+    return {"bound": "alu", "kernel": "k_scan_lanes", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz ({peak_src})",
+            "flop_per_valid_sample": FLOP_PER_SAMPLE,
+            "kernel_share_of_step": scan_ms / step_ms if step_ms else None,
+            "launches": launches}
+
+
+def run_loadpath(a):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api, inputs
+
+    cv = api.Convexifier(local)
+    path = inputs.load_path(a.lp_nx, n_steps=LP_STEPS, stretch_end=LP_STRETCH, seed=LP_SEED + rank)
+    n = path[0].shape[0]
+    K = max(1, min(a.steps, LP_STEPS))
+    train = train_proposal(cv, api, inputs, path, dev)
+    p = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=LP_LINE, depth=LP_DEPTH,
+                   recentre=a.recentre, gap_one_sided=a.gap_one_sided, **MAT)
+    pf = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=LP_LINE,
+                    depth=LP_DEPTH, **MAT)
+    kw = dict(window=a.window, gap_tol=a.gap_tol)
+
+    # ---- warm-up: load steps of the proposed form on the first 65,536 points
+    nw = min(n, 65536)
+    bw = torch.zeros(nw, dtype=torch.float64, device=dev)
+    for k in range(a.warmup):
+        Fk = torch.from_numpy(path[k % LP_STEPS][:nw]).to(dev)
+        cv.surrogate_propose(p, Fk, bw, **kw)
+        bw = cv.history_update(p, Fk, bw)
+    torch.cuda.synchronize()
+
+    # ---- timed: K load steps of 1,048,576 points, history carried over
+    Fh = torch.empty((n, 4), dtype=torch.float64).pin_memory()
+    Wh = torch.empty(n, dtype=torch.float64).pin_memory()
+    Ph = torch.empty((n, 4), dtype=torch.float64).pin_memory()
+    Fd = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    beta = torch.zeros(n, dtype=torch.float64, device=dev)
+    out = dict(W_R=torch.empty(n, dtype=torch.float64, device=dev),
+               P=torch.empty(n, 4, dtype=torch.float64, device=dev),
+               status=torch.empty(n, dtype=torch.int32, device=dev),
+               fell_back=torch.empty(n, dtype=torch.uint8, device=dev))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    gold = {}
+    if rank == 0 and a.lp_nx == 512:
+        for k in CHECK_STEPS:
+            g = load_golden(f"loadpath512_s{k:02d}")
+            if g is not None and k <= K:
+                gold[k] = g
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
+    cv.stats(reset=True)
+    cv.set_profiling(True)
+    cv.scan_timing(reset=True)
+    comp_ms, e2e_ms, per_step, fell, checks = 0.0, 0.0, [], [], {}
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(1, K + 1):
+        Fh.copy_(torch.from_numpy(path[k - 1]))
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        Fd.copy_(Fh, non_blocking=True)
+        ev[1].record()
+        cv.surrogate_propose(p, Fd, beta, out=out, **kw)
+        beta = cv.history_update(p, Fd, beta)  # Eq. (2.5) for the next load step
+        ev[2].record()
+        Wh.copy_(out["W_R"], non_blocking=True)
+        Ph.copy_(out["P"], non_blocking=True)
+        ev[3].record()
+        torch.cuda.synchronize()
+        t = ev[1].elapsed_time(ev[2])
+        comp_ms += t
+        e2e_ms += ev[0].elapsed_time(ev[3])
+        per_step.append(t)
+        fell.append(float(out["fell_back"].float().mean()))
+        if k in gold:
+            idx = gold[k]["idx"]
+            checks[k] = (Wh.numpy()[idx].copy(), Ph.numpy()[idx].copy(),
+                         float(np.abs(path[k - 1][idx] - gold[k]["F"]).max()))
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    scan_ms, scan_launches = cv.scan_timing(reset=True)
+    cv.set_profiling(False)
+    st = cv.stats(reset=True)
+    t_max = max_over_ranks(comp_ms, dist if ws > 1 else None, dev)
+    value = whole_job_rate(n, ws, K, t_max)
+    e2e_value = whole_job_rate(n, ws, K, max_over_ranks(e2e_ms, dist if ws > 1 else None, dev))
+    peak, sms, mhz, peak_src = fp32_peak_tflops(torch, dev)
+
+    if rank == 0:
+        # accuracy of the proposed form against the oracle (stored results)
+        acc = {}
+        for k, (W, P, dF) in checks.items():
+            g = gold[k]
+            acc[f"step_{k}"] = dict(err_stats(W, g["W_R"], P, g["P"]), max_abs_dF=dF,
+                                    fell_back_points=fell[k - 1])
+        # the plain full scan on the same steps: points/s on 65,536 points of
+        # the step, and its own accuracy on the 4,096 stored points
+        full, pareto = {}, {}
+        nt = min(n, 65536)
+        for k in CHECK_STEPS:
+            if k > K:
+                continue
+            bk = torch.zeros(nt, dtype=torch.float64, device=dev)
+            for j in range(k - 1):
+                bk = cv.history_update(pf, path[j][:nt], bk)
+            Fk = torch.from_numpy(path[k - 1][:nt]).to(dev)
+            ms, _, _, _, _ = timed_full_scan(cv, pf, Fk, bk, 1, torch)
+            row = {"pts_per_s": nt / (ms / 1e3), "proposed_pts_per_s": n / (per_step[k - 1] / 1e3)}
+            if k in gold:
+                g = gold[k]
+                r = cv.convexify_points(pf, g["F"], g["beta"])
+                row.update(err_stats(r["W_R"].cpu().numpy(), g["W_R"], r["P"].cpu().numpy(), g["P"]))
+                for na in (16, 32, 64):
+                    q = api.Params(n_theta_a=na, n_theta_b=na, line_points=LP_LINE, depth=LP_DEPTH,
+                                   **MAT)
+                    rq = cv.convexify_points(q, g["F"], g["beta"])
+                    msq, _, _, _, _ = timed_full_scan(cv, q, Fk, bk, 1, torch)
+                    pareto.setdefault(f"{na}x{na}", {})[f"step_{k}"] = dict(
+                        err_stats(rq["W_R"].cpu().numpy(), g["W_R"]), pts_per_s=nt / (msq / 1e3))
+            full[f"step_{k}"] = row
+        extras = {}
+        if not a.no_extras:
+            extras["north_star"] = north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz,
+                                                   peak_src, K)
+            extras["mesh128"] = mesh128_line(cv, api, torch, dev, peak, sms, mhz, peak_src,
+                                             min(K, 5))
+        cpu = None
+        if ws == 1 and not a.no_cpu_baseline:
+            cpu = loadpath_oracle_rate(path, K, host_cores(), 8)
+            cpu1 = loadpath_oracle_rate(path, K, 1, 1)
+            cpu["one_core"] = {"value": cpu1["value"], "sample": cpu1["sample"]}
+        wn, fb, rc = st["window_nodes"], st["fallbacks"], st["recentred"]
+        first_pass = max(1, wn - rc)
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": K,
+            "warmup": a.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32/f64", "data": "synthetic",
+            "config": {
+                "workload": (f"load path, {a.lp_nx}x{a.lp_nx} Q1 mesh x 4 Gauss points = {n} points, "
+                             f"load steps 1..{K} of {LP_STEPS} (stretch 1.0 -> {LP_STRETCH}), history "
+                             f"updated, {LP_ANGLES}x{LP_ANGLES} angles, window +-{a.window} "
+                             f"re-centred up to {a.recentre} times, L={LP_LINE}, t in [-0.5,0.5], "
+                             f"depth {LP_DEPTH}; surrogate-proposed with full-scan fallback"),
+                "form": "surrogate", "points_per_gpu": n, "window": a.window,
+                "recentre": a.recentre, "gap_tol": a.gap_tol,
+                "fallback_rule": ("border: the window minimum still on the window border after "
+                                  "the re-centrings" + ("" if a.gap_tol >= 1e29 else
+                                                        f"; or energy gap > {a.gap_tol}")),
+                "l2": "flushed between steps (512 MiB write)",
+                "timed": "H2D of F excluded from value (included in e2e); proposal + history update",
+                "wall_s_timed_region": wall},
+            "roofline": roofline_obj(st, scan_ms, scan_launches, comp_ms, peak, sms, mhz, peak_src,
+                                     "k_scan_lanes_traffic.json"),
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n * 4 * 8,
+                    "d2h_bytes_per_step": n * 8 + n * 4 * 8},
+            "gpu_launches": K * propose_launches(n, LP_DEPTH, a.recentre),
+            "clocks": ck,
+            "accuracy_vs_oracle": acc,
+            "fallback": {"window_nodes_first_pass": first_pass, "recentred": rc, "fallback_nodes": fb,
+                         "fallback_rate": fb / first_pass,
+                         "points_with_a_fallback_mean": sum(fell) / len(fell)},
+            "full_scan": full, "pareto": pareto, "train": train,
+            "per_step_ms": per_step,
+            **extras,
+            "stats": st,
+        }
+        print(json.dumps(line), flush=True)
+    cv.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, steps):
+    """1,048,576 material points at 16 x 16 angles, L = 201, depth 2 (the
+    full scan): throughput, the line scan's roofline and the error against the
+    stored oracle results of 4,096 points (placed at their rows)."""
+    import numpy as np
+
+    F, Fp = inputs.surrogate_inputs(NS_POINTS, seed=NS_SEED)
+    p = api.Params(n_theta_a=NS_ANGLES, n_theta_b=NS_ANGLES, line_points=NS_LINE, depth=NS_DEPTH,
+                   **MAT)
+    beta = cv.history_update(p, Fp).cpu().numpy()
+    g = load_golden("material1m_l201")
+    if g is not None:
+        F[g["idx"]] = g["F"]
+        beta[g["idx"]] = g["beta"]
+    Fd = torch.from_numpy(F).to(dev)
+    bd = torch.from_numpy(beta).to(dev)
+    ms, scan_ms, launches, st, out = timed_full_scan(cv, p, Fd, bd, steps, torch)
+    res = {"workload": (f"{NS_POINTS} material points (F = Q diag(lam, lam^-0.3) Q^T + noise, "
+                        f"lam ~ U[1, 2]), {NS_ANGLES}x{NS_ANGLES} angles, L={NS_LINE}, "
+                        f"t in [-0.5,0.5], depth {NS_DEPTH}, full scan"),
+           "value": NS_POINTS * steps / (ms / 1e3), "unit": "points/s", "steps": steps,
+           "ms_per_step": ms / steps,
+           "roofline": roofline_obj(st, scan_ms, launches, ms, peak, sms, mhz, peak_src,
+                                    "k_scan_lanes_l201_traffic.json"),
+           "stats": st}
+    if g is not None:
+        it = torch.from_numpy(g["idx"]).to(dev)
+        res["accuracy_vs_oracle"] = err_stats(out["W_R"][it].cpu().numpy(), g["W_R"],
+                                              out["P"][it].cpu().numpy(), g["P"])
+    return res
+
+
+def mesh128_line(cv, api, torch, dev, peak, sms, mhz, peak_src, steps):
+    """The 65,536-point mesh (128 x 128 Q1 x 4 Gauss points, stretch 1.3),
+    64 x 64 angles, L = 1025, depth 3, full scan."""
+    from paper_2211_14318_gb300 import inputs
+
+    F, Fp = inputs.mesh_points(NX, stretch=STRETCH, seed=0)
+    p = api.Params(n_theta_a=ANGLES, n_theta_b=ANGLES, line_points=LINE, t_half=T_HALF,
+                   depth=DEPTH, **MAT)
+    beta = cv.history_update(p, Fp).cpu().numpy()
+    g = load_golden("mesh128")
+    if g is not None:
+        F[g["idx"]] = g["F"]
+        beta[g["idx"]] = g["beta"]
+    Fd = torch.from_numpy(F).to(dev)
+    bd = torch.from_numpy(beta).to(dev)
+    ms, scan_ms, launches, st, out = timed_full_scan(cv, p, Fd, bd, steps, torch)
+    res = {"workload": workload_desc(F.shape[0]), "value": F.shape[0] * steps / (ms / 1e3),
+           "unit": "points/s", "steps": steps, "ms_per_step": ms / steps,
+           "roofline": roofline_obj(st, scan_ms, launches, ms, peak, sms, mhz, peak_src),
+           "stats": st}
+    if g is not None:
+        it = torch.from_numpy(g["idx"]).to(dev)
+        res["accuracy_vs_oracle"] = err_stats(out["W_R"][it].cpu().numpy(), g["W_R"],
+                                              out["P"][it].cpu().numpy(), g["P"])
+    return res
+
+
+def loadpath_oracle_rate(path, step, cores, npts):
+    """The FP64 CPU oracle (as it stands) on npts evenly spaced points of load
+    step `step` of the path, with the history of the earlier steps."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    mat = oracle.Material(MAT["mu"], MAT["lambda_L"], MAT["D_inf"], MAT["D0"])
+    sc = oracle.Scan(oracle.angle_directions(LP_ANGLES, LP_ANGLES), LP_LINE, 0.5, LP_DEPTH)
+    n = path[0].shape[0]
+    idx = np.linspace(0, n - 1, npts).astype(np.int64)
+    beta = np.zeros(npts)
+    for j in range(step - 1):
+        beta = oracle.history_update(mat, path[j][idx], beta)
+    t0 = time.perf_counter()
+    oracle.convexify(mat, sc, path[step - 1][idx], beta, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": npts / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": f"{npts} evenly spaced points of load step {step} ({dt:.1f} s)"}
 
 
 # ------------------------------------------------------- surrogate form
@@ -625,6 +1034,8 @@ def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.form == "loadpath":
+        run_loadpath(a)
     elif a.form == "surrogate":
         run_surrogate(a)
     elif a.form == "train":

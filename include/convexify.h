@@ -104,7 +104,9 @@ typedef struct cvx_params {
     int32_t line_points; /* odd, 3 <= L <= 2079                          */
     int32_t depth;
     int32_t flags; /* CVX_FLAG_* bits (0: the plain grid method)        */
-    int32_t reserved;
+    int32_t recentre; /* surrogate_propose: re-centrings of a proposal window
+                         whose best direction lies on its border, 0..8
+                         (0: none); ignored by the other calls          */
 } cvx_params;
 
 /* cvx_params.flags.
@@ -173,7 +175,7 @@ typedef struct cvx_stats {
     int64_t lines;          /* (node, direction) lines sampled             */
     int64_t valid_samples;  /* samples with det > 0 (algorithmic work)     */
     int64_t laminated;      /* nodes that split                            */
-    int64_t fp64_checks;    /* exact FP64 predicate evaluations            */
+    int64_t fp64_checks;    /* FP64 spot samples of the refinement certificates */
     int64_t full_passes;    /* full-line argmin passes of the hull search  */
     int64_t rare_paths;     /* hull searches that left the fast path       */
     int64_t ties;           /* nodes flagged CVX_NODE_TIE                  */
@@ -194,6 +196,10 @@ typedef struct cvx_stats {
     int64_t lines_flat;     /* lines whose sampling-pass bound is within the
                                FP32 sample error of the centre value: no
                                hull search, the bound is their lower bound  */
+    int64_t recentred;      /* surrogate_propose: window re-centrings        */
+    int64_t lines_certified; /* lines certified not to split their node (the
+                               tangent line at the centre supports every
+                               sample): no FP64 refinement needed           */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */
@@ -376,9 +382,12 @@ int surrogate_labels(cvx_handle *h, const cvx_params *p, int64_t n, const double
  * results; angle-grid directions only).  At every tree node the network
  * proposes a direction; its nearest cell (ia, ib) of the Na x Nb grid centres
  * a window of (2 window + 1)^2 directions (indices wrap), and only those lines
- * are scanned.  The node falls back to the full scan of all Na Nb directions
- * if (i) the window's best direction lies on its border, or (ii) the energy
- * gap |E_pred - V| / (1e-8 + |V|) exceeds gap_tol, where V is the
+ * are scanned.  If the window's best direction lies on its border (and the
+ * energy gap test passes), the window is moved to be centred on that
+ * direction's cell and scanned again, at most p->recentre times.  The node
+ * falls back to the full scan of all Na Nb directions if (i) the window's
+ * best direction still lies on its border, or (ii) the energy gap
+ * |E_pred - V| / (1e-8 + |V|) exceeds gap_tol, where V is the
  * window's node value and E_pred = xi W(F+) + (1 - xi) W(F-) the proposed
  * laminate evaluated exactly (F+ = F + (1 - xi) amp R, F- = F - xi amp R,
  * R = a (x) b of the proposed angles, amp = jump : R).  fell_back (n, DEVICE,

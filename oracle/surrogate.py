@@ -10,12 +10,16 @@ Per tree node, top-down as the plain method (Eq. 3.3 per point):
      directions (indices wrap);
   2. the line scan (Sec. 4, the oracle's own C scan) runs over the window's
      directions only;
-  3. the node falls back to the scan of all directions if the window's best
-     direction lies on the window border or the energy gap
+  3. if the window's best direction lies on the window border (and the energy
+     gap test below passes), the window is moved to be centred on that
+     direction's cell and scanned again, at most ``recentre`` times (a local
+     descent over the angle grid; recentre = 0 does not move it);
+  4. the node falls back to the scan of all directions if the window's best
+     direction still lies on the window border or the energy gap
      |E_pred - V| / (1e-8 + |V|) exceeds gap_tol, with V the window's node
      value and E_pred = xi W(F+) + (1 - xi) W(F-) of the proposed laminate
      (one_sided: (V - E_pred) / (1e-8 + |V|), only a better proposal counts);
-  4. the split and the recursion are those of the plain method.
+  5. the split and the recursion are those of the plain method.
 Every integer decision comes with its margin: the distance of the scaled
 angles to a rounding boundary (in cells), the scan's certified margin, and
 |gap - gap_tol| relative to gap_tol.
@@ -44,7 +48,7 @@ def _offset(i, c, N):
 
 
 def propose_convexify(orc, mat, Na, Nb, L, t_half, K, w, gap_tol, flat, mean, std, F, beta,
-                      one_sided=False):
+                      one_sided=False, recentre=0):
     """Returns (W_R, P, nodes) with nodes[p] = {heap index: record}."""
     dirs_all = orc.angle_directions(Na, Nb)
     full = orc.Scan(dirs_all, L, t_half, 1)
@@ -68,17 +72,26 @@ def propose_convexify(orc, mat, Na, Nb, L, t_half, K, w, gap_tol, flat, mean, st
             ia, ib, xi_p, Fp, Fm, dist = mlp.decode(out, Fi, Na, Nb)
             ia, ib = int(ia[0]), int(ib[0])
             E_pred = xi_p[0] * orc.energy(mat, Fp[0], b) + (1 - xi_p[0]) * orc.energy(mat, Fm[0], b)
-            idx = window_indices(ia, ib, w, Na, Nb)
-            order = np.argsort(idx, kind="stable")  # lowest global index wins ties
-            sc = orc.Scan(dirs_all[idx[order]], L, t_half, 1)
-            info = orc.scan_node(mat, sc, Fi, b)
-            gd = int(idx[order][info["dir"]])
-            lam = info["m_minus"] != m0
-            V = info["h"] if lam else rec["w"]
-            border = lam and (abs(_offset(gd // Nb, ia, Na)) >= w or abs(_offset(gd % Nb, ib, Nb)) >= w)
-            gap = ((V - E_pred) if one_sided else abs(E_pred - V)) / (1e-8 + abs(V))
-            rec.update(center=(ia, ib), center_margin=float(dist[0]), gap=gap, E_pred=E_pred,
-                       window_margin=info["margin"], window_dir=gd, window_lam=lam, V=V)
+            rec.update(center=(ia, ib), center_margin=float(dist[0]), E_pred=E_pred)
+            ca, cb = ia, ib
+            window_margin = np.inf
+            for moves in range(recentre + 1):
+                idx = window_indices(ca, cb, w, Na, Nb)
+                order = np.argsort(idx, kind="stable")  # lowest global index wins ties
+                sc = orc.Scan(dirs_all[idx[order]], L, t_half, 1)
+                info = orc.scan_node(mat, sc, Fi, b)
+                window_margin = min(window_margin, info["margin"])
+                gd = int(idx[order][info["dir"]])
+                lam = info["m_minus"] != m0
+                V = info["h"] if lam else rec["w"]
+                border = lam and (abs(_offset(gd // Nb, ca, Na)) >= w or
+                                  abs(_offset(gd % Nb, cb, Nb)) >= w)
+                gap = ((V - E_pred) if one_sided else abs(E_pred - V)) / (1e-8 + abs(V))
+                if not (border and gap <= gap_tol) or moves == recentre:
+                    break
+                ca, cb = gd // Nb, gd % Nb  # re-centre on the border minimum
+            rec.update(gap=gap, window_margin=window_margin, window_dir=gd, window_lam=lam, V=V,
+                       recentred=moves, last_center=(ca, cb))
             if border or not gap <= gap_tol:
                 info = orc.scan_node(mat, full, Fi, b)
                 gd = info["dir"]

@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
         ("dirs", ctypes.POINTER(ctypes.c_double)),
         ("energy", ctypes.c_int32), ("n_theta_a", ctypes.c_int32), ("n_theta_b", ctypes.c_int32),
         ("n_dirs", ctypes.c_int32), ("line_points", ctypes.c_int32), ("depth", ctypes.c_int32),
-        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("recentre", ctypes.c_int32),
     ]
 
 
@@ -57,7 +57,7 @@ class _Stats(ctypes.Structure):
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
         "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks", "refine_full", "lines_bounded",
-        "lines_flat")]
+        "lines_flat", "recentred", "lines_certified")]
 
 
 class _Problem(ctypes.Structure):
@@ -160,13 +160,14 @@ class Params:
     dirs: Optional[np.ndarray] = None  # custom (n, 4) rows (a1, a2, b1, b2)
     newton: bool = False  # CVX_FLAG_REFINE_NEWTON
     gap_one_sided: bool = False  # CVX_FLAG_GAP_ONE_SIDED (surrogate_propose)
+    recentre: int = 0  # surrogate_propose: window re-centrings (0..8)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
         p = _Params()
         p.mu, p.lambda_L, p.D_inf, p.D0, p.t_half = self.mu, self.lambda_L, self.D_inf, self.D0, self.t_half
         p.energy, p.n_theta_a, p.n_theta_b = self.energy, self.n_theta_a, self.n_theta_b
-        p.line_points, p.depth, p.reserved = self.line_points, self.depth, 0
+        p.line_points, p.depth, p.recentre = self.line_points, self.depth, self.recentre
         p.flags = (FLAG_REFINE_NEWTON if self.newton else 0) | (2 if self.gap_one_sided else 0)
         if self.dirs is not None:
             d = np.ascontiguousarray(self.dirs, dtype=np.float64).reshape(-1, 4)

@@ -62,6 +62,8 @@ int check_params(const cvx_params *p, bool need_line) {
     }
     if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED))
         return fail(CVX_ERR_INVALID_ARG, "unknown flags");
+    if (p->recentre < 0 || p->recentre > kMaxRecentre)
+        return fail(CVX_ERR_INVALID_ARG, "recentre must be in [0, 8], got %d", p->recentre);
     if (!need_line) return CVX_OK;
     if (p->line_points < 3 || p->line_points > 2079 || (p->line_points % 2) == 0)
         return fail(CVX_ERR_INVALID_ARG, "line_points must be odd in [3, 2079], got %d",
@@ -101,6 +103,25 @@ void direction_rows(const cvx_params *p, std::vector<double> &d64) {
             r[3] = sin(tb);
         }
     }
+}
+
+int scan_events(cvx_handle *h, int n_launches, std::vector<cudaEvent_t> &ev) {
+    ev.clear();
+    if (!h->profiling) return CVX_OK;
+    for (int l = 0; l < n_launches; ++l) {
+        std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+        if (!h->ev_pool.empty()) {
+            e = h->ev_pool.back();
+            h->ev_pool.pop_back();
+        } else {
+            CK(cudaEventCreate(&e.first), "profiling");
+            CK(cudaEventCreate(&e.second), "profiling");
+        }
+        ev.push_back(e.first);
+        ev.push_back(e.second);
+        h->ev_pending.push_back(e);
+    }
+    return CVX_OK;
 }
 
 int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s) {
@@ -245,6 +266,8 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->refine_full = (int64_t)c[C_REFFULL];
     out->lines_bounded = (int64_t)c[C_BOUNDED];
     out->lines_flat = (int64_t)c[C_FLAT];
+    out->recentred = (int64_t)c[C_RECENTRED];
+    out->lines_certified = (int64_t)c[C_CERT];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }
@@ -421,21 +444,8 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
        "convexify_points/table");
 
     std::vector<cudaEvent_t> ev;
-    if (h->profiling) {
-        for (int l = 0; l < pp.K; ++l) {
-            std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
-            if (!h->ev_pool.empty()) {
-                e = h->ev_pool.back();
-                h->ev_pool.pop_back();
-            } else {
-                CK(cudaEventCreate(&e.first), "profiling");
-                CK(cudaEventCreate(&e.second), "profiling");
-            }
-            ev.push_back(e.first);
-            ev.push_back(e.second);
-            h->ev_pending.push_back(e);
-        }
-    }
+    rc = scan_events(h, pp.K, ev);
+    if (rc) return rc;
     CK(pipe_enqueue(pp, warps, grid, s, ev.empty() ? nullptr : ev.data()), "convexify_points");
     return CVX_OK;
 }

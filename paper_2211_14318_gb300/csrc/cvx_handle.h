@@ -52,6 +52,9 @@ int cuda_fail(cudaError_t e, const char *where);
 Material material_of(const cvx_params *p);
 int check_params(const cvx_params *p, bool need_line);
 int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s);
+// With profiling on: n_launches event pairs (2 per line-scan launch, recorded
+// on the launching stream around it), registered for cvx_get_scan_timing.
+int scan_events(cvx_handle *h, int n_launches, std::vector<cudaEvent_t> &ev);
 // Direction table of the handle for a parameter set (angle grid or custom).
 int ensure_dirs(cvx_handle *h, const cvx_params *p, cudaStream_t s);
 // Direction rows (a1, a2, b1, b2) of a parameter set, FP64.

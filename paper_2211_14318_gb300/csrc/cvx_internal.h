@@ -15,6 +15,7 @@ constexpr int kItemTop = 8;    // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
 constexpr int kLaneItemMax = 256;  // directions per work item of the lane-per-line scan
 constexpr int kMaxDepth = 8;
+constexpr int kMaxRecentre = 8;  // window re-centrings per node at most (surrogate_propose)
 // Bound on the FP32 sampling error of v = kappa' W - C in sample units,
 // relative to max(kappa', |v| + C) (>= kappa' max(1, |W|)): 3.5 times the
 // largest error measured against FP64.
@@ -60,7 +61,7 @@ struct RefineOut {
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
     C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
-    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_NUM
+    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_NUM
 };
 
 // Pipeline passes over one level's queue.
@@ -134,6 +135,18 @@ struct Pipe {
     unsigned long long *fitem_ctr;
     int2 *center;                         // proposed window centre per queued node
     double *e_pred;                       // energy of the proposed laminate per queued node
+    // window re-centring: two ping-pong queues of nodes whose window minimum
+    // lay on the border, with their new centre and E_pred; per pass r a block
+    // of 2 (K + 1) counts and K + 1 item counters
+    int32_t *rq_p[2], *rq_h[2];
+    int2 *rcen[2];
+    double *rep[2];
+    int32_t *rcnt;
+    unsigned long long *ritem;
+    // where this window pass sends nodes to re-centre (nullptr: to the full scan)
+    int32_t *nx_p, *nx_h, *nx_cnt;
+    int2 *nx_cen;
+    double *nx_ep;
     // lane-per-line scan (damage energy): 1 selects it for this run's levels
     int lanes;
     int *node_u;                          // per queued node: smallest FP32 upper bound (f2key)
@@ -153,6 +166,10 @@ cudaError_t pipe_level(const Pipe &p, int level, int warps, int grid, cudaStream
 cudaError_t pipe_end(const Pipe &p, cudaStream_t s);
 // The Pipe that runs the full scan over the nodes a window pass deferred.
 Pipe fallback_pipe(const Pipe &p, int level);
+// The Pipe of window pass r (0: the level queue with the network's centres;
+// r >= 1: the nodes re-centred by pass r - 1) with re-centring allowed while
+// r < R.
+Pipe window_pipe(const Pipe &p, int level, int r, int R);
 int scan_max_blocks_per_sm(int energy, int warps, int stride);
 // Lane-per-line scan (cvx_scan_lanes.cu): whether it serves this energy (the
 // damage energy, unless the environment variable CVX_SCAN_KERNEL is "warp"),

@@ -637,15 +637,19 @@ __device__ __forceinline__ void half_min_dk(double &v, int &k, bool prefer_low) 
 // supporting-slope iteration over FP64 samples in two windows around a and
 // b (16 samples each, one per lane, for L <= 513; 32 each, two per lane,
 // above), then a certificate over the whole line that every sample outside
-// the windows lies strictly above the FP64 chord: its FP32 sample, computed
-// on the fly, less the FP32 error bound kEps32 max(kappa', |v| + C) and the
-// rounding bound of the chord evaluated in FP32 sample units, lies above
-// the chord.  Samples whose FP32 value is not finite (near det = 0) are
-// checked in FP64.  Returns false where the windows' pair does not settle
-// or the certificate fails (the caller resamples the whole line in FP64).
+// the windows lies strictly above the FP64 chord.  Each such sample is first
+// tested on its FP32 value, computed on the fly: its FP32 sample less the
+// FP32 error bound kEps32 max(kappa', |v| + C) and the rounding bound of the
+// chord evaluated in FP32 sample units lies above the chord.  Where that test
+// is inconclusive (near the tangent points, or det near 0) the sample is
+// taken in FP64 and compared with the chord exactly.  An FP64 sample on or
+// below the chord moves the pair to the lowest such sample of its side (at
+// the chord's slope) and the windows are taken around the new pair, at most
+// 4 times.  Returns false if that does not settle (the caller resamples the
+// whole line in FP64); n64 counts the FP64 spot samples.
 __device__ bool refine_hinted(const double F[4], const double R[4], double beta, const NodeCands &nc,
                               const ProbDesc &pd, float4 d32, int hab, int lane, int &a, int &b,
-                              double &wa, double &wb) {
+                              double &wa, double &wb, unsigned &n64) {
     const LineSpec ln = pd.line;
     const int m0 = ln.m0, L = ln.L;
     const double ek = nc.ek;
@@ -654,82 +658,104 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
     if (!(a >= 0 && a < m0 && b > m0 && b < L)) return false;
     const bool narrow = L <= 513;
     const int W = narrow ? 16 : 32;
-    const int loA = max(0, min(a - W / 2, m0 - W));
-    const int loB = max(m0 + 1, min(b - (W / 2 - 1), L - W));
-    // window samples: narrow, lane l < 16 holds left loA + l and lane l >= 16
-    // right loB + l - 16; wide, every lane holds left loA + l and right loB + l
-    const int kA = narrow ? loA + (lane & 15) : loA + lane;
-    const int kB = narrow ? loB + (lane & 15) : loB + lane;
-    const bool hasA = narrow ? lane < 16 : true, hasB = narrow ? lane >= 16 : true;
-    double vA = INFINITY, vB = INFINITY;
-    if (hasA && kA < m0) {
-        const double v = sample_w64_ek(F, R, kA, m0, ln.h64, beta, ek, pd.mat);
-        vA = v == v ? v : INFINITY;
-    }
-    if (hasB && kB < L) {
-        const double v = sample_w64_ek(F, R, kB, m0, ln.h64, beta, ek, pd.mat);
-        vB = v == v ? v : INFINITY;
-    }
-    auto valA = [&](int k) { return __shfl_sync(kFull, vA, narrow ? k - loA : k - loA); };
-    auto valB = [&](int k) { return __shfl_sync(kFull, vB, narrow ? 16 + k - loB : k - loB); };
-    wa = valA(a);
-    wb = valB(b);
-    if (!(wa < INFINITY && wb < INFINITY)) return false;
-    bool settled = false;
-    for (int it = 0; it < 64 && !settled; ++it) {
-        const double s = (wb - wa) / (double)(b - a);
-        int na, nb;
-        if (narrow) {
-            const bool left = lane < 16;
-            const double v = left ? vA : vB;
-            const int k = left ? kA : kB;
-            double e = v < INFINITY ? v - s * (double)(k - m0) : INFINITY;
-            int kk = v < INFINITY ? k : (left ? INT_MAX : -1);
-            half_min_dk(e, kk, left);
-            na = __shfl_sync(kFull, kk, 0);
-            nb = __shfl_sync(kFull, kk, 16);
-        } else {
-            double eA = vA < INFINITY ? vA - s * (double)(kA - m0) : INFINITY;
-            double eB = vB < INFINITY ? vB - s * (double)(kB - m0) : INFINITY;
-            int ka = vA < INFINITY ? kA : INT_MAX, kb = vB < INFINITY ? kB : -1;
-            warp_min_dk(eA, ka, true);
-            warp_min_dk(eB, kb, false);
-            na = ka;
-            nb = kb;
-        }
-        if (na == INT_MAX || nb < 0) return false;
-        settled = na == a && nb == b;
-        a = na;
-        b = nb;
-        wa = valA(a);
-        wb = valB(b);
-    }
-    if (!settled) return false;
-    // certificate over the samples outside the windows and the centre
-    const double s = (wb - wa) / (double)(b - a);
     const double kap = pd.kappa, C = nc.shift;
-    const float la = (float)(kap * wa - C), ls = (float)(kap * s);
     const float kapf = pd.kappa_f, Cf = (float)C;
     const DirLine dl = make_dir_line<CVX_ENERGY_NH_DAMAGE>(nc.nl, d32);
-    const int hiA = min(loA + W, m0), hiB = min(loB + W, L);
-    bool good = true;
-    for (int k = lane; k < L && good; k += 32) {
-        if (k == m0 || (k >= loA && k < hiA) || (k >= loB && k < hiB)) continue;
-        const float v32 =
-            sample_w<CVX_ENERGY_NH_DAMAGE>(nc.nl, dl, __fmul_rn((float)(k - m0), ln.h32));
-        if (v32 < INFINITY && v32 > -INFINITY) {
-            const float x = (float)(k - a);
-            const float Lv = __fmaf_rn(ls, x, la);
-            const float err = 2.0f * kU32 * (fabsf(la) + fabsf(ls * x) + fabsf(Lv)) +
-                              kEps32 * fmaxf(kapf, fabsf(v32) + Cf) + 1e-30f;
-            good = __fsub_rn(v32, Lv) > 1.001f * err;
-        } else {
-            const double v = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
-            const double line = wa + s * (double)(k - a);
-            good = !(v == v) || v > line + 1e-14 * fabs(line);
+    for (int round = 0; round < 4; ++round) {
+        const int loA = max(0, min(a - W / 2, m0 - W));
+        const int loB = max(m0 + 1, min(b - (W / 2 - 1), L - W));
+        // window samples: narrow, lane l < 16 holds left loA + l and lane
+        // l >= 16 right loB + l - 16; wide, every lane holds left loA + l and
+        // right loB + l
+        const int kA = narrow ? loA + (lane & 15) : loA + lane;
+        const int kB = narrow ? loB + (lane & 15) : loB + lane;
+        const bool hasA = narrow ? lane < 16 : true, hasB = narrow ? lane >= 16 : true;
+        double vA = INFINITY, vB = INFINITY;
+        if (hasA && kA < m0) {
+            const double v = sample_w64_ek(F, R, kA, m0, ln.h64, beta, ek, pd.mat);
+            vA = v == v ? v : INFINITY;
         }
+        if (hasB && kB < L) {
+            const double v = sample_w64_ek(F, R, kB, m0, ln.h64, beta, ek, pd.mat);
+            vB = v == v ? v : INFINITY;
+        }
+        auto valA = [&](int k) { return __shfl_sync(kFull, vA, k - loA); };
+        auto valB = [&](int k) { return __shfl_sync(kFull, vB, narrow ? 16 + k - loB : k - loB); };
+        wa = valA(a);
+        wb = valB(b);
+        if (!(wa < INFINITY && wb < INFINITY)) return false;
+        bool settled = false;
+        for (int it = 0; it < 64 && !settled; ++it) {
+            const double s = (wb - wa) / (double)(b - a);
+            int na, nb;
+            if (narrow) {
+                const bool left = lane < 16;
+                const double v = left ? vA : vB;
+                const int k = left ? kA : kB;
+                double e = v < INFINITY ? v - s * (double)(k - m0) : INFINITY;
+                int kk = v < INFINITY ? k : (left ? INT_MAX : -1);
+                half_min_dk(e, kk, left);
+                na = __shfl_sync(kFull, kk, 0);
+                nb = __shfl_sync(kFull, kk, 16);
+            } else {
+                double eA = vA < INFINITY ? vA - s * (double)(kA - m0) : INFINITY;
+                double eB = vB < INFINITY ? vB - s * (double)(kB - m0) : INFINITY;
+                int ka = vA < INFINITY ? kA : INT_MAX, kb = vB < INFINITY ? kB : -1;
+                warp_min_dk(eA, ka, true);
+                warp_min_dk(eB, kb, false);
+                na = ka;
+                nb = kb;
+            }
+            if (na == INT_MAX || nb < 0) return false;
+            settled = na == a && nb == b;
+            a = na;
+            b = nb;
+            wa = valA(a);
+            wb = valB(b);
+        }
+        if (!settled) return false;
+        // certificate over the samples outside the windows and the centre
+        const double s = (wb - wa) / (double)(b - a);
+        const float la = (float)(kap * wa - C), ls = (float)(kap * s);
+        const int hiA = min(loA + W, m0), hiB = min(loB + W, L);
+        double eL = INFINITY, eR = INFINITY;  // lowest v - s x of FP64 samples on or below
+        int kL = INT_MAX, kR = -1;            // the chord, per side
+        unsigned c64 = 0;
+        for (int k = lane; k < L; k += 32) {
+            if (k == m0 || (k >= loA && k < hiA) || (k >= loB && k < hiB)) continue;
+            const float v32 =
+                sample_w<CVX_ENERGY_NH_DAMAGE>(nc.nl, dl, __fmul_rn((float)(k - m0), ln.h32));
+            if (v32 < INFINITY && v32 > -INFINITY) {
+                const float x = (float)(k - a);
+                const float Lv = __fmaf_rn(ls, x, la);
+                const float err = 2.0f * kU32 * (fabsf(la) + fabsf(ls * x) + fabsf(Lv)) +
+                                  kEps32 * fmaxf(kapf, fabsf(v32) + Cf) + 1e-30f;
+                if (__fsub_rn(v32, Lv) > 1.001f * err) continue;  // above the chord
+            }
+            ++c64;
+            const double v = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
+            if (!(v == v)) continue;  // det <= 0: excluded
+            const double line = wa + s * (double)(k - a);
+            if (v > line + 1e-14 * fabs(line)) continue;
+            const double e = v - s * (double)(k - m0);
+            if (k < m0) {
+                if (e < eL || (e == eL && k < kL)) {
+                    eL = e;
+                    kL = k;
+                }
+            } else if (e < eR || (e == eR && k > kR)) {
+                eR = e;
+                kR = k;
+            }
+        }
+        n64 += c64;
+        warp_min_dk(eL, kL, true);
+        warp_min_dk(eR, kR, false);
+        if (kL == INT_MAX && kR < 0) return true;  // certified
+        if (kL != INT_MAX) a = kL;
+        if (kR >= 0) b = kR;
     }
-    return __all_sync(kFull, good);
+    return false;
 }
 
 // k_refine: one warp per screened (node, direction).  The FP64 bridge of the
@@ -754,6 +780,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
     const int nwork = P.cnt[(P.K + 1) + level];
     const int32_t *qp = P.qp[level], *qh = P.qh[level];
     unsigned long long n_full = 0;
+    unsigned n_spot = 0;  // FP64 spot samples of the certificates (per lane)
     for (int w = blockIdx.x * (blockDim.x >> 5) + warp; w < nwork;
          w += gridDim.x * (blockDim.x >> 5)) {
         const int2 wk = P.work[w];
@@ -775,7 +802,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
             int a, b;
             double wa = 0.0, wb = 0.0;
             bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, P.dir32[pd.dir_off + dir], hab,
-                                    lane, a, b, wa, wb);
+                                    lane, a, b, wa, wb, n_spot);
             if (!ok) {
                 ++n_full;
                 const double ek = P.cands[qi].ek;
@@ -890,6 +917,8 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         __syncwarp();
     }
     if (lane == 0) add_counter(P.counters, C_REFFULL, n_full);
+    n_spot = __reduce_add_sync(kFull, n_spot);
+    if (lane == 0) add_counter(P.counters, C_FP64, n_spot);
 }
 
 // -------------------------------------------------------------------------
@@ -927,22 +956,33 @@ __global__ void k_commit(const Pipe P, int level) {
         // gap_tol between the proposed laminate and the window's value, defers
         // the node to the full scan
         atomicAdd(P.counters + C_WNODES, 1ull);
-        bool fb = false;
+        bool border = false;
+        int gd = -1;
         if (bc >= 0 && ro[bc].q < nd.w) {
-            const int gd = nc.dir[bc];
+            gd = nc.dir[bc];
             const int2 c = P.center[qi];
             int di = (gd / pd.Nb - c.x) % pd.Na, dj = (gd % pd.Nb - c.y) % pd.Nb;
             if (di < 0) di += pd.Na;
             if (dj < 0) dj += pd.Nb;
             if (di > pd.Na / 2) di -= pd.Na;
             if (dj > pd.Nb / 2) dj -= pd.Nb;
-            fb |= abs(di) >= pd.window || abs(dj) >= pd.window;
+            border = abs(di) >= pd.window || abs(dj) >= pd.window;
         }
         const double gap = ((pd.flags & CVX_FLAG_GAP_ONE_SIDED) ? V - P.e_pred[qi]
                                                                 : fabs(P.e_pred[qi] - V)) /
                            (1e-8 + fabs(V));
-        fb |= !(gap <= pd.gap_tol);
-        if (fb) {
+        const bool gap_fail = !(gap <= pd.gap_tol);
+        if (border && !gap_fail && P.nx_p) {
+            // re-centre the window on its border minimum and scan it again
+            const int pos = atomicAdd(P.nx_cnt + level, 1);
+            P.nx_p[pos] = p;
+            P.nx_h[pos] = hi;
+            P.nx_cen[pos] = make_int2(gd / pd.Nb, gd % pd.Nb);
+            P.nx_ep[pos] = P.e_pred[qi];
+            atomicAdd(P.counters + C_RECENTRED, 1ull);
+            return;
+        }
+        if (border || gap_fail) {
             const int pos = atomicAdd(P.fcnt + level, 1);
             P.fq_p[level][pos] = p;
             P.fq_h[level][pos] = hi;
@@ -1109,6 +1149,8 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
     const size_t o_ref = take(sizeof(RefineOut) * maxq * kNodeCand);
     const size_t o_nu = take(sizeof(int) * maxq);
     size_t o_fqp[kMaxDepth], o_fqh[kMaxDepth], o_fcnt = 0, o_fictr = 0, o_cen = 0, o_ep = 0;
+    size_t o_rqp[2] = {0, 0}, o_rqh[2] = {0, 0}, o_rcen[2] = {0, 0}, o_rep[2] = {0, 0};
+    size_t o_rcnt = 0, o_ritem = 0;
     if (window) {
         for (int l = 0; l < K; ++l) {
             o_fqp[l] = take(sizeof(int32_t) * ((size_t)N << l));
@@ -1118,6 +1160,14 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         o_fictr = take(sizeof(unsigned long long) * (K + 1));
         o_cen = take(sizeof(int2) * maxq);
         o_ep = take(sizeof(double) * maxq);
+        for (int b = 0; b < 2; ++b) {
+            o_rqp[b] = take(sizeof(int32_t) * maxq);
+            o_rqh[b] = take(sizeof(int32_t) * maxq);
+            o_rcen[b] = take(sizeof(int2) * maxq);
+            o_rep[b] = take(sizeof(double) * maxq);
+        }
+        o_rcnt = take(sizeof(int32_t) * 2 * (K + 1) * kMaxRecentre);
+        o_ritem = take(sizeof(unsigned long long) * (K + 1) * kMaxRecentre);
     }
     if (pp) {
         Pipe &p = *pp;
@@ -1144,6 +1194,17 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         p.fitem_ctr = window ? (unsigned long long *)(ws + o_fictr) : nullptr;
         p.center = window ? (int2 *)(ws + o_cen) : nullptr;
         p.e_pred = window ? (double *)(ws + o_ep) : nullptr;
+        for (int b = 0; b < 2; ++b) {
+            p.rq_p[b] = window ? (int32_t *)(ws + o_rqp[b]) : nullptr;
+            p.rq_h[b] = window ? (int32_t *)(ws + o_rqh[b]) : nullptr;
+            p.rcen[b] = window ? (int2 *)(ws + o_rcen[b]) : nullptr;
+            p.rep[b] = window ? (double *)(ws + o_rep[b]) : nullptr;
+        }
+        p.rcnt = window ? (int32_t *)(ws + o_rcnt) : nullptr;
+        p.ritem = window ? (unsigned long long *)(ws + o_ritem) : nullptr;
+        p.nx_p = p.nx_h = p.nx_cnt = nullptr;
+        p.nx_cen = nullptr;
+        p.nx_ep = nullptr;
     }
     return off;
 }
@@ -1154,6 +1215,34 @@ size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window) {
 
 void pipe_layout(Pipe &p, char *ws) {
     pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs, p.window != 0);
+}
+
+Pipe window_pipe(const Pipe &p, int level, int r, int R) {
+    Pipe q = p;
+    q.pass = PASS_WINDOW;
+    if (r > 0) {
+        const int b = (r - 1) & 1;
+        q.cnt = p.rcnt + (size_t)2 * (p.K + 1) * (r - 1);
+        q.item_ctr = p.ritem + (size_t)(p.K + 1) * (r - 1);
+        q.qp[level] = p.rq_p[b];
+        q.qh[level] = p.rq_h[b];
+        q.center = p.rcen[b];
+        q.e_pred = p.rep[b];
+        q.ncnt = p.cnt;  // children go to the level queue of the next level
+    }
+    if (r < R) {
+        const int b = r & 1;
+        q.nx_p = p.rq_p[b];
+        q.nx_h = p.rq_h[b];
+        q.nx_cen = p.rcen[b];
+        q.nx_ep = p.rep[b];
+        q.nx_cnt = p.rcnt + (size_t)2 * (p.K + 1) * r;
+    } else {
+        q.nx_p = q.nx_h = q.nx_cnt = nullptr;
+        q.nx_cen = nullptr;
+        q.nx_ep = nullptr;
+    }
+    return q;
 }
 
 Pipe fallback_pipe(const Pipe &p, int level) {
@@ -1188,6 +1277,12 @@ cudaError_t pipe_begin(const Pipe &p, cudaStream_t s) {
             return e;
         if ((e = cudaMemsetAsync(p.fitem_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
             cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(p.rcnt, 0, sizeof(int32_t) * 2 * (p.K + 1) * kMaxRecentre, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(p.ritem, 0, sizeof(unsigned long long) * (p.K + 1) * kMaxRecentre,
+                                 s)) != cudaSuccess)
             return e;
     }
     k_init<<<(unsigned)((p.N + 255) / 256), 256, 0, s>>>(p);

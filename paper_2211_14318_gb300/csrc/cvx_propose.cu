@@ -250,6 +250,11 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     // pageable source: returns once staged
     CK(cudaMemcpyAsync((void *)pp.probs, &pd, sizeof pd, cudaMemcpyHostToDevice, s),
        "surrogate_propose/table");
+    const int R = p->recentre;
+    std::vector<cudaEvent_t> ev;  // window passes and fallback scan of every level
+    const int per_level = R + 2;
+    rc = scan_events(h, per_level * pp.K, ev);
+    if (rc) return rc;
     CK(pipe_begin(pp, s), "surrogate_propose");
     for (int l = 0; l < pp.K; ++l) {
         const long long max_nodes = n << l;
@@ -262,8 +267,12 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
             k_decode<<<(m + 255) / 256, 256, 0, s>>>(pp, l, (int)off, m, S.out);
             CK(cudaGetLastError(), "surrogate_propose/decode");
         }
-        CK(pipe_level(pp, l, warps, grid, s, nullptr), "surrogate_propose/window");
-        CK(pipe_level(fallback_pipe(pp, l), l, warps, grid, s, nullptr), "surrogate_propose/fallback");
+        cudaEvent_t *evl = ev.empty() ? nullptr : &ev[2 * per_level * l];
+        for (int r = 0; r <= R; ++r)
+            CK(pipe_level(window_pipe(pp, l, r, R), l, warps, grid, s, evl ? evl + 2 * r : nullptr),
+               "surrogate_propose/window");
+        CK(pipe_level(fallback_pipe(pp, l), l, warps, grid, s, evl ? evl + 2 * (R + 1) : nullptr),
+           "surrogate_propose/fallback");
     }
     CK(pipe_end(pp, s), "surrogate_propose");
     if (fell_back) {

@@ -40,6 +40,9 @@ constexpr int kLaneCoop = 6;    // fewer live lines than this: the whole warp on
 constexpr int kConv = 1 << 28;    // bounds settled (pair repeated or within eps/4): no further pass
 constexpr int kDrop = 1 << 29;    // lower bound above the node's reference value
 constexpr int kNoPair = 1 << 30;  // a side without a finite sample: no bridge pair
+constexpr int kCert = 1 << 27;    // certified: no sample lies on or below the tangent line at the
+                                  // centre, so the line cannot split the node
+constexpr int kTan = 1 << 26;     // the first pass took the line's tangent slope
 
 // One line of a warp's item.
 struct LaneState {
@@ -52,11 +55,18 @@ struct LaneState {
 struct LaneNode {
     NodeLine nl;
     float C, sa, cb, w0;  // sample shift, tangent-slope constants, FP32 centre sample
+    // centre expansion of the line function for the no-split certificate:
+    // d0 = d(0), B1p = B1 + 2 B2 lg0 (lg0 = log2 J0), gp = dv/dd at d0,
+    // k1e = K1 2^{-d0} (d0 > 0, else 0), invJ0 = 1 / J0
+    float d0, B1p, gp, k1e, invJ0;
+    float d0abs;  // |A0| + |lg0| (|B1| + B2 |lg0|): magnitude of the terms of d0
 };
 
 struct SideMin {
-    float eL, eR;  // minima of v - s x over the left and the right samples
-    int kL, kR;    // pair index of each minimum, -1 if the side has no finite sample
+    float eL, eR;    // minima of v - s x over the left and the right samples
+    int kL, kR;      // pair index of each minimum, -1 if the side has no finite sample
+    float eLf, eRf;  // the same minima over the far samples only (outside the near
+                     // region [2 kf - m0, 2 kn], see line_pass)
 };
 
 __device__ __forceinline__ void side_update(f32x2 B, int k, float &e, int &kk) {
@@ -74,9 +84,11 @@ __device__ __forceinline__ void side_update(f32x2 B, int k, float &e, int &kk) {
 // lane with k0 = 0 also takes the sample next to the centre on the left
 // (x = -1) and the last one on the right (x = m0) as pair m0 / 2.  The
 // samples are those of sample_w (each half of a paired instruction rounds
-// as the scalar one), at t = fl(x h).
+// as the scalar one), at t = fl(x h).  Left pairs k >= kf and right pairs
+// k < kn form the near region (x in [2 kf - m0, -1] and [1, 2 kn]); the far
+// minima leave it out.
 __device__ __forceinline__ SideMin line_pass(const NHPair &c, f32x2 H, float ns, int m0, int k0,
-                                             int kstep) {
+                                             int kstep, int kf = 0, int kn = 0) {
     SideMin r;
     r.eL = r.eR = INFINITY;
     r.kL = r.kR = -1;
@@ -85,24 +97,142 @@ __device__ __forceinline__ SideMin line_pass(const NHPair &c, f32x2 H, float ns,
     const float st = 2.0f * (float)kstep;
     const f32x2 STEP = pk2(st, st);
     f32x2 X = pk2((float)(2 * k0 - m0), (float)(2 * k0 - m0 + 1));
+    int k = k0;
 #pragma unroll 2
-    for (int k = k0; k < np; k += kstep) {
+    for (; k < kf; k += kstep) {
+        side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), k, r.eL, r.kL);
+        X = add2(X, STEP);
+    }
+    r.eLf = r.eL;
+#pragma unroll 2
+    for (; k < np; k += kstep) {
         side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), k, r.eL, r.kL);
         X = add2(X, STEP);
     }
     X = pk2((float)(2 * k0 + 1), (float)(2 * k0 + 2));
+    k = k0;
 #pragma unroll 2
-    for (int k = k0; k < np; k += kstep) {
+    for (; k < kn; k += kstep) {
         side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), k, r.eR, r.kR);
+        X = add2(X, STEP);
+    }
+    float ef = INFINITY;
+    int kk = -1;
+#pragma unroll 2
+    for (; k < np; k += kstep) {
+        side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), k, ef, kk);
         X = add2(X, STEP);
     }
     if ((m0 & 1) && k0 == 0) {
         X = pk2(-1.0f, -1.0f);
         side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), np, r.eL, r.kL);
         X = pk2((float)m0, (float)m0);
-        side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), np, r.eR, r.kR);
+        side_update(fma2(NS, X, sample_nh2(c, mul2(X, H))), np, ef, kk);
+    }
+    r.eRf = ef;
+    if (ef < r.eR) {
+        r.eR = ef;
+        r.kR = kk;
     }
     return r;
+}
+
+// Certificate that a line cannot split its node: with s0 = the line's
+// tangent slope at the centre (the slope of the first pass), every sample
+// m != m0 satisfies v(t_m) - v(0) - s0 x_m > 0 for the FP64 line function,
+// i.e. the tangent line at the centre supports the whole line strictly, so
+// the centre is a strict vertex of the lower hull (Algorithm 1).
+//  - far samples (outside the near region): from the pass's far minimum at
+//    s0 less its rounding bound and the FP32 sample error bound eps, against
+//    the centre sample plus eps;
+//  - near samples (x in [xl, -1] and [1, xr]): the second-order remainder
+//    computed from the centre expansion, so that its error scales with t
+//    instead of with |v|: with u = t cof F:R / J0, ell = log2(1 + u),
+//      d(t) - d0 - d'(0) t = A2 t^2 + B1p (ell - u / ln 2) + B2 ell^2 = Dd,
+//    log1p(u) - u from the series of 2 atanh(u / (2 + u)), and for d0 > 0
+//      v(t) - v(0) - v'(0) t = gp Dd - K1 2^{-d0} (e^{-y} - 1 + y),
+//    y = (d - d0) ln 2 (series), for d0 <= 0 it is (1 + K2) Dd.  A sample is
+//    certified when that value exceeds 16 u ((S1 + |s0|) |x| + (1 + |d0|_abs)
+//    S2 x^2), S1 and S2 the magnitudes of the first- and second-order terms
+//    per sample, built from the absolute sums sum |F_i R_i| and
+//    sum |cof F_i R_i| (so that a cancellation in F:R or cof F:R does not hide
+//    the rounding of its terms): the rounding of the FP32 line constants, of t
+//    and of the FP32 arithmetic, all first- or second-order in t.  Samples
+//    where d changes sign, or |u| or |y| leave the series' range, are not
+//    certified.
+__device__ bool flat_certificate(const LaneNode &N, const DirLine &dl, float4 d32, float h, int m0,
+                                 int xl, int xr, float s0, float eFar, float kap) {
+    const float C = N.C, w0 = N.w0;
+    const float kLn2f = 0.693147180559945309f, kInvLn2 = 1.442695040888963407f;
+    // far samples: every far m has b_m = v_m - s0 x_m >= qf, and its sample
+    // error is at most kEps32 max(kappa', |b_m| + |s0| m0 + C), so the FP64
+    // value exceeds the tangent line at the centre if qf less that bound at
+    // b_m = qf (the worst case) exceeds the centre sample plus its bound
+    if (eFar < INFINITY) {
+        const float qf = eFar - 3.2f * kU32 * (fabsf(eFar) + 2.0f * fabsf(s0) * (float)m0) - 1e-30f;
+        const float ef = kEps32 * fmaxf(kap, fabsf(qf) + fabsf(s0) * (float)m0 + C);
+        if (!(qf - ef > w0 + eps32_at(w0, kap, C))) return false;
+    }
+    const float rJ = dl.cJ * N.invJ0;
+    const float xm = (float)max(-xl, xr);
+    if (!(fabsf(rJ) * xm * h <= 0.25f)) return false;
+    const float dprime = dl.A1 + N.B1p * rJ * kInvLn2;
+    if (!(fabsf(dprime) * xm * h * kLn2f <= 0.5f)) return false;
+    const float A2 = dl.A2, B2 = N.nl.B2, B1p = N.B1p, gp = N.gp, k1e = N.k1e, d0 = N.d0;
+    // absolute sums of the terms of F:R and cof F:R
+    const float R0 = d32.x * d32.z, R1 = d32.x * d32.w, R2 = d32.y * d32.z, R3 = d32.y * d32.w;
+    const float cA = fabsf(N.nl.F[0] * R0) + fabsf(N.nl.F[1] * R1) + fabsf(N.nl.F[2] * R2) +
+                     fabsf(N.nl.F[3] * R3);
+    const float cJA = fabsf(N.nl.cof[0] * R0) + fabsf(N.nl.cof[1] * R1) +
+                      fabsf(N.nl.cof[2] * R2) + fabsf(N.nl.cof[3] * R3);
+    const float rJa = cJA * fabsf(N.invJ0);
+    const float dpa = N.nl.mu * cA + fabsf(B1p) * rJa * kInvLn2;
+    const float S1 = h * gp * dpa;
+    const float S2 = h * h * (gp * (A2 + fabsf(B1p) * rJa * rJa * 0.5f * kInvLn2 +
+                                    B2 * rJa * rJa * kInvLn2 * kInvLn2) +
+                              k1e * kLn2f * kLn2f * dpa * dpa * 0.5f);
+    const float c1 = 16.0f * kU32 * (S1 + fabsf(s0));
+    const float c2 = 16.0f * kU32 * (1.0f + N.d0abs) * S2;
+    bool ok = true;
+    for (int x = xl; x <= xr && ok; ++x) {
+        if (x == 0) continue;
+        const float t = __fmul_rn((float)x, h);
+        const float u = rJ * t;
+        const float z = __fdividef(u, 2.0f + u);
+        const float z2 = z * z;
+        // log1p(u) - u = -u z + 2 z^3 (1/3 + z^2/5 + z^4/7 + z^6/9 + ...)
+        const float lm =
+            __fmaf_rn(2.0f * z * z2,
+                      __fmaf_rn(z2, __fmaf_rn(z2, __fmaf_rn(z2, 1.0f / 9.0f, 1.0f / 7.0f), 0.2f),
+                                1.0f / 3.0f),
+                      -u * z);
+        const float ell = (u + lm) * kInvLn2;
+        const float Dd = __fmaf_rn(A2 * t, t, __fmaf_rn(B1p, lm * kInvLn2, B2 * ell * ell));
+        const float dd = __fmaf_rn(dprime, t, Dd);
+        float rem;
+        if (d0 > 0.0f) {
+            if (!(d0 + dd > 0.0f)) return false;
+            const float y = dd * kLn2f;
+            // e^{-y} - 1 + y = y^2 (1/2 - y/6 + y^2/24 - y^3/120 + y^4/720 - y^5/5040)
+            const float ph =
+                y * y *
+                __fmaf_rn(-y,
+                          __fmaf_rn(-y,
+                                    __fmaf_rn(-y, __fmaf_rn(-y, __fmaf_rn(y, 1.0f / 5040.0f,
+                                                                          -1.0f / 720.0f),
+                                                            1.0f / 120.0f),
+                                              -1.0f / 24.0f),
+                                    1.0f / 6.0f),
+                          0.5f);
+            rem = __fmaf_rn(gp, Dd, -k1e * ph);
+        } else {
+            if (!(d0 + dd <= 0.0f)) return false;
+            rem = gp * Dd;
+        }
+        const float ax = fabsf((float)x);
+        ok = rem > ax * __fmaf_rn(c2, ax, c1);
+    }
+    return ok;
 }
 
 // Warp-wide minimum of one side over the lanes' partial passes.
@@ -193,9 +323,14 @@ __device__ __forceinline__ int lane_window_dir(const ProbDesc &pd, int2 c, int j
 
 }  // namespace
 
-__global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P, int level) {
+#ifndef CVX_LANE_MIN_BLOCKS
+#define CVX_LANE_MIN_BLOCKS 4  // CTAs of 256 threads per SM the registers target
+#endif
+
+__global__ void __launch_bounds__(32 * kLaneWarps, CVX_LANE_MIN_BLOCKS)
+    k_scan_lanes(const Pipe P, int level) {
     __shared__ LaneState s_st[kLaneWarps][kLaneItemMax];
-    __shared__ int s_gd[kLaneWarps][kLaneItemMax];
+    __shared__ float s_ef[kLaneWarps][kLaneItemMax];  // far minimum of the first pass
     __shared__ unsigned short s_live[kLaneWarps][kLaneItemMax];
     __shared__ LaneNode s_nd[kLaneWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -204,11 +339,11 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
     const long long n_items = (long long)n_nodes * P.C;
     const int32_t *qp = P.qp[level], *qh = P.qh[level];
     LaneState *st = s_st[warp];
-    int *gdl = s_gd[warp];
+    float *efl = s_ef[warp];
     unsigned short *live = s_live[warp];
     LaneNode &N = s_nd[warp];
     unsigned long long n_valid = 0;
-    unsigned n_lines = 0, n_drop = 0, n_flat = 0, n_extra = 0;
+    unsigned n_lines = 0, n_drop = 0, n_flat = 0, n_extra = 0, n_cert = 0;
 
     for (;;) {
         long long item = 0;
@@ -231,6 +366,18 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
             d0.A1 = d0.A2 = d0.cJ = 0.0f;
             d0.J0 = N.nl.J0;
             N.w0 = sample_w<CVX_ENERGY_NH_DAMAGE>(N.nl, d0, 0.0f);
+            {
+                const double J0 = N.nl.J0, lg0 = J0 > 0.0 ? log2(J0) : 0.0;
+                const double dc = (double)N.nl.A0 + lg0 * ((double)N.nl.B1 + (double)N.nl.B2 * lg0);
+                const double e2 = exp2(-dc);
+                N.d0 = (float)dc;
+                N.B1p = (float)((double)N.nl.B1 + 2.0 * (double)N.nl.B2 * lg0);
+                N.gp = (float)(dc < 0.0 ? 1.0 + (double)N.nl.K2 : 1.0 + (double)N.nl.K1 * kLn2d * e2);
+                N.k1e = dc > 0.0 ? (float)((double)N.nl.K1 * e2) : 0.0f;
+                N.invJ0 = J0 > 0.0 ? (float)(1.0 / J0) : 0.0f;
+                N.d0abs = (float)(fabs((double)N.nl.A0) +
+                                  fabs(lg0) * (fabs((double)N.nl.B1) + (double)N.nl.B2 * fabs(lg0)));
+            }
         }
         __syncwarp();
         const LineSpec ln = pd.line;
@@ -240,6 +387,10 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
         const int2 cen = win ? P.center[qi] : make_int2(0, 0);
         const float kap = pd.kappa_f, C = N.C, w0 = N.w0, sa = N.sa, cb = N.cb;
         const float epsc = eps32_at(w0, kap, C);
+        // global direction of line j of block blk of this item
+        auto gdir = [&](int blk, int j) {
+            return win ? lane_window_dir(pd, cen, d0 + blk + j) : d0 + blk + j;
+        };
         const f32x2 H = pk2(ln.h32, ln.h32);
         NHPair node = nh_pair_node(N.nl);
         node.J0 = pk2(N.nl.J0, N.nl.J0);
@@ -258,22 +409,30 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
             const int Pn = (nb + 31) >> 5;
             float umin = INFINITY, s_prev = 0.0f;
             bool warm = false;
+            // near region of the no-split certificate: |x| up to Xn samples
+            // (even, at most 0.04 in t and 32 samples)
+            const int np = m0 >> 1;
+            const int Xn = min(min(32, (int)(0.04f / ln.h32)), m0) & ~1;
+            const int kf = max(0, np - Xn / 2), kn = min(np, Xn / 2);
             for (int q = 0; q < Pn; ++q) {
                 const int j = lane * Pn + q;
                 if (j >= nb) break;
-                const int gd = win ? lane_window_dir(pd, cen, d0 + blk + j) : d0 + blk + j;
+                const int gd = gdir(blk, j);
                 const DirLine dl = make_dir_line<CVX_ENERGY_NH_DAMAGE>(N.nl, P.dir32[doff + gd]);
                 const NHPair c = line_pair(node, dl);
+                const bool tangent = !warm;
                 const float s0 = warm ? s_prev : sa * __fmaf_rn(cb, dl.cJ, dl.A1);
-                const Bounds b = pass_bounds(c, H, s0, m0, line_pass(c, H, -s0, m0, 0, 1));
+                const SideMin sm = line_pass(c, H, -s0, m0, 0, 1, kf, kn);
+                const Bounds b = pass_bounds(c, H, s0, m0, sm);
                 LaneState t;
                 t.q_lo = b.q_lo;
                 t.q_hi = b.q_hi;
                 t.s = b.s;
                 t.ab = enc_ab(b.a, b.b);
                 if (b.q_hi - b.q_lo <= 0.25f * eps32_at(b.q_lo, kap, C)) t.ab |= kConv;
+                if (tangent) t.ab |= kTan;
                 st[j] = t;
-                gdl[j] = gd;
+                efl[j] = fminf(sm.eLf, sm.eRf);
                 umin = fminf(umin, b.q_hi);
                 warm = b.a >= 0 && b.q_hi < w0 - epsc;
                 s_prev = b.s;
@@ -315,16 +474,16 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
                     for (int i = lane; i < n_live; i += 32) {
                         const int j = live[i];
                         const DirLine dl =
-                            make_dir_line<CVX_ENERGY_NH_DAMAGE>(N.nl, P.dir32[doff + gdl[j]]);
+                            make_dir_line<CVX_ENERGY_NH_DAMAGE>(N.nl, P.dir32[doff + gdir(blk, j)]);
                         const NHPair c = line_pair(node, dl);
                         LaneState t = st[j];
                         const Bounds b = pass_bounds(c, H, t.s, m0, line_pass(c, H, -t.s, m0, 0, 1));
                         const int ab = enc_ab(b.a, b.b);
-                        const bool same = ab == t.ab;
+                        const bool same = ab == (t.ab & ~kTan);
                         t.q_lo = fmaxf(t.q_lo, b.q_lo);
                         t.q_hi = fminf(t.q_hi, b.q_hi);
                         t.s = b.s;
-                        t.ab = ab;
+                        t.ab = ab | (t.ab & kTan);
                         if (same || t.q_hi - t.q_lo <= 0.25f * eps32_at(t.q_lo, kap, C)) t.ab |= kConv;
                         st[j] = t;
                         um = fminf(um, b.q_hi);
@@ -334,7 +493,7 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
                     for (int i = 0; i < n_live; ++i) {
                         const int j = live[i];
                         const DirLine dl =
-                            make_dir_line<CVX_ENERGY_NH_DAMAGE>(N.nl, P.dir32[doff + gdl[j]]);
+                            make_dir_line<CVX_ENERGY_NH_DAMAGE>(N.nl, P.dir32[doff + gdir(blk, j)]);
                         const NHPair c = line_pair(node, dl);
                         LaneState t = st[j];
                         SideMin sm = line_pass(c, H, -t.s, m0, lane, 32);
@@ -342,11 +501,11 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
                         warp_side(sm.eR, sm.kR);
                         const Bounds b = pass_bounds(c, H, t.s, m0, sm);
                         const int ab = enc_ab(b.a, b.b);
-                        const bool same = ab == t.ab;
+                        const bool same = ab == (t.ab & ~kTan);
                         t.q_lo = fmaxf(t.q_lo, b.q_lo);
                         t.q_hi = fminf(t.q_hi, b.q_hi);
                         t.s = b.s;
-                        t.ab = ab;
+                        t.ab = ab | (t.ab & kTan);
                         if (same || t.q_hi - t.q_lo <= 0.25f * eps32_at(t.q_lo, kap, C)) t.ab |= kConv;
                         __syncwarp();
                         if (lane == 0) st[j] = t;
@@ -368,15 +527,49 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
             }
             const float mref = fminf(w0, U);
             const float thr = mref + eps32_at(mref, kap, C);
+            // lines that would be candidates although they do not split
+            // clearly (their bound does not clear the reference value): try
+            // to certify that they cannot split, so that they need no FP64
+            // refinement.  Only lines whose first pass took the tangent slope
+            // have the far minimum the certificate needs.
+            {
+                int n_try = 0;
+                for (int base = 0; base < nb; base += 32) {
+                    const int j = base + lane;
+                    bool tr = false;
+                    if (j < nb) {
+                        const LaneState s = st[j];
+                        tr = (s.ab & kTan) && !(s.ab & (kDrop | kNoPair)) && !(s.q_hi < w0 - epsc) &&
+                             s.q_lo - eps32_at(s.q_lo, kap, C) <= thr;
+                    }
+                    const unsigned bal = __ballot_sync(kFull, tr);
+                    if (tr) live[n_try + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)j;
+                    n_try += __popc(bal);
+                }
+                __syncwarp();
+                for (int i = lane; i < n_try; i += 32) {
+                    const int j = live[i];
+                    const float4 d32 = P.dir32[doff + gdir(blk, j)];
+                    const DirLine dl = make_dir_line<CVX_ENERGY_NH_DAMAGE>(N.nl, d32);
+                    const float s0 = sa * __fmaf_rn(cb, dl.cJ, dl.A1);
+                    if (flat_certificate(N, dl, d32, ln.h32, m0, 2 * kf - m0, 2 * kn, s0, efl[j], kap))
+                        st[j].ab |= kCert;
+                }
+                __syncwarp();
+            }
             unsigned taken = 0;  // bit t: line lane + 32 t of the block
             unsigned dropm = 0;  // bit t: that line is dropped
+            unsigned certm = 0;  // bit t: that line is certified not to split
             for (int t = 0, j = lane; j < nb; ++t, j += 32) {
                 const LaneState s = st[j];
-                const bool dr = (s.ab & kDrop) || s.q_lo - eps32_at(s.q_lo, kap, C) > thr;
-                dropm |= dr ? 1u << t : 0u;
+                const bool ce = (s.ab & kCert) != 0;
+                const bool dr = !ce && ((s.ab & kDrop) || s.q_lo - eps32_at(s.q_lo, kap, C) > thr);
+                dropm |= (dr || ce) ? 1u << t : 0u;
+                certm |= ce ? 1u << t : 0u;
                 qhi = fminf(qhi, s.q_hi);
                 n_drop += dr ? 1u : 0u;
-                n_flat += (!dr && s.q_lo >= w0 - epsc) ? 1u : 0u;
+                n_cert += ce ? 1u : 0u;
+                n_flat += (!dr && !ce && s.q_lo >= w0 - epsc) ? 1u : 0u;
             }
             bool held_taken = false;
             float nq = INFINITY;
@@ -387,7 +580,7 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
                 for (int t = 0, j = lane; j < nb; ++t, j += 32) {
                     if (((taken | dropm) >> t) & 1u) continue;
                     const float q = st[j].q_lo;
-                    const int gd = gdl[j];
+                    const int gd = gdir(blk, j);
                     if (q < bq || (q == bq && gd < bd)) {
                         bq = q;
                         bd = gd;
@@ -418,8 +611,10 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
                 }
             }
             // what was not kept: the smallest lower bound of the rest
+            // (a certified line cannot split the node nor lower its value
+            // below W(F): it bounds nothing the decision needs)
             for (int t = 0, j = lane; j < nb; ++t, j += 32)
-                if (!((taken >> t) & 1u)) drop = fminf(drop, st[j].q_lo);
+                if (!(((taken | certm) >> t) & 1u)) drop = fminf(drop, st[j].q_lo);
             if (lane < kItemTop && !held_taken) drop = fminf(drop, tq);
             tq = nq;
             td = nd;
@@ -453,7 +648,9 @@ __global__ void __launch_bounds__(32 * kLaneWarps, 4) k_scan_lanes(const Pipe P,
     for (int o = 16; o; o >>= 1) n_valid += __shfl_xor_sync(kFull, n_valid, o);
     n_drop = __reduce_add_sync(kFull, n_drop);
     n_flat = __reduce_add_sync(kFull, n_flat);
+    n_cert = __reduce_add_sync(kFull, n_cert);
     if (lane == 0) {
+        if (n_cert) atomicAdd(P.counters + C_CERT, (unsigned long long)n_cert);
         if (n_lines) atomicAdd(P.counters + C_LINES, (unsigned long long)n_lines);
         if (n_drop) atomicAdd(P.counters + C_BOUNDED, (unsigned long long)n_drop);
         if (n_flat) atomicAdd(P.counters + C_FLAT, (unsigned long long)n_flat);

@@ -309,3 +309,55 @@ def test_full_size_training_and_held_out_quality(cv, orc):
     assert lam.sum() > 50_000
     assert np.mean((da == 0) & (db == 0)) >= 0.85
     assert np.mean((da <= 1) & (db <= 1)) >= 0.99
+
+
+def test_propose_recentring_matches_oracle(cv, orc):
+    """Window re-centring: a fixed network proposing a cell three cells away
+    from point k's full-scan direction, window half-width 1, up to 4
+    re-centrings; the GPU's fallback decisions, directions and W^R against
+    the proposed-form oracle with the same network and re-centring rule."""
+    from oracle import surrogate as osur
+    from paper_2211_14318_gb300 import api, inputs
+
+    F, Fp = inputs.material_points(16, seed=37)
+    mat = _omat(orc)
+    beta = orc.history_update(mat, Fp)
+    Na = Nb = 12
+    sc = orc.Scan(orc.angle_directions(Na, Nb), 151, 0.5, 1)
+    _, _, tro, _ = orc.convexify(mat, sc, F, beta)
+    k = next(q for q in range(16) if tro[q, 0]["flags"] & orc.LAMINATED)
+    r0 = tro[k, 0]
+    d = int(r0["dir"])
+    flat = _constant_net(math.pi * ((d // Nb + 3) % Na) / Na, math.pi * (d % Nb) / Nb, r0["xi"],
+                         tro[k, 2]["F"] - tro[k, 1]["F"])
+    cv.surrogate_set_weights(flat, np.zeros(6), np.ones(6))
+    for depth, R in ((1, 4), (2, 4), (2, 0)):
+        p = api.Params(n_theta_a=Na, n_theta_b=Nb, line_points=151, depth=depth, recentre=R, **MAT)
+        cv.stats(reset=True)
+        r = cv.surrogate_propose(p, F, beta, window=1, gap_tol=1e30, want_tree=True)
+        st = cv.stats(reset=True)
+        WRo, Po, trees = osur.propose_convexify(orc, mat, Na, Nb, 151, 0.5, depth, 1, 1e30, flat,
+                                                np.zeros(6), np.ones(6), F, beta, recentre=R)
+        tg = api.tree_numpy(r["tree"], 16, p.tree_size)
+        WR = r["W_R"].cpu().numpy()
+        fb = r["fell_back"].cpu().numpy()
+        n_rec = sum(rec.get("recentred", 0) for t in trees for rec in t.values())
+        checked = 0
+        for q in range(16):
+            clear = all(rec.get("margin", np.inf) > TIE and rec.get("window_margin", np.inf) > TIE
+                        for rec in trees[q].values() if rec["flags"] & orc.SCANNED)
+            if not clear:
+                continue
+            ofb = any(rec["flags"] & osur.FALLBACK for rec in trees[q].values())
+            assert bool(fb[q]) == ofb, (depth, R, q)
+            for i, rec in trees[q].items():
+                if rec["flags"] & orc.LAMINATED:
+                    assert tg[q, i]["dir"] == rec["dir"], (depth, R, q, i)
+                    assert bool(tg[q, i]["flags"] & api.NODE_FALLBACK) == bool(rec["flags"] & osur.FALLBACK)
+            assert abs(WR[q] - WRo[q]) <= 1e-6 * (1e-8 + abs(WRo[q]))
+            checked += 1
+        assert checked >= 8
+        if R == 0:
+            assert st["recentred"] == 0
+        else:
+            assert st["recentred"] >= 1 and n_rec >= 1

@@ -112,3 +112,42 @@ def test_one_sided_gap_falls_back_on_a_subset(orc):
                 assert fb1 == border
                 seen += 1
     assert seen >= 1
+
+
+def test_recentring_walks_to_the_full_scan_direction(orc):
+    """A fixed network proposing a cell several cells away from the full
+    scan's direction, window half-width 1: without re-centring the window's
+    best lies on its border and the node falls back; with enough re-centrings
+    the window walks to the full scan's direction (a local descent over the
+    angle grid), does not fall back, and the result is the plain method's."""
+    mat, F, beta = _points(orc, 12, 36)
+    Na = Nb = 12
+    sc = orc.Scan(orc.angle_directions(Na, Nb), 151, 0.5, 1)
+    WRo, Po, tro, _ = orc.convexify(mat, sc, F, beta)
+    walked = 0
+    for p in range(F.shape[0]):
+        r = tro[p, 0]
+        if not r["flags"] & orc.LAMINATED or r["margin"] < 1e-9:
+            continue
+        d = int(r["dir"])
+        ia, ib = d // Nb, d % Nb
+        jump = tro[p, 2]["F"] - tro[p, 1]["F"]
+        off = ((ia + 3) % Na, ib)  # three cells away along theta_a
+        flat = _constant_net(math.pi * off[0] / Na, math.pi * off[1] / Nb, r["xi"], jump)
+        kw = dict(Na=Na, Nb=Nb, L=151, t_half=0.5, K=1, w=1, gap_tol=1e30, flat=flat,
+                  mean=np.zeros(6), std=np.ones(6), F=F[p:p + 1], beta=beta[p:p + 1])
+        _, _, t0 = osur.propose_convexify(orc, mat, recentre=0, **kw)
+        WR, P, t6 = osur.propose_convexify(orc, mat, recentre=6, **kw)
+        rec0, rec6 = t0[0][0], t6[0][0]
+        assert rec0["center"] == off and rec6["center"] == off
+        if rec0["flags"] & osur.FALLBACK and not rec6["flags"] & osur.FALLBACK:
+            assert rec6["recentred"] >= 1 and rec6["dir"] == d
+            assert WR[0] == WRo[p]
+            np.testing.assert_array_equal(P[0], Po[p])
+            walked += 1
+        # a result without fallback always is the window's own interior minimum
+        if not rec6["flags"] & osur.FALLBACK and rec6["flags"] & orc.LAMINATED:
+            ca, cb = rec6["last_center"]
+            assert abs(osur._offset(rec6["dir"] // Nb, ca, Na)) < 1
+            assert abs(osur._offset(rec6["dir"] % Nb, cb, Nb)) < 1
+    assert walked >= 2
