@@ -11,9 +11,9 @@
 namespace cvx {
 
 constexpr int kWarpTop = 4;    // best directions kept per warp
-constexpr int kItemTop = 8;    // per work item
+constexpr int kItemTop = 16;   // per work item
 constexpr int kNodeCand = 16;  // candidates refined in FP64 per node
-constexpr int kLaneItemMax = 256;  // directions per work item of the lane-per-line scan
+constexpr int kLaneItemMax = 256;  // lines per block of a work item of the lane-per-line scan
 constexpr int kMaxDepth = 8;
 constexpr int kMaxRecentre = 8;  // window re-centrings per node at most (surrogate_propose)
 // Bound on the FP32 sampling error of v = kappa' W - C in sample units,
@@ -177,11 +177,11 @@ int scan_max_blocks_per_sm(int energy, int warps, int stride);
 bool lane_scan_enabled(int energy);
 int lane_scan_blocks_per_sm();
 cudaError_t launch_scan_lanes(const Pipe &p, int level, int sms, cudaStream_t s);
-// Directions per work item of the lane-per-line scan: whole nodes up to
-// kLaneItemMax directions, smaller items (multiples of 32) when the nodes are
-// too few for every warp of the grid to get two items.
+// Directions per work item of the lane-per-line scan: whole nodes (a warp
+// takes them in blocks of kLaneItemMax lines), smaller items (multiples of
+// 32) when the nodes are too few for every warp of the grid to get two items.
 inline int lane_dirs_per_item(long long n_nodes, int D, long long total_warps, int cap) {
-    int dpi = D < kLaneItemMax ? D : kLaneItemMax;
+    int dpi = D;
     if (cap > 0 && cap < dpi) dpi = cap;
     const long long want = total_warps * 2;
     if (n_nodes * ((D + dpi - 1) / dpi) < want) {
