@@ -61,7 +61,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--form", default="loadpath",
-                    choices=["loadpath", "full-scan", "surrogate", "train"],
+                    choices=["loadpath", "full-scan", "batch", "surrogate", "train"],
                     help="loadpath: the metric's workload (default); full-scan: the 65,536-point "
                          "mesh alone; surrogate: the load path with the older report; train: "
                          "training and inference of the proposal network (own lines)")
@@ -71,6 +71,10 @@ def args_parse():
     ap.add_argument("--window", type=int, default=4, help="surrogate window half-width (cells)")
     ap.add_argument("--recentre", type=int, default=4, help="surrogate window re-centrings")
     ap.add_argument("--lp-nx", type=int, default=512, help="load-path mesh size (512: 1,048,576 points)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="loadpath with N > 1: weak = one load path per rank; strong = one "
+                         "load path split into contiguous point ranges weighted by expected "
+                         "tree size")
     ap.add_argument("--no-extras", action="store_true",
                     help="loadpath: skip the 1M-point L = 201 and the 65,536-point mesh lines")
     ap.add_argument("--gap-one-sided", action="store_true",
@@ -102,6 +106,27 @@ def max_over_ranks(x, dist=None, device=None):
 def whole_job_rate(n_per_rank, ws, steps, t_max_ms):
     """Points all ranks convexified / the slowest rank's time (weak scaling)."""
     return ws * n_per_rank * steps / (t_max_ms / 1e3)
+
+
+def rank_ranges(weights, ws):
+    """Contiguous point ranges [lo, hi) of one problem, one per rank, whose
+    total weights (expected tree size per point) are as equal as contiguous
+    cuts allow: rank r's range ends where the weight prefix sum first reaches
+    (r + 1) / ws of the total."""
+    import numpy as np
+
+    w = np.asarray(weights, dtype=np.float64)
+    c = np.cumsum(w)
+    total = c[-1] if c.size else 0.0
+    cuts = [0]
+    for r in range(1, ws):
+        cuts.append(int(np.searchsorted(c, total * r / ws, side="left")) + 1 if total > 0 else
+                    (w.size * r) // ws)
+    cuts.append(w.size)
+    cuts = [min(max(x, 0), w.size) for x in cuts]
+    for i in range(1, len(cuts)):
+        cuts[i] = max(cuts[i], cuts[i - 1])
+    return [(cuts[r], cuts[r + 1]) for r in range(ws)]
 
 
 def host_cores():
@@ -547,14 +572,29 @@ def run_loadpath(a):
     from paper_2211_14318_gb300 import api, inputs
 
     cv = api.Convexifier(local)
-    path = inputs.load_path(a.lp_nx, n_steps=LP_STEPS, stretch_end=LP_STRETCH, seed=LP_SEED + rank)
-    n = path[0].shape[0]
+    strong = ws > 1 and a.scaling == "strong"
+    path = inputs.load_path(a.lp_nx, n_steps=LP_STEPS, stretch_end=LP_STRETCH,
+                            seed=LP_SEED + (0 if strong else rank))
     K = max(1, min(a.steps, LP_STEPS))
     train = train_proposal(cv, api, inputs, path, dev)
     p = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=LP_LINE, depth=LP_DEPTH,
                    recentre=a.recentre, gap_one_sided=a.gap_one_sided, **MAT)
     pf = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=LP_LINE,
                     depth=LP_DEPTH, **MAT)
+    n_all = path[0].shape[0]
+    lo, hi = 0, n_all
+    if strong:
+        # one problem split into contiguous ranges weighted by expected tree
+        # size: a point past its history at the last timed step (psi0 > beta)
+        # is expected to split (about 3 more scanned nodes at depth 3)
+        bK = torch.zeros(n_all, dtype=torch.float64, device=dev)
+        for j in range(K - 1):
+            bK = cv.history_update(pf, path[j], bK)
+        ps = cv.history_update(pf, path[K - 1])
+        wts = (1.0 + 3.0 * (ps > bK).double()).cpu().numpy()
+        lo, hi = rank_ranges(wts, ws)[rank]
+        path = [x[lo:hi].copy() for x in path]
+    n = path[0].shape[0]
     kw = dict(window=a.window, gap_tol=a.gap_tol)
 
     # ---- warm-up: load steps of the proposed form on the first 65,536 points
@@ -578,7 +618,7 @@ def run_loadpath(a):
                fell_back=torch.empty(n, dtype=torch.uint8, device=dev))
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     gold = {}
-    if rank == 0 and a.lp_nx == 512:
+    if rank == 0 and a.lp_nx == 512 and not strong:
         for k in CHECK_STEPS:
             g = load_golden(f"loadpath512_s{k:02d}")
             if g is not None and k <= K:
@@ -625,8 +665,13 @@ def run_loadpath(a):
     cv.set_profiling(False)
     st = cv.stats(reset=True)
     t_max = max_over_ranks(comp_ms, dist if ws > 1 else None, dev)
-    value = whole_job_rate(n, ws, K, t_max)
-    e2e_value = whole_job_rate(n, ws, K, max_over_ranks(e2e_ms, dist if ws > 1 else None, dev))
+    e2e_max = max_over_ranks(e2e_ms, dist if ws > 1 else None, dev)
+    if strong:  # all ranks together convexified the one problem
+        value = n_all * K / (t_max / 1e3)
+        e2e_value = n_all * K / (e2e_max / 1e3)
+    else:
+        value = whole_job_rate(n, ws, K, t_max)
+        e2e_value = whole_job_rate(n, ws, K, e2e_max)
     peak, sms, mhz, peak_src = fp32_peak_tflops(torch, dev)
 
     if rank == 0:
@@ -677,14 +722,16 @@ def run_loadpath(a):
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": K,
             "warmup": a.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32/f64", "data": "synthetic",
+            "scaling": "strong" if strong else "weak", "vs_baseline": None,
+            "dtype": "bf16/f32/f64", "data": "synthetic",
             "config": {
-                "workload": (f"load path, {a.lp_nx}x{a.lp_nx} Q1 mesh x 4 Gauss points = {n} points, "
+                "workload": (f"load path, {a.lp_nx}x{a.lp_nx} Q1 mesh x 4 Gauss points = {n_all} points, "
                              f"load steps 1..{K} of {LP_STEPS} (stretch 1.0 -> {LP_STRETCH}), history "
                              f"updated, {LP_ANGLES}x{LP_ANGLES} angles, window +-{a.window} "
                              f"re-centred up to {a.recentre} times, L={LP_LINE}, t in [-0.5,0.5], "
                              f"depth {LP_DEPTH}; surrogate-proposed with full-scan fallback"),
                 "form": "surrogate", "points_per_gpu": n, "window": a.window,
+                "rank_range": [lo, hi] if strong else None,
                 "recentre": a.recentre, "gap_tol": a.gap_tol,
                 "fallback_rule": ("border: the window minimum still on the window border after "
                                   "the re-centrings" + ("" if a.gap_tol >= 1e29 else
@@ -1030,12 +1077,106 @@ def run_train(a):
     cv.close()
 
 
+# ------------------------------------------------------------- batched form
+def run_batch(a):
+    """The batched form: 256 meshes with log-uniform point counts in
+    [1e3, 1e5] (about 5.5 M points), per-problem stretch, angle grid (32^2 or
+    64^2), line (513 or 1025) and depth (2 or 3), in one autotuned,
+    graph-captured run; a step is one graph replay over all problems.  Also
+    the same batch with the launch shape fixed to the warp-per-line scan's
+    default (8 warps, no item cap), for the autotuner's gain."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api, inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    probs = inputs.batch_problems(256, seed=0)
+    cache = os.path.join(tempfile.gettempdir(), f"cvx_tune_{os.getpid()}.json")
+    if os.path.exists(cache):
+        os.remove(cache)
+    os.environ["CVX_AUTOTUNE_CACHE"] = cache
+
+    def make(cv):
+        items, total = [], 0
+        for pr in probs:
+            p = api.Params(n_theta_a=pr.n_angle, n_theta_b=pr.n_angle, line_points=pr.L,
+                           depth=pr.depth, **MAT)
+            beta = cv.history_update(p, pr.F_prev)
+            items.append((p, torch.as_tensor(pr.F, device=dev), beta))
+            total += pr.F.shape[0]
+        return items, total
+
+    def timed(cv, items):
+        t0 = time.perf_counter()
+        outs = cv.convexify_batch(items)  # autotune + capture (+ launch)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        for _ in range(a.warmup):
+            cv.convexify_batch(items, outs=outs)
+        torch.cuda.synchronize()
+        cv.stats(reset=True)
+        ms = 0.0
+        for _ in range(a.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cv.convexify_batch(items, outs=outs)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms, setup, cv.stats(reset=True), cv.batch_tuning()
+
+    cv = api.Convexifier(0)
+    items, total = make(cv)
+    ms, setup, st, tune = timed(cv, items)
+    cv.close()
+    # the default launch shape, through the cache file (the library's key:
+    # energy and the set of (L, directions, depth))
+    keys = sorted({f"{pr.L}.{pr.n_angle * pr.n_angle}.{pr.depth}" for pr in probs})
+    with open(cache, "w") as f:
+        f.write("{\n  \"e0_" + "_".join(keys) + "\": [8, 0]\n}\n")
+    cv2 = api.Convexifier(0)
+    items2, _ = make(cv2)
+    ms_def, _, _, tune_def = timed(cv2, items2)
+    cv2.close()
+    os.remove(cache)
+    flop = FLOP_PER_SAMPLE * st["valid_samples"]
+    peak = fp32_peak_tflops(torch, dev)[0]
+    line = {
+        "metric": "quadrature points convexified/s (W^R+P), batched form",
+        "value": total * a.steps / (ms / 1e3), "unit": "points/s", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": {"workload": (f"256 meshes, {total} points (log-uniform 1e3..1e5 per mesh), "
+                                "stretch U[1.1, 1.8], 32^2 or 64^2 angles, L 513 or 1025, "
+                                "depth 2 or 3, one captured CUDA graph per replay"),
+                   "form": "batch"},
+        "autotune": {"warps_per_cta": tune[0], "dirs_per_item_cap": tune[1],
+                     "meaning": "warps 0 = lane-per-line scan", "setup_s": setup,
+                     "default_shape_pts_per_s": total * a.steps / (ms_def / 1e3),
+                     "default_shape": list(tune_def[:2]), "from_cache": tune_def[2],
+                     "gain": ms_def / ms},
+        "step_flop_rate": {"achieved": flop / (ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                           "frac": flop / (ms / 1e3) / 1e12 / peak,
+                           "note": "30 FLOP per valid sample over the whole replay (all kernels): "
+                                   "a lower bound of the line scan's own rate"},
+        "stats": st,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.form == "loadpath":
         run_loadpath(a)
+    elif a.form == "batch":
+        run_batch(a)
     elif a.form == "surrogate":
         run_surrogate(a)
     elif a.form == "train":

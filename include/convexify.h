@@ -200,6 +200,10 @@ typedef struct cvx_stats {
     int64_t lines_certified; /* lines certified not to split their node (the
                                tangent line at the centre supports every
                                sample): no FP64 refinement needed           */
+    int64_t edge_splits;    /* splits with an end on the end of its line
+                               (CVX_NODE_EDGE): the laminate is limited by the
+                               line window t_half (Sec. 4.1 asks for a radius
+                               "sufficiently large")                        */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */
@@ -279,6 +283,18 @@ int cvx_hull_bridge(cvx_handle *h, int64_t n_lines, int32_t L, const float *w,
 int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double *F,
                      const double *beta_k, double *W_R, double *P, cvx_laminate *root,
                      cvx_node *tree, int32_t *status, cvx_stream s);
+
+/* Tangent of the relaxed energy over lamination trees (the tree output of
+ * convexify_points or surrogate_propose with the same parameters): with the
+ * laminates held fixed, Eq. (5.2) differentiated once more, i.e. Algorithm 3
+ * evaluating the second derivative at the leaves,
+ *   A = sum over the leaves of (product of split weights) d^2W/dFdF(F_leaf),
+ * d^2W/dFdF from Eq. (2.12) in FP64.  A is n x 16 (DEVICE), row-major
+ * A[16 p + 4 a + b] = dP_a / dF_b over the row-major entries of F; NaN for a
+ * point whose root does not exist or has det F <= 0.  beta_k (n) and tree
+ * (n x (2^{K+1}-1), K = p->depth) are DEVICE arrays.  Asynchronous. */
+int cvx_tree_tangent(cvx_handle *h, const cvx_params *p, int64_t n, const double *beta_k,
+                     const cvx_node *tree, double *A, cvx_stream s);
 
 /* ------------------------------------------------------------ batched form */
 

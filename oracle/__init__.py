@@ -117,6 +117,8 @@ def lib() -> ctypes.CDLL:
         L.orc_scan_node.argtypes = [vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_convexify.restype = None
         L.orc_convexify.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, i32]
+        L.orc_tree_tangent.restype = None
+        L.orc_tree_tangent.argtypes = [vp, i32, i64, vp, vp, vp]
         L.orc_tree_size.restype = i32
         L.orc_tree_size.argtypes = [i32]
         L.orc_node_size.restype = i32
@@ -320,6 +322,18 @@ def convexify(mat: Material, sc: Scan, F: np.ndarray, beta_k: np.ndarray, nthrea
     lib().orc_convexify(mat.ref, sc.ref, n, _p(F), _p(beta_k), _p(WR), _p(P), _p(tree), _p(st),
                         int(nthreads))
     return WR, P, tree, st
+
+
+def tree_tangent(mat: Material, depth: int, tree: np.ndarray, beta_k: np.ndarray) -> np.ndarray:
+    """Tangent of W^R, (n, 4, 4) with A[p, i, k] = dP_i / dF_k, by Algorithm 3
+    over the given trees (NODE_DTYPE, n x (2^{K+1}-1), xi and weight fields as
+    convexify writes them)."""
+    tree = np.ascontiguousarray(tree, dtype=NODE_DTYPE)
+    n = tree.shape[0]
+    beta_k = np.ascontiguousarray(beta_k, dtype=np.float64).reshape(n)
+    A = np.zeros((n, 16))
+    lib().orc_tree_tangent(mat.ref, int(depth), n, _p(tree), _p(beta_k), _p(A))
+    return A.reshape(n, 4, 4)
 
 
 def cores() -> int:

@@ -649,6 +649,40 @@ static void eval_tree(const orc_material *mat, double beta_k, const orc_node *tr
         P[k] = (1.0 - nd->xi) * Pm[k] + nd->xi * Pp[k];
 }
 
+/* Algorithm 3 for the tangent: the same xi-weighted recursion as eval_tree
+ * applied to the second derivative (Eq. 5.2 differentiated once more with
+ * the laminate held fixed), leaves evaluating orc_tangent. */
+static void eval_tree_tangent(const orc_material *mat, double beta_k, const orc_node *tree,
+                              int32_t i, double A[16])
+{
+    const orc_node *nd = &tree[i];
+    if (!(nd->flags & ORC_LAMINATED)) {
+        orc_tangent(mat, nd->F, beta_k, A);
+        return;
+    }
+    double Am[16], Ap[16];
+    eval_tree_tangent(mat, beta_k, tree, 2 * i + 1, Am);
+    eval_tree_tangent(mat, beta_k, tree, 2 * i + 2, Ap);
+    for (int k = 0; k < 16; ++k)
+        A[k] = (1.0 - nd->xi) * Am[k] + nd->xi * Ap[k];
+}
+
+/* Tangent of W^R at n points from their trees (n x (2^{K+1}-1) nodes, the
+ * layout orc_convexify writes; the tree's xi fields are used). */
+void orc_tree_tangent(const orc_material *mat, int32_t depth, int64_t n, const orc_node *tree,
+                      const double *beta_k, double *A)
+{
+    int32_t nt = (1 << (depth + 1)) - 1;
+    for (int64_t p = 0; p < n; ++p) {
+        if (!(tree[p * nt].flags & ORC_EXISTS)) {
+            for (int k = 0; k < 16; ++k)
+                A[16 * p + k] = NAN;
+            continue;
+        }
+        eval_tree_tangent(mat, beta_k[p], tree + p * nt, 0, A + 16 * p);
+    }
+}
+
 int32_t orc_tree_size(int32_t depth)
 {
     return (1 << (depth + 1)) - 1;

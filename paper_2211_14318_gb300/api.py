@@ -57,7 +57,7 @@ class _Stats(ctypes.Structure):
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
         "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks", "refine_full", "lines_bounded",
-        "lines_flat", "recentred", "lines_certified")]
+        "lines_flat", "recentred", "lines_certified", "edge_splits")]
 
 
 class _Problem(ctypes.Structure):
@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
         "cvx_hull_bridge": [vp, i64, i32, vp, vp, vp, vp, vp],
         "convexify_points": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp, vp, vp],
         "convexify_points_static": [ctypes.POINTER(_Params), i64, vp, vp, vp, vp, vp, vp],
+        "cvx_tree_tangent": [vp, ctypes.POINTER(_Params), i64, vp, vp, vp, vp],
         "convexify_batch": [vp, ctypes.c_int, ctypes.POINTER(_Problem), vp],
         "surrogate_set_weights": [vp, vp, vp, vp],
         "surrogate_get_weights": [vp, vp, vp, vp],
@@ -131,7 +132,7 @@ def exported_symbols() -> Sequence[str]:
     return ("cvx_create", "cvx_destroy", "cvx_last_error", "cvx_get_stats", "cvx_struct_size",
             "cvx_set_tuning", "cvx_set_profiling", "cvx_get_scan_timing",
             "cvx_energy", "cvx_history_update", "cvx_sample_lines", "cvx_hull_bridge",
-            "convexify_points", "convexify_points_static", "convexify_batch",
+            "convexify_points", "convexify_points_static", "convexify_batch", "cvx_tree_tangent",
             "cvx_get_batch_tuning", "surrogate_set_weights", "surrogate_get_weights",
             "surrogate_forward", "surrogate_loss_grad", "surrogate_train", "surrogate_save",
             "surrogate_load", "cvx_gemm_bf16", "surrogate_labels", "surrogate_propose")
@@ -331,6 +332,18 @@ class Convexifier:
                                       _ptr(P), _ptr(root), _ptr(tree), _ptr(st), _stream(stream)),
                "convexify_points")
         return dict(W_R=W_R, P=P, status=st, tree=tree, root=root)
+
+    def tree_tangent(self, p: Params, beta, tree, n: int, stream=None):
+        """Tangent of W^R (n, 4, 4) over a tree output (Algorithm 3 on second
+        derivatives)."""
+        import torch
+
+        beta = self._dev(beta, torch.float64).reshape(n)
+        A = torch.empty(n, 4, 4, dtype=torch.float64, device=beta.device)
+        c = p.c()
+        _check(lib().cvx_tree_tangent(self._h, ctypes.byref(c), n, _ptr(beta), _ptr(tree), _ptr(A),
+                                      _stream(stream)), "cvx_tree_tangent")
+        return A
 
     def convexify_batch(self, problems, outs: Optional[list] = None, want_root: bool = False,
                         stream=None):

@@ -268,6 +268,7 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->lines_flat = (int64_t)c[C_FLAT];
     out->recentred = (int64_t)c[C_RECENTRED];
     out->lines_certified = (int64_t)c[C_CERT];
+    out->edge_splits = (int64_t)c[C_EDGE];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }
@@ -371,6 +372,22 @@ int cvx_hull_bridge(cvx_handle *h, int64_t n_lines, int32_t L, const float *w, i
     DeviceGuard g(h->device);
     CK(launch_hull(n_lines, L, w, m_minus, m_plus, hval, h->d_counters, (cudaStream_t)s),
        "cvx_hull_bridge");
+    return CVX_OK;
+}
+
+int cvx_tree_tangent(cvx_handle *h, const cvx_params *p, int64_t n, const double *beta_k,
+                     const cvx_node *tree, double *A, cvx_stream s) {
+    int rc = check_params(p, false);
+    if (rc) return rc;
+    if (p->depth < 0 || p->depth > kMaxDepth)
+        return fail(CVX_ERR_INVALID_ARG, "depth must be in [0, 8], got %d", p->depth);
+    if (!h) return fail(CVX_ERR_INVALID_ARG, "handle is NULL");
+    if (n < 0) return fail(CVX_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!beta_k || !tree || !A)) return fail(CVX_ERR_INVALID_ARG, "NULL array");
+    DeviceGuard g(h->device);
+    CK(launch_tree_tangent(n, (1 << (p->depth + 1)) - 1, tree, beta_k, material_of(p), A,
+                           (cudaStream_t)s),
+       "cvx_tree_tangent");
     return CVX_OK;
 }
 

@@ -73,6 +73,48 @@ __host__ __device__ inline void stress64(const double F[4], double beta_k, const
     for (int k = 0; k < 4; ++k) P[k] = g * (m.mu * (F[k] - FiT[k]) + m.lam * lj * FiT[k]);
 }
 
+// Tangent d^2 W / dF dF in FP64 (Eq. 2.12 differentiated once more), as a
+// 4 x 4 matrix over the row-major entries of F: A[4 a + b] = dP_a / dF_b.
+// With s = psi0(F), g = dW/ds = 1 - D(max(s, beta_k)), and on loading
+// (s > beta_k) dg/ds = -D'(s) = -(D_inf / D_0) e^{-s/D_0}:
+//   A = g d^2psi0/dF^2 + dg/ds (dpsi0/dF) (x) (dpsi0/dF),
+//   dpsi0/dF = mu F + (lam ln J - mu) F^{-T},
+//   d^2psi0 / dF_aA dF_bB = mu d_ab d_AB + lam G_aA G_bB + (mu - lam ln J) G_aB G_bA,
+// G = F^{-T} (d G_aA / dF_bB = -G_aB G_bA, d ln J / dF = G).
+__device__ inline void tangent64(const double F[4], double beta_k, const Material &m,
+                                 double A[16]) {
+    if (m.energy == CVX_ENERGY_DOUBLE_WELL) {
+        for (int k = 0; k < 16; ++k) A[k] = 0.0;
+        A[0] = 12.0 * F[0] * F[0] - 4.0;
+        A[5] = A[10] = A[15] = 2.0;
+        return;
+    }
+    double lj, J;
+    const double s = psi0_nh64(F, m, &lj, &J);
+    if (!(J > 0.0)) {
+        for (int k = 0; k < 16; ++k) A[k] = nan("");
+        return;
+    }
+    const double beta = s > beta_k ? s : beta_k;
+    const double g = 1.0 - m.Dinf * (1.0 - exp(-beta / m.D0));
+    const double dg = s > beta_k ? -(m.Dinf / m.D0) * exp(-s / m.D0) : 0.0;
+    const double iJ = 1.0 / J;
+    // G = F^{-T} in row-major entries: G_11 = F22/J, G_12 = -F21/J, G_21 = -F12/J, G_22 = F11/J
+    const double G[4] = {F[3] * iJ, -F[2] * iJ, -F[1] * iJ, F[0] * iJ};
+    const double c = m.mu - m.lam * lj;
+    double dp[4];
+    for (int k = 0; k < 4; ++k) dp[k] = m.mu * F[k] - c * G[k];
+    for (int a = 0; a < 2; ++a)
+        for (int aa = 0; aa < 2; ++aa)
+            for (int b = 0; b < 2; ++b)
+                for (int bb = 0; bb < 2; ++bb) {
+                    const int r = 2 * a + aa, q = 2 * b + bb;
+                    const double d2 = (a == b && aa == bb ? m.mu : 0.0) + m.lam * G[r] * G[q] +
+                                      c * G[2 * a + bb] * G[2 * b + aa];
+                    A[4 * r + q] = g * d2 + dg * dp[r] * dp[q];
+                }
+}
+
 // -------------------------------------------------------------------------
 // FP64 line function g(t) = W(F + t R) with g' and g'' in closed form, for the
 // common-tangent refinement of a split.  Along the line

@@ -61,7 +61,7 @@ struct RefineOut {
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
     C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
-    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_NUM
+    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_EDGE, C_NUM
 };
 
 // Pipeline passes over one level's queue.
@@ -203,6 +203,8 @@ cudaError_t launch_sample_lines(int64_t n, const double *F, const double *beta,
                                 LineSpec line, float *w, cudaStream_t s);
 cudaError_t launch_hull(int64_t n, int L, const float *w, int32_t *mm, int32_t *mp, double *h,
                         unsigned long long *counters, cudaStream_t s);
+cudaError_t launch_tree_tangent(int64_t n, int NT, const cvx_node *tree, const double *beta,
+                                Material m, double *A, cudaStream_t s);
 
 // Per-warp shared-memory stride of a line of L samples (16-byte aligned).
 __host__ __device__ inline int line_stride(int L) { return (L + 3) & ~3; }

@@ -99,6 +99,37 @@ cudaError_t launch_sample_lines(int64_t n, const double *F, const double *beta,
     return cudaGetLastError();
 }
 
+// Tangent of W^R over lamination trees (Algorithm 3 on second derivatives):
+// the sum over the leaves of (path weight) d^2W/dFdF(F_leaf).
+__global__ void k_tree_tangent(int64_t n, int NT, const cvx_node *tree, const double *beta,
+                               Material m, double *A) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const cvx_node *tr = tree + p * NT;
+    double acc[16];
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    if (!(tr[0].flags & CVX_NODE_EXISTS) || !(tr[0].w == tr[0].w)) {
+        for (int k = 0; k < 16; ++k) A[16 * p + k] = nan("");
+        return;
+    }
+    for (int i = 0; i < NT; ++i) {
+        const cvx_node &nd = tr[i];
+        if (!(nd.flags & CVX_NODE_EXISTS) || (nd.flags & CVX_NODE_LAMINATED)) continue;
+        const double F[4] = {nd.F[0], nd.F[1], nd.F[2], nd.F[3]};
+        double Al[16];
+        tangent64(F, beta[p], m, Al);
+        for (int k = 0; k < 16; ++k) acc[k] += nd.weight * Al[k];
+    }
+    for (int k = 0; k < 16; ++k) A[16 * p + k] = acc[k];
+}
+
+cudaError_t launch_tree_tangent(int64_t n, int NT, const cvx_node *tree, const double *beta,
+                                Material m, double *A, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_tree_tangent<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(n, NT, tree, beta, m, A);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(128) k_hull(int64_t n, int L, const float *w_in, int32_t *mm,
                                               int32_t *mp, double *hv,
                                               unsigned long long *counters) {

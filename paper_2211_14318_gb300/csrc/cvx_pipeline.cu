@@ -1006,7 +1006,10 @@ __global__ void k_commit(const Pipe P, int level) {
     }
     const RefineOut b = ro[bc];
     int fl = CVX_NODE_LAMINATED;
-    if (b.a == 0 || b.b == pd.line.L - 1) fl |= CVX_NODE_EDGE;
+    if (b.a == 0 || b.b == pd.line.L - 1) {
+        fl |= CVX_NODE_EDGE;
+        atomicAdd(P.counters + C_EDGE, 1ull);
+    }
     if (second == b.q) {
         fl |= CVX_NODE_TIE;
         atomicAdd(P.counters + C_TIES, 1ull);

@@ -68,3 +68,57 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(A()) is None
     assert capsys.readouterr().out == ""
+
+
+def _range_worker(rank, ws, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    # expected tree size per point: 1 + 3 where the point is past its history
+    w = 1.0 + 3.0 * (np.random.default_rng(5).random(10001) < 0.3)
+    lo, hi = bench.rank_ranges(w, ws)[rank]
+    t = torch.tensor([lo, hi], dtype=torch.int64)
+    allr = [torch.zeros(2, dtype=torch.int64) for _ in range(ws)]
+    dist.all_gather(allr, t)
+    q.put((rank, [tuple(x.tolist()) for x in allr], float(w[lo:hi].sum()), float(w.sum())))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_split_one_problem_into_weighted_contiguous_ranges():
+    """Strong-scaling split: every rank computes the same contiguous ranges
+    of one problem; together they cover it exactly once, and the expected
+    tree sizes are balanced to within one point's weight."""
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_range_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in range(2))
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, r0, w0, tot), (_, r1, w1, _) = res
+    assert r0 == r1  # every rank derives the same split
+    (a0, b0), (a1, b1) = r0
+    assert a0 == 0 and b0 == a1 and b1 == 10001
+    assert abs(w0 - w1) <= 4.0 and w0 + w1 == tot
+
+
+def test_rank_ranges_edge_cases():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.rank_ranges([1.0] * 8, 4) == [(0, 2), (2, 4), (4, 6), (6, 8)]
+    assert bench.rank_ranges([], 2) == [(0, 0), (0, 0)]
+    r = bench.rank_ranges([5.0, 1, 1, 1, 1, 1], 2)
+    assert r[0][0] == 0 and r[-1][1] == 6 and r[0][1] == r[1][0]

@@ -442,3 +442,36 @@ def test_newton_refinement_matches_oracle(cv, orc):
     assert np.max(_rel(WR[good], WRo[good]), initial=0) < 1e-6
     Pn = np.linalg.norm(Po, axis=1)
     assert np.max(np.linalg.norm(P[good] - Po[good], axis=1) / (1e-8 + Pn[good]), initial=0) < 1e-5
+
+
+def test_tree_tangent_matches_oracle(cv, orc):
+    """Tangent of W^R (Eq. 5.2 / Algorithm 3 on second derivatives, laminate
+    held fixed): the GPU over its own tree against the oracle's tangent of W
+    summed over the same leaves, and on untied points against the oracle's
+    tree tangent of its own tree (pinned by central differences of the
+    oracle's P); NaN for det F <= 0."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    mat = _omat(orc)
+    F, Fp = inputs.material_points(64, seed=70, lam_hi=1.8)
+    beta = orc.history_update(mat, Fp)
+    F[5] = [1.0, 0.0, 0.0, -1.0]
+    p = api.Params(n_theta_a=16, n_theta_b=16, line_points=201, depth=2, **MAT)
+    out = cv.convexify_points(p, F, beta, want_tree=True)
+    A = cv.tree_tangent(p, beta, out["tree"], 64).cpu().numpy()
+    tree = api.tree_numpy(out["tree"], 64, p.tree_size)
+    assert np.all(np.isnan(A[5]))
+    for q in range(64):
+        if q == 5:
+            continue
+        leaf = (tree[q]["flags"] & api.NODE_EXISTS > 0) & (tree[q]["flags"] & api.NODE_LAMINATED == 0)
+        Ao = sum(tree[q, i]["weight"] * orc.tangent(mat, tree[q, i]["F"], beta[q])
+                 for i in np.nonzero(leaf)[0])
+        np.testing.assert_allclose(A[q], Ao, rtol=1e-12, atol=1e-12 * np.abs(Ao).max())
+    sc = orc.Scan(orc.angle_directions(16, 16), 201, 0.5, 2)
+    _, _, tro, _ = orc.convexify(mat, sc, F, beta)
+    Aor = orc.tree_tangent(mat, 2, tro, beta)
+    compared, untied = _compare_trees(orc, api, tree, tro, 201)
+    untied[5] = False
+    assert untied.sum() > 40
+    np.testing.assert_allclose(A[untied], Aor[untied], rtol=1e-10, atol=1e-10)

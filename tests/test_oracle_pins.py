@@ -477,3 +477,56 @@ def test_directions_cover_half_circle(orc):
     np.testing.assert_allclose(d[:, 0] ** 2 + d[:, 1] ** 2, 1.0, atol=1e-15)
     np.testing.assert_allclose(d[5], [math.cos(math.pi / 4), math.sin(math.pi / 4),
                                       math.cos(2 * math.pi / 3), math.sin(2 * math.pi / 3)])
+
+
+def _stable(orc, t0, t1):
+    """Same lamination decisions (directions, bridge indices, flags)."""
+    return (np.array_equal(t0["dir"], t1["dir"]) and np.array_equal(t0["m_minus"], t1["m_minus"])
+            and np.array_equal(t0["m_plus"], t1["m_plus"])
+            and np.array_equal(t0["flags"], t1["flags"]))
+
+
+def test_relaxed_stress_and_tangent_are_derivatives_of_the_relaxation(orc):
+    """With the laminate fixed, W^R(F) = sum_leaves xi_path W(F + t_leaf R) (the
+    leaves move with F), so P = dW^R/dF (Eq. 5.2, Algorithm 3) and the tree
+    tangent A = dP/dF (the same recursion on second derivatives): central
+    differences of the oracle's own W^R and P, at points whose decisions do
+    not change under the perturbation, match P and A; A is symmetric and at
+    depth 0 it is the tangent of W."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F, Fp = inputs.material_points(24, seed=61, lam_hi=1.8)
+    beta = orc.history_update(mat, Fp)
+    sc = orc.Scan(orc.angle_directions(12, 12), 151, 0.5, 2)
+    WR, P, tr, _ = orc.convexify(mat, sc, F, beta)
+    A = orc.tree_tangent(mat, 2, tr, beta)
+    np.testing.assert_allclose(A, np.transpose(A, (0, 2, 1)), rtol=1e-12, atol=1e-12)
+    d = 1e-6
+    checked = 0
+    for p in range(F.shape[0]):
+        if not tr[p, 0]["flags"] & orc.LAMINATED:
+            continue
+        ok = True
+        dW, dP = np.zeros(4), np.zeros((4, 4))
+        for k in range(4):
+            Fs = np.repeat(F[p:p + 1], 2, axis=0)
+            Fs[0, k] += d
+            Fs[1, k] -= d
+            W2, P2, t2, _ = orc.convexify(mat, sc, Fs, np.repeat(beta[p:p + 1], 2))
+            if not (_stable(orc, t2[0], tr[p]) and _stable(orc, t2[1], tr[p])):
+                ok = False
+                break
+            dW[k] = (W2[0] - W2[1]) / (2 * d)
+            dP[:, k] = (P2[0] - P2[1]) / (2 * d)
+        if not ok:
+            continue
+        np.testing.assert_allclose(dW, P[p], rtol=1e-6, atol=1e-8)
+        np.testing.assert_allclose(dP, A[p], rtol=1e-5, atol=1e-6)
+        checked += 1
+    assert checked >= 5
+    sc0 = orc.Scan(orc.angle_directions(12, 12), 151, 0.5, 0)
+    _, _, t0, _ = orc.convexify(mat, sc0, F[:4], beta[:4])
+    A0 = orc.tree_tangent(mat, 0, t0, beta[:4])
+    for p in range(4):
+        np.testing.assert_array_equal(A0[p], orc.tangent(mat, F[p], beta[p]))
