@@ -61,7 +61,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--form", default="loadpath",
-                    choices=["loadpath", "full-scan", "batch", "surrogate", "train"],
+                    choices=["loadpath", "full-scan", "northstar", "batch", "surrogate", "train"],
                     help="loadpath: the metric's workload (default); full-scan: the 65,536-point "
                          "mesh alone; surrogate: the load path with the older report; train: "
                          "training and inference of the proposal network (own lines)")
@@ -75,6 +75,11 @@ def args_parse():
                     help="loadpath with N > 1: weak = one load path per rank; strong = one "
                          "load path split into contiguous point ranges weighted by expected "
                          "tree size")
+    ap.add_argument("--ns-points", type=int, default=1 << 20,
+                    help="northstar: material points (default 1,048,576)")
+    ap.add_argument("--profile-step", type=int, default=0,
+                    help="loadpath: bracket this timed load step with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--no-extras", action="store_true",
                     help="loadpath: skip the 1M-point L = 201 and the 65,536-point mesh lines")
     ap.add_argument("--gap-one-sided", action="store_true",
@@ -641,8 +646,12 @@ def run_loadpath(a):
         ev[0].record()
         Fd.copy_(Fh, non_blocking=True)
         ev[1].record()
+        if k == a.profile_step:
+            torch.cuda.profiler.start()
         cv.surrogate_propose(p, Fd, beta, out=out, **kw)
         beta = cv.history_update(p, Fd, beta)  # Eq. (2.5) for the next load step
+        if k == a.profile_step:
+            torch.cuda.profiler.stop()
         ev[2].record()
         Wh.copy_(out["W_R"], non_blocking=True)
         Ph.copy_(out["P"], non_blocking=True)
@@ -767,21 +776,22 @@ def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, st
     stored oracle results of 4,096 points (placed at their rows)."""
     import numpy as np
 
-    F, Fp = inputs.surrogate_inputs(NS_POINTS, seed=NS_SEED)
+    npts = getattr(a, "ns_points", NS_POINTS)
+    F, Fp = inputs.surrogate_inputs(npts, seed=NS_SEED)
     p = api.Params(n_theta_a=NS_ANGLES, n_theta_b=NS_ANGLES, line_points=NS_LINE, depth=NS_DEPTH,
                    **MAT)
     beta = cv.history_update(p, Fp).cpu().numpy()
-    g = load_golden("material1m_l201")
+    g = load_golden("material1m_l201") if npts == NS_POINTS else None
     if g is not None:
         F[g["idx"]] = g["F"]
         beta[g["idx"]] = g["beta"]
     Fd = torch.from_numpy(F).to(dev)
     bd = torch.from_numpy(beta).to(dev)
     ms, scan_ms, launches, st, out = timed_full_scan(cv, p, Fd, bd, steps, torch)
-    res = {"workload": (f"{NS_POINTS} material points (F = Q diag(lam, lam^-0.3) Q^T + noise, "
+    res = {"workload": (f"{npts} material points (F = Q diag(lam, lam^-0.3) Q^T + noise, "
                         f"lam ~ U[1, 2]), {NS_ANGLES}x{NS_ANGLES} angles, L={NS_LINE}, "
                         f"t in [-0.5,0.5], depth {NS_DEPTH}, full scan"),
-           "value": NS_POINTS * steps / (ms / 1e3), "unit": "points/s", "steps": steps,
+           "value": npts * steps / (ms / 1e3), "unit": "points/s", "steps": steps,
            "ms_per_step": ms / steps,
            "roofline": roofline_obj(st, scan_ms, launches, ms, peak, sms, mhz, peak_src,
                                     "k_scan_lanes_l201_traffic.json"),
@@ -1169,6 +1179,27 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+def run_northstar(a):
+    """The full scan of material points at 16 x 16 angles, L = 201, depth 2
+    (1,048,576 points by default) on its own: one JSON line."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api, inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    cv = api.Convexifier(0)
+    peak, sms, mhz, peak_src = fp32_peak_tflops(torch, dev)
+    res = north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, a.steps)
+    res.update(metric="quadrature points convexified/s (W^R+P), full scan", n_gpus=1,
+               warmup=2, higher_is_better=True, dtype="f32/f64", data="synthetic")
+    print(json.dumps(res), flush=True)
+    cv.close()
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
@@ -1177,6 +1208,8 @@ def main():
         run_loadpath(a)
     elif a.form == "batch":
         run_batch(a)
+    elif a.form == "northstar":
+        run_northstar(a)
     elif a.form == "surrogate":
         run_surrogate(a)
     elif a.form == "train":
