@@ -34,6 +34,8 @@ NODE_DTYPE = np.dtype(
         ("m_minus", "<i4"),
         ("m_plus", "<i4"),
         ("flags", "<i4"),
+        ("wexp", "<i4"),
+        ("pad", "<i4"),
     ]
 )
 EXISTS, SCANNED, LAMINATED, LEAF, NEWTON = 1, 2, 4, 8, 16
@@ -59,7 +61,7 @@ class _Scan(ctypes.Structure):
         ("depth", ctypes.c_int32),
         ("round32", ctypes.c_int32),
         ("newton", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("adaptive", ctypes.c_int32),
     ]
 
 
@@ -222,14 +224,15 @@ class Scan:
     """Direction set, line (L samples on [-t_half, t_half]) and depth K."""
 
     def __init__(self, dirs: np.ndarray, L: int, t_half: float, depth: int, round32: bool = False,
-                 newton: bool = False):
+                 newton: bool = False, adaptive: int = 0):
         self.dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 4)
         self.L, self.t_half, self.depth, self.round32 = int(L), float(t_half), int(depth), bool(round32)
         self.newton = bool(newton)
+        self.adaptive = int(adaptive)  # window doublings allowed per node
         self._c = _Scan(
             self.dirs.shape[0], self.L,
             self.dirs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-            self.t_half, self.depth, int(self.round32), int(self.newton), 0,
+            self.t_half, self.depth, int(self.round32), int(self.newton), self.adaptive,
         )
 
     @property

@@ -51,7 +51,7 @@ typedef struct {
     int32_t depth;      /* lamination depth K                            */
     int32_t round32;    /* 1: hull decisions on samples rounded to FP32  */
     int32_t newton;     /* 1: refine each split by common-tangent Newton */
-    int32_t pad;
+    int32_t adaptive;   /* > 0: window doublings allowed per node (below)  */
 } orc_scan;
 
 /* One node of the per-point lamination tree in heap layout: node i has
@@ -67,6 +67,8 @@ typedef struct {
     int32_t m_minus; /* bridge vertex sample index (0..L-1)               */
     int32_t m_plus;
     int32_t flags;   /* bit0 exists, bit1 scanned, bit2 laminated, bit3 leaf */
+    int32_t wexp;    /* the node's line window is t_half 2^wexp               */
+    int32_t pad;
 } orc_node;
 
 enum { ORC_EXISTS = 1, ORC_SCANNED = 2, ORC_LAMINATED = 4, ORC_LEAF = 8, ORC_NEWTON = 16 };
@@ -572,9 +574,14 @@ int32_t orc_newton_tangent(const orc_material *m, const double F[4], double beta
  *   V_K(G) = W(G)                              if G does not laminate;
  *   V_K(G) = xi V_{K-1}(F+) + (1-xi) V_{K-1}(F-) otherwise,
  * with (R*, F+-, xi) from the line scan of W at G.  The tree is stored in
- * heap layout; leaves carry the product of split weights (Algorithm 2's xi). */
+ * heap layout; leaves carry the product of split weights (Algorithm 2's xi).
+ *
+ * Adaptive window (sc->adaptive > 0; Sec. 4.1 asks for a radius r
+ * "sufficiently large"): a node whose split has an end on the end of its line
+ * is scanned again with the line window doubled (t_half 2^e, the same L), at
+ * most sc->adaptive doublings; the node's children start from its window. */
 static void build_tree(const orc_material *mat, const orc_scan *sc, double beta_k,
-                       orc_node *tree, int32_t i, int32_t depth_left)
+                       orc_node *tree, int32_t i, int32_t depth_left, int32_t e0)
 {
     orc_node *nd = &tree[i];
     nd->w = orc_energy(mat, nd->F, beta_k);
@@ -584,21 +591,32 @@ static void build_tree(const orc_material *mat, const orc_scan *sc, double beta_
     nd->h = nd->w;
     nd->xi = 0.0;
     nd->margin = INFINITY;
+    nd->wexp = e0;
     if (depth_left == 0) {
         nd->flags |= ORC_LEAF;
         return;
     }
     double h, margin;
-    int32_t mm, mp;
-    int32_t j = orc_scan_node(mat, sc, nd->F, beta_k, NULL, NULL, NULL, NULL, &h, &mm, &mp,
-                              &margin);
+    int32_t mm, mp, j;
+    int32_t m0 = (sc->L - 1) / 2;
+    int32_t e = e0;
+    orc_scan sce = *sc;
+    for (;;) {
+        sce.t_half = ldexp(sc->t_half, e);
+        j = orc_scan_node(mat, &sce, nd->F, beta_k, NULL, NULL, NULL, NULL, &h, &mm, &mp, &margin);
+        if (mm != m0 && (mm == 0 || mp == sc->L - 1) && e < sc->adaptive) {
+            ++e;
+            continue;
+        }
+        break;
+    }
+    nd->wexp = e;
     nd->flags |= ORC_SCANNED;
     nd->dir = j;
     nd->h = h;
     nd->m_minus = mm;
     nd->m_plus = mp;
     nd->margin = margin;
-    int32_t m0 = (sc->L - 1) / 2;
     if (mm == m0) {
         nd->flags |= ORC_LEAF;
         return;
@@ -606,13 +624,13 @@ static void build_tree(const orc_material *mat, const orc_scan *sc, double beta_
     nd->flags |= ORC_LAMINATED;
     double R[4];
     rank_one(sc->dir + 4 * j, R);
-    double hstep = 2.0 * sc->t_half / (double)(sc->L - 1);
+    double hstep = 2.0 * sce.t_half / (double)(sc->L - 1);
     double tm = (double)(mm - m0) * hstep, tp = (double)(mp - m0) * hstep;
     /* Algorithm 2: xi = |F - F-|_1 / |F+ - F-|_1 = (m0 - m-)/(m+ - m-) */
     nd->xi = (double)(m0 - mm) / (double)(mp - mm);
     double tmN, tpN, hN;
     if (sc->newton &&
-        orc_newton_tangent(mat, nd->F, beta_k, R, sc->t_half, tm, tp, h, &tmN, &tpN, &hN)) {
+        orc_newton_tangent(mat, nd->F, beta_k, R, sce.t_half, tm, tp, h, &tmN, &tpN, &hN)) {
         tm = tmN;
         tp = tpN;
         nd->h = hN;
@@ -626,8 +644,8 @@ static void build_tree(const orc_material *mat, const orc_scan *sc, double beta_
     }
     cm->weight = nd->weight * (1.0 - nd->xi);
     cp->weight = nd->weight * nd->xi;
-    build_tree(mat, sc, beta_k, tree, 2 * i + 1, depth_left - 1);
-    build_tree(mat, sc, beta_k, tree, 2 * i + 2, depth_left - 1);
+    build_tree(mat, sc, beta_k, tree, 2 * i + 1, depth_left - 1, e);
+    build_tree(mat, sc, beta_k, tree, 2 * i + 2, depth_left - 1, e);
 }
 
 /* Algorithm 3: recursive evaluation of W, P as the xi-weighted sum over
@@ -717,7 +735,7 @@ void orc_convexify(const orc_material *mat, const orc_scan *sc, int64_t n, const
         }
         memcpy(tr[0].F, Fp, sizeof(double) * 4);
         tr[0].weight = 1.0;
-        build_tree(mat, sc, beta_k[p], tr, 0, sc->depth);
+        build_tree(mat, sc, beta_k[p], tr, 0, sc->depth, 0);
         eval_tree(mat, beta_k[p], tr, 0, &W_R[p], P + 4 * p);
         status[p] = ORC_OK;
         if (!tree)

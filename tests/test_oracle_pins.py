@@ -530,3 +530,47 @@ def test_relaxed_stress_and_tangent_are_derivatives_of_the_relaxation(orc):
     A0 = orc.tree_tangent(mat, 0, t0, beta[:4])
     for p in range(4):
         np.testing.assert_array_equal(A0[p], orc.tangent(mat, F[p], beta[p]))
+
+
+def test_adaptive_window_reaches_the_double_well_envelope(orc):
+    """Adaptive line window (Sec. 4.1: the radius must be sufficiently large):
+    the double well's split of F = diag(0, 1) has its ends at F11 = -1 and 1,
+    outside a window of t_half = 0.25.  Without doublings the split ends on
+    the line's ends and W^R > 0; with doublings allowed the window grows to
+    t_half = 2 (the ends at t = +-1 are then interior samples, at 1 the ends
+    would still be on the line's ends), and the result is the closed form:
+    W^R = 0, F+- = diag(+-1, 1), xi = 1/2."""
+    dw = orc.Material(energy=1)
+    F = np.array([[0.0, 0.0, 0.0, 1.0]])
+    sc0 = orc.Scan(orc.angle_directions(4, 4), 101, 0.25, 1)
+    W0, _, t0, _ = orc.convexify(dw, sc0, F, np.zeros(1))
+    assert t0[0, 0]["m_minus"] == 0 and t0[0, 0]["m_plus"] == 100 and W0[0] > 0.1
+    sc = orc.Scan(orc.angle_directions(4, 4), 101, 0.25, 1, adaptive=5)
+    W, P, t, _ = orc.convexify(dw, sc, F, np.zeros(1))
+    r = t[0, 0]
+    assert r["wexp"] == 3 and (r["m_minus"], r["m_plus"]) == (25, 75) and r["xi"] == 0.5
+    assert abs(W[0]) < 1e-12 and np.max(np.abs(P[0])) < 1e-12
+    np.testing.assert_allclose(t[0, 1]["F"], [-1, 0, 0, 1], atol=1e-12)
+    np.testing.assert_allclose(t[0, 2]["F"], [1, 0, 0, 1], atol=1e-12)
+    assert t[0, 1]["wexp"] == 3  # children start from their parent's window
+
+
+def test_adaptive_window_splits_are_interior_or_at_the_cap(orc):
+    """NH with damage: with doublings allowed every split has both ends inside
+    its line unless the node used all its doublings, and with none allowed
+    (the default) the result is the plain method's."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(1.0, 5.0, 0.99, 0.5)
+    F, Fp = inputs.material_points(16, seed=81, lam_hi=1.8)
+    beta = orc.history_update(mat, Fp)
+    dirs = orc.angle_directions(8, 8)
+    W0, _, t0, _ = orc.convexify(mat, orc.Scan(dirs, 101, 0.5, 2), F, beta)
+    Wz, _, tz, _ = orc.convexify(mat, orc.Scan(dirs, 101, 0.5, 2, adaptive=0), F, beta)
+    np.testing.assert_array_equal(W0, Wz)
+    W, _, t, _ = orc.convexify(mat, orc.Scan(dirs, 101, 0.5, 2, adaptive=5), F, beta)
+    lam = (t["flags"] & orc.LAMINATED) > 0
+    assert lam.sum() >= 8
+    edge = (t["m_minus"] == 0) | (t["m_plus"] == 100)
+    assert np.all(~lam | ~edge | (t["wexp"] == 5))
+    assert np.any(lam & (t["wexp"] > 0))
