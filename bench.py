@@ -719,6 +719,8 @@ def run_loadpath(a):
         if not a.no_extras:
             extras["north_star"] = north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz,
                                                    peak_src, K)
+            extras["north_star_adaptive_window"] = north_star_line(
+                a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, 3, doublings=5)
             extras["mesh128"] = mesh128_line(cv, api, torch, dev, peak, sms, mhz, peak_src,
                                              min(K, 5))
         cpu = None
@@ -770,16 +772,19 @@ def run_loadpath(a):
         dist.destroy_process_group()
 
 
-def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, steps):
+def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, steps, doublings=0):
     """1,048,576 material points at 16 x 16 angles, L = 201, depth 2 (the
     full scan): throughput, the line scan's roofline and the error against the
-    stored oracle results of 4,096 points (placed at their rows)."""
+    stored oracle results of 4,096 points (placed at their rows).  With
+    doublings > 0 the adaptive line window (t_half up to 0.5 2^doublings): the
+    same workload with laminates no longer cut at t = +-0.5 (no stored oracle
+    results: its W^R is compared with the fixed window's instead)."""
     import numpy as np
 
     npts = getattr(a, "ns_points", NS_POINTS)
     F, Fp = inputs.surrogate_inputs(npts, seed=NS_SEED)
     p = api.Params(n_theta_a=NS_ANGLES, n_theta_b=NS_ANGLES, line_points=NS_LINE, depth=NS_DEPTH,
-                   **MAT)
+                   window_doublings=doublings, **MAT)
     beta = cv.history_update(p, Fp).cpu().numpy()
     g = load_golden("material1m_l201") if npts == NS_POINTS else None
     if g is not None:
@@ -790,16 +795,27 @@ def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, st
     ms, scan_ms, launches, st, out = timed_full_scan(cv, p, Fd, bd, steps, torch)
     res = {"workload": (f"{npts} material points (F = Q diag(lam, lam^-0.3) Q^T + noise, "
                         f"lam ~ U[1, 2]), {NS_ANGLES}x{NS_ANGLES} angles, L={NS_LINE}, "
-                        f"t in [-0.5,0.5], depth {NS_DEPTH}, full scan"),
+                        f"t in [-0.5,0.5]" + (f" doubled up to {doublings} times per node"
+                                              if doublings else "") +
+                        f", depth {NS_DEPTH}, full scan"),
            "value": npts * steps / (ms / 1e3), "unit": "points/s", "steps": steps,
            "ms_per_step": ms / steps,
            "roofline": roofline_obj(st, scan_ms, launches, ms, peak, sms, mhz, peak_src,
                                     "k_scan_lanes_l201_traffic.json"),
            "stats": st}
-    if g is not None:
+    if g is not None and not doublings:
         it = torch.from_numpy(g["idx"]).to(dev)
         res["accuracy_vs_oracle"] = err_stats(out["W_R"][it].cpu().numpy(), g["W_R"],
                                               out["P"][it].cpu().numpy(), g["P"])
+    if doublings:
+        q = api.Params(n_theta_a=NS_ANGLES, n_theta_b=NS_ANGLES, line_points=NS_LINE,
+                       depth=NS_DEPTH, **MAT)
+        fixed = cv.convexify_points(q, Fd, bd)["W_R"]
+        d = fixed - out["W_R"]  # W units: how much lower the wider windows relax
+        res["W_R_drop_vs_fixed_window"] = {
+            "mean": float(d.mean()), "max": float(d.max()), "min": float(d.min()),
+            "points_lower": float((d > 0).double().mean()),
+            "mean_fixed_W_R": float(fixed.mean())}
     return res
 
 

@@ -121,7 +121,16 @@ typedef struct cvx_params {
 /* CVX_FLAG_GAP_ONE_SIDED (surrogate_propose only): the energy-gap fallback
  * test becomes (V - E_pred) / (1e-8 + |V|) > gap_tol, i.e. a node falls back
  * only when the proposed laminate is better than what its window found. */
+/* CVX_FLAG_WINDOW_DOUBLINGS(n), n = 1..8 (convexify_points and
+ * convexify_batch): adaptive line window.  Sec. 4.1 asks for a radius
+ * "sufficiently large"; a node whose split has an end on the end of its line
+ * (CVX_NODE_EDGE) is scanned again with the line window doubled (t_half 2^e,
+ * the same L), at most n doublings; the node's children start from its
+ * window, and cvx_node.window_exp records e.  0 (the default): the window is
+ * t_half for every node. */
 enum cvx_param_flags { CVX_FLAG_REFINE_NEWTON = 1, CVX_FLAG_GAP_ONE_SIDED = 2 };
+#define CVX_FLAG_WINDOW_DOUBLINGS(n) ((int32_t)(n) << 8)
+#define CVX_WINDOW_DOUBLINGS_OF(flags) (((flags) >> 8) & 15)
 
 /* Node of the per-point lamination tree (Sec. 4.3, Algorithm 2), heap layout:
  * node i has children 2i+1 (F-) and 2i+2 (F+); 2^{K+1}-1 nodes per point. */
@@ -139,7 +148,7 @@ typedef struct cvx_node {
     int32_t m_plus;  /* sample index of F+                                     */
     int32_t flags;   /* CVX_NODE_* bits                                        */
     float gap;       /* FP32 gap between the two best directions' hull values  */
-    int32_t pad;
+    int32_t window_exp; /* the node's line window is t_half 2^window_exp       */
 } cvx_node;
 
 enum cvx_node_flags {
@@ -204,6 +213,8 @@ typedef struct cvx_stats {
                                (CVX_NODE_EDGE): the laminate is limited by the
                                line window t_half (Sec. 4.1 asks for a radius
                                "sufficiently large")                        */
+    int64_t window_doublings; /* nodes rescanned with a doubled line window
+                               (CVX_FLAG_WINDOW_DOUBLINGS)                  */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */

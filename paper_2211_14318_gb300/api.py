@@ -29,7 +29,7 @@ FLAG_REFINE_NEWTON = 1
 NODE_DTYPE = np.dtype([
     ("F", "<f8", (4,)), ("w", "<f8"), ("h", "<f8"), ("xi", "<f8"), ("weight", "<f8"),
     ("dir", "<i4"), ("m_minus", "<i4"), ("m_plus", "<i4"), ("flags", "<i4"),
-    ("gap", "<f4"), ("pad", "<i4"),
+    ("gap", "<f4"), ("window_exp", "<i4"),
 ])
 LAMINATE_DTYPE = np.dtype([
     ("laminated", "<i4"), ("dir", "<i4"), ("m_minus", "<i4"), ("m_plus", "<i4"),
@@ -57,7 +57,7 @@ class _Stats(ctypes.Structure):
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
         "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks", "refine_full", "lines_bounded",
-        "lines_flat", "recentred", "lines_certified", "edge_splits")]
+        "lines_flat", "recentred", "lines_certified", "edge_splits", "window_doublings")]
 
 
 class _Problem(ctypes.Structure):
@@ -162,6 +162,7 @@ class Params:
     newton: bool = False  # CVX_FLAG_REFINE_NEWTON
     gap_one_sided: bool = False  # CVX_FLAG_GAP_ONE_SIDED (surrogate_propose)
     recentre: int = 0  # surrogate_propose: window re-centrings (0..8)
+    window_doublings: int = 0  # adaptive line window: doublings per node (0..8)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
@@ -169,7 +170,8 @@ class Params:
         p.mu, p.lambda_L, p.D_inf, p.D0, p.t_half = self.mu, self.lambda_L, self.D_inf, self.D0, self.t_half
         p.energy, p.n_theta_a, p.n_theta_b = self.energy, self.n_theta_a, self.n_theta_b
         p.line_points, p.depth, p.recentre = self.line_points, self.depth, self.recentre
-        p.flags = (FLAG_REFINE_NEWTON if self.newton else 0) | (2 if self.gap_one_sided else 0)
+        p.flags = ((FLAG_REFINE_NEWTON if self.newton else 0) | (2 if self.gap_one_sided else 0)
+                   | (int(self.window_doublings) << 8))
         if self.dirs is not None:
             d = np.ascontiguousarray(self.dirs, dtype=np.float64).reshape(-1, 4)
             self._keep = [d]

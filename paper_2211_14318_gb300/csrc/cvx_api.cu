@@ -60,8 +60,10 @@ int check_params(const cvx_params *p, bool need_line) {
             return fail(CVX_ERR_INVALID_ARG,
                         "material out of range (mu > 0, lambda >= 0, 0 <= D_inf < 1, D0 > 0)");
     }
-    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED))
+    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED | CVX_FLAG_WINDOW_DOUBLINGS(15)))
         return fail(CVX_ERR_INVALID_ARG, "unknown flags");
+    if (CVX_WINDOW_DOUBLINGS_OF(p->flags) > kMaxRecentre)
+        return fail(CVX_ERR_INVALID_ARG, "window doublings must be in [0, 8]");
     if (p->recentre < 0 || p->recentre > kMaxRecentre)
         return fail(CVX_ERR_INVALID_ARG, "recentre must be in [0, 8], got %d", p->recentre);
     if (!need_line) return CVX_OK;
@@ -269,6 +271,7 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->recentred = (int64_t)c[C_RECENTRED];
     out->lines_certified = (int64_t)c[C_CERT];
     out->edge_splits = (int64_t)c[C_EDGE];
+    out->window_doublings = (int64_t)c[C_DOUBLED];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }
@@ -447,7 +450,8 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
     pp.stride32 = pp.stride64 = pd.line.stride;
     pp.energy = p->energy;
     pp.lanes = lanes ? 1 : 0;
-    const size_t pipe_sz = align_up(pipe_bytes(pp.N, pp.K, pp.C, 1));
+    pp.adaptive = CVX_WINDOW_DOUBLINGS_OF(p->flags);
+    const size_t pipe_sz = align_up(pipe_bytes(pp.N, pp.K, pp.C, 1, false, pp.adaptive > 0));
     const size_t tree_sz = tree ? 0 : sizeof(cvx_node) * (size_t)n * pd.NT;
     rc = ensure_ws(h, pipe_sz + tree_sz, s);
     if (rc) return rc;
@@ -461,7 +465,7 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
        "convexify_points/table");
 
     std::vector<cudaEvent_t> ev;
-    rc = scan_events(h, pp.K, ev);
+    rc = scan_events(h, pp.K * (pp.adaptive + 1), ev);
     if (rc) return rc;
     CK(pipe_enqueue(pp, warps, grid, s, ev.empty() ? nullptr : ev.data()), "convexify_points");
     return CVX_OK;

@@ -139,7 +139,7 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
         return fail(CVX_ERR_UNSUPPORTED, "lane-per-line scan not available for this energy");
     const long long lane_warps = (long long)h->sm_count * lane_scan_blocks_per_sm() * 8;
     lo.table.assign(np, ProbDesc{});
-    int C = 1;
+    int C = 1, A = 0;
     long long off = 0;
     size_t tree_bytes = 0;
     std::vector<size_t> tree_off(np);
@@ -153,6 +153,7 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
         pd.D = p.dirs ? p.n_dirs : p.n_theta_a * p.n_theta_b;
         pd.dir_off = dir_off[i];
         pd.flags = p.flags;
+        A = std::max(A, (int)CVX_WINDOW_DOUBLINGS_OF(p.flags));
         pd.K = p.depth;
         pd.NT = (1 << (p.depth + 1)) - 1;
         pd.dpi = lanes ? lane_dirs_per_item(N, pd.D, lane_warps, dpi_cap)
@@ -180,7 +181,8 @@ int build_layout(cvx_handle *h, int np, const cvx_problem *pr, const std::vector
     pp.stride32 = pp.stride64 = stride;
     pp.energy = energy;
     pp.lanes = lanes ? 1 : 0;
-    const size_t pipe_sz = (pipe_bytes(N, K, C, np) + 255) & ~(size_t)255;
+    pp.adaptive = A;
+    const size_t pipe_sz = (pipe_bytes(N, K, C, np, false, A > 0) + 255) & ~(size_t)255;
     int rc = ensure_ws(h, pipe_sz + tree_bytes, s);
     if (rc) return rc;
     pipe_layout(pp, h->ws);

@@ -61,7 +61,7 @@ struct RefineOut {
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
     C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
-    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_EDGE, C_NUM
+    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_EDGE, C_DOUBLED, C_NUM
 };
 
 // Pipeline passes over one level's queue.
@@ -149,11 +149,15 @@ struct Pipe {
     double *nx_ep;
     // lane-per-line scan (damage energy): 1 selects it for this run's levels
     int lanes;
+    // adaptive line window: the largest number of doublings of any problem
+    // (the rescan passes use the re-centring queues)
+    int adaptive;
     int *node_u;                          // per queued node: smallest FP32 upper bound (f2key)
 };
 
 // Bytes of the workspace part that depends on the shape (see pipe_layout).
-size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window = false);
+size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window = false,
+                  bool rescan = false);
 // Carves the workspace into the Pipe's buffers (p.N, K, C, n_probs, window set).
 void pipe_layout(Pipe &p, char *ws);
 // Enqueues the whole pipeline (zeroing, init, K levels, leaves) on s.
@@ -170,6 +174,20 @@ Pipe fallback_pipe(const Pipe &p, int level);
 // r >= 1: the nodes re-centred by pass r - 1) with re-centring allowed while
 // r < R.
 Pipe window_pipe(const Pipe &p, int level, int r, int R);
+// The Pipe of full-scan pass r of a level with adaptive line windows (0: the
+// level queue; r >= 1: the nodes pass r - 1 sent back with a doubled window),
+// sending nodes back while r < A.
+Pipe rescan_pipe(const Pipe &p, int level, int r, int A);
+
+// The line of a node with window exponent e: spacing h 2^e (exact in FP32
+// and FP64).
+__host__ __device__ inline LineSpec scaled_line(LineSpec l, int e) {
+    if (e) {
+        l.h32 = ldexpf(l.h32, e);
+        l.h64 = ldexp(l.h64, e);
+    }
+    return l;
+}
 int scan_max_blocks_per_sm(int energy, int warps, int stride);
 // Lane-per-line scan (cvx_scan_lanes.cu): whether it serves this energy (the
 // damage energy, unless the environment variable CVX_SCAN_KERNEL is "warp"),

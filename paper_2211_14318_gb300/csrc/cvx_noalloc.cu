@@ -79,6 +79,9 @@ extern "C" int convexify_points_static(const cvx_params *p, int64_t n, const dou
     // static limit
     int rc = check_params(p, true);
     if (rc) return rc;
+    if (CVX_WINDOW_DOUBLINGS_OF(p->flags))
+        return err(CVX_ERR_UNSUPPORTED,
+                   "convexify_points_static: adaptive line windows are not supported");
     const int64_t D64 = p->dirs ? (int64_t)p->n_dirs : (int64_t)p->n_theta_a * p->n_theta_b;
     if (D64 < 1 || D64 > kStaticMaxDirs)
         return err(CVX_ERR_INVALID_ARG,

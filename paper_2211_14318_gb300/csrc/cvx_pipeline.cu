@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
     __shared__ float s_w0;
     __shared__ float s_shift;  // the point's sample shift C
     __shared__ float s_sa, s_cb;  // centre-slope constants of the node (damage energy)
+    __shared__ int s_e;           // the node's window exponent
     __shared__ int s_ukey;     // smallest q_hi screened so far in this item (f2key order)
     __shared__ int2 s_c;
     __shared__ unsigned s_hc[kScanWarps][HC_N];
@@ -185,8 +186,9 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
                     s_nl = make_node_line(F, beta, s_pd.mat);
                     s_shift = (float)line_shift(s_pd.mat, beta);
                     s_ukey = f2key(INFINITY);
+                    s_e = nd->window_exp;
                     if (EK == CVX_ENERGY_NH_DAMAGE)
-                        center_slope_consts(s_nl, s_pd.line.h64, s_sa, s_cb);
+                        center_slope_consts(s_nl, scaled_line(s_pd.line, s_e).h64, s_sa, s_cb);
                 }
             }
         }
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(32 * kScanWarps, CVX_SCAN_MIN_BLOCKS) k_scan(c
         if (item >= n_items) break;
         const int ch = (int)(item % P.C);
         if (ch >= pass_chunks(s_pd, P.pass)) continue;
-        const LineSpec ln = s_pd.line;
+        const LineSpec ln = scaled_line(s_pd.line, s_e);
         const LineGeom g{ln.L, ln.m0, ln.nfull};
         float tl[4];
 #pragma unroll
@@ -648,9 +650,8 @@ __device__ __forceinline__ void half_min_dk(double &v, int &k, bool prefer_low) 
 // 4 times.  Returns false if that does not settle (the caller resamples the
 // whole line in FP64); n64 counts the FP64 spot samples.
 __device__ bool refine_hinted(const double F[4], const double R[4], double beta, const NodeCands &nc,
-                              const ProbDesc &pd, float4 d32, int hab, int lane, int &a, int &b,
-                              double &wa, double &wb, unsigned &n64) {
-    const LineSpec ln = pd.line;
+                              const ProbDesc &pd, const LineSpec &ln, float4 d32, int hab, int lane,
+                              int &a, int &b, double &wa, double &wb, unsigned &n64) {
     const int m0 = ln.m0, L = ln.L;
     const double ek = nc.ek;
     a = hab & 0xffff;
@@ -787,10 +788,10 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
         const int qi = wk.x, c = wk.y;
         const int p = qp[qi], hi = qh[qi];
         const ProbDesc &pd = P.probs[P.pid[p]];
-        const LineSpec ln = pd.line;
+        const cvx_node *nd = node_ptr(pd, p, hi);
+        const LineSpec ln = scaled_line(pd.line, nd->window_exp);
         const int m0 = ln.m0;
         const int dir = P.cands[qi].dir[c];
-        const cvx_node *nd = node_ptr(pd, p, hi);
         const double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
         const double *d = P.dir64 + 4 * ((long long)pd.dir_off + dir);
         const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
@@ -801,7 +802,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
             // the scan's FP32 pair as the start, windows in FP64, FP32 certificate
             int a, b;
             double wa = 0.0, wb = 0.0;
-            bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, P.dir32[pd.dir_off + dir], hab,
+            bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, ln, P.dir32[pd.dir_off + dir], hab,
                                     lane, a, b, wa, wb, n_spot);
             if (!ok) {
                 ++n_full;
@@ -990,6 +991,18 @@ __global__ void k_commit(const Pipe P, int level) {
             return;
         }
     }
+    // adaptive line window: a split with an end on the end of its line is
+    // scanned again with the window doubled (Sec. 4.1: r sufficiently large)
+    if (P.pass == PASS_FULL && P.nx_p && bc >= 0 && ro[bc].q < nd.w &&
+        (ro[bc].a == 0 || ro[bc].b == pd.line.L - 1) &&
+        nd.window_exp < CVX_WINDOW_DOUBLINGS_OF(pd.flags)) {
+        nd.window_exp += 1;
+        const int pos = atomicAdd(P.nx_cnt + level, 1);
+        P.nx_p[pos] = p;
+        P.nx_h[pos] = hi;
+        atomicAdd(P.counters + C_DOUBLED, 1ull);
+        return;
+    }
     nd.flags |= CVX_NODE_SCANNED | (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW));
     if (P.pass == PASS_FALLBACK) nd.flags |= CVX_NODE_FALLBACK;
     atomicAdd(P.counters + C_NODES, 1ull);
@@ -1023,14 +1036,15 @@ __global__ void k_commit(const Pipe P, int level) {
     const double *d = P.dir64 + 4 * ((long long)pd.dir_off + nd.dir);
     const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
                          __dmul_rn(d[1], d[3])};
-    double tm = __dmul_rn((double)(b.a - m0), pd.line.h64);
-    double tp = __dmul_rn((double)(b.b - m0), pd.line.h64);
+    const LineSpec lnd = scaled_line(pd.line, nd.window_exp);
+    double tm = __dmul_rn((double)(b.a - m0), lnd.h64);
+    double tp = __dmul_rn((double)(b.b - m0), lnd.h64);
     const bool leaf_children = level + 1 >= pd.K;
     const double beta = pd.beta[p - pd.point_off];
     double xi = (double)(m0 - b.a) / (double)(b.b - b.a);
     if (pd.flags & CVX_FLAG_REFINE_NEWTON) {
         double hN;
-        if (newton_tangent64(nd.F, R, beta, pd.mat, pd.line.h64 * m0, b.q, tm, tp, hN)) {
+        if (newton_tangent64(nd.F, R, beta, pd.mat, lnd.h64 * m0, b.q, tm, tp, hN)) {
             xi = -tm / (tp - tm);
             nd.h = hN;
             nd.flags |= CVX_NODE_NEWTON;
@@ -1051,7 +1065,7 @@ __global__ void k_commit(const Pipe P, int level) {
         c.dir = -1;
         c.m_minus = c.m_plus = m0;
         c.gap = 0.0f;
-        c.pad = 0;
+        c.window_exp = nd.window_exp;  // children start from their parent's window
         c.flags = CVX_NODE_EXISTS | (leaf_children ? CVX_NODE_LEAF : 0);
     }
     if (!leaf_children) {
@@ -1129,7 +1143,7 @@ __global__ void k_leaf(const Pipe P) {
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_probs,
-                         bool window) {
+                         bool window, bool rescan) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -1163,6 +1177,8 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         o_fictr = take(sizeof(unsigned long long) * (K + 1));
         o_cen = take(sizeof(int2) * maxq);
         o_ep = take(sizeof(double) * maxq);
+    }
+    if (window || rescan) {
         for (int b = 0; b < 2; ++b) {
             o_rqp[b] = take(sizeof(int32_t) * maxq);
             o_rqh[b] = take(sizeof(int32_t) * maxq);
@@ -1197,14 +1213,15 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         p.fitem_ctr = window ? (unsigned long long *)(ws + o_fictr) : nullptr;
         p.center = window ? (int2 *)(ws + o_cen) : nullptr;
         p.e_pred = window ? (double *)(ws + o_ep) : nullptr;
+        const bool rq = window || rescan;
         for (int b = 0; b < 2; ++b) {
-            p.rq_p[b] = window ? (int32_t *)(ws + o_rqp[b]) : nullptr;
-            p.rq_h[b] = window ? (int32_t *)(ws + o_rqh[b]) : nullptr;
-            p.rcen[b] = window ? (int2 *)(ws + o_rcen[b]) : nullptr;
-            p.rep[b] = window ? (double *)(ws + o_rep[b]) : nullptr;
+            p.rq_p[b] = rq ? (int32_t *)(ws + o_rqp[b]) : nullptr;
+            p.rq_h[b] = rq ? (int32_t *)(ws + o_rqh[b]) : nullptr;
+            p.rcen[b] = rq ? (int2 *)(ws + o_rcen[b]) : nullptr;
+            p.rep[b] = rq ? (double *)(ws + o_rep[b]) : nullptr;
         }
-        p.rcnt = window ? (int32_t *)(ws + o_rcnt) : nullptr;
-        p.ritem = window ? (unsigned long long *)(ws + o_ritem) : nullptr;
+        p.rcnt = rq ? (int32_t *)(ws + o_rcnt) : nullptr;
+        p.ritem = rq ? (unsigned long long *)(ws + o_ritem) : nullptr;
         p.nx_p = p.nx_h = p.nx_cnt = nullptr;
         p.nx_cen = nullptr;
         p.nx_ep = nullptr;
@@ -1212,12 +1229,12 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
     return off;
 }
 
-size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window) {
-    return pipe_carve(nullptr, nullptr, N, K, C, n_probs, window);
+size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window, bool rescan) {
+    return pipe_carve(nullptr, nullptr, N, K, C, n_probs, window, rescan);
 }
 
 void pipe_layout(Pipe &p, char *ws) {
-    pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs, p.window != 0);
+    pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs, p.window != 0, p.adaptive > 0);
 }
 
 Pipe window_pipe(const Pipe &p, int level, int r, int R) {
@@ -1239,6 +1256,32 @@ Pipe window_pipe(const Pipe &p, int level, int r, int R) {
         q.nx_h = p.rq_h[b];
         q.nx_cen = p.rcen[b];
         q.nx_ep = p.rep[b];
+        q.nx_cnt = p.rcnt + (size_t)2 * (p.K + 1) * r;
+    } else {
+        q.nx_p = q.nx_h = q.nx_cnt = nullptr;
+        q.nx_cen = nullptr;
+        q.nx_ep = nullptr;
+    }
+    return q;
+}
+
+Pipe rescan_pipe(const Pipe &p, int level, int r, int A) {
+    Pipe q = p;
+    q.pass = PASS_FULL;
+    if (r > 0) {
+        const int b = (r - 1) & 1;
+        q.cnt = p.rcnt + (size_t)2 * (p.K + 1) * (r - 1);
+        q.item_ctr = p.ritem + (size_t)(p.K + 1) * (r - 1);
+        q.qp[level] = p.rq_p[b];
+        q.qh[level] = p.rq_h[b];
+        q.ncnt = p.cnt;  // children go to the level queue of the next level
+    }
+    if (r < A) {
+        const int b = r & 1;
+        q.nx_p = p.rq_p[b];
+        q.nx_h = p.rq_h[b];
+        q.nx_cen = nullptr;
+        q.nx_ep = nullptr;
         q.nx_cnt = p.rcnt + (size_t)2 * (p.K + 1) * r;
     } else {
         q.nx_p = q.nx_h = q.nx_cnt = nullptr;
@@ -1275,17 +1318,19 @@ cudaError_t pipe_begin(const Pipe &p, cudaStream_t s) {
     if ((e = cudaMemsetAsync(p.item_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
         cudaSuccess)
         return e;
-    if (p.window) {
-        if ((e = cudaMemsetAsync(p.fcnt, 0, sizeof(int32_t) * 2 * (p.K + 1), s)) != cudaSuccess)
-            return e;
-        if ((e = cudaMemsetAsync(p.fitem_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
-            cudaSuccess)
-            return e;
+    if (p.window || p.adaptive) {
         if ((e = cudaMemsetAsync(p.rcnt, 0, sizeof(int32_t) * 2 * (p.K + 1) * kMaxRecentre, s)) !=
             cudaSuccess)
             return e;
         if ((e = cudaMemsetAsync(p.ritem, 0, sizeof(unsigned long long) * (p.K + 1) * kMaxRecentre,
                                  s)) != cudaSuccess)
+            return e;
+    }
+    if (p.window) {
+        if ((e = cudaMemsetAsync(p.fcnt, 0, sizeof(int32_t) * 2 * (p.K + 1), s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(p.fitem_ctr, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
+            cudaSuccess)
             return e;
     }
     k_init<<<(unsigned)((p.N + 255) / 256), 256, 0, s>>>(p);
@@ -1339,9 +1384,14 @@ cudaError_t pipe_enqueue(const Pipe &p, int warps, int grid, cudaStream_t s, cud
     cudaError_t e;
     if (p.N == 0) return cudaSuccess;
     if ((e = pipe_begin(p, s)) != cudaSuccess) return e;
+    const int A = p.adaptive;
     for (int l = 0; l < p.K; ++l)
-        if ((e = pipe_level(p, l, warps, grid, s, ev ? ev + 2 * l : nullptr)) != cudaSuccess)
-            return e;
+        for (int r = 0; r <= A; ++r) {
+            const Pipe q = A ? rescan_pipe(p, l, r, A) : p;
+            if ((e = pipe_level(q, l, warps, grid, s, ev ? ev + 2 * (l * (A + 1) + r) : nullptr)) !=
+                cudaSuccess)
+                return e;
+        }
     return pipe_end(p, s);
 }
 

@@ -174,6 +174,8 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     if (rc) return rc;
     if (!h) return fail(CVX_ERR_INVALID_ARG, "handle is NULL");
     if (p->dirs) return fail(CVX_ERR_INVALID_ARG, "the proposal window needs the angle grid");
+    if (CVX_WINDOW_DOUBLINGS_OF(p->flags))
+        return fail(CVX_ERR_UNSUPPORTED, "surrogate_propose: adaptive line windows are not supported");
     if (window < 0 || 2 * window + 1 > std::min(p->n_theta_a, p->n_theta_b))
         return fail(CVX_ERR_INVALID_ARG, "window must satisfy 0 <= 2 w + 1 <= min(Na, Nb)");
     if (!(gap_tol >= 0.0)) return fail(CVX_ERR_INVALID_ARG, "gap_tol must be >= 0");

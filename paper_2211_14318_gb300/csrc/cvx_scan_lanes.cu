@@ -60,6 +60,7 @@ struct LaneNode {
     // k1e = K1 2^{-d0} (d0 > 0, else 0), invJ0 = 1 / J0
     float d0, B1p, gp, k1e, invJ0;
     float d0abs;  // |A0| + |lg0| (|B1| + B2 |lg0|): magnitude of the terms of d0
+    int e;        // the node's window exponent (line spacing h 2^e)
 };
 
 struct SideMin {
@@ -361,7 +362,8 @@ __global__ void __launch_bounds__(32 * kLaneWarps, CVX_LANE_MIN_BLOCKS)
             const double beta = pd.beta[p - pd.point_off];
             N.nl = make_node_line(F, beta, pd.mat);
             N.C = (float)line_shift(pd.mat, beta);
-            center_slope_consts(N.nl, pd.line.h64, N.sa, N.cb);
+            N.e = nd->window_exp;
+            center_slope_consts(N.nl, scaled_line(pd.line, N.e).h64, N.sa, N.cb);
             DirLine d0;
             d0.A1 = d0.A2 = d0.cJ = 0.0f;
             d0.J0 = N.nl.J0;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(32 * kLaneWarps, CVX_LANE_MIN_BLOCKS)
             }
         }
         __syncwarp();
-        const LineSpec ln = pd.line;
+        const LineSpec ln = scaled_line(pd.line, N.e);
         const int m0 = ln.m0;
         const int D = win ? pd.wD : pd.D, dpi = win ? pd.wdpi : pd.dpi, doff = pd.dir_off;
         const int d0 = ch * dpi, nl_item = min(D, d0 + dpi) - d0;

@@ -475,3 +475,52 @@ def test_tree_tangent_matches_oracle(cv, orc):
     untied[5] = False
     assert untied.sum() > 40
     np.testing.assert_allclose(A[untied], Aor[untied], rtol=1e-10, atol=1e-10)
+
+
+def test_adaptive_window_double_well_closed_form(cv):
+    """Adaptive line window on the double well (the warp-per-line scan):
+    F = diag(0, 1) with t_half = 0.25 needs three doublings before the split
+    diag(+-1, 1) is interior; then W^R = 0, xi = 1/2, P = 0."""
+    from paper_2211_14318_gb300 import api
+
+    p = api.Params(energy=api.ENERGY_DOUBLE_WELL, n_theta_a=4, n_theta_b=4, line_points=101,
+                   t_half=0.25, depth=1, window_doublings=5)
+    cv.stats(reset=True)
+    out = cv.convexify_points(p, np.array([[0.0, 0, 0, 1.0]]), np.zeros(1), want_tree=True)
+    st = cv.stats(reset=True)
+    tr = api.tree_numpy(out["tree"], 1, p.tree_size)[0]
+    assert tr[0]["window_exp"] == 3 and (tr[0]["m_minus"], tr[0]["m_plus"]) == (25, 75)
+    assert tr[0]["xi"] == 0.5 and st["window_doublings"] == 3
+    np.testing.assert_allclose(tr[1]["F"], [-1, 0, 0, 1], atol=1e-12)
+    np.testing.assert_allclose(tr[2]["F"], [1, 0, 0, 1], atol=1e-12)
+    assert abs(out["W_R"].item()) < 1e-12 and np.max(np.abs(out["P"].cpu().numpy())) < 1e-12
+
+
+def test_adaptive_window_matches_oracle(cv, orc):
+    """NH with damage, up to 5 doublings of t_half = 0.5 (|t| up to 16),
+    depth 2: decisions, window exponents and split points bit-exact on untied
+    nodes, W^R and P to the bars; splits are interior unless the node used
+    all its doublings."""
+    from paper_2211_14318_gb300 import api, inputs
+
+    mat = _omat(orc)
+    F, Fp = inputs.material_points(48, seed=82, lam_hi=1.8)
+    beta = orc.history_update(mat, Fp)
+    p = api.Params(n_theta_a=12, n_theta_b=12, line_points=151, t_half=0.5, depth=2,
+                   window_doublings=5, **MAT)
+    out = cv.convexify_points(p, F, beta, want_tree=True)
+    tg = api.tree_numpy(out["tree"], F.shape[0], p.tree_size)
+    sc = orc.Scan(orc.angle_directions(12, 12), 151, 0.5, 2, adaptive=5)
+    WRo, Po, to, _ = orc.convexify(mat, sc, F, beta)
+    compared, untied = _compare_trees(orc, api, tg, to, 151)
+    scanned = (to["flags"] & orc.SCANNED) > 0
+    assert np.all(tg["window_exp"][untied][scanned[untied]] == to["wexp"][untied][scanned[untied]])
+    assert compared >= 48 and untied.mean() > 0.8
+    WR, P = out["W_R"].cpu().numpy(), out["P"].cpu().numpy()
+    assert np.max(_rel(WR[untied], WRo[untied])) < 1e-6
+    Pn = np.linalg.norm(Po, axis=1)
+    assert np.max(np.linalg.norm(P[untied] - Po[untied], axis=1) / (1e-8 + Pn[untied])) < 1e-5
+    lam = (tg["flags"] & api.NODE_LAMINATED) > 0
+    edge = (tg["m_minus"] == 0) | (tg["m_plus"] == 150)
+    assert np.all(~lam | ~edge | (tg["window_exp"] == 5))
+    assert np.any(lam & (tg["window_exp"] > 0))
