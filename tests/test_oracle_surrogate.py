@@ -5,6 +5,7 @@ plain method; the window enumerates (2w + 1)^2 wrapped grid cells."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import mlp
 from oracle import surrogate as osur
@@ -151,3 +152,93 @@ def test_recentring_walks_to_the_full_scan_direction(orc):
             assert abs(osur._offset(rec6["dir"] // Nb, ca, Na)) < 1
             assert abs(osur._offset(rec6["dir"] % Nb, cb, Nb)) < 1
     assert walked >= 2
+
+
+def test_mirror_angles_keep_the_energy(orc):
+    """The reflection of a rank-one direction about the principal axes of F
+    keeps W on every point of the line (isotropy: I1 and J unchanged); a
+    mirror that pairs the axes the wrong way round does not."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat, F, beta = _points(orc, 24, 41)
+    rng = np.random.default_rng(3)
+    F = F + 0.1 * rng.standard_normal(F.shape) * np.array([0, 1, 1, 0])  # break the symmetry of F
+    worst, wrong = 0.0, 0.0
+    for p in range(F.shape[0]):
+        if F[p, 0] * F[p, 3] - F[p, 1] * F[p, 2] <= 0.2:
+            continue
+        ta, tb = rng.uniform(0, math.pi, 2)
+        ma, mb = osur.mirror_angles(F[p], ta, tb)
+        p1, p2 = osur.principal_angles(F[p])
+        for t in (-0.4, -0.1, 0.05, 0.3):
+            def w(a, b):
+                R = np.outer([math.cos(a), math.sin(a)], [math.cos(b), math.sin(b)]).reshape(4)
+                return orc.energy(mat, F[p] + t * R, beta[p])
+            w0 = w(ta, tb)
+            if not np.isfinite(w0):
+                continue
+            worst = max(worst, abs(w(ma, mb) - w0) / (1 + abs(w0)))
+            wrong = max(wrong, abs(w(2 * p2 - ta, 2 * p1 - tb) - w0) / (1 + abs(w0)))
+    assert worst < 1e-12
+    assert wrong > 1e-4
+
+
+def test_mirror_cell_of_a_diagonal_F():
+    """For a diagonal F the principal axes are the coordinate axes, so the
+    mirror of cell (ia, ib) is (-ia, -ib) mod N, half a cell from any
+    rounding boundary."""
+    for F in (np.array([1.3, 0.0, 0.0, 0.9]), np.array([0.8, 0.0, 0.0, 1.2])):
+        for gd in (0, 5, 7 * 16 + 3, 255):
+            mc, dist = osur.mirror_cell(F, gd, 16, 16)
+            assert mc == ((-(gd // 16)) % 16, (-(gd % 16)) % 16)
+            assert dist == pytest.approx(0.5)
+
+
+def test_mirror_window_recovers_the_twin_basin(orc):
+    """Load-path nodes whose hull value over the angles has two mirrored
+    basins (one the full scan's direction d, the other its twin near the
+    mirror cell of d): a fixed network proposing the mirror cell of d makes
+    the window settle in the twin basin, and only the mirror window brings
+    the result back to the plain method's, bit for bit."""
+    from paper_2211_14318_gb300 import inputs
+
+    mat = orc.Material(*MAT)
+    path = inputs.load_path(16, n_steps=20, stretch_end=1.8, seed=7)
+    beta = None
+    for k in range(9):
+        beta = orc.history_update(mat, path[k], beta)
+    Na = Nb = 32
+    dirs = orc.angle_directions(Na, Nb)
+    F0, b0 = path[9][:24], beta[:24]
+    _, _, tr, _ = orc.convexify(mat, orc.Scan(dirs, 151, 0.5, 3), F0, b0)
+    # the level-2 nodes as points of their own (depth 1)
+    F = np.array([tr[p, 6]["F"] for p in range(24) if tr[p, 6]["flags"] & orc.LAMINATED])
+    b = np.array([b0[p] for p in range(24) if tr[p, 6]["flags"] & orc.LAMINATED])
+    sc = orc.Scan(dirs, 151, 0.5, 1)
+    WRo, Po, tro, _ = orc.convexify(mat, sc, F, b)
+    recovered = 0
+    for p in range(F.shape[0]):
+        r = tro[p, 0]
+        if not r["flags"] & orc.LAMINATED or r["margin"] < 1e-9:
+            continue
+        d = int(r["dir"])
+        mc, _ = osur.mirror_cell(F[p], d, Na, Nb)
+        flat = _constant_net(math.pi * mc[0] / Na, math.pi * mc[1] / Nb, r["xi"],
+                             tro[p, 2]["F"] - tro[p, 1]["F"])
+        kw = dict(Na=Na, Nb=Nb, L=151, t_half=0.5, K=1, w=1, gap_tol=1e30, flat=flat,
+                  mean=np.zeros(6), std=np.ones(6), F=F[p:p + 1], beta=b[p:p + 1], recentre=4)
+        W0, _, t0 = osur.propose_convexify(orc, mat, mirror=False, **kw)
+        W1, P1, t1 = osur.propose_convexify(orc, mat, mirror=True, **kw)
+        rec0, rec1 = t0[0][0], t1[0][0]
+        if rec0["flags"] & osur.FALLBACK or rec1["flags"] & osur.FALLBACK:
+            continue
+        if rec0["dir"] != d:  # the window settled in the twin basin
+            assert W0[0] > WRo[p]
+            assert rec1["mirror_won"] and not rec1["mirror_inside"]
+            assert rec1["dir"] == d
+            assert W1[0] == WRo[p]
+            np.testing.assert_array_equal(P1[0], Po[p])
+            recovered += 1
+        else:
+            assert rec1["dir"] == d and W1[0] == WRo[p]
+    assert recovered >= 5
