@@ -70,6 +70,8 @@ def args_parse():
                     help="surrogate energy-gap fallback tolerance (1e30: border test only)")
     ap.add_argument("--window", type=int, default=4, help="surrogate window half-width (cells)")
     ap.add_argument("--recentre", type=int, default=4, help="surrogate window re-centrings")
+    ap.add_argument("--no-mirror", action="store_true",
+                    help="surrogate form without the mirror window (twin basins of an isotropic W)")
     ap.add_argument("--lp-nx", type=int, default=512, help="load-path mesh size (512: 1,048,576 points)")
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="loadpath with N > 1: weak = one load path per rank; strong = one "
@@ -510,14 +512,15 @@ def train_proposal(cv, api, inputs, path, dev):
             "loss_first": float(log[0]), "loss_last": float(log[-1])}
 
 
-def propose_launches(n, K, R):
+def propose_launches(n, K, R, mirror=False):
     """Kernels of this library one surrogate_propose call and its history
     update launch: k_init; per level and 65,536-node chunk the features, five
-    tensor-core GEMMs and the decoding; per level R + 1 window passes and the
-    fallback pass (line scan, select, refine, commit each); k_leaf,
-    k_fell_back; k_history."""
+    tensor-core GEMMs and the decoding; per level R + 1 window passes, R + 1
+    mirror-window passes (with the mirror window) and the fallback pass (line
+    scan, select, refine, commit each); k_leaf, k_fell_back; k_history."""
     chunks = sum(-(-(n << l) // 65536) for l in range(K))
-    return 1 + 7 * chunks + 4 * (R + 2) * K + 3
+    passes = (R + 1) * (2 if mirror else 1) + 1
+    return 1 + 7 * chunks + 4 * passes * K + 3
 
 
 def timed_full_scan(cv, p, F, beta, steps, torch):
@@ -583,7 +586,8 @@ def run_loadpath(a):
     K = max(1, min(a.steps, LP_STEPS))
     train = train_proposal(cv, api, inputs, path, dev)
     p = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=LP_LINE, depth=LP_DEPTH,
-                   recentre=a.recentre, gap_one_sided=a.gap_one_sided, **MAT)
+                   recentre=a.recentre, gap_one_sided=a.gap_one_sided, mirror=not a.no_mirror,
+                   **MAT)
     pf = api.Params(n_theta_a=LP_ANGLES, n_theta_b=LP_ANGLES, line_points=LP_LINE,
                     depth=LP_DEPTH, **MAT)
     n_all = path[0].shape[0]
@@ -729,7 +733,7 @@ def run_loadpath(a):
             cpu1 = loadpath_oracle_rate(path, K, 1, 1)
             cpu["one_core"] = {"value": cpu1["value"], "sample": cpu1["sample"]}
         wn, fb, rc = st["window_nodes"], st["fallbacks"], st["recentred"]
-        first_pass = max(1, wn - rc)
+        first_pass = max(1, wn - rc - st["mirror_windows"])
         line = {
             "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": K,
             "warmup": a.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
@@ -739,9 +743,12 @@ def run_loadpath(a):
                 "workload": (f"load path, {a.lp_nx}x{a.lp_nx} Q1 mesh x 4 Gauss points = {n_all} points, "
                              f"load steps 1..{K} of {LP_STEPS} (stretch 1.0 -> {LP_STRETCH}), history "
                              f"updated, {LP_ANGLES}x{LP_ANGLES} angles, window +-{a.window} "
-                             f"re-centred up to {a.recentre} times, L={LP_LINE}, t in [-0.5,0.5], "
+                             f"re-centred up to {a.recentre} times"
+                             + ("" if a.no_mirror else f", mirror window +-{(a.window + 1) // 2}")
+                             + f", L={LP_LINE}, t in [-0.5,0.5], "
                              f"depth {LP_DEPTH}; surrogate-proposed with full-scan fallback"),
                 "form": "surrogate", "points_per_gpu": n, "window": a.window,
+                "mirror_window": None if a.no_mirror else (a.window + 1) // 2,
                 "rank_range": [lo, hi] if strong else None,
                 "recentre": a.recentre, "gap_tol": a.gap_tol,
                 "fallback_rule": ("border: the window minimum still on the window border after "
@@ -755,11 +762,12 @@ def run_loadpath(a):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": n * 4 * 8,
                     "d2h_bytes_per_step": n * 8 + n * 4 * 8},
-            "gpu_launches": K * propose_launches(n, LP_DEPTH, a.recentre),
+            "gpu_launches": K * propose_launches(n, LP_DEPTH, a.recentre, not a.no_mirror),
             "clocks": ck,
             "accuracy_vs_oracle": acc,
             "fallback": {"window_nodes_first_pass": first_pass, "recentred": rc, "fallback_nodes": fb,
                          "fallback_rate": fb / first_pass,
+                         "mirror_windows": st["mirror_windows"], "mirror_won": st["mirror_won"],
                          "points_with_a_fallback_mean": sum(fell) / len(fell)},
             "full_scan": full, "pareto": pareto, "train": train,
             "per_step_ms": per_step,
@@ -931,7 +939,8 @@ def run_surrogate(a):
 
     # ---- load path
     p = api.Params(n_theta_a=S_ANGLES, n_theta_b=S_ANGLES, line_points=S_LINE, depth=S_DEPTH,
-                   gap_one_sided=a.gap_one_sided, **MAT)
+                   gap_one_sided=a.gap_one_sided, recentre=a.recentre, mirror=not a.no_mirror,
+                   **MAT)
     n = path[0].shape[0]
     sub = np.linspace(0, n - 1, min(a.check_points, n)).astype(int)
     sub_t = torch.from_numpy(sub).to(dev)

@@ -121,6 +121,19 @@ typedef struct cvx_params {
 /* CVX_FLAG_GAP_ONE_SIDED (surrogate_propose only): the energy-gap fallback
  * test becomes (V - E_pred) / (1e-8 + |V|) > gap_tol, i.e. a node falls back
  * only when the proposed laminate is better than what its window found. */
+/* CVX_FLAG_MIRROR_WINDOW (surrogate_propose only): mirror window.  An
+ * isotropic W (Sec. 2: W depends on F through I1 and J) takes the same values
+ * on the line F + t a(x)b and on its reflection F + t (M1 a)(x)(M2 b), M1 and
+ * M2 the reflections about the principal axes of F (F = Q1 S Q2^T,
+ * M = Q diag(1, -1) Q^T, M1 F M2 = F), so the node value over the angles has
+ * mirrored twin basins of nearly equal value on the grid.  A node whose window
+ * split along d is scanned once more in a window of half-width (w + 1) / 2
+ * around the grid cell of the mirror of d (theta_a -> 2 phi1 - theta_a,
+ * theta_b -> 2 phi2 - theta_b, phi the principal angles), with the same
+ * re-centring; it takes the lower of the two values (the lower direction index
+ * on equal values) and falls back to the full scan if the mirror window's best
+ * direction still lies on its border.  Skipped when the mirror window lies
+ * inside the node's last window. */
 /* CVX_FLAG_WINDOW_DOUBLINGS(n), n = 1..8 (convexify_points and
  * convexify_batch): adaptive line window.  Sec. 4.1 asks for a radius
  * "sufficiently large"; a node whose split has an end on the end of its line
@@ -128,7 +141,11 @@ typedef struct cvx_params {
  * the same L), at most n doublings; the node's children start from its
  * window, and cvx_node.window_exp records e.  0 (the default): the window is
  * t_half for every node. */
-enum cvx_param_flags { CVX_FLAG_REFINE_NEWTON = 1, CVX_FLAG_GAP_ONE_SIDED = 2 };
+enum cvx_param_flags {
+    CVX_FLAG_REFINE_NEWTON = 1,
+    CVX_FLAG_GAP_ONE_SIDED = 2,
+    CVX_FLAG_MIRROR_WINDOW = 4
+};
 #define CVX_FLAG_WINDOW_DOUBLINGS(n) ((int32_t)(n) << 8)
 #define CVX_WINDOW_DOUBLINGS_OF(flags) (((flags) >> 8) & 15)
 
@@ -215,6 +232,9 @@ typedef struct cvx_stats {
                                "sufficiently large")                        */
     int64_t window_doublings; /* nodes rescanned with a doubled line window
                                (CVX_FLAG_WINDOW_DOUBLINGS)                  */
+    int64_t mirror_windows; /* surrogate_propose: nodes scanned in a mirror
+                               window (CVX_FLAG_MIRROR_WINDOW)              */
+    int64_t mirror_won;     /* ... whose mirror window held the lower value  */
 } cvx_stats;
 
 /* ----------------------------------------------------------------- handles */

@@ -57,7 +57,8 @@ class _Stats(ctypes.Structure):
         "points", "nodes_scanned", "lines", "valid_samples", "laminated", "fp64_checks",
         "full_passes", "rare_paths", "ties", "iter_caps", "window_steps", "rounds", "fp64_window",
         "fp64_rare", "fp64_center", "refined", "overflow", "window_nodes", "fallbacks", "refine_full", "lines_bounded",
-        "lines_flat", "recentred", "lines_certified", "edge_splits", "window_doublings")]
+        "lines_flat", "recentred", "lines_certified", "edge_splits", "window_doublings",
+        "mirror_windows", "mirror_won")]
 
 
 class _Problem(ctypes.Structure):
@@ -163,6 +164,7 @@ class Params:
     gap_one_sided: bool = False  # CVX_FLAG_GAP_ONE_SIDED (surrogate_propose)
     recentre: int = 0  # surrogate_propose: window re-centrings (0..8)
     window_doublings: int = 0  # adaptive line window: doublings per node (0..8)
+    mirror: bool = False  # CVX_FLAG_MIRROR_WINDOW (surrogate_propose)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Params:
@@ -171,7 +173,7 @@ class Params:
         p.energy, p.n_theta_a, p.n_theta_b = self.energy, self.n_theta_a, self.n_theta_b
         p.line_points, p.depth, p.recentre = self.line_points, self.depth, self.recentre
         p.flags = ((FLAG_REFINE_NEWTON if self.newton else 0) | (2 if self.gap_one_sided else 0)
-                   | (int(self.window_doublings) << 8))
+                   | (4 if self.mirror else 0) | (int(self.window_doublings) << 8))
         if self.dirs is not None:
             d = np.ascontiguousarray(self.dirs, dtype=np.float64).reshape(-1, 4)
             self._keep = [d]

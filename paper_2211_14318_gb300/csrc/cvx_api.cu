@@ -60,7 +60,8 @@ int check_params(const cvx_params *p, bool need_line) {
             return fail(CVX_ERR_INVALID_ARG,
                         "material out of range (mu > 0, lambda >= 0, 0 <= D_inf < 1, D0 > 0)");
     }
-    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED | CVX_FLAG_WINDOW_DOUBLINGS(15)))
+    if (p->flags & ~(CVX_FLAG_REFINE_NEWTON | CVX_FLAG_GAP_ONE_SIDED | CVX_FLAG_MIRROR_WINDOW |
+                     CVX_FLAG_WINDOW_DOUBLINGS(15)))
         return fail(CVX_ERR_INVALID_ARG, "unknown flags");
     if (CVX_WINDOW_DOUBLINGS_OF(p->flags) > kMaxRecentre)
         return fail(CVX_ERR_INVALID_ARG, "window doublings must be in [0, 8]");
@@ -272,6 +273,8 @@ int cvx_get_stats(cvx_handle *h, cvx_stats *out, int reset) {
     out->lines_certified = (int64_t)c[C_CERT];
     out->edge_splits = (int64_t)c[C_EDGE];
     out->window_doublings = (int64_t)c[C_DOUBLED];
+    out->mirror_windows = (int64_t)c[C_MIRROR];
+    out->mirror_won = (int64_t)c[C_MIRROR_WON];
     if (reset) CK(cudaMemset(h->d_counters, 0, sizeof c), "cvx_get_stats");
     return CVX_OK;
 }

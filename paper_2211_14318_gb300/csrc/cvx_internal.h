@@ -52,6 +52,14 @@ struct NodeCands {
     double shift; // sample shift C in FP64 (line_shift)
 };
 
+// A window decision carried to the node's mirror window (surrogate_propose,
+// CVX_FLAG_MIRROR_WINDOW): the FP64 value and bridge of the best direction,
+// the second-best value and the node flags (iteration cap, overflow).
+struct WinRec {
+    double q, second;
+    int dir, a, b, flags;
+};
+
 struct RefineOut {
     double q;  // FP64 chord value at 0 of the bridge of the left and right sets
     int a, b;
@@ -61,7 +69,8 @@ struct RefineOut {
 enum CounterIdx {
     C_POINTS = 0, C_NODES, C_LINES, C_VALID, C_LAMINATED, C_FP64, C_FULL, C_RARE, C_TIES,
     C_CAPS, C_WSTEPS, C_ROUNDS, C_FP64W, C_FP64R, C_FP64C, C_REFINED, C_OVERFLOW, C_WNODES,
-    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_EDGE, C_DOUBLED, C_NUM
+    C_FALLBACK, C_REFFULL, C_BOUNDED, C_FLAT, C_RECENTRED, C_CERT, C_EDGE, C_DOUBLED, C_MIRROR,
+    C_MIRROR_WON, C_NUM
 };
 
 // Pipeline passes over one level's queue.
@@ -93,6 +102,7 @@ struct ProbDesc {
     // grid, wD = (2w + 1)^2 directions in wchunks items of wdpi; gap_tol of
     // the fallback test
     int window, Na, Nb, wD, wchunks, wdpi;
+    int mwindow;  // half-width of the mirror window (0: none)
     double gap_tol;
     long long point_off, n;
     const double *F, *beta;
@@ -153,11 +163,27 @@ struct Pipe {
     // (the rescan passes use the re-centring queues)
     int adaptive;
     int *node_u;                          // per queued node: smallest FP32 upper bound (f2key)
+    // mirror windows (CVX_FLAG_MIRROR_WINDOW): a main-stage window pass sends
+    // nodes that split to the mirror queue with the mirror cell of their best
+    // direction and that direction's result; the mirror stage's passes read
+    // the problem table with the mirror window's geometry (mprobs) and, after
+    // its first pass, the re-centring queues with records rrec
+    int mirror_on;                        // 1: the run has mirror windows (buffers carved)
+    int mirror;                           // 1: a pass of the mirror stage
+    const ProbDesc *mprobs;
+    int32_t *mq_p, *mq_h;                 // mirror queue of the current level
+    int2 *mcen;
+    WinRec *mrec;
+    int32_t *mcnt;                        // its counts (as cnt)
+    unsigned long long *mitem;
+    WinRec *rrec[2];
+    WinRec *rec;                          // records of the queue a mirror-stage pass reads
+    WinRec *nx_rec;                       // where it sends re-centred nodes' records
 };
 
 // Bytes of the workspace part that depends on the shape (see pipe_layout).
 size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window = false,
-                  bool rescan = false);
+                  bool rescan = false, bool mirror = false);
 // Carves the workspace into the Pipe's buffers (p.N, K, C, n_probs, window set).
 void pipe_layout(Pipe &p, char *ws);
 // Enqueues the whole pipeline (zeroing, init, K levels, leaves) on s.
@@ -174,6 +200,9 @@ Pipe fallback_pipe(const Pipe &p, int level);
 // r >= 1: the nodes re-centred by pass r - 1) with re-centring allowed while
 // r < R.
 Pipe window_pipe(const Pipe &p, int level, int r, int R);
+// The Pipe of mirror-stage pass r (0: the mirror queue; r >= 1: the nodes
+// re-centred by pass r - 1) with re-centring allowed while r < R.
+Pipe mirror_pipe(const Pipe &p, int level, int r, int R);
 // The Pipe of full-scan pass r of a level with adaptive line windows (0: the
 // level queue; r >= 1: the nodes pass r - 1 sent back with a doubled window),
 // sending nodes back while r < A.

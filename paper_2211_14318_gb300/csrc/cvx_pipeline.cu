@@ -922,6 +922,41 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
     if (lane == 0) add_counter(P.counters, C_FP64, n_spot);
 }
 
+// Offset of grid index i from the centre c on a periodic axis of N cells, in
+// (-N/2, N/2].
+__device__ __forceinline__ int wrap_offset(int i, int c, int N) {
+    int d = (i - c) % N;
+    if (d < 0) d += N;
+    return d > N / 2 ? d - N : d;
+}
+
+// Grid cell nearest to the reflection of direction gd (angles pi i / Na,
+// pi j / Nb) about the principal axes of F: theta_a -> 2 phi1 - theta_a,
+// theta_b -> 2 phi2 - theta_b, with phi1 (phi2) the angle of the eigenvector
+// of F F^T (F^T F) with the larger eigenvalue, 0.5 atan2(2B, A - C) for the
+// symmetric [[A, B], [B, C]].  An isotropic W takes the same values on both
+// lines (the reflections M1, M2 satisfy M1 F M2 = F and keep |.| and det).
+// FP64 with explicit rounding in the order (2 phi) Na / pi - i.
+__device__ int2 mirror_cell(const double F[4], int gd, int Na, int Nb) {
+    constexpr double kPi = 3.14159265358979323846;
+    const double f00 = F[0], f01 = F[1], f10 = F[2], f11 = F[3];
+    const double y1 = __dmul_rn(2.0, __dadd_rn(__dmul_rn(f00, f10), __dmul_rn(f01, f11)));
+    const double x1 = __dsub_rn(__dadd_rn(__dmul_rn(f00, f00), __dmul_rn(f01, f01)),
+                                __dadd_rn(__dmul_rn(f10, f10), __dmul_rn(f11, f11)));
+    const double y2 = __dmul_rn(2.0, __dadd_rn(__dmul_rn(f00, f01), __dmul_rn(f10, f11)));
+    const double x2 = __dsub_rn(__dadd_rn(__dmul_rn(f00, f00), __dmul_rn(f10, f10)),
+                                __dadd_rn(__dmul_rn(f01, f01), __dmul_rn(f11, f11)));
+    const double p1 = __dmul_rn(0.5, atan2(y1, x1)), p2 = __dmul_rn(0.5, atan2(y2, x2));
+    const double ua = __dsub_rn(__ddiv_rn(__dmul_rn(__dmul_rn(2.0, p1), (double)Na), kPi),
+                                (double)(gd / Nb));
+    const double ub = __dsub_rn(__ddiv_rn(__dmul_rn(__dmul_rn(2.0, p2), (double)Nb), kPi),
+                                (double)(gd % Nb));
+    int ma = (int)floor(__dadd_rn(ua, 0.5)) % Na, mb = (int)floor(__dadd_rn(ub, 0.5)) % Nb;
+    if (ma < 0) ma += Na;
+    if (mb < 0) mb += Nb;
+    return make_int2(ma, mb);
+}
+
 // -------------------------------------------------------------------------
 // k_commit: one thread per queued node.  Split points in FP64 with explicit
 // rounding (no contraction): t = (m - m0) h, F+- = F + t R, xi = (m0-m-)/(m+-m-).
@@ -951,35 +986,43 @@ __global__ void k_commit(const Pipe P, int level) {
     const double V = (bc >= 0 && ro[bc].q < nd.w) ? ro[bc].q : nd.w;
     const double shift = line_shift(pd.mat, pd.beta[p - pd.point_off]);
     const bool overflow = !(((double)nc.qcut - (double)nc.eps + shift) / pd.kappa > V);
+    // the node's decision: the best refined direction, or (mirror stage) the
+    // main window's when that one holds the lower value
+    const bool split = bc >= 0 && ro[bc].q < nd.w;
+    RefineOut best = bc >= 0 ? ro[bc] : RefineOut{nd.w, m0, m0, 0, 0};
+    int bdir = bc >= 0 ? nc.dir[bc] : -1;
+    int xfl = (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW)) |
+              (overflow ? CVX_NODE_OVERFLOW : 0);
     if (P.pass == PASS_WINDOW) {
         // fallback test of a proposal window: the window's best direction on
-        // its border, or an energy gap |E_pred - V| / (1e-8 + |V|) above
-        // gap_tol between the proposed laminate and the window's value, defers
-        // the node to the full scan
+        // its border, or (main stage) an energy gap |E_pred - V| / (1e-8 + |V|)
+        // above gap_tol between the proposed laminate and the window's value,
+        // defers the node to the full scan
         atomicAdd(P.counters + C_WNODES, 1ull);
         bool border = false;
-        int gd = -1;
-        if (bc >= 0 && ro[bc].q < nd.w) {
-            gd = nc.dir[bc];
+        const int gd = split ? nc.dir[bc] : -1;
+        if (split) {
             const int2 c = P.center[qi];
-            int di = (gd / pd.Nb - c.x) % pd.Na, dj = (gd % pd.Nb - c.y) % pd.Nb;
-            if (di < 0) di += pd.Na;
-            if (dj < 0) dj += pd.Nb;
-            if (di > pd.Na / 2) di -= pd.Na;
-            if (dj > pd.Nb / 2) dj -= pd.Nb;
-            border = abs(di) >= pd.window || abs(dj) >= pd.window;
+            border = abs(wrap_offset(gd / pd.Nb, c.x, pd.Na)) >= pd.window ||
+                     abs(wrap_offset(gd % pd.Nb, c.y, pd.Nb)) >= pd.window;
         }
-        const double gap = ((pd.flags & CVX_FLAG_GAP_ONE_SIDED) ? V - P.e_pred[qi]
-                                                                : fabs(P.e_pred[qi] - V)) /
-                           (1e-8 + fabs(V));
-        const bool gap_fail = !(gap <= pd.gap_tol);
+        bool gap_fail = false;
+        if (!P.mirror) {
+            const double gap = ((pd.flags & CVX_FLAG_GAP_ONE_SIDED) ? V - P.e_pred[qi]
+                                                                    : fabs(P.e_pred[qi] - V)) /
+                               (1e-8 + fabs(V));
+            gap_fail = !(gap <= pd.gap_tol);
+        }
         if (border && !gap_fail && P.nx_p) {
             // re-centre the window on its border minimum and scan it again
             const int pos = atomicAdd(P.nx_cnt + level, 1);
             P.nx_p[pos] = p;
             P.nx_h[pos] = hi;
             P.nx_cen[pos] = make_int2(gd / pd.Nb, gd % pd.Nb);
-            P.nx_ep[pos] = P.e_pred[qi];
+            if (P.mirror)
+                P.nx_rec[pos] = P.rec[qi];
+            else
+                P.nx_ep[pos] = P.e_pred[qi];
             atomicAdd(P.counters + C_RECENTRED, 1ull);
             return;
         }
@@ -990,7 +1033,49 @@ __global__ void k_commit(const Pipe P, int level) {
             atomicAdd(P.counters + C_FALLBACK, 1ull);
             return;
         }
+        if (!P.mirror && P.mirror_on && split) {
+            // scan the twin basin: the window around the mirror cell of gd,
+            // unless it lies inside this window
+            const int2 mc = mirror_cell(nd.F, gd, pd.Na, pd.Nb);
+            const int2 c = P.center[qi];
+            const bool inside = abs(wrap_offset(mc.x, c.x, pd.Na)) + pd.mwindow <= pd.window &&
+                                abs(wrap_offset(mc.y, c.y, pd.Nb)) + pd.mwindow <= pd.window;
+            if (!inside) {
+                const int pos = atomicAdd(P.mcnt + level, 1);
+                P.mq_p[pos] = p;
+                P.mq_h[pos] = hi;
+                P.mcen[pos] = mc;
+                WinRec r;
+                r.q = ro[bc].q;
+                r.second = second;
+                r.dir = gd;
+                r.a = ro[bc].a;
+                r.b = ro[bc].b;
+                r.flags = xfl;
+                P.mrec[pos] = r;
+                atomicAdd(P.counters + C_MIRROR, 1ull);
+                return;
+            }
+        }
+        if (P.mirror) {
+            // the lower of the two windows' values; the lower direction index
+            // on equal values (a main-window record always splits)
+            const WinRec r = P.rec[qi];
+            if (split && (ro[bc].q < r.q || (ro[bc].q == r.q && gd < r.dir))) {
+                second = fmin(second, r.q);
+                atomicAdd(P.counters + C_MIRROR_WON, 1ull);
+            } else {
+                second = fmin(r.second, bc >= 0 ? ro[bc].q : (double)INFINITY);
+                best.q = r.q;
+                best.a = r.a;
+                best.b = r.b;
+                best.ok = 1;
+                bdir = r.dir;
+            }
+            xfl |= r.flags;
+        }
     }
+    const bool lam = best.q < nd.w && bdir >= 0;
     // adaptive line window: a split with an end on the end of its line is
     // scanned again with the window doubled (Sec. 4.1: r sufficiently large)
     if (P.pass == PASS_FULL && P.nx_p && bc >= 0 && ro[bc].q < nd.w &&
@@ -1003,21 +1088,18 @@ __global__ void k_commit(const Pipe P, int level) {
         atomicAdd(P.counters + C_DOUBLED, 1ull);
         return;
     }
-    nd.flags |= CVX_NODE_SCANNED | (nc.flags & (CVX_NODE_ITER_CAP | CVX_NODE_OVERFLOW));
+    nd.flags |= CVX_NODE_SCANNED | xfl;
     if (P.pass == PASS_FALLBACK) nd.flags |= CVX_NODE_FALLBACK;
     atomicAdd(P.counters + C_NODES, 1ull);
-    nd.gap = (float)(second - (bc >= 0 ? ro[bc].q : nd.w));
-    if (overflow) {
-        nd.flags |= CVX_NODE_OVERFLOW;
-        atomicAdd(P.counters + C_OVERFLOW, 1ull);
-    }
+    nd.gap = (float)(second - (bdir >= 0 ? best.q : nd.w));
+    if (xfl & CVX_NODE_OVERFLOW) atomicAdd(P.counters + C_OVERFLOW, 1ull);
     // the centre splits off iff the chord lies strictly below W(F) (FP64)
-    if (bc < 0 || !(ro[bc].q < nd.w)) {
-        nd.dir = bc >= 0 ? nc.dir[bc] : -1;
+    if (!lam) {
+        nd.dir = bdir;
         nd.flags |= CVX_NODE_LEAF;
         return;
     }
-    const RefineOut b = ro[bc];
+    const RefineOut b = best;
     int fl = CVX_NODE_LAMINATED;
     if (b.a == 0 || b.b == pd.line.L - 1) {
         fl |= CVX_NODE_EDGE;
@@ -1028,7 +1110,7 @@ __global__ void k_commit(const Pipe P, int level) {
         atomicAdd(P.counters + C_TIES, 1ull);
     }
     nd.flags |= fl;
-    nd.dir = nc.dir[bc];
+    nd.dir = bdir;
     nd.m_minus = b.a;
     nd.m_plus = b.b;
     nd.h = b.q;
@@ -1143,7 +1225,7 @@ __global__ void k_leaf(const Pipe P) {
 static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_probs,
-                         bool window, bool rescan) {
+                         bool window, bool rescan, bool mirror) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -1168,6 +1250,8 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
     size_t o_fqp[kMaxDepth], o_fqh[kMaxDepth], o_fcnt = 0, o_fictr = 0, o_cen = 0, o_ep = 0;
     size_t o_rqp[2] = {0, 0}, o_rqh[2] = {0, 0}, o_rcen[2] = {0, 0}, o_rep[2] = {0, 0};
     size_t o_rcnt = 0, o_ritem = 0;
+    // the mirror stage's re-centring passes count in a second block
+    const int rblocks = kMaxRecentre * (mirror ? 2 : 1);
     if (window) {
         for (int l = 0; l < K; ++l) {
             o_fqp[l] = take(sizeof(int32_t) * ((size_t)N << l));
@@ -1185,8 +1269,20 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
             o_rcen[b] = take(sizeof(int2) * maxq);
             o_rep[b] = take(sizeof(double) * maxq);
         }
-        o_rcnt = take(sizeof(int32_t) * 2 * (K + 1) * kMaxRecentre);
-        o_ritem = take(sizeof(unsigned long long) * (K + 1) * kMaxRecentre);
+        o_rcnt = take(sizeof(int32_t) * 2 * (K + 1) * rblocks);
+        o_ritem = take(sizeof(unsigned long long) * (K + 1) * rblocks);
+    }
+    size_t o_mprobs = 0, o_mqp = 0, o_mqh = 0, o_mcen = 0, o_mrec = 0, o_mcnt = 0, o_mitem = 0;
+    size_t o_rrec[2] = {0, 0};
+    if (window && mirror) {
+        o_mprobs = take(sizeof(ProbDesc) * (size_t)n_probs);
+        o_mqp = take(sizeof(int32_t) * maxq);
+        o_mqh = take(sizeof(int32_t) * maxq);
+        o_mcen = take(sizeof(int2) * maxq);
+        o_mrec = take(sizeof(WinRec) * maxq);
+        o_mcnt = take(sizeof(int32_t) * 2 * (K + 1));
+        o_mitem = take(sizeof(unsigned long long) * (K + 1));
+        for (int b = 0; b < 2; ++b) o_rrec[b] = take(sizeof(WinRec) * maxq);
     }
     if (pp) {
         Pipe &p = *pp;
@@ -1225,16 +1321,30 @@ static size_t pipe_carve(Pipe *pp, char *ws, long long N, int K, int C, int n_pr
         p.nx_p = p.nx_h = p.nx_cnt = nullptr;
         p.nx_cen = nullptr;
         p.nx_ep = nullptr;
+        const bool mq = window && mirror;
+        p.mirror_on = mq ? 1 : 0;
+        p.mirror = 0;
+        p.mprobs = mq ? (const ProbDesc *)(ws + o_mprobs) : nullptr;
+        p.mq_p = mq ? (int32_t *)(ws + o_mqp) : nullptr;
+        p.mq_h = mq ? (int32_t *)(ws + o_mqh) : nullptr;
+        p.mcen = mq ? (int2 *)(ws + o_mcen) : nullptr;
+        p.mrec = mq ? (WinRec *)(ws + o_mrec) : nullptr;
+        p.mcnt = mq ? (int32_t *)(ws + o_mcnt) : nullptr;
+        p.mitem = mq ? (unsigned long long *)(ws + o_mitem) : nullptr;
+        for (int b = 0; b < 2; ++b) p.rrec[b] = mq ? (WinRec *)(ws + o_rrec[b]) : nullptr;
+        p.rec = p.nx_rec = nullptr;
     }
     return off;
 }
 
-size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window, bool rescan) {
-    return pipe_carve(nullptr, nullptr, N, K, C, n_probs, window, rescan);
+size_t pipe_bytes(long long N, int K, int C, int n_probs, bool window, bool rescan,
+                  bool mirror) {
+    return pipe_carve(nullptr, nullptr, N, K, C, n_probs, window, rescan, mirror);
 }
 
 void pipe_layout(Pipe &p, char *ws) {
-    pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs, p.window != 0, p.adaptive > 0);
+    pipe_carve(&p, ws, p.N, p.K, p.C, p.n_probs, p.window != 0, p.adaptive > 0,
+               p.mirror_on != 0);
 }
 
 Pipe window_pipe(const Pipe &p, int level, int r, int R) {
@@ -1261,6 +1371,46 @@ Pipe window_pipe(const Pipe &p, int level, int r, int R) {
         q.nx_p = q.nx_h = q.nx_cnt = nullptr;
         q.nx_cen = nullptr;
         q.nx_ep = nullptr;
+    }
+    return q;
+}
+
+Pipe mirror_pipe(const Pipe &p, int level, int r, int R) {
+    Pipe q = p;
+    q.pass = PASS_WINDOW;
+    q.mirror = 1;
+    q.probs = p.mprobs;
+    q.e_pred = nullptr;
+    if (r == 0) {
+        q.cnt = p.mcnt;
+        q.item_ctr = p.mitem;
+        q.qp[level] = p.mq_p;
+        q.qh[level] = p.mq_h;
+        q.center = p.mcen;
+        q.rec = p.mrec;
+    } else {
+        const int b = (r - 1) & 1;
+        q.cnt = p.rcnt + (size_t)2 * (p.K + 1) * (kMaxRecentre + r - 1);
+        q.item_ctr = p.ritem + (size_t)(p.K + 1) * (kMaxRecentre + r - 1);
+        q.qp[level] = p.rq_p[b];
+        q.qh[level] = p.rq_h[b];
+        q.center = p.rcen[b];
+        q.rec = p.rrec[b];
+    }
+    q.ncnt = p.cnt;  // children go to the level queue of the next level
+    if (r < R) {
+        const int b = r & 1;
+        q.nx_p = p.rq_p[b];
+        q.nx_h = p.rq_h[b];
+        q.nx_cen = p.rcen[b];
+        q.nx_ep = nullptr;
+        q.nx_rec = p.rrec[b];
+        q.nx_cnt = p.rcnt + (size_t)2 * (p.K + 1) * (kMaxRecentre + r);
+    } else {
+        q.nx_p = q.nx_h = q.nx_cnt = nullptr;
+        q.nx_cen = nullptr;
+        q.nx_ep = nullptr;
+        q.nx_rec = nullptr;
     }
     return q;
 }
@@ -1319,11 +1469,19 @@ cudaError_t pipe_begin(const Pipe &p, cudaStream_t s) {
         cudaSuccess)
         return e;
     if (p.window || p.adaptive) {
-        if ((e = cudaMemsetAsync(p.rcnt, 0, sizeof(int32_t) * 2 * (p.K + 1) * kMaxRecentre, s)) !=
+        const int rb = kMaxRecentre * (p.mirror_on ? 2 : 1);
+        if ((e = cudaMemsetAsync(p.rcnt, 0, sizeof(int32_t) * 2 * (p.K + 1) * rb, s)) !=
             cudaSuccess)
             return e;
-        if ((e = cudaMemsetAsync(p.ritem, 0, sizeof(unsigned long long) * (p.K + 1) * kMaxRecentre,
-                                 s)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(p.ritem, 0, sizeof(unsigned long long) * (p.K + 1) * rb, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    if (p.mirror_on) {
+        if ((e = cudaMemsetAsync(p.mcnt, 0, sizeof(int32_t) * 2 * (p.K + 1), s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(p.mitem, 0, sizeof(unsigned long long) * (p.K + 1), s)) !=
+            cudaSuccess)
             return e;
     }
     if (p.window) {

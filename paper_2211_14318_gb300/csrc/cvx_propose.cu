@@ -6,8 +6,10 @@
 // energy E_pred of the proposed laminate; the line scan then covers only the
 // (2w + 1)^2 directions of the window (PASS_WINDOW), and k_commit defers to
 // the full scan (PASS_FALLBACK) every node whose window decision fails the
-// fallback test: best direction on the window border, decision not certified
-// within the window, or |E_pred - V| / (1e-8 + |V|) > gap_tol.
+// fallback test: best direction on the window border after the re-centrings,
+// or |E_pred - V| / (1e-8 + |V|) > gap_tol.  With CVX_FLAG_MIRROR_WINDOW a
+// node whose window split is scanned again around the mirror cell of its
+// direction (the twin basin of an isotropic W) and takes the lower value.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -216,6 +218,8 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     pd.wdpi = lanes ? lane_dirs_per_item(n, pd.wD, lane_warps, 0)
                     : dirs_per_item(n, pd.wD, grid, warps, 0);
     pd.wchunks = (pd.wD + pd.wdpi - 1) / pd.wdpi;
+    const bool mirror = (p->flags & CVX_FLAG_MIRROR_WINDOW) != 0;
+    pd.mwindow = mirror ? (window + 1) / 2 : 0;
     pd.gap_tol = gap_tol;
     pd.point_off = 0;
     pd.n = n;
@@ -226,16 +230,24 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     pd.status = status;
     pd.root = root;
 
+    // the mirror window's geometry (the mirror stage's problem table is pd
+    // with these, built once pd is complete)
+    const int mwD = (2 * pd.mwindow + 1) * (2 * pd.mwindow + 1);
+    const int mwdpi = lanes ? lane_dirs_per_item(n, mwD, lane_warps, 0)
+                            : dirs_per_item(n, mwD, grid, warps, 0);
+    const int mwchunks = (mwD + mwdpi - 1) / mwdpi;
+
     Pipe pp = {};
     pp.n_probs = 1;
     pp.N = n;
     pp.K = p->depth;
-    pp.C = std::max(pd.chunks, pd.wchunks);
+    pp.C = std::max(std::max(pd.chunks, pd.wchunks), mirror ? mwchunks : 0);
+    pp.mirror_on = mirror ? 1 : 0;
     pp.stride32 = pp.stride64 = pd.line.stride;
     pp.energy = p->energy;
     pp.window = 1;
     pp.lanes = lanes ? 1 : 0;
-    const size_t pipe_sz = up256(pipe_bytes(pp.N, pp.K, pp.C, 1, true));
+    const size_t pipe_sz = up256(pipe_bytes(pp.N, pp.K, pp.C, 1, true, false, mirror));
     const size_t tree_sz = tree ? 0 : sizeof(cvx_node) * (size_t)n * pd.NT;
     rc = ensure_ws(h, pipe_sz + tree_sz, s);
     if (rc) return rc;
@@ -252,9 +264,17 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
     // pageable source: returns once staged
     CK(cudaMemcpyAsync((void *)pp.probs, &pd, sizeof pd, cudaMemcpyHostToDevice, s),
        "surrogate_propose/table");
+    ProbDesc pm = pd;
+    pm.window = pd.mwindow;
+    pm.wD = mwD;
+    pm.wdpi = mwdpi;
+    pm.wchunks = mwchunks;
+    if (mirror)
+        CK(cudaMemcpyAsync((void *)pp.mprobs, &pm, sizeof pm, cudaMemcpyHostToDevice, s),
+           "surrogate_propose/table");
     const int R = p->recentre;
-    std::vector<cudaEvent_t> ev;  // window passes and fallback scan of every level
-    const int per_level = R + 2;
+    std::vector<cudaEvent_t> ev;  // window passes, mirror passes and fallback scan of every level
+    const int per_level = (R + 1) * (mirror ? 2 : 1) + 1;
     rc = scan_events(h, per_level * pp.K, ev);
     if (rc) return rc;
     CK(pipe_begin(pp, s), "surrogate_propose");
@@ -270,10 +290,16 @@ int surrogate_propose(cvx_handle *h, const cvx_params *p, int64_t n, const doubl
             CK(cudaGetLastError(), "surrogate_propose/decode");
         }
         cudaEvent_t *evl = ev.empty() ? nullptr : &ev[2 * per_level * l];
-        for (int r = 0; r <= R; ++r)
-            CK(pipe_level(window_pipe(pp, l, r, R), l, warps, grid, s, evl ? evl + 2 * r : nullptr),
+        int e = 0;
+        for (int r = 0; r <= R; ++r, ++e)
+            CK(pipe_level(window_pipe(pp, l, r, R), l, warps, grid, s, evl ? evl + 2 * e : nullptr),
                "surrogate_propose/window");
-        CK(pipe_level(fallback_pipe(pp, l), l, warps, grid, s, evl ? evl + 2 * (R + 1) : nullptr),
+        if (mirror)
+            for (int r = 0; r <= R; ++r, ++e)
+                CK(pipe_level(mirror_pipe(pp, l, r, R), l, warps, grid, s,
+                              evl ? evl + 2 * e : nullptr),
+                   "surrogate_propose/mirror");
+        CK(pipe_level(fallback_pipe(pp, l), l, warps, grid, s, evl ? evl + 2 * e : nullptr),
            "surrogate_propose/fallback");
     }
     CK(pipe_end(pp, s), "surrogate_propose");

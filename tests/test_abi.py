@@ -70,7 +70,7 @@ def _err(cvxlib):
     ("mu", -1.0, "material"),
     ("energy", 7, "energy"),
     ("n_theta_a", 0, "angle grid"),
-    ("flags", 4, "flags"),
+    ("flags", 8, "flags"),
 ])
 def test_invalid_params_rejected_before_cuda(cvxlib, field, value, msg):
     from paper_2211_14318_gb300 import api
