@@ -125,6 +125,18 @@ def lib() -> ctypes.CDLL:
         L.orc_tree_size.argtypes = [i32]
         L.orc_node_size.restype = i32
         L.orc_node_size.argtypes = []
+        L.orc_grid_count.restype = i64
+        L.orc_grid_count.argtypes = [vp]
+        L.orc_grid_point.restype = None
+        L.orc_grid_point.argtypes = [vp, i64, vp]
+        L.orc_r11_directions.restype = None
+        L.orc_r11_directions.argtypes = [vp]
+        L.orc_grid_energy.restype = None
+        L.orc_grid_energy.argtypes = [vp, vp, d, i32, vp, i32]
+        L.orc_grid_query.restype = None
+        L.orc_grid_query.argtypes = [vp, vp, d, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, i32]
+        L.orc_grid_step.restype = d
+        L.orc_grid_step.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, i32]
         assert L.orc_node_size() == NODE_DTYPE.itemsize, "node layout mismatch"
         _lib = L
     return _lib
@@ -349,3 +361,122 @@ def cores() -> int:
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(_LIB)
+
+
+# ---------------------------------------------------------------------------
+# Global-grid rank-one convexification: Eq. (4.3) on the cuboid grid of
+# Sec. 5.2 with the reduced direction set R^1_1 of Eq. (5.1)
+# ---------------------------------------------------------------------------
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 4), ("lo", ctypes.c_double * 4),
+                ("delta", ctypes.c_double * 4)]
+
+
+class Grid:
+    """Cuboid grid of Sec. 5.2: component c of F (F11, F12, F21, F22) takes
+    lo[c] + i delta[c], i = 0 .. n[c] - 1 (flat index with F22 fastest)."""
+
+    def __init__(self, n, lo, delta):
+        self.n = tuple(int(x) for x in n)
+        self.lo = tuple(float(x) for x in lo)
+        self.delta = tuple(float(x) for x in delta)
+        self._c = _Grid((ctypes.c_int32 * 4)(*self.n), (ctypes.c_double * 4)(*self.lo),
+                        (ctypes.c_double * 4)(*self.delta))
+
+    @classmethod
+    def from_bounds(cls, diag, off, delta):
+        """Grid with the same bounds (lo, hi) on both diagonal entries, the
+        same on both off-diagonal entries, spacing delta (diagonal,
+        off-diagonal); hi is a grid value."""
+        (dlo, dhi), (olo, ohi) = diag, off
+        dd, do = delta
+        nd = int(round((dhi - dlo) / dd)) + 1
+        no = int(round((ohi - olo) / do)) + 1
+        return cls((nd, no, no, nd), (dlo, olo, olo, dlo), (dd, do, do, dd))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+    @property
+    def count(self) -> int:
+        return int(lib().orc_grid_count(self.ref))
+
+    def points(self) -> np.ndarray:
+        """(N, 4) grid points in flat-index order."""
+        axes = [self.lo[c] + np.arange(self.n[c]) * self.delta[c] for c in range(4)]
+        return np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 4)
+
+
+def r11_directions() -> np.ndarray:
+    """(16, 4) grid-index offsets of the directions of Eq. (5.1)."""
+    off = np.zeros((16, 4), dtype=np.int32)
+    lib().orc_r11_directions(_p(off))
+    return off
+
+
+def grid_energy(mat: Material, grid: Grid, beta_k: float, abs_det: bool = False,
+                nthreads: int = 0) -> np.ndarray:
+    """W^0 on the grid (abs_det: ln|det F| for det F < 0, the Sec. 6.1 reading)."""
+    W = np.empty(grid.count)
+    lib().orc_grid_energy(mat.ref, grid.ref, float(beta_k), int(abs_det), _p(W), int(nthreads))
+    return W
+
+
+def grid_step(grid: Grid, off: np.ndarray, W: np.ndarray, want_h: bool = False,
+              nthreads: int = 0):
+    """One iteration of Eq. (4.3): (W_next, dir, l_minus, l_plus, decrease[, h])."""
+    off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    N = grid.count
+    Wn = np.empty(N)
+    d = np.empty(N, dtype=np.int32)
+    lm = np.empty(N, dtype=np.int32)
+    lp = np.empty(N, dtype=np.int32)
+    h = np.empty((N, off.shape[0])) if want_h else None
+    dec = lib().orc_grid_step(grid.ref, off.shape[0], _p(off), _p(W), _p(Wn), _p(d), _p(lm),
+                              _p(lp), _p(h) if want_h else None, int(nthreads))
+    out = (Wn, d, lm, lp, float(dec))
+    return out + (h,) if want_h else out
+
+
+def grid_convexify(mat: Material, grid: Grid, beta_k: float, off: np.ndarray, kmax: int = 20,
+                   tol: float = 1e-4, abs_det: bool = False, nthreads: int = 0):
+    """The global iteration (Sec. 4.1): W^0 = W on the grid, W^{k+1} by
+    Eq. (4.3), stopped after kmax iterations or once the largest decrease is
+    at most tol (Sec. 6).  Returns (W^k list, forest, decreases) with forest[k]
+    = (dir, l_minus, l_plus) of iteration k + 1."""
+    W = [grid_energy(mat, grid, beta_k, abs_det, nthreads)]
+    forest, decs = [], []
+    for _ in range(kmax):
+        Wn, d, lm, lp, dec = grid_step(grid, off, W[-1], nthreads=nthreads)
+        W.append(Wn)
+        forest.append((d, lm, lp))
+        decs.append(dec)
+        if dec <= tol:
+            break
+    return W, forest, decs
+
+
+def forest_array(forest) -> np.ndarray:
+    """(K, N, 3) int32 records (dir, l_minus, l_plus) from grid_convexify's forest."""
+    return np.ascontiguousarray(np.stack([np.stack(f, axis=-1) for f in forest]), dtype=np.int32)
+
+
+def grid_query(mat: Material, grid: Grid, beta_k: float, off: np.ndarray, WK: np.ndarray, forest,
+               F: np.ndarray, abs_det: bool = False, nthreads: int = 0):
+    """(W_interp, W_tree, P, leaves) at points F after K = len(forest)
+    iterations: the multilinear interpolation of W^K, and Algorithm 3 over
+    Algorithm 2's tree."""
+    off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+    fa = forest_array(forest) if not isinstance(forest, np.ndarray) else np.ascontiguousarray(forest, dtype=np.int32)
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 4)
+    n = F.shape[0]
+    wi, wt, P = np.empty(n), np.empty(n), np.empty((n, 4))
+    nl = np.empty(n, dtype=np.int64)
+    lib().orc_grid_query(mat.ref, grid.ref, float(beta_k), int(abs_det), _p(off), fa.shape[0],
+                         _p(np.ascontiguousarray(WK, dtype=np.float64)), _p(fa), n, _p(F), _p(wi),
+                         _p(wt), _p(P), _p(nl), int(nthreads))
+    return wi, wt, P, nl

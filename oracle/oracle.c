@@ -747,3 +747,342 @@ int32_t orc_node_size(void)
 {
     return (int32_t)sizeof(orc_node);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Global-grid rank-one convexification: Eq. (4.3) on the cuboid grid of     */
+/* Sec. 5.2 with the reduced direction set R^1_1 of Eq. (5.1)                */
+/* ------------------------------------------------------------------------- */
+
+/* Grid of Sec. 5.2: component c of F (order F11, F12, F21, F22) takes the
+ * values lo[c] + i delta[c], i = 0 .. n[c] - 1; flat index
+ * ((i0 n1 + i1) n2 + i2) n3 + i3. */
+typedef struct {
+    int32_t n[4];
+    double lo[4];
+    double delta[4];
+} orc_grid;
+
+int64_t orc_grid_count(const orc_grid *g)
+{
+    return (int64_t)g->n[0] * g->n[1] * g->n[2] * g->n[3];
+}
+
+static void grid_index(const orc_grid *g, int64_t idx, int32_t i[4])
+{
+    for (int c = 3; c >= 0; --c) {
+        i[c] = (int32_t)(idx % g->n[c]);
+        idx /= g->n[c];
+    }
+}
+
+static int64_t grid_flat(const orc_grid *g, const int32_t i[4])
+{
+    return (((int64_t)i[0] * g->n[1] + i[1]) * g->n[2] + i[2]) * g->n[3] + i[3];
+}
+
+void orc_grid_point(const orc_grid *g, int64_t idx, double F[4])
+{
+    int32_t i[4];
+    grid_index(g, idx, i);
+    for (int c = 0; c < 4; ++c)
+        F[c] = g->lo[c] + (double)i[c] * g->delta[c];
+}
+
+/* Eq. (5.1): a (x) b with a, b in Z^2, |a|_inf = |b|_inf = 1, one of each
+ * pair +-a (x) b (the sign of a direction gives the same line): a and b run
+ * over (1,0), (0,1), (1,1), (1,-1); direction 4 ia + ib.  Written as the
+ * grid-index offset (a1 b1, a1 b2, a2 b1, a2 b2) of one step. */
+void orc_r11_directions(int32_t *off)
+{
+    static const int32_t v[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
+    for (int ia = 0; ia < 4; ++ia)
+        for (int ib = 0; ib < 4; ++ib) {
+            int32_t *o = off + 4 * (4 * ia + ib);
+            o[0] = v[ia][0] * v[ib][0];
+            o[1] = v[ia][0] * v[ib][1];
+            o[2] = v[ia][1] * v[ib][0];
+            o[3] = v[ia][1] * v[ib][1];
+        }
+}
+
+/* Energy and stress at a grid point.  abs_det = 0: as orc_energy /
+ * orc_stress (NaN where det F <= 0).  abs_det = 1, the reading of the grid
+ * study of Sec. 6.1: the Neo-Hooke energy takes ln|det F| (and the stress
+ * F^{-T} = cof F / det F, the derivative of ln|det F| for det F != 0), so that
+ * det F < 0 is a mirror image of det F > 0 rather than excluded. */
+static double grid_W(const orc_material *m, const double F[4], double beta_k, int32_t abs_det)
+{
+    if (m->energy == 1 || !abs_det)
+        return orc_energy(m, F, beta_k);
+    double I1, J;
+    nh_invariants(F, &I1, &J);
+    J = fabs(J);
+    if (!(J > 0.0))
+        return NAN;
+    return orc_W_of_psi0(orc_psi0_nh(I1, J, m->mu, m->lam), beta_k, m->Dinf, m->D0);
+}
+
+static void grid_P(const orc_material *m, const double F[4], double beta_k, int32_t abs_det,
+                   double P[4])
+{
+    double I1, J;
+    nh_invariants(F, &I1, &J);
+    if (m->energy == 1 || !abs_det || J > 0.0) {
+        orc_stress(m, F, beta_k, P);
+        return;
+    }
+    if (!(J < 0.0)) {
+        P[0] = P[1] = P[2] = P[3] = NAN;
+        return;
+    }
+    double s = orc_psi0_nh(I1, -J, m->mu, m->lam);
+    double beta = s > beta_k ? s : beta_k;
+    double gd = 1.0 - orc_damage(beta, m->Dinf, m->D0);
+    double FiT[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
+    double lj = log(-J);
+    for (int i = 0; i < 4; ++i)
+        P[i] = gd * (m->mu * F[i] - m->mu * FiT[i] + m->lam * lj * FiT[i]);
+}
+
+/* W^0 on the grid: the energy at every grid point (NaN where it is not
+ * defined). */
+void orc_grid_energy(const orc_material *m, const orc_grid *g, double beta_k, int32_t abs_det,
+                     double *W, int32_t nthreads)
+{
+    int64_t N = orc_grid_count(g);
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t idx = 0; idx < N; ++idx) {
+        double F[4];
+        orc_grid_point(g, idx, F);
+        W[idx] = grid_W(m, F, beta_k, abs_det);
+    }
+}
+
+/* Range of steps l with grid index i + l off inside the grid. */
+static void line_range(const orc_grid *g, const int32_t i[4], const int32_t off[4],
+                       int32_t *lo, int32_t *hi)
+{
+    int32_t a = -(1 << 30), b = 1 << 30;
+    for (int c = 0; c < 4; ++c) {
+        if (off[c] > 0) {
+            int32_t l0 = -i[c] / off[c], l1 = (g->n[c] - 1 - i[c]) / off[c];
+            if (l0 > a) a = l0;
+            if (l1 < b) b = l1;
+        } else if (off[c] < 0) {
+            int32_t l0 = -(g->n[c] - 1 - i[c]) / (-off[c]), l1 = i[c] / (-off[c]);
+            if (l0 > a) a = l0;
+            if (l1 < b) b = l1;
+        }
+    }
+    *lo = a;
+    *hi = b;
+}
+
+/* One global iteration, Eq. (4.3).  For every grid point F and direction R
+ * (grid-index offset off[j]): the values Win at the grid points F + l R of
+ * the line through F inside the grid (Eq. 4.5; every point of the line is a
+ * grid point, so no interpolation is needed), Algorithm 1 on the finite ones
+ * (orc_line_bridge), read at l = 0.  Wout[F] = min(Win[F], min_j h_j); the
+ * laminate is the lowest j with h_j < Win[F] at the minimum: dir[F] = j and
+ * its bridge ends lm[F] < 0 < lp[F] (dir = -1, lm = lp = 0 otherwise).
+ * Points where Win is not finite keep it.  hdir (N x nd, may be NULL)
+ * receives every h_j.  Returns the largest decrease Win - Wout over the
+ * points where both are finite. */
+double orc_grid_step(const orc_grid *g, int32_t nd, const int32_t *off, const double *Win,
+                     double *Wout, int32_t *dir, int32_t *lm, int32_t *lp, double *hdir,
+                     int32_t nthreads)
+{
+    int64_t N = orc_grid_count(g);
+    int32_t nmax = 0;
+    for (int c = 0; c < 4; ++c)
+        if (g->n[c] > nmax)
+            nmax = g->n[c];
+    double dec = 0.0;
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256) reduction(max : dec)
+#endif
+    for (int64_t idx = 0; idx < N; ++idx) {
+        int32_t i[4];
+        grid_index(g, idx, i);
+        double w0 = Win[idx];
+        int32_t bj = -1, bm = 0, bp = 0;
+        double best = w0;
+        int32_t L = 2 * nmax + 1, M = nmax;
+        double *w = (double *)malloc(sizeof(double) * L);
+        uint8_t *valid = (uint8_t *)malloc(L);
+        for (int32_t j = 0; j < nd; ++j) {
+            const int32_t *o = off + 4 * j;
+            double h = w0;
+            if (isfinite(w0)) {
+                int32_t l0, l1;
+                line_range(g, i, o, &l0, &l1);
+                for (int32_t m = 0; m < L; ++m) {
+                    int32_t l = m - M;
+                    valid[m] = 0;
+                    w[m] = 0.0;
+                    if (l < l0 || l > l1)
+                        continue;
+                    int32_t ii[4];
+                    for (int c = 0; c < 4; ++c)
+                        ii[c] = i[c] + l * o[c];
+                    double v = Win[grid_flat(g, ii)];
+                    if (isfinite(v)) {
+                        w[m] = v;
+                        valid[m] = 1;
+                    }
+                }
+                int32_t mm, mp;
+                h = orc_line_bridge(L, w, valid, &mm, &mp, NULL);
+                if (mm != M && h < best) {
+                    best = h;
+                    bj = j;
+                    bm = mm - M;
+                    bp = mp - M;
+                }
+            }
+            if (hdir)
+                hdir[idx * nd + j] = h;
+        }
+        free(w);
+        free(valid);
+        Wout[idx] = best;
+        if (dir) {
+            dir[idx] = bj;
+            lm[idx] = bm;
+            lp[idx] = bp;
+        }
+        if (isfinite(w0) && isfinite(best) && w0 - best > dec)
+            dec = w0 - best;
+    }
+    return dec;
+}
+
+/* Interpolation decomposition of F (Sec. 5.3, Algorithm 2): the corners of
+ * the grid cell that contains F and their multilinear weights
+ * prod_c (1 - t_c or t_c), t_c = (F_c - lo_c) / delta_c - i_c; a t_c within
+ * 1e-12 of 0 or 1 counts as 0 or 1, so that a grid point is its own single
+ * corner; corners of weight 0 are left out.  Returns the number of corners,
+ * 0 if F lies outside the grid. */
+static int32_t grid_decompose(const orc_grid *g, const double F[4], int64_t *cidx, double *cw)
+{
+    int32_t i0[4];
+    double t[4];
+    for (int c = 0; c < 4; ++c) {
+        double u = (F[c] - g->lo[c]) / g->delta[c];
+        if (u < -1e-12 || u > (double)(g->n[c] - 1) + 1e-12)
+            return 0;
+        double f = floor(u);
+        double r = u - f;
+        if (r > 1.0 - 1e-12) {
+            f += 1.0;
+            r = 0.0;
+        } else if (r < 1e-12) {
+            r = 0.0;
+        }
+        int32_t ii = (int32_t)f;
+        if (ii > g->n[c] - 1)
+            ii = g->n[c] - 1;
+        if (ii < 0)
+            ii = 0;
+        i0[c] = ii;
+        t[c] = r;
+    }
+    int32_t nc = 0;
+    for (int corner = 0; corner < 16; ++corner) {
+        double w = 1.0;
+        int32_t ii[4];
+        for (int c = 0; c < 4; ++c) {
+            int up = (corner >> (3 - c)) & 1;
+            w *= up ? t[c] : 1.0 - t[c];
+            ii[c] = i0[c] + up;
+        }
+        if (w == 0.0)
+            continue;
+        cidx[nc] = grid_flat(g, ii);
+        cw[nc] = w;
+        ++nc;
+    }
+    return nc;
+}
+
+/* Algorithm 2's tree below grid point idx at order d, evaluated by
+ * Algorithm 3: the laminate of the latest iteration k <= d that split idx
+ * (forest[k - 1]) gives the children F-+ = F + l-+ R at order k - 1 with
+ * weights 1 - xi and xi, xi = -l- / (l+ - l-) (Algorithm 2's
+ * |F - F-|_1 / |F+ - F-|_1); a point no iteration up to d split is a leaf,
+ * where W and P are evaluated.  Adds weight * (W, P) of the leaves. */
+static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k, int32_t abs_det,
+                      const int32_t *off, const int32_t *forest, int64_t idx, int32_t d,
+                      double weight, double *W, double P[4], int64_t *leaves)
+{
+    int64_t N = orc_grid_count(g);
+    int32_t k = d;
+    while (k >= 1 && forest[3 * ((int64_t)(k - 1) * N + idx)] < 0)
+        --k;
+    if (k < 1) {
+        double F[4], Pl[4];
+        orc_grid_point(g, idx, F);
+        *W += weight * grid_W(mat, F, beta_k, abs_det);
+        grid_P(mat, F, beta_k, abs_det, Pl);
+        for (int c = 0; c < 4; ++c)
+            P[c] += weight * Pl[c];
+        ++*leaves;
+        return;
+    }
+    const int32_t *lam = forest + 3 * ((int64_t)(k - 1) * N + idx);
+    const int32_t *o = off + 4 * lam[0];
+    int32_t lm = lam[1], lp = lam[2];
+    double xi = (double)(-lm) / (double)(lp - lm);
+    int32_t i[4], im[4], ip[4];
+    grid_index(g, idx, i);
+    for (int c = 0; c < 4; ++c) {
+        im[c] = i[c] + lm * o[c];
+        ip[c] = i[c] + lp * o[c];
+    }
+    grid_tree(mat, g, beta_k, abs_det, off, forest, grid_flat(g, im), k - 1,
+              weight * (1.0 - xi), W, P, leaves);
+    grid_tree(mat, g, beta_k, abs_det, off, forest, grid_flat(g, ip), k - 1, weight * xi, W, P,
+              leaves);
+}
+
+/* Relaxed energy and stress at arbitrary points from K global iterations:
+ * W_interp = the multilinear interpolation of W^K (Sec. 4.1: values off the
+ * grid by interpolation); W_tree, P = Algorithm 3 over Algorithm 2's tree
+ * (the interpolation corners at order K, then the forest).  forest holds
+ * K x N records (dir, l-, l+) (dir = -1: no split).  leaves[p] counts the
+ * tree's leaves.  Outside the grid: NaN, leaves 0. */
+void orc_grid_query(const orc_material *mat, const orc_grid *g, double beta_k, int32_t abs_det,
+                    const int32_t *off, int32_t K, const double *WK, const int32_t *forest,
+                    int64_t n, const double *F, double *W_interp, double *W_tree, double *P,
+                    int64_t *leaves, int32_t nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t cidx[16];
+        double cw[16];
+        int32_t nc = grid_decompose(g, F + 4 * p, cidx, cw);
+        double wi = 0.0, wt = 0.0, Pp[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t nl = 0;
+        for (int32_t c = 0; c < nc; ++c) {
+            wi += cw[c] * WK[cidx[c]];
+            grid_tree(mat, g, beta_k, abs_det, off, forest, cidx[c], K, cw[c], &wt, Pp, &nl);
+        }
+        if (nc == 0)
+            wi = wt = Pp[0] = Pp[1] = Pp[2] = Pp[3] = NAN;
+        W_interp[p] = wi;
+        W_tree[p] = wt;
+        for (int c = 0; c < 4; ++c)
+            P[4 * p + c] = Pp[c];
+        leaves[p] = nl;
+    }
+}
