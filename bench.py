@@ -61,7 +61,8 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--form", default="loadpath",
-                    choices=["loadpath", "full-scan", "northstar", "batch", "surrogate", "train"],
+                    choices=["loadpath", "full-scan", "northstar", "batch", "surrogate", "train",
+                             "grid"],
                     help="loadpath: the metric's workload (default); full-scan: the 65,536-point "
                          "mesh alone; surrogate: the load path with the older report; train: "
                          "training and inference of the proposal network (own lines)")
@@ -226,25 +227,40 @@ SCAN_SOURCES = ("cvx_pipeline.cu", "cvx_bridge.cuh", "cvx_device.cuh", "cvx_line
                 "cvx_internal.h", "cvx_scan_lanes.cu")
 
 
-def scan_source_hash():
-    """Hash of the sources the line-scan kernel is compiled from."""
+GRID_SOURCES = ("cvx_grid.cu", "cvx_device.cuh", "cvx_internal.h", "cvx_handle.h")
+
+
+def _header_defs():
+    """The parts of include/convexify.h a kernel compiles against: the header
+    without its comments and function prototypes (types, enums, macros)."""
+    import re
+
+    txt = open(os.path.join(ROOT, "include", "convexify.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"^int\s+\w+\s*\([^;]*\);", "", txt, flags=re.S | re.M)
+    return "\n".join(ln.rstrip() for ln in txt.splitlines() if ln.strip()).encode()
+
+
+def scan_source_hash(sources=SCAN_SOURCES):
+    """Hash of the sources a kernel is compiled from (the line scan's by
+    default)."""
     h = hashlib.sha256()
     c = os.path.join(ROOT, "paper_2211_14318_gb300", "csrc")
-    for f in SCAN_SOURCES:
+    for f in sources:
         h.update(open(os.path.join(c, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "convexify.h"), "rb").read())
+    h.update(_header_defs())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(valid_per_launch, name="k_scan_traffic.json"):
-    """DRAM bytes per scan launch from the committed ncu summary, scaled to
-    this launch's work; None if the kernel changed since the capture."""
+def traffic_per_launch(valid_per_launch, name="k_scan_traffic.json", sources=SCAN_SOURCES):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    launch's work; None if the kernel changed since the capture."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         t = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if t.get("source_sha") != scan_source_hash():
+    if t.get("source_sha") != scan_source_hash(sources):
         return None
     per_sample = t["dram_bytes"] / max(1, t["valid_samples"])
     return per_sample * valid_per_launch
@@ -727,6 +743,8 @@ def run_loadpath(a):
                 a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, 3, doublings=5)
             extras["mesh128"] = mesh128_line(cv, api, torch, dev, peak, sms, mhz, peak_src,
                                              min(K, 5))
+            extras["global_grid"] = global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz,
+                                                     peak_src, cpu=ws == 1 and not a.no_cpu_baseline)
         cpu = None
         if ws == 1 and not a.no_cpu_baseline:
             cpu = loadpath_oracle_rate(path, K, host_cores(), 8)
@@ -852,6 +870,180 @@ def mesh128_line(cv, api, torch, dev, peak, sms, mhz, peak_src, steps):
         res["accuracy_vs_oracle"] = err_stats(out["W_R"][it].cpu().numpy(), g["W_R"],
                                               out["P"][it].cpu().numpy(), g["P"])
     return res
+
+
+# The global-grid study of Sec. 6.1 (Table tab:2Dconvexification, NH row)
+GRID61 = dict(diag=(0.1, 3.4), off=(-2.55, 2.55), delta=(0.15, 0.15), beta=0.06, kmax=20,
+              tol=1e-4, mat=dict(mu=1.0, lambda_L=0.5, D_inf=0.9, D0=0.3))
+# the strong-scaling study of Sec. 6.4 times a 43,681-point grid (11 x 19 x 19 x 11
+# points) whose bounds are not printed; this one has that shape at delta 0.15
+GRID_SCALING = dict(diag=(0.4, 1.9), off=(-1.35, 1.35), delta=(0.15, 0.15))
+FP64_FMA_PER_SM = 2       # FP64 FMA per SM per clock on GB300 (1.25 TFLOP/s nominal)
+GRID_FLOP_PER_POINT_DIR = 12  # Algorithm 1 (2 predicates x 4) + the chord at the point (4)
+
+
+def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10,
+                     cpu=True):
+    """The paper's own algorithm on the grid of its Sec. 6.1 study: 648,025
+    grid points, R^1_1, W^0 then Eq. (4.3) until the largest decrease is at
+    most 1e-4 (15 steps), timed whole on the device (L2 flushed before each
+    run); the line kernel's roofline against the FP64 pipe; Algorithms 2/3 at
+    1,048,576 query points; accuracy against the stored oracle results."""
+    import numpy as np
+
+    c = GRID61
+    g = api.GridSpec.from_bounds(c["diag"], c["off"], c["delta"])
+    off = api.grid_r11()
+    p = api.Params(**c["mat"])
+    N, nd = g.count, off.shape[0]
+    out = dict(W=torch.empty(N, dtype=torch.float64, device=dev),
+               forest=torch.empty(c["kmax"], N, 3, dtype=torch.int32, device=dev),
+               decs=torch.empty(c["kmax"], dtype=torch.float64, device=dev),
+               iters=torch.empty(1, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def run(kmax=c["kmax"]):
+        return cv.grid_convexify(p, g, c["beta"], off, kmax=kmax, tol=c["tol"], abs_det=True,
+                                 out=out)
+
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    K = int(out["iters"].cpu()[0])
+    ms = []
+    for _ in range(runs):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    # the line kernel alone: a run with kmax = K (no skipped launches), events
+    # on the launching stream around each line-kernel launch
+    flush.zero_()
+    cv.set_profiling(True)
+    cv.scan_timing(reset=True)
+    run(K)
+    torch.cuda.synchronize()
+    lines_ms, launches = cv.scan_timing(reset=True)
+    cv.set_profiling(False)
+    flop = GRID_FLOP_PER_POINT_DIR * N * nd * launches
+    peak = sms * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flop / (lines_ms / 1e3) / 1e12 if lines_ms > 0 else None
+    traffic = traffic_per_launch(N * nd, "k_grid_lines_traffic.json", GRID_SOURCES)
+    res = {"workload": (f"global grid of the Sec. 6.1 NH study: {g.n[0]}x{g.n[1]}x{g.n[2]}x{g.n[3]} "
+                        f"= {N} grid points (delta 0.15, diagonal {list(c['diag'])}, off-diagonal "
+                        f"{list(c['off'])}), R^1_1 ({nd} directions), beta_k {c['beta']}, "
+                        f"W^0 then Eq. (4.3) to tol {c['tol']} (kmax {c['kmax']}), ln|det F|"),
+           "value": N * K / (t / 1e3), "unit": "grid-point updates/s (points x steps)",
+           "steps_to_tol": K, "ms_to_tol": t, "ms_runs": ms,
+           "l2": "flushed before each run (256 MiB write); the grid (5.2 MB) fits in L2 within a run",
+           "roofline": {"bound": "alu", "kernel": "k_grid_lines", "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+                        "traffic": traffic,
+                        "peak_source": (f"{sms} SMs x {FP64_FMA_PER_SM} FP64 FMA x 2 x {mhz:.0f} MHz "
+                                        f"(nominal FP64 rate; {peak_src})"),
+                        "flop_per_point_direction": GRID_FLOP_PER_POINT_DIR,
+                        "kernel_ms_per_launch": lines_ms / max(1, launches),
+                        "kernel_share": lines_ms / t, "launches": launches},
+           "gpu_launches_per_run": 1 + 1 + c["kmax"] * 3 + 1}
+    # Algorithms 2 and 3 at 1,048,576 points of the grid's box
+    lo = np.array(g.lo)
+    hi = lo + (np.array(g.n) - 1) * np.array(g.delta)
+    Fq = torch.from_numpy(inputs.cuboid_points(lo, hi, 1 << 20, seed=62)).to(dev)
+    fo = out["forest"][:K]
+    for _ in range(2):
+        cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, abs_det=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    wi, wt, Pq, nl = cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, abs_det=True)
+    e1.record()
+    torch.cuda.synchronize()
+    qms = e0.elapsed_time(e1)
+    res["query"] = {"points": int(Fq.shape[0]), "pts_per_s": Fq.shape[0] / (qms / 1e3),
+                    "ms": qms, "leaves_mean": float(nl.double().mean()),
+                    "leaves_max": int(nl.max()),
+                    "tree_minus_interp_max": float((wt - wi).abs().max())}
+    gold = load_golden("grid61")
+    if gold is not None:
+        Wg = out["W"].cpu().numpy()[gold["idx"]]
+        d = np.asarray(gold["decs"])
+        dg = out["decs"].cpu().numpy()[:K]
+        wi2, wt2, P2, nl2 = cv.grid_query(p, g, c["beta"], off, out["W"], fo, gold["F_query"],
+                                          abs_det=True)
+        res["accuracy_vs_oracle"] = {
+            "steps_equal": bool(K == d.size),
+            "decrease_max_abs_diff": float(np.max(np.abs(dg - d))) if K == d.size else None,
+            "W_K": err_stats(Wg, gold["W_K"]),
+            "query": err_stats(wt2.cpu().numpy(), gold["W_tree"], P2.cpu().numpy(), gold["P"]),
+            "query_leaves_equal": float(np.mean(nl2.cpu().numpy() == gold["leaves"]))}
+    # the shape of the Sec. 6.4 strong-scaling grid (context for the paper's timings)
+    gs = api.GridSpec.from_bounds(GRID_SCALING["diag"], GRID_SCALING["off"], GRID_SCALING["delta"])
+    for _ in range(2):
+        o2 = cv.grid_convexify(p, gs, c["beta"], off, kmax=c["kmax"], tol=c["tol"], abs_det=True,
+                               want_forest=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    o2 = cv.grid_convexify(p, gs, c["beta"], off, kmax=c["kmax"], tol=c["tol"], abs_det=True,
+                           want_forest=False)
+    e1.record()
+    torch.cuda.synchronize()
+    res["grid_43681"] = {"grid": list(gs.n), "points": gs.count,
+                         "steps_to_tol": int(o2["iters"].cpu()[0]), "ms_to_tol": e0.elapsed_time(e1),
+                         "paper_context": ("Sec. 6.4: 1960.7 s on 1 thread, 49.06 s on 64 threads of a "
+                                           "Xeon Phi 7210 for a 43,681-point grid with R^1_1, no tree "
+                                           "(bounds not printed)")}
+    if cpu:
+        res["cpu_baseline"] = grid_oracle_rate(out["W"], K)
+    return res
+
+
+def grid_oracle_rate(WK, K):
+    """The FP64 CPU oracle (as it stands) taking one step of Eq. (4.3) on the
+    whole 648,025-point grid from the device's W^K (all host cores)."""
+    import oracle
+
+    oracle.build()
+    c = GRID61
+    go = oracle.Grid.from_bounds(c["diag"], c["off"], c["delta"])
+    off = oracle.r11_directions()
+    W = WK.cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.grid_step(go, off, W)
+    dt = time.perf_counter() - t0
+    return {"value": go.count / dt, "unit": "grid-point updates/s (points x steps)",
+            "cores": host_cores(), "kind": "oracle",
+            "sample": f"one step of Eq. (4.3) on the whole {go.count}-point grid ({dt:.2f} s)"}
+
+
+def run_grid(a):
+    """The global-grid form alone: one JSON line."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2211_14318_gb300 import api, inputs
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(0)
+    cv = api.Convexifier(0)
+    _, sms, mhz, peak_src = fp32_peak_tflops(torch, dev)
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None else "0")
+    clocks.start()
+    res = global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src,
+                           runs=max(3, a.steps), cpu=not a.no_cpu_baseline)
+    ck = clocks.stop()
+    res.update(metric="grid-point updates/s of the global-grid rank-one convexification (Eq. 4.3)",
+               n_gpus=1, warmup=2, higher_is_better=True, dtype="f64", data="synthetic",
+               clocks=ck)
+    print(json.dumps(res), flush=True)
+    cv.close()
 
 
 def loadpath_oracle_rate(path, step, cores, npts):
@@ -1235,6 +1427,8 @@ def main():
         run_batch(a)
     elif a.form == "northstar":
         run_northstar(a)
+    elif a.form == "grid":
+        run_grid(a)
     elif a.form == "surrogate":
         run_surrogate(a)
     elif a.form == "train":

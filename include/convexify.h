@@ -264,8 +264,8 @@ int cvx_set_profiling(cvx_handle *h, int enable);
 int cvx_get_scan_timing(cvx_handle *h, double *ms, int64_t *launches, int reset);
 
 /* sizeof of the ABI structs, for bindings to check their layouts:
- * which = 0 cvx_params, 1 cvx_node, 2 cvx_laminate, 3 cvx_stats, 4 cvx_problem;
- * -1 otherwise. */
+ * which = 0 cvx_params, 1 cvx_node, 2 cvx_laminate, 3 cvx_stats, 4 cvx_problem,
+ * 5 cvx_grid; -1 otherwise. */
 int cvx_struct_size(int which);
 
 /* Sets the launch shape of the line-scan kernel of convexify_points: warps per
@@ -326,6 +326,98 @@ int convexify_points(cvx_handle *h, const cvx_params *p, int64_t n, const double
  * (n x (2^{K+1}-1), K = p->depth) are DEVICE arrays.  Asynchronous. */
 int cvx_tree_tangent(cvx_handle *h, const cvx_params *p, int64_t n, const double *beta_k,
                      const cvx_node *tree, double *A, cvx_stream s);
+
+/* --------------------------------------------------------- global-grid form */
+
+/* The paper's own algorithm (Secs. 4.1-4.3, 5.1-5.3): W is stored on a grid of
+ * deformation gradients and Eq. (4.3) is iterated on the whole grid,
+ *   W^{k+1}(F) = min( W^k(F), min_R hull_l[ W^k(F + l R) ](0) ),
+ * where the inner term is Algorithm 1's lower hull of the values of W^k at the
+ * grid points of the line through F, read at F.  The lamination forest records
+ * per iteration and grid point the winning laminate; Algorithm 2 builds the
+ * tree of an arbitrary F from it (multilinear-interpolation corners where F is
+ * not a grid point, Sec. 5.3) and Algorithm 3 evaluates W and P over it.
+ *
+ * Grid (Sec. 5.2, the cuboid form): component c of F (order F11, F12, F21, F22)
+ * takes the values lo[c] + i delta[c], i = 0 .. n[c] - 1; flat index
+ * ((i0 n1 + i1) n2 + i2) n3 + i3; 1 <= n[c] <= 512, at most 2^31 - 1 points.
+ *
+ * Directions are grid-index offsets o (nd x 4 int32, HOST): one step of a line
+ * moves component c by o[c] grid steps, i.e. F + l R with R_c = o[c] delta[c]
+ * (the matrix a (x) b of Eq. 5.1 scaled by delta when all delta[c] are equal,
+ * as in the study of Sec. 6.1).  Every offset must be nonzero and rank-one
+ * (o0 o3 = o1 o2), |o[c]| <= 512, 1 <= nd <= 4096.  cvx_grid_r11 writes the 16
+ * directions of Eq. (5.1) in the order used by the ties rule below.
+ *
+ * Lines are the maximal runs of grid points F + l R inside the grid.  Values
+ * that are not finite (det F <= 0, see abs_det) are left out of the hulls and
+ * keep their value.  A point laminates along the lowest direction index whose
+ * hull value is strictly below both W^k(F) and every lower-indexed
+ * direction's; its record is (dir, l-, l+) with l- < 0 < l+ the hull vertices
+ * around it in line steps, and F+- = F + l+- R with weight xi = -l-/(l+ - l-)
+ * of F+ (Algorithm 2's |F - F-|_1 / |F+ - F-|_1); (-1, 0, 0) if it does not.
+ * Hull predicates and chord values are FP64 with every operation rounded on
+ * its own, so a step is reproducible bit for bit.
+ *
+ * abs_det (energy of the grid study): 0 = Eq. (2.9) with det F <= 0 excluded
+ * (NaN); 1 = the Neo-Hooke term takes ln|det F|, so that det F < 0 mirrors
+ * det F > 0 (the reading under which the convergence history printed for the
+ * Sec. 6.1 study is reproduced); ignored for the double-well test energy. */
+typedef struct cvx_grid {
+    int32_t n[4];
+    double lo[4];
+    double delta[4];
+} cvx_grid;
+
+/* The reduced direction set R^1_1 of Eq. (5.1) as grid-index offsets: a, b run
+ * over (1,0), (0,1), (1,1), (1,-1) (one of each pair +-v: the sign of a (x) b
+ * gives the same line); row 4 ia + ib = (a1 b1, a1 b2, a2 b1, a2 b2).
+ * off: HOST, 16 x 4. */
+int cvx_grid_r11(int32_t *off);
+
+/* W^0 on the grid: W (DEVICE, N values in flat order) = the energy of the
+ * material in p (mu, lambda_L, D_inf, D0, energy; the line fields are not
+ * used) at every grid point with history beta_k. */
+int cvx_grid_energy(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
+                    int32_t abs_det, double *W, cvx_stream s);
+
+/* One iteration of Eq. (4.3): W_out from W_in (DEVICE, N each, no aliasing);
+ * lam (DEVICE, N x 3 int32, nullable) = the laminate records; dec (DEVICE
+ * scalar, nullable) = the largest decrease W_in - W_out over the points where
+ * both are finite.  Workspace: the handle's (about 12 bytes per point and
+ * direction, in chunks of at most 512 MB, plus the line starts). */
+int cvx_grid_step(cvx_handle *h, const cvx_grid *g, int32_t nd, const int32_t *off,
+                  const double *W_in, double *W_out, int32_t *lam, double *dec, cvx_stream s);
+
+/* The global iteration (Sec. 4.1): W^0 = cvx_grid_energy, then Eq. (4.3) until
+ * the largest decrease of a step is at most tol or kmax steps were taken
+ * (1 <= kmax <= 64; the study of Sec. 6 uses tol = 1e-4, kmax = 20).  The stop
+ * is decided on the device: nothing waits on the host, and the steps after
+ * the stop return at once.  Outputs (DEVICE): W (N) = W^K; iters (one int32)
+ * = K; forest (kmax x N x 3 int32, nullable) = the records of step k at
+ * forest + 3 N k (rows k >= K are not written); decs (kmax, nullable) = the
+ * largest decrease of each step (0 after the stop). */
+int cvx_grid_convexify(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
+                       int32_t abs_det, int32_t nd, const int32_t *off, int32_t kmax, double tol,
+                       double *W, int32_t *forest, double *decs, int32_t *iters, cvx_stream s);
+
+/* Relaxed energy and stress at n arbitrary points F (DEVICE, n x 4) after K
+ * iterations (WK = W^K, forest = K x N x 3 records, both DEVICE):
+ *   W_interp (n): the multilinear interpolation of W^K (Sec. 4.1, values off
+ *     the grid by interpolation);
+ *   W_tree (n), P (n x 4): Algorithm 3 over Algorithm 2's tree: the cell
+ *     corners of F with their interpolation weights (one corner if F is a grid
+ *     point; coordinates within 1e-12 grid steps of a grid value count as on
+ *     it) at order K, each expanded through the latest iteration k <= order
+ *     that split it (children at order k - 1), W and P (Eq. 2.12) at the
+ *     leaves;
+ *   leaves (n int64, nullable): the leaves of the tree.
+ * NaN (leaves 0) outside the grid.  nd and off must be those of the run that
+ * made the forest.  0 <= K <= 64. */
+int cvx_grid_query(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
+                   int32_t abs_det, int32_t nd, const int32_t *off, int32_t K, const double *WK,
+                   const int32_t *forest, int64_t n, const double *F, double *W_interp,
+                   double *W_tree, double *P, int64_t *leaves, cvx_stream s);
 
 /* ------------------------------------------------------------ batched form */
 

@@ -69,6 +69,11 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 4), ("lo", ctypes.c_double * 4),
+                ("delta", ctypes.c_double * 4)]
+
+
 class _TrainCfg(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("init", ctypes.c_int32), ("seed", ctypes.c_uint64)]
@@ -120,6 +125,14 @@ def lib() -> ctypes.CDLL:
                               ctypes.c_double, vp, vp, vp, vp, vp, vp, vp],
         "cvx_get_batch_tuning": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)],
+        "cvx_grid_r11": [vp],
+        "cvx_grid_energy": [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Grid), ctypes.c_double,
+                            i32, vp, vp],
+        "cvx_grid_step": [vp, ctypes.POINTER(_Grid), i32, vp, vp, vp, vp, vp, vp],
+        "cvx_grid_convexify": [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Grid), ctypes.c_double,
+                               i32, i32, vp, i32, ctypes.c_double, vp, vp, vp, vp, vp],
+        "cvx_grid_query": [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Grid), ctypes.c_double,
+                           i32, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -136,7 +149,9 @@ def exported_symbols() -> Sequence[str]:
             "convexify_points", "convexify_points_static", "convexify_batch", "cvx_tree_tangent",
             "cvx_get_batch_tuning", "surrogate_set_weights", "surrogate_get_weights",
             "surrogate_forward", "surrogate_loss_grad", "surrogate_train", "surrogate_save",
-            "surrogate_load", "cvx_gemm_bf16", "surrogate_labels", "surrogate_propose")
+            "surrogate_load", "cvx_gemm_bf16", "surrogate_labels", "surrogate_propose",
+            "cvx_grid_r11", "cvx_grid_energy", "cvx_grid_step", "cvx_grid_convexify",
+            "cvx_grid_query")
 
 
 def _check(rc: int, what: str):
@@ -191,6 +206,43 @@ class Params:
     @property
     def tree_size(self) -> int:
         return (1 << (self.depth + 1)) - 1
+
+
+@dataclass
+class GridSpec:
+    """cvx_grid: the cuboid deformation-gradient grid of Sec. 5.2; component c
+    of F (F11, F12, F21, F22) takes lo[c] + i delta[c], i = 0 .. n[c] - 1
+    (flat index with F22 fastest)."""
+    n: tuple
+    lo: tuple
+    delta: tuple
+
+    @classmethod
+    def from_bounds(cls, diag, off, delta):
+        """Both diagonal entries on diag = (lo, hi), both off-diagonal entries
+        on off = (lo, hi), spacings delta = (diagonal, off-diagonal); hi is a
+        grid value (the parametrisation of Table tab:2Dconvexification)."""
+        (dlo, dhi), (olo, ohi) = diag, off
+        dd, do = delta
+        nd = int(round((dhi - dlo) / dd)) + 1
+        no = int(round((ohi - olo) / do)) + 1
+        return cls((nd, no, no, nd), (dlo, olo, olo, dlo), (dd, do, do, dd))
+
+    @property
+    def count(self) -> int:
+        return int(np.prod(self.n))
+
+    def c(self) -> _Grid:
+        return _Grid((ctypes.c_int32 * 4)(*[int(x) for x in self.n]),
+                     (ctypes.c_double * 4)(*[float(x) for x in self.lo]),
+                     (ctypes.c_double * 4)(*[float(x) for x in self.delta]))
+
+
+def grid_r11() -> np.ndarray:
+    """(16, 4) int32 grid-index offsets of the directions of Eq. (5.1)."""
+    off = np.zeros((16, 4), dtype=np.int32)
+    _check(lib().cvx_grid_r11(off.ctypes.data), "cvx_grid_r11")
+    return off
 
 
 def _ptr(t) -> Optional[int]:
@@ -499,6 +551,84 @@ class Convexifier:
 
     def surrogate_load(self, path: str):
         _check(lib().surrogate_load(self._h, path.encode()), "surrogate_load")
+
+    # ------------------------------------------------------ global-grid form
+    def grid_energy(self, p: Params, grid: GridSpec, beta_k: float, abs_det: bool = False,
+                    stream=None):
+        """W^0 on the grid (N values, flat order)."""
+        import torch
+
+        W = torch.empty(grid.count, dtype=torch.float64, device=f"cuda:{self.device}")
+        c, g = p.c(), grid.c()
+        _check(lib().cvx_grid_energy(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
+                                     int(abs_det), _ptr(W), _stream(stream)), "cvx_grid_energy")
+        return W
+
+    def grid_step(self, grid: GridSpec, off, W_in, stream=None):
+        """One iteration of Eq. (4.3): (W_out, lam (N x 3 int32), dec (device scalar))."""
+        import torch
+
+        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+        W_in = self._dev(W_in, torch.float64).reshape(-1)
+        W_out = torch.empty_like(W_in)
+        lam = torch.empty(grid.count, 3, dtype=torch.int32, device=W_in.device)
+        dec = torch.empty(1, dtype=torch.float64, device=W_in.device)
+        g = grid.c()
+        _check(lib().cvx_grid_step(self._h, ctypes.byref(g), off.shape[0], off.ctypes.data,
+                                   _ptr(W_in), _ptr(W_out), _ptr(lam), _ptr(dec),
+                                   _stream(stream)), "cvx_grid_step")
+        return W_out, lam, dec
+
+    def grid_convexify(self, p: Params, grid: GridSpec, beta_k: float, off, kmax: int = 20,
+                       tol: float = 1e-4, abs_det: bool = False, want_forest: bool = True,
+                       out: Optional[dict] = None, stream=None):
+        """The global iteration of Sec. 4.1 on the device: dict with W (= W^K),
+        forest (kmax x N x 3, rows >= K unwritten), decs (kmax) and iters (a
+        device int32; read it to get K).  ``out`` may hold preallocated
+        tensors with those names."""
+        import torch
+
+        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+        dev = f"cuda:{self.device}"
+        N = grid.count
+        o = dict(out) if out else {}
+        W = o.get("W") if o.get("W") is not None else torch.empty(N, dtype=torch.float64, device=dev)
+        forest = None
+        if want_forest:
+            forest = o.get("forest")
+            if forest is None:
+                forest = torch.empty(kmax, N, 3, dtype=torch.int32, device=dev)
+        decs = o.get("decs") if o.get("decs") is not None else torch.empty(kmax, dtype=torch.float64, device=dev)
+        iters = o.get("iters") if o.get("iters") is not None else torch.empty(1, dtype=torch.int32, device=dev)
+        c, g = p.c(), grid.c()
+        _check(lib().cvx_grid_convexify(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
+                                        int(abs_det), off.shape[0], off.ctypes.data, int(kmax),
+                                        float(tol), _ptr(W), _ptr(forest), _ptr(decs),
+                                        _ptr(iters), _stream(stream)), "cvx_grid_convexify")
+        return dict(W=W, forest=forest, decs=decs, iters=iters)
+
+    def grid_query(self, p: Params, grid: GridSpec, beta_k: float, off, WK, forest, F,
+                   abs_det: bool = False, K: Optional[int] = None, stream=None):
+        """(W_interp, W_tree, P, leaves) at points F from W^K and the first K
+        forest rows (K = len(forest) unless given)."""
+        import torch
+
+        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+        WK = self._dev(WK, torch.float64).reshape(-1)
+        fa = self._dev(forest, torch.int32).reshape(-1, grid.count, 3)
+        K = fa.shape[0] if K is None else int(K)
+        F = self._dev(F, torch.float64).reshape(-1, 4)
+        n = F.shape[0]
+        wi = torch.empty(n, dtype=torch.float64, device=F.device)
+        wt = torch.empty(n, dtype=torch.float64, device=F.device)
+        P = torch.empty(n, 4, dtype=torch.float64, device=F.device)
+        nl = torch.empty(n, dtype=torch.int64, device=F.device)
+        c, g = p.c(), grid.c()
+        _check(lib().cvx_grid_query(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
+                                    int(abs_det), off.shape[0], off.ctypes.data, K, _ptr(WK),
+                                    _ptr(fa), n, _ptr(F), _ptr(wi), _ptr(wt), _ptr(P), _ptr(nl),
+                                    _stream(stream)), "cvx_grid_query")
+        return wi, wt, P, nl
 
     def batch_tuning(self):
         """(warps per CTA, directions-per-item cap, taken from the cache) of the

@@ -311,6 +311,7 @@ int cvx_struct_size(int which) {
     case 2: return (int)sizeof(cvx_laminate);
     case 3: return (int)sizeof(cvx_stats);
     case 4: return (int)sizeof(cvx_problem);
+    case 5: return (int)sizeof(cvx_grid);
     default: return -1;
     }
 }

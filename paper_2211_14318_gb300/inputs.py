@@ -162,3 +162,11 @@ def surrogate_inputs(n: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Training / held-out points for the learned proposal: material points
     with lam ~ U[1, 2]."""
     return material_points(n, seed=seed, lam_lo=1.0, lam_hi=2.0)
+
+
+def cuboid_points(lo, hi, n: int, seed: int = 0) -> np.ndarray:
+    """(n, 4) deformation gradients drawn uniformly from the box lo <= F <= hi
+    (per entry F11, F12, F21, F22): query points of the global-grid form."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64),
+                       size=(n, 4))

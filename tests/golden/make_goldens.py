@@ -20,6 +20,13 @@ Workloads (the sizes the benchmark runs, subsampled evenly):
   in {1, 10, 20} with the history of the earlier steps (Eq. 2.5);
   128 x 128 angles, L = 2049, t in [-0.5, 0.5], depth 3.
 
+* ``grid61``: the global-grid study of Sec. 6.1 (Table tab:2Dconvexification,
+  NH row: mu = 1, lambda = 0.5, D_inf = 0.9, D_0 = 0.3, beta_k = 0.06; grid
+  delta 0.15, diagonal [0.1, 3.4], off-diagonal [-2.55, 2.55]: 648,025
+  points; R^1_1; tol 1e-4, kmax 20; ln|det F|): the decrease of every step,
+  W^K at 4,096 evenly spaced grid points, and Algorithms 2 and 3 over the
+  forest at 1,024 points drawn uniformly from the grid's box (seed 61).
+
 Usage: python tests/golden/make_goldens.py [--only NAME ...] [--threads N]
 The load-path files take hours of CPU time (the oracle is plain FP64 C).
 """
@@ -104,6 +111,33 @@ def write(name, desc, na, L, t_half, depth, thunk, threads):
     print(f"{name}: {N_SUB} points in {dt:.0f} s -> {path}", flush=True)
 
 
+GRID61 = dict(mat=dict(mu=1.0, lam=0.5, Dinf=0.9, D0=0.3), beta=0.06, diag=(0.1, 3.4),
+              off=(-2.55, 2.55), delta=(0.15, 0.15), kmax=20, tol=1e-4)
+
+
+def write_grid61(threads):
+    c = GRID61
+    mat = oracle.Material(**c["mat"])
+    g = oracle.Grid.from_bounds(c["diag"], c["off"], c["delta"])
+    off = oracle.r11_directions()
+    t0 = time.perf_counter()
+    W, forest, decs = oracle.grid_convexify(mat, g, c["beta"], off, kmax=c["kmax"], tol=c["tol"],
+                                            abs_det=True, nthreads=threads)
+    dt = time.perf_counter() - t0
+    idx = subsample(g.count)
+    P = g.points()
+    Fq = inputs.cuboid_points(P.min(0), P.max(0), 1024, seed=61)
+    wi, wt, Pq, nl = oracle.grid_query(mat, g, c["beta"], off, W[-1], forest, Fq, abs_det=True,
+                                       nthreads=threads)
+    meta = dict(workload="Sec. 6.1 NH grid study, 648,025 points, R^1_1, tol 1e-4, kmax 20, "
+                "ln|det F|", **{k: v for k, v in c.items() if k != "mat"}, material=c["mat"],
+                oracle_seconds=dt, threads=threads, iterations=len(decs))
+    path = os.path.join(HERE, "grid61.npz")
+    np.savez_compressed(path, meta=np.array(json.dumps(meta)), decs=np.array(decs), idx=idx,
+                        W_K=W[-1][idx], F_query=Fq, W_interp=wi, W_tree=wt, P=Pq, leaves=nl)
+    print(f"grid61: {len(decs)} iterations in {dt:.1f} s -> {path}", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="*", default=None)
@@ -114,6 +148,8 @@ def main():
         if a.only and name not in a.only:
             continue
         write(name, desc, na, L, t_half, depth, thunk, a.threads or oracle.cores())
+    if not a.only or "grid61" in a.only:
+        write_grid61(a.threads or oracle.cores())
 
 
 if __name__ == "__main__":

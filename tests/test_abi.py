@@ -162,3 +162,68 @@ def test_static_entry_rejects_direction_counts_before_cuda(cvxlib, na, nb, msg):
     rc = cvxlib.convexify_points_static(ctypes.byref(c), 4, None, None, None, None, None, None)
     assert rc == -1
     assert msg in _err(cvxlib)
+
+
+def test_grid_struct_and_r11_table(cvxlib, orc):
+    """cvx_grid's layout matches the binding, and the library's table of the
+    directions of Eq. (5.1) is the same reading, in the same order, as the
+    oracle's (the order decides ties between directions)."""
+    from paper_2211_14318_gb300 import api
+
+    assert cvxlib.cvx_struct_size(5) == ctypes.sizeof(api._Grid)
+    np_off = api.grid_r11()
+    assert np_off.shape == (16, 4)
+    assert (np_off == orc.r11_directions()).all()
+    g = api.GridSpec.from_bounds((0.1, 3.4), (-2.55, 2.55), (0.15, 0.15))
+    assert g.count == 648025 and g.n == (23, 35, 35, 23)
+
+
+@pytest.mark.parametrize("n,off,msg", [
+    ((0, 3, 3, 3), None, "grid points"),
+    ((3, 3, 3, 600), None, "grid points"),
+    ((3, 3, 3, 3), [[0, 0, 0, 0]], "zero"),
+    ((3, 3, 3, 3), [[1, 1, 0, 1]], "rank-one"),
+    ((3, 3, 3, 3), [[1000, 0, 0, 0]], "offset"),
+])
+def test_grid_validation_before_cuda(cvxlib, n, off, msg):
+    import numpy as np
+
+    from paper_2211_14318_gb300 import api
+
+    g = api.GridSpec(n, (0.0,) * 4, (0.1,) * 4).c()
+    o = np.ascontiguousarray(off if off is not None else api.grid_r11(), dtype=np.int32)
+    rc = cvxlib.cvx_grid_step(None, ctypes.byref(g), o.shape[0], o.ctypes.data, None, None,
+                              None, None, None)
+    assert rc == -1
+    assert msg in _err(cvxlib)
+
+
+def test_grid_calls_reject_bad_arguments_before_cuda(cvxlib):
+    import numpy as np
+
+    from paper_2211_14318_gb300 import api
+
+    g = api.GridSpec((3, 3, 3, 3), (0.5,) * 4, (0.25,) * 4).c()
+    c = api.Params().c()
+    o = api.grid_r11()
+    assert cvxlib.cvx_grid_convexify(None, ctypes.byref(c), ctypes.byref(g), 0.0, 0, 16,
+                                     o.ctypes.data, 0, 1e-4, None, None, None, None, None) == -1
+    assert "kmax" in _err(cvxlib)
+    assert cvxlib.cvx_grid_convexify(None, ctypes.byref(c), ctypes.byref(g), 0.0, 0, 16,
+                                     o.ctypes.data, 20, float("nan"), None, None, None, None,
+                                     None) == -1
+    assert "tol" in _err(cvxlib)
+    assert cvxlib.cvx_grid_convexify(None, ctypes.byref(c), ctypes.byref(g), 0.0, 0, 16,
+                                     o.ctypes.data, 20, 1e-4, None, None, None, None, None) == -1
+    assert "handle" in _err(cvxlib)
+    assert cvxlib.cvx_grid_query(None, ctypes.byref(c), ctypes.byref(g), 0.0, 0, 16,
+                                 o.ctypes.data, 65, None, None, 1, None, None, None, None, None,
+                                 None) == -1
+    assert "K must" in _err(cvxlib)
+    assert cvxlib.cvx_grid_step(None, ctypes.byref(g), 0, o.ctypes.data, None, None, None, None,
+                                None) == -1
+    assert "direction count" in _err(cvxlib)
+    assert cvxlib.cvx_grid_energy(None, ctypes.byref(c), ctypes.byref(g), float("inf"), 0, None,
+                                  None) == -1
+    assert "handle" in _err(cvxlib) or "beta" in _err(cvxlib)
+    assert cvxlib.cvx_grid_r11(None) == -1
