@@ -131,6 +131,16 @@ def lib() -> ctypes.CDLL:
         L.orc_grid_point.argtypes = [vp, i64, vp]
         L.orc_r11_directions.restype = None
         L.orc_r11_directions.argtypes = [vp]
+        L.orc_r11_directions3.restype = None
+        L.orc_r11_directions3.argtypes = [vp]
+        L.orc_psi0_stvk.restype = d
+        L.orc_psi0_stvk.argtypes = [d, d, d, d]
+        L.orc_invariants.restype = None
+        L.orc_invariants.argtypes = [i32, vp, vp, vp, vp]
+        L.orc_energy_dim.restype = d
+        L.orc_energy_dim.argtypes = [vp, i32, vp, d, i32]
+        L.orc_stress_dim.restype = None
+        L.orc_stress_dim.argtypes = [vp, i32, vp, d, i32, vp]
         L.orc_grid_energy.restype = None
         L.orc_grid_energy.argtypes = [vp, vp, d, i32, vp, i32]
         L.orc_grid_query.restype = None
@@ -148,7 +158,8 @@ def _p(a: np.ndarray) -> int:
 
 class Material:
     """Material of Sec. 2: Lame (mu, lam), damage (D_inf, D_0); energy 0 = NH
-    with damage (Eq. 2.9), 1 = separable double-well test energy."""
+    with damage (Eqs. 2.3, 2.9), 1 = separable double-well test energy,
+    2 = St. Venant-Kirchhoff with damage (Eqs. 2.2, 2.9)."""
 
     def __init__(self, mu=1.0, lam=5.0, Dinf=0.99, D0=0.5, energy=0):
         self.mu, self.lam, self.Dinf, self.D0, self.energy = mu, lam, Dinf, D0, energy
@@ -162,6 +173,36 @@ class Material:
 def psi0_nh(I1: float, J: float, mu: float, lam: float) -> float:
     """Eq. (2.3) in the invariants."""
     return lib().orc_psi0_nh(I1, J, mu, lam)
+
+
+def psi0_stvk(I1: float, I2: float, mu: float, lam: float) -> float:
+    """Eq. (2.2) in the invariants."""
+    return lib().orc_psi0_stvk(I1, I2, mu, lam)
+
+
+def invariants(F) -> tuple:
+    """(I1, I2, J) of C = F^T F for F in R^{2x2} (plane strain) or R^{3x3}
+    (row-major)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    d = 2 if F.size == 4 else 3
+    out = np.zeros(3)
+    lib().orc_invariants(d, _p(F), _p(out[0:]), _p(out[1:]), _p(out[2:]))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def energy_dim(mat: Material, F, beta_k: float, rule: int = 0) -> float:
+    """W(F), Eq. (2.9), for F in R^{2x2} (plane strain) or R^{3x3} under a grid
+    rule for det F <= 0 (0 excluded, 1 kept; see grid_energy)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    return lib().orc_energy_dim(mat.ref, 2 if F.size == 4 else 3, _p(F), beta_k, int(rule))
+
+
+def stress_dim(mat: Material, F, beta_k: float, rule: int = 0) -> np.ndarray:
+    """P = dW/dF (row-major, d x d entries) of energy_dim."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    P = np.zeros(F.size)
+    lib().orc_stress_dim(mat.ref, 2 if F.size == 4 else 3, _p(F), beta_k, int(rule), _p(P))
+    return P
 
 
 def W_of_psi0(s: float, beta_k: float, Dinf: float, D0: float) -> float:
@@ -370,31 +411,48 @@ if __name__ == "__main__":  # pragma: no cover
 
 
 class _Grid(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32 * 4), ("lo", ctypes.c_double * 4),
-                ("delta", ctypes.c_double * 4)]
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32 * 9), ("lo", ctypes.c_double * 9),
+                ("delta", ctypes.c_double * 9)]
 
 
 class Grid:
-    """Cuboid grid of Sec. 5.2: component c of F (F11, F12, F21, F22) takes
-    lo[c] + i delta[c], i = 0 .. n[c] - 1 (flat index with F22 fastest)."""
+    """Cuboid grid of Sec. 5.2 for F in R^{d x d}: component c of F (row-major;
+    4 components for d = 2, 9 for d = 3) takes lo[c] + i delta[c],
+    i = 0 .. n[c] - 1 (flat index with the last component fastest)."""
 
     def __init__(self, n, lo, delta):
         self.n = tuple(int(x) for x in n)
         self.lo = tuple(float(x) for x in lo)
         self.delta = tuple(float(x) for x in delta)
-        self._c = _Grid((ctypes.c_int32 * 4)(*self.n), (ctypes.c_double * 4)(*self.lo),
-                        (ctypes.c_double * 4)(*self.delta))
+        D = len(self.n)
+        assert D in (4, 9) and len(self.lo) == D and len(self.delta) == D
+        self.dim = 2 if D == 4 else 3
+        pad = (0,) * (9 - D)
+        self._c = _Grid(self.dim, (ctypes.c_int32 * 9)(*(self.n + pad)),
+                        (ctypes.c_double * 9)(*(self.lo + (0.0,) * (9 - D))),
+                        (ctypes.c_double * 9)(*(self.delta + (0.0,) * (9 - D))))
+
+    @property
+    def D(self) -> int:
+        return len(self.n)
 
     @classmethod
-    def from_bounds(cls, diag, off, delta):
-        """Grid with the same bounds (lo, hi) on both diagonal entries, the
-        same on both off-diagonal entries, spacing delta (diagonal,
-        off-diagonal); hi is a grid value."""
+    def from_bounds(cls, diag, off, delta, dim: int = 2):
+        """Grid with the same bounds (lo, hi) on every diagonal entry and the
+        same on every off-diagonal entry, spacing delta (diagonal,
+        off-diagonal); hi is a grid value (Tables tab:2Dconvexification,
+        tab:3Dconvexification)."""
         (dlo, dhi), (olo, ohi) = diag, off
         dd, do = delta
         nd = int(round((dhi - dlo) / dd)) + 1
         no = int(round((ohi - olo) / do)) + 1
-        return cls((nd, no, no, nd), (dlo, olo, olo, dlo), (dd, do, do, dd))
+        n, lo, de = [], [], []
+        for i in range(dim):
+            for j in range(dim):
+                n.append(nd if i == j else no)
+                lo.append(dlo if i == j else olo)
+                de.append(dd if i == j else do)
+        return cls(n, lo, de)
 
     @property
     def ref(self):
@@ -405,30 +463,41 @@ class Grid:
         return int(lib().orc_grid_count(self.ref))
 
     def points(self) -> np.ndarray:
-        """(N, 4) grid points in flat-index order."""
-        axes = [self.lo[c] + np.arange(self.n[c]) * self.delta[c] for c in range(4)]
-        return np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, 4)
+        """(N, D) grid points in flat-index order."""
+        axes = [self.lo[c] + np.arange(self.n[c]) * self.delta[c] for c in range(self.D)]
+        return np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, self.D)
 
 
-def r11_directions() -> np.ndarray:
-    """(16, 4) grid-index offsets of the directions of Eq. (5.1)."""
-    off = np.zeros((16, 4), dtype=np.int32)
-    lib().orc_r11_directions(_p(off))
+def r11_directions(dim: int = 2) -> np.ndarray:
+    """Grid-index offsets of the directions of Eq. (5.1): (16, 4) for d = 2,
+    (169, 9) for d = 3."""
+    if dim == 2:
+        off = np.zeros((16, 4), dtype=np.int32)
+        lib().orc_r11_directions(_p(off))
+    else:
+        off = np.zeros((169, 9), dtype=np.int32)
+        lib().orc_r11_directions3(_p(off))
     return off
 
 
+def _rule(abs_det: bool, rule):
+    return int(rule) if rule is not None else (1 if abs_det else 0)
+
+
 def grid_energy(mat: Material, grid: Grid, beta_k: float, abs_det: bool = False,
-                nthreads: int = 0) -> np.ndarray:
-    """W^0 on the grid (abs_det: ln|det F| for det F < 0, the Sec. 6.1 reading)."""
+                nthreads: int = 0, rule=None) -> np.ndarray:
+    """W^0 on the grid.  rule (det F <= 0): 0 excluded (NaN); 1 (abs_det=True)
+    ln|det F| for Eq. (2.3), and Eq. (2.2) kept everywhere."""
     W = np.empty(grid.count)
-    lib().orc_grid_energy(mat.ref, grid.ref, float(beta_k), int(abs_det), _p(W), int(nthreads))
+    lib().orc_grid_energy(mat.ref, grid.ref, float(beta_k), _rule(abs_det, rule), _p(W),
+                          int(nthreads))
     return W
 
 
 def grid_step(grid: Grid, off: np.ndarray, W: np.ndarray, want_h: bool = False,
               nthreads: int = 0):
     """One iteration of Eq. (4.3): (W_next, dir, l_minus, l_plus, decrease[, h])."""
-    off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+    off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, grid.D)
     W = np.ascontiguousarray(W, dtype=np.float64)
     N = grid.count
     Wn = np.empty(N)
@@ -443,16 +512,21 @@ def grid_step(grid: Grid, off: np.ndarray, W: np.ndarray, want_h: bool = False,
 
 
 def grid_convexify(mat: Material, grid: Grid, beta_k: float, off: np.ndarray, kmax: int = 20,
-                   tol: float = 1e-4, abs_det: bool = False, nthreads: int = 0):
+                   tol: float = 1e-4, abs_det: bool = False, nthreads: int = 0, rule=None,
+                   keep_all: bool = True):
     """The global iteration (Sec. 4.1): W^0 = W on the grid, W^{k+1} by
     Eq. (4.3), stopped after kmax iterations or once the largest decrease is
     at most tol (Sec. 6).  Returns (W^k list, forest, decreases) with forest[k]
-    = (dir, l_minus, l_plus) of iteration k + 1."""
-    W = [grid_energy(mat, grid, beta_k, abs_det, nthreads)]
+    = (dir, l_minus, l_plus) of iteration k + 1 (keep_all=False: only W^0 and
+    W^K are kept)."""
+    W = [grid_energy(mat, grid, beta_k, abs_det, nthreads, rule)]
     forest, decs = [], []
     for _ in range(kmax):
         Wn, d, lm, lp, dec = grid_step(grid, off, W[-1], nthreads=nthreads)
-        W.append(Wn)
+        if keep_all or len(W) < 2:
+            W.append(Wn)
+        else:
+            W[-1] = Wn
         forest.append((d, lm, lp))
         decs.append(dec)
         if dec <= tol:
@@ -466,17 +540,18 @@ def forest_array(forest) -> np.ndarray:
 
 
 def grid_query(mat: Material, grid: Grid, beta_k: float, off: np.ndarray, WK: np.ndarray, forest,
-               F: np.ndarray, abs_det: bool = False, nthreads: int = 0):
-    """(W_interp, W_tree, P, leaves) at points F after K = len(forest)
+               F: np.ndarray, abs_det: bool = False, nthreads: int = 0, rule=None):
+    """(W_interp, W_tree, P, leaves) at points F (n x D) after K = len(forest)
     iterations: the multilinear interpolation of W^K, and Algorithm 3 over
     Algorithm 2's tree."""
-    off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+    D = grid.D
+    off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, D)
     fa = forest_array(forest) if not isinstance(forest, np.ndarray) else np.ascontiguousarray(forest, dtype=np.int32)
-    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 4)
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, D)
     n = F.shape[0]
-    wi, wt, P = np.empty(n), np.empty(n), np.empty((n, 4))
+    wi, wt, P = np.empty(n), np.empty(n), np.empty((n, D))
     nl = np.empty(n, dtype=np.int64)
-    lib().orc_grid_query(mat.ref, grid.ref, float(beta_k), int(abs_det), _p(off), fa.shape[0],
-                         _p(np.ascontiguousarray(WK, dtype=np.float64)), _p(fa), n, _p(F), _p(wi),
-                         _p(wt), _p(P), _p(nl), int(nthreads))
+    lib().orc_grid_query(mat.ref, grid.ref, float(beta_k), _rule(abs_det, rule), _p(off),
+                         fa.shape[0], _p(np.ascontiguousarray(WK, dtype=np.float64)), _p(fa), n,
+                         _p(F), _p(wi), _p(wt), _p(P), _p(nl), int(nthreads))
     return wi, wt, P, nl

@@ -122,8 +122,17 @@ static void nh_invariants(const double F[4], double *I1, double *J)
     *J = F[0] * F[3] - F[1] * F[2];
 }
 
+double orc_psi0_stvk(double I1, double I2, double mu, double lam);
+void orc_invariants(int32_t d, const double *F, double *I1, double *I2, double *J);
+
+/* psi0(F) of the material (Eq. 2.3, or Eq. 2.2 for energy 2), plane strain. */
 double orc_psi0_F(const orc_material *m, const double F[4])
 {
+    if (m->energy == 2) {
+        double I1, I2, J;
+        orc_invariants(2, F, &I1, &I2, &J);
+        return orc_psi0_stvk(I1, I2, m->mu, m->lam);
+    }
     double I1, J;
     nh_invariants(F, &I1, &J);
     return orc_psi0_nh(I1, J, m->mu, m->lam);
@@ -138,11 +147,21 @@ static double dw_energy(const double F[4])
     return a * a + F[1] * F[1] + F[2] * F[2] + d * d;
 }
 
-/* Incremental stress potential W(F), Eq. (2.9); NaN where det F <= 0. */
+static void stvk_dpsi0(const orc_material *m, int32_t d, const double *F, double *G);
+
+/* Incremental stress potential W(F), Eq. (2.9); NaN where det F <= 0.
+ * energy 0: Eq. (2.3); 2: Eq. (2.2) (plane strain); 1: the double well. */
 double orc_energy(const orc_material *m, const double F[4], double beta_k)
 {
     if (m->energy == 1)
         return dw_energy(F);
+    if (m->energy == 2) {
+        double I1, I2, J;
+        orc_invariants(2, F, &I1, &I2, &J);
+        if (!(J > 0.0))
+            return NAN;
+        return orc_W_of_psi0(orc_psi0_stvk(I1, I2, m->mu, m->lam), beta_k, m->Dinf, m->D0);
+    }
     double I1, J;
     nh_invariants(F, &I1, &J);
     if (!(J > 0.0))
@@ -162,6 +181,21 @@ void orc_stress(const orc_material *m, const double F[4], double beta_k, double 
         P[1] = 2.0 * F[1];
         P[2] = 2.0 * F[2];
         P[3] = 2.0 * (F[3] - 1.0);
+        return;
+    }
+    if (m->energy == 2) {
+        double I1, I2, J, G[4];
+        orc_invariants(2, F, &I1, &I2, &J);
+        if (!(J > 0.0)) {
+            P[0] = P[1] = P[2] = P[3] = NAN;
+            return;
+        }
+        double s = orc_psi0_stvk(I1, I2, m->mu, m->lam);
+        double beta = s > beta_k ? s : beta_k;
+        double g = 1.0 - orc_damage(beta, m->Dinf, m->D0);
+        stvk_dpsi0(m, 2, F, G);
+        for (int i = 0; i < 4; ++i)
+            P[i] = g * G[i];
         return;
     }
     double I1, J;
@@ -189,6 +223,11 @@ void orc_stress(const orc_material *m, const double F[4], double beta_k, double 
  * from d(F^{-T})_iJ / dF_kL = -Fit_iL Fit_kJ and d ln J / dF = F^{-T}. */
 void orc_tangent(const orc_material *m, const double F[4], double beta_k, double A[16])
 {
+    if (m->energy == 2) { /* not built for Eq. (2.2) */
+        for (int i = 0; i < 16; ++i)
+            A[i] = NAN;
+        return;
+    }
     if (m->energy == 1) {
         for (int i = 0; i < 16; ++i)
             A[i] = 0.0;
@@ -522,6 +561,8 @@ int32_t orc_newton_tangent(const orc_material *m, const double F[4], double beta
                            const double R[4], double t_half, double tm0, double tp0,
                            double h_grid, double *tm_out, double *tp_out, double *h_out)
 {
+    if (m->energy == 2) /* line derivatives are written for Eq. (2.3) only */
+        return 0;
     double tm = tm0, tp = tp0;
     int converged = 0;
     for (int it = 0; it < 8; ++it) {
@@ -749,49 +790,194 @@ int32_t orc_node_size(void)
 }
 
 /* ------------------------------------------------------------------------- */
+/* St. Venant-Kirchhoff (Eq. 2.2) and the three-dimensional invariants        */
+/* ------------------------------------------------------------------------- */
+
+/* Eq. (2.2): psi0 = lam/8 (I1 - 3)^2 + mu/4 (I1^2 - 2 I1 - 2 I2 + 3). */
+double orc_psi0_stvk(double I1, double I2, double mu, double lam)
+{
+    return lam / 8.0 * (I1 - 3.0) * (I1 - 3.0) + mu / 4.0 * (I1 * I1 - 2.0 * I1 - 2.0 * I2 + 3.0);
+}
+
+/* C = F^T F of F in R^{d x d} (row-major), d = 2 or 3. */
+static void right_cauchy_green(int32_t d, const double *F, double *C)
+{
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double c = 0.0;
+            for (int k = 0; k < d; ++k)
+                c += F[d * k + i] * F[d * k + j];
+            C[d * i + j] = c;
+        }
+}
+
+static double det3(const double *F)
+{
+    return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6])
+         + F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+/* Cofactor matrix of a 3 x 3 F (d det F / dF); F^{-T} = cof F / det F. */
+static void cof3(const double *F, double *c)
+{
+    c[0] = F[4] * F[8] - F[5] * F[7];
+    c[1] = F[5] * F[6] - F[3] * F[8];
+    c[2] = F[3] * F[7] - F[4] * F[6];
+    c[3] = F[2] * F[7] - F[1] * F[8];
+    c[4] = F[0] * F[8] - F[2] * F[6];
+    c[5] = F[1] * F[6] - F[0] * F[7];
+    c[6] = F[1] * F[5] - F[2] * F[4];
+    c[7] = F[2] * F[3] - F[0] * F[5];
+    c[8] = F[0] * F[4] - F[1] * F[3];
+}
+
+/* Invariants of Sec. 2 for F in R^{d x d}: I1 = tr C, I2 = tr Cof C (the sum of
+ * the principal 2 x 2 minors of C), J = det F.  d = 2 is plane strain: C is
+ * embedded with C33 = 1, so I1 gains 1 and I2 gains C11 + C22. */
+void orc_invariants(int32_t d, const double *F, double *I1, double *I2, double *J)
+{
+    double C[9];
+    right_cauchy_green(d, F, C);
+    if (d == 2) {
+        *I1 = C[0] + C[3] + 1.0;
+        *I2 = (C[0] * C[3] - C[1] * C[2]) + C[0] + C[3];
+        *J = F[0] * F[3] - F[1] * F[2];
+    } else {
+        *I1 = C[0] + C[4] + C[8];
+        *I2 = (C[0] * C[4] - C[1] * C[3]) + (C[0] * C[8] - C[2] * C[6])
+            + (C[4] * C[8] - C[5] * C[7]);
+        *J = det3(F);
+    }
+}
+
+/* psi0 of the material at F in R^{d x d}: Eq. (2.3) (energy 0) with |J|
+ * (the caller decides what det F <= 0 means), or Eq. (2.2) (energy 2). */
+static double psi0_d(const orc_material *m, int32_t d, const double *F, double *Jout)
+{
+    double I1, I2, J;
+    if (d == 2 && m->energy == 0) {
+        nh_invariants(F, &I1, &J);
+        *Jout = J;
+        return orc_psi0_nh(I1, fabs(J), m->mu, m->lam);
+    }
+    orc_invariants(d, F, &I1, &I2, &J);
+    *Jout = J;
+    if (m->energy == 2)
+        return orc_psi0_stvk(I1, I2, m->mu, m->lam);
+    return orc_psi0_nh(I1, fabs(J), m->mu, m->lam);
+}
+
+/* dpsi0/dF at F in R^{d x d} (d x d entries):
+ *   Eq. (2.3): mu F - mu F^{-T} + lam ln|J| F^{-T}  (d ln|J| / dF = F^{-T});
+ *   Eq. (2.2): F (lam/2 (I1 - 3) 1 + mu (C - 1)) (2 F dpsi0/dC with
+ *              dI1/dC = 1, dI2/dC = I1 1 - C; the d x d blocks of C and 1). */
+static void stvk_dpsi0(const orc_material *m, int32_t d, const double *F, double *G)
+{
+    double I1, I2, J;
+    orc_invariants(d, F, &I1, &I2, &J);
+    {
+        double C[9], S[9];
+        right_cauchy_green(d, F, C);
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j)
+                S[d * i + j] = m->mu * (C[d * i + j] - (i == j ? 1.0 : 0.0))
+                             + (i == j ? 0.5 * m->lam * (I1 - 3.0) : 0.0);
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                double g = 0.0;
+                for (int k = 0; k < d; ++k)
+                    g += F[d * i + k] * S[d * k + j];
+                G[d * i + j] = g;
+            }
+    }
+}
+
+static void dpsi0_d(const orc_material *m, int32_t d, const double *F, double *G)
+{
+    int D = d * d;
+    if (m->energy == 2) {
+        stvk_dpsi0(m, d, F, G);
+        return;
+    }
+    double I1, I2, J;
+    orc_invariants(d, F, &I1, &I2, &J);
+    double c[9];
+    if (d == 2) {
+        c[0] = F[3];
+        c[1] = -F[2];
+        c[2] = -F[1];
+        c[3] = F[0];
+    } else {
+        cof3(F, c);
+    }
+    double lj = log(fabs(J));
+    for (int k = 0; k < D; ++k) {
+        double fit = c[k] / J;
+        G[k] = m->mu * F[k] - m->mu * fit + m->lam * lj * fit;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Global-grid rank-one convexification: Eq. (4.3) on the cuboid grid of     */
 /* Sec. 5.2 with the reduced direction set R^1_1 of Eq. (5.1)                */
 /* ------------------------------------------------------------------------- */
 
-/* Grid of Sec. 5.2: component c of F (order F11, F12, F21, F22) takes the
- * values lo[c] + i delta[c], i = 0 .. n[c] - 1; flat index
- * ((i0 n1 + i1) n2 + i2) n3 + i3. */
+/* Grid of Sec. 5.2 for F in R^{d x d}: component c of F (row-major, D = d^2
+ * components) takes the values lo[c] + i delta[c], i = 0 .. n[c] - 1; flat
+ * index with the last component fastest. */
 typedef struct {
-    int32_t n[4];
-    double lo[4];
-    double delta[4];
+    int32_t dim;
+    int32_t n[9];
+    double lo[9];
+    double delta[9];
 } orc_grid;
+
+static int grid_D(const orc_grid *g)
+{
+    return g->dim * g->dim;
+}
 
 int64_t orc_grid_count(const orc_grid *g)
 {
-    return (int64_t)g->n[0] * g->n[1] * g->n[2] * g->n[3];
+    int64_t N = 1;
+    for (int c = 0; c < grid_D(g); ++c)
+        N *= g->n[c];
+    return N;
 }
 
-static void grid_index(const orc_grid *g, int64_t idx, int32_t i[4])
+static void grid_index(const orc_grid *g, int64_t idx, int32_t *i)
 {
-    for (int c = 3; c >= 0; --c) {
+    for (int c = grid_D(g) - 1; c >= 0; --c) {
         i[c] = (int32_t)(idx % g->n[c]);
         idx /= g->n[c];
     }
 }
 
-static int64_t grid_flat(const orc_grid *g, const int32_t i[4])
+static int64_t grid_flat(const orc_grid *g, const int32_t *i)
 {
-    return (((int64_t)i[0] * g->n[1] + i[1]) * g->n[2] + i[2]) * g->n[3] + i[3];
+    int64_t f = 0;
+    for (int c = 0; c < grid_D(g); ++c)
+        f = f * g->n[c] + i[c];
+    return f;
 }
 
-void orc_grid_point(const orc_grid *g, int64_t idx, double F[4])
+void orc_grid_point(const orc_grid *g, int64_t idx, double *F)
 {
-    int32_t i[4];
+    int32_t i[9];
     grid_index(g, idx, i);
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < grid_D(g); ++c)
         F[c] = g->lo[c] + (double)i[c] * g->delta[c];
 }
 
-/* Eq. (5.1): a (x) b with a, b in Z^2, |a|_inf = |b|_inf = 1, one of each
- * pair +-a (x) b (the sign of a direction gives the same line): a and b run
- * over (1,0), (0,1), (1,1), (1,-1); direction 4 ia + ib.  Written as the
- * grid-index offset (a1 b1, a1 b2, a2 b1, a2 b2) of one step. */
+/* Eq. (5.1): a (x) b with a, b in Z^d, |a|_inf = |b|_inf = 1, one of each pair
+ * +-a (x) b (the sign of a direction gives the same line), written as the
+ * grid-index offset (a_i b_j, row-major) of one step.
+ * d = 2: a and b run over (1,0), (0,1), (1,1), (1,-1); direction 4 ia + ib.
+ * d = 3 (the reading for the nine-dimensional study of Sec. 6.8): the 13
+ * vectors of {-1,0,1}^3 with first nonzero entry +1, in the order axes,
+ * face diagonals, body diagonals: (1,0,0), (0,1,0), (0,0,1), (1,1,0), (1,-1,0),
+ * (1,0,1), (1,0,-1), (0,1,1), (0,1,-1), (1,1,1), (1,1,-1), (1,-1,1),
+ * (1,-1,-1); direction 13 ia + ib, 169 in all. */
 void orc_r11_directions(int32_t *off)
 {
     static const int32_t v[4][2] = {{1, 0}, {0, 1}, {1, 1}, {1, -1}};
@@ -805,48 +991,93 @@ void orc_r11_directions(int32_t *off)
         }
 }
 
-/* Energy and stress at a grid point.  abs_det = 0: as orc_energy /
- * orc_stress (NaN where det F <= 0).  abs_det = 1, the reading of the grid
- * study of Sec. 6.1: the Neo-Hooke energy takes ln|det F| (and the stress
- * F^{-T} = cof F / det F, the derivative of ln|det F| for det F != 0), so that
- * det F < 0 is a mirror image of det F > 0 rather than excluded. */
-static double grid_W(const orc_material *m, const double F[4], double beta_k, int32_t abs_det)
+void orc_r11_directions3(int32_t *off)
 {
-    if (m->energy == 1 || !abs_det)
-        return orc_energy(m, F, beta_k);
-    double I1, J;
-    nh_invariants(F, &I1, &J);
-    J = fabs(J);
-    if (!(J > 0.0))
-        return NAN;
-    return orc_W_of_psi0(orc_psi0_nh(I1, J, m->mu, m->lam), beta_k, m->Dinf, m->D0);
+    static const int32_t v[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0}, {1, -1, 0},
+                                     {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                     {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+    for (int ia = 0; ia < 13; ++ia)
+        for (int ib = 0; ib < 13; ++ib) {
+            int32_t *o = off + 9 * (13 * ia + ib);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    o[3 * i + j] = v[ia][i] * v[ib][j];
+        }
 }
 
-static void grid_P(const orc_material *m, const double F[4], double beta_k, int32_t abs_det,
-                   double P[4])
+/* What det F <= 0 means on the grid (rule), the readings of the studies of
+ * Sec. 6.1:
+ *   0: excluded (NaN), as on the per-point path;
+ *   1: Eq. (2.3) takes ln|det F|, so det F < 0 mirrors det F > 0 (the NH
+ *      study); Eq. (2.2) is a polynomial in F and is kept everywhere (the
+ *      STVK study); only det F = 0 stays excluded for Eq. (2.3). */
+
+/* Energy at a grid point (d = g->dim); the double well exists for d = 2. */
+static double grid_W(const orc_material *m, int32_t d, const double *F, double beta_k,
+                     int32_t rule)
 {
-    double I1, J;
-    nh_invariants(F, &I1, &J);
-    if (m->energy == 1 || !abs_det || J > 0.0) {
+    if (m->energy == 1)
+        return d == 2 ? orc_energy(m, F, beta_k) : NAN;
+    if (d == 2 && m->energy == 0 && rule == 0)
+        return orc_energy(m, F, beta_k);
+    double J;
+    double s = psi0_d(m, d, F, &J);
+    if (!(J > 0.0) && (rule == 0 || (m->energy == 0 && !(J < 0.0))))
+        return NAN;
+    return orc_W_of_psi0(s, beta_k, m->Dinf, m->D0);
+}
+
+/* dW/dF at a grid point (D entries): (1 - D(max(s, beta_k))) dpsi0/dF; NaN
+ * where grid_W is excluded. */
+static void grid_P(const orc_material *m, int32_t d, const double *F, double beta_k,
+                   int32_t rule, double *P)
+{
+    int D = d * d;
+    if (m->energy == 1) {
+        if (d == 2) {
+            orc_stress(m, F, beta_k, P);
+        } else {
+            for (int c = 0; c < D; ++c)
+                P[c] = NAN;
+        }
+        return;
+    }
+    if (d == 2 && m->energy == 0 && rule == 0) {
         orc_stress(m, F, beta_k, P);
         return;
     }
-    if (!(J < 0.0)) {
-        P[0] = P[1] = P[2] = P[3] = NAN;
+    double J;
+    double s = psi0_d(m, d, F, &J);
+    int excluded = !(J > 0.0) && (rule == 0 || (m->energy == 0 && !(J < 0.0)));
+    if (excluded) {
+        for (int c = 0; c < D; ++c)
+            P[c] = NAN;
         return;
     }
-    double s = orc_psi0_nh(I1, -J, m->mu, m->lam);
     double beta = s > beta_k ? s : beta_k;
     double gd = 1.0 - orc_damage(beta, m->Dinf, m->D0);
-    double FiT[4] = {F[3] / J, -F[2] / J, -F[1] / J, F[0] / J};
-    double lj = log(-J);
-    for (int i = 0; i < 4; ++i)
-        P[i] = gd * (m->mu * F[i] - m->mu * FiT[i] + m->lam * lj * FiT[i]);
+    double G[9];
+    dpsi0_d(m, d, F, G);
+    for (int c = 0; c < D; ++c)
+        P[c] = gd * G[c];
+}
+
+/* W and P = dW/dF at one F in R^{d x d} under a grid rule (for tests). */
+double orc_energy_dim(const orc_material *m, int32_t d, const double *F, double beta_k,
+                      int32_t rule)
+{
+    return grid_W(m, d, F, beta_k, rule);
+}
+
+void orc_stress_dim(const orc_material *m, int32_t d, const double *F, double beta_k,
+                    int32_t rule, double *P)
+{
+    grid_P(m, d, F, beta_k, rule, P);
 }
 
 /* W^0 on the grid: the energy at every grid point (NaN where it is not
  * defined). */
-void orc_grid_energy(const orc_material *m, const orc_grid *g, double beta_k, int32_t abs_det,
+void orc_grid_energy(const orc_material *m, const orc_grid *g, double beta_k, int32_t rule,
                      double *W, int32_t nthreads)
 {
     int64_t N = orc_grid_count(g);
@@ -856,18 +1087,18 @@ void orc_grid_energy(const orc_material *m, const orc_grid *g, double beta_k, in
 #pragma omp parallel for schedule(static)
 #endif
     for (int64_t idx = 0; idx < N; ++idx) {
-        double F[4];
+        double F[9];
         orc_grid_point(g, idx, F);
-        W[idx] = grid_W(m, F, beta_k, abs_det);
+        W[idx] = grid_W(m, g->dim, F, beta_k, rule);
     }
 }
 
 /* Range of steps l with grid index i + l off inside the grid. */
-static void line_range(const orc_grid *g, const int32_t i[4], const int32_t off[4],
-                       int32_t *lo, int32_t *hi)
+static void line_range(const orc_grid *g, const int32_t *i, const int32_t *off, int32_t *lo,
+                       int32_t *hi)
 {
     int32_t a = -(1 << 30), b = 1 << 30;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < grid_D(g); ++c) {
         if (off[c] > 0) {
             int32_t l0 = -i[c] / off[c], l1 = (g->n[c] - 1 - i[c]) / off[c];
             if (l0 > a) a = l0;
@@ -883,22 +1114,23 @@ static void line_range(const orc_grid *g, const int32_t i[4], const int32_t off[
 }
 
 /* One global iteration, Eq. (4.3).  For every grid point F and direction R
- * (grid-index offset off[j]): the values Win at the grid points F + l R of
- * the line through F inside the grid (Eq. 4.5; every point of the line is a
- * grid point, so no interpolation is needed), Algorithm 1 on the finite ones
- * (orc_line_bridge), read at l = 0.  Wout[F] = min(Win[F], min_j h_j); the
- * laminate is the lowest j with h_j < Win[F] at the minimum: dir[F] = j and
- * its bridge ends lm[F] < 0 < lp[F] (dir = -1, lm = lp = 0 otherwise).
- * Points where Win is not finite keep it.  hdir (N x nd, may be NULL)
- * receives every h_j.  Returns the largest decrease Win - Wout over the
+ * (grid-index offset off[j], D entries): the values Win at the grid points
+ * F + l R of the line through F inside the grid (Eq. 4.5; every point of the
+ * line is a grid point, so no interpolation is needed), Algorithm 1 on the
+ * finite ones (orc_line_bridge), read at l = 0.  Wout[F] = min(Win[F],
+ * min_j h_j); the laminate is the lowest j with h_j < Win[F] at the minimum:
+ * dir[F] = j and its bridge ends lm[F] < 0 < lp[F] (dir = -1, lm = lp = 0
+ * otherwise).  Points where Win is not finite keep it.  hdir (N x nd, may be
+ * NULL) receives every h_j.  Returns the largest decrease Win - Wout over the
  * points where both are finite. */
 double orc_grid_step(const orc_grid *g, int32_t nd, const int32_t *off, const double *Win,
                      double *Wout, int32_t *dir, int32_t *lm, int32_t *lp, double *hdir,
                      int32_t nthreads)
 {
     int64_t N = orc_grid_count(g);
+    int D = grid_D(g);
     int32_t nmax = 0;
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < D; ++c)
         if (g->n[c] > nmax)
             nmax = g->n[c];
     double dec = 0.0;
@@ -908,7 +1140,7 @@ double orc_grid_step(const orc_grid *g, int32_t nd, const int32_t *off, const do
 #pragma omp parallel for schedule(dynamic, 256) reduction(max : dec)
 #endif
     for (int64_t idx = 0; idx < N; ++idx) {
-        int32_t i[4];
+        int32_t i[9];
         grid_index(g, idx, i);
         double w0 = Win[idx];
         int32_t bj = -1, bm = 0, bp = 0;
@@ -917,7 +1149,7 @@ double orc_grid_step(const orc_grid *g, int32_t nd, const int32_t *off, const do
         double *w = (double *)malloc(sizeof(double) * L);
         uint8_t *valid = (uint8_t *)malloc(L);
         for (int32_t j = 0; j < nd; ++j) {
-            const int32_t *o = off + 4 * j;
+            const int32_t *o = off + D * j;
             double h = w0;
             if (isfinite(w0)) {
                 int32_t l0, l1;
@@ -928,8 +1160,8 @@ double orc_grid_step(const orc_grid *g, int32_t nd, const int32_t *off, const do
                     w[m] = 0.0;
                     if (l < l0 || l > l1)
                         continue;
-                    int32_t ii[4];
-                    for (int c = 0; c < 4; ++c)
+                    int32_t ii[9];
+                    for (int c = 0; c < D; ++c)
                         ii[c] = i[c] + l * o[c];
                     double v = Win[grid_flat(g, ii)];
                     if (isfinite(v)) {
@@ -967,13 +1199,15 @@ double orc_grid_step(const orc_grid *g, int32_t nd, const int32_t *off, const do
  * the grid cell that contains F and their multilinear weights
  * prod_c (1 - t_c or t_c), t_c = (F_c - lo_c) / delta_c - i_c; a t_c within
  * 1e-12 of 0 or 1 counts as 0 or 1, so that a grid point is its own single
- * corner; corners of weight 0 are left out.  Returns the number of corners,
- * 0 if F lies outside the grid. */
-static int32_t grid_decompose(const orc_grid *g, const double F[4], int64_t *cidx, double *cw)
+ * corner; corners of weight 0 are left out (2^D candidates, corner bit c of
+ * the corner number counted from the first component).  Returns the number
+ * of corners, 0 if F lies outside the grid. */
+static int32_t grid_decompose(const orc_grid *g, const double *F, int64_t *cidx, double *cw)
 {
-    int32_t i0[4];
-    double t[4];
-    for (int c = 0; c < 4; ++c) {
+    int D = grid_D(g);
+    int32_t i0[9];
+    double t[9];
+    for (int c = 0; c < D; ++c) {
         double u = (F[c] - g->lo[c]) / g->delta[c];
         if (u < -1e-12 || u > (double)(g->n[c] - 1) + 1e-12)
             return 0;
@@ -994,11 +1228,11 @@ static int32_t grid_decompose(const orc_grid *g, const double F[4], int64_t *cid
         t[c] = r;
     }
     int32_t nc = 0;
-    for (int corner = 0; corner < 16; ++corner) {
+    for (int corner = 0; corner < (1 << D); ++corner) {
         double w = 1.0;
-        int32_t ii[4];
-        for (int c = 0; c < 4; ++c) {
-            int up = (corner >> (3 - c)) & 1;
+        int32_t ii[9];
+        for (int c = 0; c < D; ++c) {
+            int up = (corner >> (D - 1 - c)) & 1;
             w *= up ? t[c] : 1.0 - t[c];
             ii[c] = i0[c] + up;
         }
@@ -1017,72 +1251,80 @@ static int32_t grid_decompose(const orc_grid *g, const double F[4], int64_t *cid
  * weights 1 - xi and xi, xi = -l- / (l+ - l-) (Algorithm 2's
  * |F - F-|_1 / |F+ - F-|_1); a point no iteration up to d split is a leaf,
  * where W and P are evaluated.  Adds weight * (W, P) of the leaves. */
-static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k, int32_t abs_det,
+static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k, int32_t rule,
                       const int32_t *off, const int32_t *forest, int64_t idx, int32_t d,
-                      double weight, double *W, double P[4], int64_t *leaves)
+                      double weight, double *W, double *P, int64_t *leaves)
 {
     int64_t N = orc_grid_count(g);
+    int D = grid_D(g);
     int32_t k = d;
     while (k >= 1 && forest[3 * ((int64_t)(k - 1) * N + idx)] < 0)
         --k;
     if (k < 1) {
-        double F[4], Pl[4];
+        double F[9], Pl[9];
         orc_grid_point(g, idx, F);
-        *W += weight * grid_W(mat, F, beta_k, abs_det);
-        grid_P(mat, F, beta_k, abs_det, Pl);
-        for (int c = 0; c < 4; ++c)
+        *W += weight * grid_W(mat, g->dim, F, beta_k, rule);
+        grid_P(mat, g->dim, F, beta_k, rule, Pl);
+        for (int c = 0; c < D; ++c)
             P[c] += weight * Pl[c];
         ++*leaves;
         return;
     }
     const int32_t *lam = forest + 3 * ((int64_t)(k - 1) * N + idx);
-    const int32_t *o = off + 4 * lam[0];
+    const int32_t *o = off + D * lam[0];
     int32_t lm = lam[1], lp = lam[2];
     double xi = (double)(-lm) / (double)(lp - lm);
-    int32_t i[4], im[4], ip[4];
+    int32_t i[9], im[9], ip[9];
     grid_index(g, idx, i);
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < D; ++c) {
         im[c] = i[c] + lm * o[c];
         ip[c] = i[c] + lp * o[c];
     }
-    grid_tree(mat, g, beta_k, abs_det, off, forest, grid_flat(g, im), k - 1,
-              weight * (1.0 - xi), W, P, leaves);
-    grid_tree(mat, g, beta_k, abs_det, off, forest, grid_flat(g, ip), k - 1, weight * xi, W, P,
+    grid_tree(mat, g, beta_k, rule, off, forest, grid_flat(g, im), k - 1, weight * (1.0 - xi), W,
+              P, leaves);
+    grid_tree(mat, g, beta_k, rule, off, forest, grid_flat(g, ip), k - 1, weight * xi, W, P,
               leaves);
 }
 
 /* Relaxed energy and stress at arbitrary points from K global iterations:
  * W_interp = the multilinear interpolation of W^K (Sec. 4.1: values off the
  * grid by interpolation); W_tree, P = Algorithm 3 over Algorithm 2's tree
- * (the interpolation corners at order K, then the forest).  forest holds
- * K x N records (dir, l-, l+) (dir = -1: no split).  leaves[p] counts the
- * tree's leaves.  Outside the grid: NaN, leaves 0. */
-void orc_grid_query(const orc_material *mat, const orc_grid *g, double beta_k, int32_t abs_det,
+ * (the interpolation corners at order K, then the forest).  F and P hold D
+ * entries per point; forest holds K x N records (dir, l-, l+) (dir = -1: no
+ * split).  leaves[p] counts the tree's leaves.  Outside the grid: NaN,
+ * leaves 0. */
+void orc_grid_query(const orc_material *mat, const orc_grid *g, double beta_k, int32_t rule,
                     const int32_t *off, int32_t K, const double *WK, const int32_t *forest,
                     int64_t n, const double *F, double *W_interp, double *W_tree, double *P,
                     int64_t *leaves, int32_t nthreads)
 {
+    int D = grid_D(g);
 #ifdef _OPENMP
     if (nthreads > 0)
         omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
     for (int64_t p = 0; p < n; ++p) {
-        int64_t cidx[16];
-        double cw[16];
-        int32_t nc = grid_decompose(g, F + 4 * p, cidx, cw);
-        double wi = 0.0, wt = 0.0, Pp[4] = {0.0, 0.0, 0.0, 0.0};
+        int64_t *cidx = (int64_t *)malloc(sizeof(int64_t) << D);
+        double *cw = (double *)malloc(sizeof(double) << D);
+        int32_t nc = grid_decompose(g, F + D * p, cidx, cw);
+        double wi = 0.0, wt = 0.0, Pp[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         int64_t nl = 0;
         for (int32_t c = 0; c < nc; ++c) {
             wi += cw[c] * WK[cidx[c]];
-            grid_tree(mat, g, beta_k, abs_det, off, forest, cidx[c], K, cw[c], &wt, Pp, &nl);
+            grid_tree(mat, g, beta_k, rule, off, forest, cidx[c], K, cw[c], &wt, Pp, &nl);
         }
-        if (nc == 0)
-            wi = wt = Pp[0] = Pp[1] = Pp[2] = Pp[3] = NAN;
+        if (nc == 0) {
+            wi = wt = NAN;
+            for (int c = 0; c < D; ++c)
+                Pp[c] = NAN;
+        }
         W_interp[p] = wi;
         W_tree[p] = wt;
-        for (int c = 0; c < 4; ++c)
-            P[4 * p + c] = Pp[c];
+        for (int c = 0; c < D; ++c)
+            P[D * p + c] = Pp[c];
         leaves[p] = nl;
+        free(cidx);
+        free(cw);
     }
 }

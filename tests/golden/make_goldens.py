@@ -27,6 +27,15 @@ Workloads (the sizes the benchmark runs, subsampled evenly):
   W^K at 4,096 evenly spaced grid points, and Algorithms 2 and 3 over the
   forest at 1,024 points drawn uniformly from the grid's box (seed 61).
 
+* ``grid3d``: the nine-dimensional study of Sec. 6.8 (Table
+  tab:3Dconvexification, NH: beta_k fitted to the printed W(1), diagonal
+  [1.0, 3.4], off-diagonal [-0.15, 0.15], delta 0.15: 3,581,577 points;
+  R^1_1 for d = 3, 169 directions; tol 1e-4, kmax 20): the decreases, W^K at
+  4,096 evenly spaced grid points and on the uni-, bi- and triaxial paths.
+* ``stvk61``: the STVK study of Sec. 6.1 (beta_k 0.07, delta 0.1, diagonal
+  [0.1, 2.0], off-diagonal [-2.0, 2.0]: 672,400 points; R^1_1; Eq. (2.2)
+  kept where det F <= 0): the decreases and W^K at 4,096 grid points.
+
 Usage: python tests/golden/make_goldens.py [--only NAME ...] [--threads N]
 The load-path files take hours of CPU time (the oracle is plain FP64 C).
 """
@@ -138,6 +147,63 @@ def write_grid61(threads):
     print(f"grid61: {len(decs)} iterations in {dt:.1f} s -> {path}", flush=True)
 
 
+def _fit_beta_identity(mat, W_identity):
+    """beta_k from W(1) = -(1 - D(beta_k)) beta_k by bisection (monotone)."""
+    lo, hi = 1e-9, 1.0
+    f = lambda b: oracle.energy(mat, [1, 0, 0, 1], b) - W_identity  # noqa: E731
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (f(lo) > 0) == (f(mid) > 0):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def write_grid3d(threads):
+    mat = oracle.Material(**GRID61["mat"])
+    rows = [[float(v) for v in ln.split()] for ln in open(os.path.join(HERE, "nh3d_paths.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    beta = _fit_beta_identity(mat, rows[0][1])
+    g = oracle.Grid.from_bounds((1.0, 3.4), (-0.15, 0.15), (0.15, 0.15), dim=3)
+    t0 = time.perf_counter()
+    W, _, decs = oracle.grid_convexify(mat, g, beta, oracle.r11_directions(3), kmax=20,
+                                       tol=1e-4, nthreads=threads, keep_all=False)
+    dt = time.perf_counter() - t0
+    st = np.ones(9, dtype=np.int64)
+    for c in range(7, -1, -1):
+        st[c] = st[c + 1] * g.n[c + 1]
+    paths = np.array([[np.dot([k, 1, 1, 1, 1, 1, 1, 1, 0], st) for k in range(17)],
+                      [np.dot([k, 1, 1, 1, k, 1, 1, 1, 0], st) for k in range(17)],
+                      [np.dot([k, 1, 1, 1, k, 1, 1, 1, k], st) for k in range(17)]])
+    idx = subsample(g.count)
+    meta = dict(workload="Sec. 6.8 nine-dimensional NH study, 3,581,577 points, R^1_1 (d = 3), "
+                "tol 1e-4, kmax 20", beta=beta, material=GRID61["mat"], oracle_seconds=dt,
+                threads=threads, iterations=len(decs))
+    path = os.path.join(HERE, "grid3d.npz")
+    np.savez_compressed(path, meta=np.array(json.dumps(meta)), decs=np.array(decs), idx=idx,
+                        W_K=W[-1][idx], paths=paths, W_paths=W[-1][paths], W0_paths=W[0][paths])
+    print(f"grid3d: {len(decs)} iterations in {dt:.1f} s -> {path}", flush=True)
+
+
+def write_stvk61(threads):
+    m = GRID61["mat"]
+    mat = oracle.Material(m["mu"], m["lam"], m["Dinf"], m["D0"], energy=2)
+    g = oracle.Grid.from_bounds((0.1, 2.0), (-2.0, 2.0), (0.1, 0.1))
+    t0 = time.perf_counter()
+    W, _, decs = oracle.grid_convexify(mat, g, 0.07, oracle.r11_directions(), kmax=20, tol=1e-4,
+                                       rule=1, nthreads=threads, keep_all=False)
+    dt = time.perf_counter() - t0
+    idx = subsample(g.count)
+    meta = dict(workload="Sec. 6.1 STVK grid study, 672,400 points, R^1_1, tol 1e-4, kmax 20, "
+                "Eq. (2.2) kept where det F <= 0", beta=0.07, material=m, oracle_seconds=dt,
+                threads=threads, iterations=len(decs))
+    path = os.path.join(HERE, "stvk61.npz")
+    np.savez_compressed(path, meta=np.array(json.dumps(meta)), decs=np.array(decs), idx=idx,
+                        W_K=W[-1][idx])
+    print(f"stvk61: {len(decs)} iterations in {dt:.1f} s -> {path}", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", nargs="*", default=None)
@@ -150,6 +216,10 @@ def main():
         write(name, desc, na, L, t_half, depth, thunk, a.threads or oracle.cores())
     if not a.only or "grid61" in a.only:
         write_grid61(a.threads or oracle.cores())
+    if not a.only or "stvk61" in a.only:
+        write_stvk61(a.threads or oracle.cores())
+    if not a.only or "grid3d" in a.only:
+        write_grid3d(a.threads or oracle.cores())
 
 
 if __name__ == "__main__":
