@@ -903,7 +903,7 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def run(kmax=c["kmax"]):
-        return cv.grid_convexify(p, g, c["beta"], off, kmax=kmax, tol=c["tol"], abs_det=True,
+        return cv.grid_convexify(p, g, c["beta"], off, kmax=kmax, tol=c["tol"], det_rule=1,
                                  out=out)
 
     for _ in range(2):
@@ -955,11 +955,11 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
     Fq = torch.from_numpy(inputs.cuboid_points(lo, hi, 1 << 20, seed=62)).to(dev)
     fo = out["forest"][:K]
     for _ in range(2):
-        cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, abs_det=True)
+        cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, det_rule=1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    wi, wt, Pq, nl = cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, abs_det=True)
+    wi, wt, Pq, nl = cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, det_rule=1)
     e1.record()
     torch.cuda.synchronize()
     qms = e0.elapsed_time(e1)
@@ -973,7 +973,7 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
         d = np.asarray(gold["decs"])
         dg = out["decs"].cpu().numpy()[:K]
         wi2, wt2, P2, nl2 = cv.grid_query(p, g, c["beta"], off, out["W"], fo, gold["F_query"],
-                                          abs_det=True)
+                                          det_rule=1)
         res["accuracy_vs_oracle"] = {
             "steps_equal": bool(K == d.size),
             "decrease_max_abs_diff": float(np.max(np.abs(dg - d))) if K == d.size else None,
@@ -983,12 +983,12 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
     # the shape of the Sec. 6.4 strong-scaling grid (context for the paper's timings)
     gs = api.GridSpec.from_bounds(GRID_SCALING["diag"], GRID_SCALING["off"], GRID_SCALING["delta"])
     for _ in range(2):
-        o2 = cv.grid_convexify(p, gs, c["beta"], off, kmax=c["kmax"], tol=c["tol"], abs_det=True,
+        o2 = cv.grid_convexify(p, gs, c["beta"], off, kmax=c["kmax"], tol=c["tol"], det_rule=1,
                                want_forest=False)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    o2 = cv.grid_convexify(p, gs, c["beta"], off, kmax=c["kmax"], tol=c["tol"], abs_det=True,
+    o2 = cv.grid_convexify(p, gs, c["beta"], off, kmax=c["kmax"], tol=c["tol"], det_rule=1,
                            want_forest=False)
     e1.record()
     torch.cuda.synchronize()
@@ -997,8 +997,85 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
                          "paper_context": ("Sec. 6.4: 1960.7 s on 1 thread, 49.06 s on 64 threads of a "
                                            "Xeon Phi 7210 for a 43,681-point grid with R^1_1, no tree "
                                            "(bounds not printed)")}
+    res["stvk61"] = grid_study_line(cv, api, torch, dev, flush, "stvk61", sms, mhz)
+    res["grid3d"] = grid_study_line(cv, api, torch, dev, flush, "grid3d", sms, mhz)
     if cpu:
         res["cpu_baseline"] = grid_oracle_rate(out["W"], K)
+    return res
+
+
+def grid_study_line(cv, api, torch, dev, flush, name, sms, mhz, runs=5):
+    """The STVK study of Sec. 6.1 (672,400 points, Eq. 2.2 kept where
+    det F <= 0) or the nine-dimensional NH study of Sec. 6.8 (3,581,577
+    points, 169 directions): time to tol, the line kernel's FP64 rate and the
+    accuracy against the stored oracle run (and the printed curves)."""
+    import numpy as np
+
+    gold = load_golden(name)
+    c = GRID61["mat"]
+    if name == "stvk61":
+        g = api.GridSpec.from_bounds((0.1, 2.0), (-2.0, 2.0), (0.1, 0.1))
+        p = api.Params(energy=api.ENERGY_STVK_DAMAGE, **c)
+        beta, rule, off = 0.07, 1, api.grid_r11(2)
+    else:
+        g = api.GridSpec.from_bounds((1.0, 3.4), (-0.15, 0.15), (0.15, 0.15), dim=3)
+        p = api.Params(**c)
+        beta = gold["meta"]["beta"] if gold is not None else 0.0625
+        rule, off = 0, api.grid_r11(3)
+    N, nd = g.count, off.shape[0]
+    out = dict(W=torch.empty(N, dtype=torch.float64, device=dev),
+               forest=torch.empty(20, N, 3, dtype=torch.int32, device=dev),
+               decs=torch.empty(20, dtype=torch.float64, device=dev),
+               iters=torch.empty(1, dtype=torch.int32, device=dev))
+
+    def run(kmax=20):
+        return cv.grid_convexify(p, g, beta, off, kmax=kmax, tol=1e-4, det_rule=rule, out=out)
+
+    run()
+    torch.cuda.synchronize()
+    K = int(out["iters"].cpu()[0])
+    ms = []
+    for _ in range(runs):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    flush.zero_()
+    cv.set_profiling(True)
+    cv.scan_timing(reset=True)
+    run(K)
+    torch.cuda.synchronize()
+    lines_ms, launches = cv.scan_timing(reset=True)
+    cv.set_profiling(False)
+    chunks = max(1, launches // K)
+    flop = GRID_FLOP_PER_POINT_DIR * N * nd * K
+    peak = sms * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = flop / (lines_ms / 1e3) / 1e12 if lines_ms > 0 else None
+    res = {"workload": (f"{'STVK study of Sec. 6.1' if name == 'stvk61' else 'nine-dimensional NH study of Sec. 6.8'}: "
+                        f"{N} grid points, {nd} directions, tol 1e-4"),
+           "value": N * K / (t / 1e3), "unit": "grid-point updates/s (points x steps)",
+           "steps_to_tol": K, "ms_to_tol": t,
+           "line_kernel": {"achieved_tflops": achieved, "frac_of_fp64_peak": achieved / peak if achieved else None,
+                           "ms_per_step": lines_ms / K, "launches_per_step": chunks,
+                           "share": lines_ms / t}}
+    if gold is not None:
+        WK = out["W"].cpu().numpy()
+        acc = {"steps_equal": bool(K == gold["decs"].size),
+               "decrease_max_abs_diff": float(np.max(np.abs(out["decs"].cpu().numpy()[:K] - gold["decs"])))
+               if K == gold["decs"].size else None,
+               "W_K": err_stats(WK[gold["idx"]], gold["W_K"])}
+        if name == "grid3d":
+            rows = np.array([[float(v) for v in ln.split()] for ln in
+                             open(os.path.join(GOLDEN, "nh3d_paths.txt"))
+                             if ln.strip() and not ln.startswith("#")])
+            acc["paths_vs_oracle_max_abs"] = float(np.max(np.abs(WK[gold["paths"]] - gold["W_paths"])))
+            acc["biaxial_vs_printed_max_abs"] = float(np.max(np.abs(WK[gold["paths"][1]] - rows[:, 4])))
+            acc["triaxial_vs_printed_max_abs"] = float(np.max(np.abs(WK[gold["paths"][2]] - rows[:, 6])))
+        res["accuracy_vs_oracle"] = acc
     return res
 
 

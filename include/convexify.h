@@ -74,9 +74,12 @@ enum cvx_point_status {
 enum cvx_energy_kind {
     CVX_ENERGY_NH_DAMAGE = 0,  /* plane-strain Neo-Hooke with exponential damage,
                                   Eqs. (2.3)-(2.9)                              */
-    CVX_ENERGY_DOUBLE_WELL = 1 /* test energy (F11^2-1)^2 + F12^2 + F21^2 +
+    CVX_ENERGY_DOUBLE_WELL = 1, /* test energy (F11^2-1)^2 + F12^2 + F21^2 +
                                   (F22-1)^2, closed-form envelope; not in the
                                   paper                                         */
+    CVX_ENERGY_STVK_DAMAGE = 2 /* St. Venant-Kirchhoff, Eq. (2.2), with the
+                                  damage of Eqs. (2.4)-(2.9); the global-grid
+                                  calls only (CVX_ERR_UNSUPPORTED elsewhere)    */
 };
 
 typedef struct cvx_handle cvx_handle;
@@ -337,20 +340,23 @@ int cvx_tree_tangent(cvx_handle *h, const cvx_params *p, int64_t n, const double
  * per iteration and grid point the winning laminate; Algorithm 2 builds the
  * tree of an arbitrary F from it (multilinear-interpolation corners where F is
  * not a grid point, Sec. 5.3) and Algorithm 3 evaluates W and P over it.
+ * Both the two-dimensional studies (F in R^{2x2}, plane strain, Sec. 6.1) and
+ * the nine-dimensional one (F in R^{3x3}, Sec. 6.8) are covered.
  *
- * Grid (Sec. 5.2, the cuboid form): component c of F (order F11, F12, F21, F22)
- * takes the values lo[c] + i delta[c], i = 0 .. n[c] - 1; flat index
- * ((i0 n1 + i1) n2 + i2) n3 + i3; 1 <= n[c] <= 512, at most 2^31 - 1 points.
+ * Grid (Sec. 5.2, the cuboid form): dim = d = 2 or 3; the D = d^2 components
+ * of F (row-major: F11, F12, ...) take the values lo[c] + i delta[c],
+ * i = 0 .. n[c] - 1; flat index with the last component fastest;
+ * 1 <= n[c] <= 512, at most 2^31 - 1 points.  Entries c >= D are ignored.
  *
- * Directions are grid-index offsets o (nd x 4 int32, HOST): one step of a line
+ * Directions are grid-index offsets o (nd x D int32, HOST): one step of a line
  * moves component c by o[c] grid steps, i.e. F + l R with R_c = o[c] delta[c]
  * (the matrix a (x) b of Eq. 5.1 scaled by delta when all delta[c] are equal,
- * as in the study of Sec. 6.1).  Every offset must be nonzero and rank-one
- * (o0 o3 = o1 o2), |o[c]| <= 512, 1 <= nd <= 4096.  cvx_grid_r11 writes the 16
- * directions of Eq. (5.1) in the order used by the ties rule below.
+ * as in the studies of Secs. 6.1 and 6.8).  Every offset must be nonzero and
+ * rank-one as a d x d matrix, |o[c]| <= 512, 1 <= nd <= 4096.  cvx_grid_r11
+ * writes the directions of Eq. (5.1) in the order used by the ties rule below.
  *
  * Lines are the maximal runs of grid points F + l R inside the grid.  Values
- * that are not finite (det F <= 0, see abs_det) are left out of the hulls and
+ * that are not finite (excluded by det_rule) are left out of the hulls and
  * keep their value.  A point laminates along the lowest direction index whose
  * hull value is strictly below both W^k(F) and every lower-indexed
  * direction's; its record is (dir, l-, l+) with l- < 0 < l+ the hull vertices
@@ -359,63 +365,69 @@ int cvx_tree_tangent(cvx_handle *h, const cvx_params *p, int64_t n, const double
  * Hull predicates and chord values are FP64 with every operation rounded on
  * its own, so a step is reproducible bit for bit.
  *
- * abs_det (energy of the grid study): 0 = Eq. (2.9) with det F <= 0 excluded
- * (NaN); 1 = the Neo-Hooke term takes ln|det F|, so that det F < 0 mirrors
- * det F > 0 (the reading under which the convergence history printed for the
- * Sec. 6.1 study is reproduced); ignored for the double-well test energy. */
+ * Energy: the material of p (mu, lambda_L, D_inf, D0; energy NH_DAMAGE,
+ * STVK_DAMAGE, or DOUBLE_WELL for dim = 2; the line fields are not used).
+ * det_rule (what det F <= 0 means, the readings of the studies of Sec. 6.1):
+ * 0 = excluded (NaN), as on the per-point path; 1 = kept: the Neo-Hooke term
+ * takes ln|det F| (det F < 0 mirrors det F > 0; det F = 0 stays excluded) and
+ * Eq. (2.2), a polynomial in F, is kept everywhere. */
 typedef struct cvx_grid {
-    int32_t n[4];
-    double lo[4];
-    double delta[4];
+    int32_t dim;
+    int32_t n[9];
+    double lo[9];
+    double delta[9];
 } cvx_grid;
 
-/* The reduced direction set R^1_1 of Eq. (5.1) as grid-index offsets: a, b run
- * over (1,0), (0,1), (1,1), (1,-1) (one of each pair +-v: the sign of a (x) b
- * gives the same line); row 4 ia + ib = (a1 b1, a1 b2, a2 b1, a2 b2).
- * off: HOST, 16 x 4. */
-int cvx_grid_r11(int32_t *off);
+/* The reduced direction set R^1_1 of Eq. (5.1) as grid-index offsets, one of
+ * each pair +-a (x) b (the sign gives the same line), row-major a_i b_j.
+ * dim = 2: a, b over (1,0), (0,1), (1,1), (1,-1); row 4 ia + ib; off is
+ * 16 x 4.  dim = 3: a, b over the 13 vectors of {-1,0,1}^3 whose first
+ * nonzero entry is +1, in the order (1,0,0), (0,1,0), (0,0,1), (1,1,0),
+ * (1,-1,0), (1,0,1), (1,0,-1), (0,1,1), (0,1,-1), (1,1,1), (1,1,-1), (1,-1,1),
+ * (1,-1,-1); row 13 ia + ib; off is 169 x 9.  off: HOST. */
+int cvx_grid_r11(int32_t dim, int32_t *off);
 
-/* W^0 on the grid: W (DEVICE, N values in flat order) = the energy of the
- * material in p (mu, lambda_L, D_inf, D0, energy; the line fields are not
- * used) at every grid point with history beta_k. */
+/* W^0 on the grid: W (DEVICE, N values in flat order) = the energy at every
+ * grid point with history beta_k. */
 int cvx_grid_energy(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
-                    int32_t abs_det, double *W, cvx_stream s);
+                    int32_t det_rule, double *W, cvx_stream s);
 
 /* One iteration of Eq. (4.3): W_out from W_in (DEVICE, N each, no aliasing);
  * lam (DEVICE, N x 3 int32, nullable) = the laminate records; dec (DEVICE
  * scalar, nullable) = the largest decrease W_in - W_out over the points where
- * both are finite.  Workspace: the handle's (about 12 bytes per point and
- * direction, in chunks of at most 512 MB, plus the line starts). */
+ * both are finite.  Workspace: the handle's (12 bytes per point and
+ * direction, in chunks of at most 1 GB, plus the line starts). */
 int cvx_grid_step(cvx_handle *h, const cvx_grid *g, int32_t nd, const int32_t *off,
                   const double *W_in, double *W_out, int32_t *lam, double *dec, cvx_stream s);
 
 /* The global iteration (Sec. 4.1): W^0 = cvx_grid_energy, then Eq. (4.3) until
  * the largest decrease of a step is at most tol or kmax steps were taken
- * (1 <= kmax <= 64; the study of Sec. 6 uses tol = 1e-4, kmax = 20).  The stop
- * is decided on the device: nothing waits on the host, and the steps after
- * the stop return at once.  Outputs (DEVICE): W (N) = W^K; iters (one int32)
- * = K; forest (kmax x N x 3 int32, nullable) = the records of step k at
+ * (1 <= kmax <= 64; the studies of Sec. 6 use tol = 1e-4, kmax = 20).  The
+ * stop is decided on the device: nothing waits on the host, and the steps
+ * after the stop return at once.  Outputs (DEVICE): W (N) = W^K; iters (one
+ * int32) = K; forest (kmax x N x 3 int32, nullable) = the records of step k at
  * forest + 3 N k (rows k >= K are not written); decs (kmax, nullable) = the
  * largest decrease of each step (0 after the stop). */
 int cvx_grid_convexify(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
-                       int32_t abs_det, int32_t nd, const int32_t *off, int32_t kmax, double tol,
+                       int32_t det_rule, int32_t nd, const int32_t *off, int32_t kmax, double tol,
                        double *W, int32_t *forest, double *decs, int32_t *iters, cvx_stream s);
 
-/* Relaxed energy and stress at n arbitrary points F (DEVICE, n x 4) after K
+/* Relaxed energy and stress at n arbitrary points F (DEVICE, n x D) after K
  * iterations (WK = W^K, forest = K x N x 3 records, both DEVICE):
  *   W_interp (n): the multilinear interpolation of W^K (Sec. 4.1, values off
  *     the grid by interpolation);
- *   W_tree (n), P (n x 4): Algorithm 3 over Algorithm 2's tree: the cell
- *     corners of F with their interpolation weights (one corner if F is a grid
- *     point; coordinates within 1e-12 grid steps of a grid value count as on
- *     it) at order K, each expanded through the latest iteration k <= order
- *     that split it (children at order k - 1), W and P (Eq. 2.12) at the
- *     leaves;
+ *   W_tree (n), P (n x D): Algorithm 3 over Algorithm 2's tree: the cell
+ *     corners of F (up to 2^D) with their interpolation weights (one corner if
+ *     F is a grid point; coordinates within 1e-12 grid steps of a grid value
+ *     count as on it) at order K, each expanded through the latest iteration
+ *     k <= order that split it (children at order k - 1), W and P (Eq. 2.12)
+ *     at the leaves;
  *   leaves (n int64, nullable): the leaves of the tree.
  * NaN (leaves 0) outside the grid.  nd and off must be those of the run that
- * made the forest.  0 <= K <= 64. */
+ * made the forest.  0 <= K <= 64.  Workspace: W and P at every grid point and
+ * a bitmask of the iterations that split it ((D + 2) 8 bytes per point). */
 int cvx_grid_query(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
-                   int32_t abs_det, int32_t nd, const int32_t *off, int32_t K, const double *WK,
+                   int32_t det_rule, int32_t nd, const int32_t *off, int32_t K, const double *WK,
                    const int32_t *forest, int64_t n, const double *F, double *W_interp,
                    double *W_tree, double *P, int64_t *leaves, cvx_stream s);
 

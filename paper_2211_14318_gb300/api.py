@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libconvexify.so")
 CVX_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "TIMEOUT", -5: "NOT_TRAINED",
           -6: "UNSUPPORTED"}
-ENERGY_NH_DAMAGE, ENERGY_DOUBLE_WELL = 0, 1
+ENERGY_NH_DAMAGE, ENERGY_DOUBLE_WELL, ENERGY_STVK_DAMAGE = 0, 1, 2
 PT_NONPOS_DET, PT_TIE, PT_EDGE, PT_ITER_CAP, PT_OVERFLOW, PT_FALLBACK = 1, 2, 4, 8, 16, 32
 NODE_EXISTS, NODE_SCANNED, NODE_LAMINATED, NODE_LEAF, NODE_TIE, NODE_EDGE = 1, 2, 4, 8, 16, 32
 NODE_ITER_CAP, NODE_OVERFLOW, NODE_NEWTON, NODE_FALLBACK = 64, 128, 256, 512
@@ -70,8 +70,8 @@ class _Problem(ctypes.Structure):
 
 
 class _Grid(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32 * 4), ("lo", ctypes.c_double * 4),
-                ("delta", ctypes.c_double * 4)]
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32 * 9), ("lo", ctypes.c_double * 9),
+                ("delta", ctypes.c_double * 9)]
 
 
 class _TrainCfg(ctypes.Structure):
@@ -125,7 +125,7 @@ def lib() -> ctypes.CDLL:
                               ctypes.c_double, vp, vp, vp, vp, vp, vp, vp],
         "cvx_get_batch_tuning": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)],
-        "cvx_grid_r11": [vp],
+        "cvx_grid_r11": [i32, vp],
         "cvx_grid_energy": [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Grid), ctypes.c_double,
                             i32, vp, vp],
         "cvx_grid_step": [vp, ctypes.POINTER(_Grid), i32, vp, vp, vp, vp, vp, vp],
@@ -210,38 +210,56 @@ class Params:
 
 @dataclass
 class GridSpec:
-    """cvx_grid: the cuboid deformation-gradient grid of Sec. 5.2; component c
-    of F (F11, F12, F21, F22) takes lo[c] + i delta[c], i = 0 .. n[c] - 1
-    (flat index with F22 fastest)."""
+    """cvx_grid: the cuboid deformation-gradient grid of Sec. 5.2; the D = d^2
+    components of F (row-major; D = 4 for d = 2, 9 for d = 3) take
+    lo[c] + i delta[c], i = 0 .. n[c] - 1 (flat index with the last component
+    fastest)."""
     n: tuple
     lo: tuple
     delta: tuple
 
     @classmethod
-    def from_bounds(cls, diag, off, delta):
-        """Both diagonal entries on diag = (lo, hi), both off-diagonal entries
-        on off = (lo, hi), spacings delta = (diagonal, off-diagonal); hi is a
-        grid value (the parametrisation of Table tab:2Dconvexification)."""
+    def from_bounds(cls, diag, off, delta, dim: int = 2):
+        """Every diagonal entry on diag = (lo, hi), every off-diagonal entry on
+        off = (lo, hi), spacings delta = (diagonal, off-diagonal); hi is a grid
+        value (the parametrisation of Tables tab:2Dconvexification and
+        tab:3Dconvexification)."""
         (dlo, dhi), (olo, ohi) = diag, off
         dd, do = delta
         nd = int(round((dhi - dlo) / dd)) + 1
         no = int(round((ohi - olo) / do)) + 1
-        return cls((nd, no, no, nd), (dlo, olo, olo, dlo), (dd, do, do, dd))
+        n, lo, de = [], [], []
+        for i in range(dim):
+            for j in range(dim):
+                n.append(nd if i == j else no)
+                lo.append(dlo if i == j else olo)
+                de.append(dd if i == j else do)
+        return cls(tuple(n), tuple(lo), tuple(de))
+
+    @property
+    def D(self) -> int:
+        return len(self.n)
+
+    @property
+    def dim(self) -> int:
+        return 2 if self.D == 4 else 3
 
     @property
     def count(self) -> int:
         return int(np.prod(self.n))
 
     def c(self) -> _Grid:
-        return _Grid((ctypes.c_int32 * 4)(*[int(x) for x in self.n]),
-                     (ctypes.c_double * 4)(*[float(x) for x in self.lo]),
-                     (ctypes.c_double * 4)(*[float(x) for x in self.delta]))
+        pad = 9 - self.D
+        return _Grid(self.dim, (ctypes.c_int32 * 9)(*([int(x) for x in self.n] + [0] * pad)),
+                     (ctypes.c_double * 9)(*([float(x) for x in self.lo] + [0.0] * pad)),
+                     (ctypes.c_double * 9)(*([float(x) for x in self.delta] + [0.0] * pad)))
 
 
-def grid_r11() -> np.ndarray:
-    """(16, 4) int32 grid-index offsets of the directions of Eq. (5.1)."""
-    off = np.zeros((16, 4), dtype=np.int32)
-    _check(lib().cvx_grid_r11(off.ctypes.data), "cvx_grid_r11")
+def grid_r11(dim: int = 2) -> np.ndarray:
+    """Grid-index offsets of the directions of Eq. (5.1): (16, 4) int32 for
+    d = 2, (169, 9) for d = 3."""
+    off = np.zeros((16, 4) if dim == 2 else (169, 9), dtype=np.int32)
+    _check(lib().cvx_grid_r11(int(dim), off.ctypes.data), "cvx_grid_r11")
     return off
 
 
@@ -553,7 +571,7 @@ class Convexifier:
         _check(lib().surrogate_load(self._h, path.encode()), "surrogate_load")
 
     # ------------------------------------------------------ global-grid form
-    def grid_energy(self, p: Params, grid: GridSpec, beta_k: float, abs_det: bool = False,
+    def grid_energy(self, p: Params, grid: GridSpec, beta_k: float, det_rule: int = 0,
                     stream=None):
         """W^0 on the grid (N values, flat order)."""
         import torch
@@ -561,14 +579,14 @@ class Convexifier:
         W = torch.empty(grid.count, dtype=torch.float64, device=f"cuda:{self.device}")
         c, g = p.c(), grid.c()
         _check(lib().cvx_grid_energy(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
-                                     int(abs_det), _ptr(W), _stream(stream)), "cvx_grid_energy")
+                                     int(det_rule), _ptr(W), _stream(stream)), "cvx_grid_energy")
         return W
 
     def grid_step(self, grid: GridSpec, off, W_in, stream=None):
         """One iteration of Eq. (4.3): (W_out, lam (N x 3 int32), dec (device scalar))."""
         import torch
 
-        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, grid.D)
         W_in = self._dev(W_in, torch.float64).reshape(-1)
         W_out = torch.empty_like(W_in)
         lam = torch.empty(grid.count, 3, dtype=torch.int32, device=W_in.device)
@@ -580,7 +598,7 @@ class Convexifier:
         return W_out, lam, dec
 
     def grid_convexify(self, p: Params, grid: GridSpec, beta_k: float, off, kmax: int = 20,
-                       tol: float = 1e-4, abs_det: bool = False, want_forest: bool = True,
+                       tol: float = 1e-4, det_rule: int = 0, want_forest: bool = True,
                        out: Optional[dict] = None, stream=None):
         """The global iteration of Sec. 4.1 on the device: dict with W (= W^K),
         forest (kmax x N x 3, rows >= K unwritten), decs (kmax) and iters (a
@@ -588,7 +606,7 @@ class Convexifier:
         tensors with those names."""
         import torch
 
-        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, grid.D)
         dev = f"cuda:{self.device}"
         N = grid.count
         o = dict(out) if out else {}
@@ -602,30 +620,30 @@ class Convexifier:
         iters = o.get("iters") if o.get("iters") is not None else torch.empty(1, dtype=torch.int32, device=dev)
         c, g = p.c(), grid.c()
         _check(lib().cvx_grid_convexify(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
-                                        int(abs_det), off.shape[0], off.ctypes.data, int(kmax),
+                                        int(det_rule), off.shape[0], off.ctypes.data, int(kmax),
                                         float(tol), _ptr(W), _ptr(forest), _ptr(decs),
                                         _ptr(iters), _stream(stream)), "cvx_grid_convexify")
         return dict(W=W, forest=forest, decs=decs, iters=iters)
 
     def grid_query(self, p: Params, grid: GridSpec, beta_k: float, off, WK, forest, F,
-                   abs_det: bool = False, K: Optional[int] = None, stream=None):
-        """(W_interp, W_tree, P, leaves) at points F from W^K and the first K
-        forest rows (K = len(forest) unless given)."""
+                   det_rule: int = 0, K: Optional[int] = None, stream=None):
+        """(W_interp, W_tree, P (n x D), leaves) at points F (n x D) from W^K
+        and the first K forest rows (K = len(forest) unless given)."""
         import torch
 
-        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, 4)
+        off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, grid.D)
         WK = self._dev(WK, torch.float64).reshape(-1)
         fa = self._dev(forest, torch.int32).reshape(-1, grid.count, 3)
         K = fa.shape[0] if K is None else int(K)
-        F = self._dev(F, torch.float64).reshape(-1, 4)
+        F = self._dev(F, torch.float64).reshape(-1, grid.D)
         n = F.shape[0]
         wi = torch.empty(n, dtype=torch.float64, device=F.device)
         wt = torch.empty(n, dtype=torch.float64, device=F.device)
-        P = torch.empty(n, 4, dtype=torch.float64, device=F.device)
+        P = torch.empty(n, grid.D, dtype=torch.float64, device=F.device)
         nl = torch.empty(n, dtype=torch.int64, device=F.device)
         c, g = p.c(), grid.c()
         _check(lib().cvx_grid_query(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
-                                    int(abs_det), off.shape[0], off.ctypes.data, K, _ptr(WK),
+                                    int(det_rule), off.shape[0], off.ctypes.data, K, _ptr(WK),
                                     _ptr(fa), n, _ptr(F), _ptr(wi), _ptr(wt), _ptr(P), _ptr(nl),
                                     _stream(stream)), "cvx_grid_query")
         return wi, wt, P, nl

@@ -50,11 +50,15 @@ Material material_of(const cvx_params *p) {
     return m;
 }
 
-int check_params(const cvx_params *p, bool need_line) {
+int check_params(const cvx_params *p, bool need_line, bool allow_stvk) {
     if (!p) return fail(CVX_ERR_INVALID_ARG, "params is NULL");
-    if (p->energy != CVX_ENERGY_NH_DAMAGE && p->energy != CVX_ENERGY_DOUBLE_WELL)
+    if (p->energy == CVX_ENERGY_STVK_DAMAGE && !allow_stvk)
+        return fail(CVX_ERR_UNSUPPORTED,
+                    "the St. Venant-Kirchhoff energy is built for the global-grid calls only");
+    if (p->energy != CVX_ENERGY_NH_DAMAGE && p->energy != CVX_ENERGY_DOUBLE_WELL &&
+        p->energy != CVX_ENERGY_STVK_DAMAGE)
         return fail(CVX_ERR_INVALID_ARG, "unknown energy kind %d", p->energy);
-    if (p->energy == CVX_ENERGY_NH_DAMAGE) {
+    if (p->energy != CVX_ENERGY_DOUBLE_WELL) {
         if (!(p->mu > 0.0) || !(p->lambda_L >= 0.0) || !(p->D_inf >= 0.0 && p->D_inf < 1.0) ||
             !(p->D0 > 0.0))
             return fail(CVX_ERR_INVALID_ARG,

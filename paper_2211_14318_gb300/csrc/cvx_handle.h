@@ -50,7 +50,8 @@ namespace cvx {
 int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *where);
 Material material_of(const cvx_params *p);
-int check_params(const cvx_params *p, bool need_line);
+// allow_stvk: the St. Venant-Kirchhoff energy (global-grid calls only).
+int check_params(const cvx_params *p, bool need_line, bool allow_stvk = false);
 int ensure_ws(cvx_handle *h, size_t bytes, cudaStream_t s);
 // With profiling on: n_launches event pairs (2 per line-scan launch, recorded
 // on the launching stream around it), registered for cvx_get_scan_timing.

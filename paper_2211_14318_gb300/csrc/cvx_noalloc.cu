@@ -20,7 +20,7 @@
 
 namespace cvx {
 int set_error_message(int code, const char *msg);  // cvx_api.cu
-int check_params(const cvx_params *p, bool need_line);  // cvx_api.cu
+int check_params(const cvx_params *p, bool need_line, bool allow_stvk = false);  // cvx_api.cu
 }
 
 using namespace cvx;

@@ -176,6 +176,10 @@ def test_grid_struct_and_r11_table(cvxlib, orc):
     assert (np_off == orc.r11_directions()).all()
     g = api.GridSpec.from_bounds((0.1, 3.4), (-2.55, 2.55), (0.15, 0.15))
     assert g.count == 648025 and g.n == (23, 35, 35, 23)
+    off3 = api.grid_r11(3)
+    assert off3.shape == (169, 9) and (off3 == orc.r11_directions(3)).all()
+    g3 = api.GridSpec.from_bounds((1.0, 3.4), (-0.15, 0.15), (0.15, 0.15), dim=3)
+    assert g3.count == 3581577 and g3.D == 9
 
 
 @pytest.mark.parametrize("n,off,msg", [
@@ -191,7 +195,7 @@ def test_grid_validation_before_cuda(cvxlib, n, off, msg):
     from paper_2211_14318_gb300 import api
 
     g = api.GridSpec(n, (0.0,) * 4, (0.1,) * 4).c()
-    o = np.ascontiguousarray(off if off is not None else api.grid_r11(), dtype=np.int32)
+    o = np.ascontiguousarray(off if off is not None else api.grid_r11(2), dtype=np.int32)
     rc = cvxlib.cvx_grid_step(None, ctypes.byref(g), o.shape[0], o.ctypes.data, None, None,
                               None, None, None)
     assert rc == -1
@@ -226,4 +230,39 @@ def test_grid_calls_reject_bad_arguments_before_cuda(cvxlib):
     assert cvxlib.cvx_grid_energy(None, ctypes.byref(c), ctypes.byref(g), float("inf"), 0, None,
                                   None) == -1
     assert "handle" in _err(cvxlib) or "beta" in _err(cvxlib)
-    assert cvxlib.cvx_grid_r11(None) == -1
+    assert cvxlib.cvx_grid_r11(2, None) == -1
+    buf = np.zeros(64, dtype=np.int32)
+    assert cvxlib.cvx_grid_r11(4, buf.ctypes.data) == -1
+    assert "dim" in _err(cvxlib)
+    g.dim = 4
+    assert cvxlib.cvx_grid_step(None, ctypes.byref(g), 16, o.ctypes.data, None, None, None, None,
+                                None) == -1
+    assert "dim" in _err(cvxlib)
+    g.dim = 2
+    assert cvxlib.cvx_grid_energy(None, ctypes.byref(c), ctypes.byref(g), 0.0, 2, None,
+                                  None) == -1
+    assert "det_rule" in _err(cvxlib)
+    g3 = api.GridSpec((3,) * 9, (0.5,) * 9, (0.25,) * 9).c()
+    dw = api.Params(energy=api.ENERGY_DOUBLE_WELL).c()
+    assert cvxlib.cvx_grid_energy(None, ctypes.byref(dw), ctypes.byref(g3), 0.0, 0, None,
+                                  None) == -1
+    assert "two-dimensional" in _err(cvxlib)
+    # a rank-two offset in nine components
+    o3 = np.zeros((1, 9), dtype=np.int32)
+    o3[0, 0] = o3[0, 4] = 1
+    assert cvxlib.cvx_grid_step(None, ctypes.byref(g3), 1, o3.ctypes.data, None, None, None,
+                                None, None) == -1
+    assert "rank-one" in _err(cvxlib)
+
+
+def test_stvk_energy_is_grid_only(cvxlib):
+    """Eq. (2.2) is built for the global-grid calls; the per-point calls say
+    so before any CUDA call."""
+    from paper_2211_14318_gb300 import api
+
+    c = api.Params(energy=api.ENERGY_STVK_DAMAGE).c()
+    assert cvxlib.convexify_points(None, ctypes.byref(c), 4, None, None, None, None, None, None,
+                                   None, None) == -6
+    assert "global-grid" in _err(cvxlib)
+    assert cvxlib.convexify_points_static(ctypes.byref(c), 4, None, None, None, None, None,
+                                          None) == -6

@@ -62,7 +62,7 @@ def study(orc):
     mat = orc.Material(**NH61)
     go = orc.Grid.from_bounds(DIAG61, OFF61, DELTA61)
     off = orc.r11_directions()
-    W, forest, decs = orc.grid_convexify(mat, go, BETA61, off, kmax=20, tol=1e-4, abs_det=True)
+    W, forest, decs = orc.grid_convexify(mat, go, BETA61, off, kmax=20, tol=1e-4, rule=1)
     return dict(W=W, forest=orc.forest_array(forest), decs=decs, off=off)
 
 
@@ -75,7 +75,7 @@ def test_grid_energy_matches_oracle(cv, orc, abs_det):
     from paper_2211_14318_gb300 import api
 
     go, gg = _both_grids(orc, api)
-    Wg = cv.grid_energy(_params(api), gg, BETA61, abs_det).cpu().numpy()
+    Wg = cv.grid_energy(_params(api), gg, BETA61, int(abs_det)).cpu().numpy()
     Wo = orc.grid_energy(orc.Material(**NH61), go, BETA61, abs_det)
     assert np.array_equal(np.isnan(Wg), np.isnan(Wo))
     f = np.isfinite(Wo)
@@ -171,7 +171,7 @@ def test_device_loop_matches_the_oracle_loop(cv, orc, study):
 
     gg = api.GridSpec.from_bounds(DIAG61, OFF61, DELTA61)
     off = api.grid_r11()
-    out = cv.grid_convexify(_params(api), gg, BETA61, off, kmax=20, tol=1e-4, abs_det=True)
+    out = cv.grid_convexify(_params(api), gg, BETA61, off, kmax=20, tol=1e-4, det_rule=1)
     K = int(out["iters"].cpu()[0])
     assert K == len(study["decs"]) == 15
     decs = out["decs"].cpu().numpy()
@@ -191,15 +191,21 @@ def test_device_loop_matches_the_oracle_loop(cv, orc, study):
         hs = np.sort(h, axis=1)
         w0 = study["W"][k]
         fin = np.isfinite(w0)
-        # a clear split: the best hull value is clear of the point's own
-        # value and of the second best; a clear non-split: every hull value
-        # other than the point's own is clear above it
-        above = np.where(h != w0[:, None], h - w0[:, None], np.inf).min(axis=1)
-        clear = fin & (((w0 - hs[:, 0] > 1e-10) & (hs[:, 1] - hs[:, 0] > 1e-10)) |
-                       ((hs[:, 0] == w0) & (above > 1e-10)))
         g, o = forest[k], study["forest"][k]
-        assert clear.mean() > 0.5
+        # a clear split of the oracle: its best hull value is clear of the
+        # point's own value and of the second best; there the direction is
+        # unique.  A chord equal to the point's value (the point lies on a
+        # segment a previous step made straight) is a tie between splitting
+        # and not splitting that the last bit decides, so elsewhere only
+        # validity is required: in the oracle's own values the device's
+        # choice is within 1e-10 of the best.
+        clear = fin & (w0 - hs[:, 0] > 1e-10) & (hs[:, 1] - hs[:, 0] > 1e-10)
+        assert clear.sum() > 1000
         assert np.array_equal(g[clear, 0], o[clear, 0]), f"step {k + 1}: directions differ"
+        gj = g[fin, 0]
+        hg = np.where(gj >= 0, h[fin][np.arange(gj.size), np.maximum(gj, 0)], w0[fin])
+        best = np.minimum(w0[fin], hs[fin, 0])
+        assert np.max(hg - best) < 1e-10, f"step {k + 1}: a device laminate is not the best"
         split = clear & (g[:, 0] >= 0)
         other = split & np.any(g[:, 1:] != o[:, 1:], axis=1)
         if other.any():
@@ -210,7 +216,7 @@ def test_device_loop_matches_the_oracle_loop(cv, orc, study):
             chord = (lp * wa - lm * wb) / (lp - lm)
             ho = h[q, d]
             assert np.max(np.abs(chord - ho) / (1 + np.abs(ho))) < 1e-12, f"step {k + 1}"
-        assert other.mean() < 0.05
+        assert other.sum() < 0.05 * split.sum() + 1
 
 
 def test_query_on_the_oracle_forest(cv, orc, study):
@@ -232,9 +238,9 @@ def test_query_on_the_oracle_forest(cv, orc, study):
     ])
     mat = orc.Material(**NH61)
     wi_o, wt_o, P_o, nl_o = orc.grid_query(mat, go, BETA61, study["off"], study["W"][-1],
-                                           study["forest"], F, abs_det=True)
+                                           study["forest"], F, rule=1)
     wi, wt, Pg, nl = cv.grid_query(_params(api), gg, BETA61, api.grid_r11(), study["W"][-1],
-                                   study["forest"], F, abs_det=True)
+                                   study["forest"], F, det_rule=1)
     wi, wt, Pg, nl = (x.cpu().numpy() for x in (wi, wt, Pg, nl))
     assert _eq_nan(wi, wi_o)
     assert np.array_equal(nl, nl_o)
@@ -255,14 +261,14 @@ def test_query_tree_matches_the_interpolated_relaxation(cv):
 
     gg = api.GridSpec.from_bounds(DIAG61, OFF61, DELTA61)
     off = api.grid_r11()
-    out = cv.grid_convexify(_params(api), gg, BETA61, off, kmax=20, tol=1e-4, abs_det=True)
+    out = cv.grid_convexify(_params(api), gg, BETA61, off, kmax=20, tol=1e-4, det_rule=1)
     K = int(out["iters"].cpu()[0])
     rng = np.random.default_rng(5)
     lo = np.array(gg.lo)
     hi = lo + (np.array(gg.n) - 1) * np.array(gg.delta)
     F = rng.uniform(lo, hi, size=(20000, 4))
     wi, wt, P, nl = cv.grid_query(_params(api), gg, BETA61, off, out["W"], out["forest"][:K], F,
-                                  abs_det=True)
+                                  det_rule=1)
     wi, wt, nl = wi.cpu().numpy(), wt.cpu().numpy(), nl.cpu().numpy()
     f = np.isfinite(wi)
     assert f.mean() > 0.99
@@ -290,3 +296,153 @@ def test_double_well_reaches_the_closed_form(cv):
     inner = np.abs(P[:, 0]) < 1.0
     assert np.all(f0[inner, 0] == 0)
     assert out["decs"].cpu().numpy()[1] == 0.0
+
+
+# ---------------------------------------------------------------- STVK, d = 3
+
+STVK61 = dict(diag=(0.1, 2.0), off=(-2.0, 2.0), delta=(0.1, 0.1), beta=0.07)
+GRID3D = dict(diag=(1.0, 3.4), off=(-0.15, 0.15), delta=(0.15, 0.15))
+
+
+def _load_npz(name):
+    import json
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"{name}.npz")
+    g = dict(np.load(path))
+    g["meta"] = json.loads(str(g["meta"]))
+    return g
+
+
+@pytest.mark.parametrize("case", ["stvk2d", "stvk2d_kept", "nh3d", "stvk3d"])
+def test_grid_energies_of_both_dimensions_match_oracle(cv, orc, case):
+    """W^0 of Eq. (2.2) (plane strain and 3-D) and of Eq. (2.3) in 3-D, with
+    det F <= 0 excluded or kept, against the oracle at every grid point."""
+    from paper_2211_14318_gb300 import api
+
+    energy, rule = {"stvk2d": (2, 0), "stvk2d_kept": (2, 1), "nh3d": (0, 0), "stvk3d": (2, 0)}[case]
+    if case.endswith("3d"):
+        go = orc.Grid.from_bounds(GRID3D["diag"], GRID3D["off"], GRID3D["delta"], dim=3)
+        gg = api.GridSpec.from_bounds(GRID3D["diag"], GRID3D["off"], GRID3D["delta"], dim=3)
+    else:
+        go = orc.Grid.from_bounds(STVK61["diag"], STVK61["off"], STVK61["delta"])
+        gg = api.GridSpec.from_bounds(STVK61["diag"], STVK61["off"], STVK61["delta"])
+    mat = orc.Material(NH61["mu"], NH61["lam"], NH61["Dinf"], NH61["D0"], energy=energy)
+    Wo = orc.grid_energy(mat, go, 0.07, rule=rule)
+    Wg = cv.grid_energy(_params(api, energy=energy), gg, 0.07, rule).cpu().numpy()
+    assert np.array_equal(np.isnan(Wg), np.isnan(Wo))
+    f = np.isfinite(Wo)
+    assert f.sum() > 0.4 * f.size
+    assert np.max(np.abs(Wg[f] - Wo[f]) / (1.0 + np.abs(Wo[f]))) < 1e-13
+    if case == "stvk2d":
+        assert (~f).sum() > 0
+
+
+def test_stvk_study_steps_bit_exact_and_device_loop(cv, orc):
+    """The STVK study of Sec. 6.1 (672,400 points, Eq. 2.2 kept where
+    det F <= 0): three steps from the oracle's iterates bit for bit, and the
+    device loop against the stored oracle run (steps, decreases, W^K)."""
+    from paper_2211_14318_gb300 import api
+
+    go = orc.Grid.from_bounds(STVK61["diag"], STVK61["off"], STVK61["delta"])
+    gg = api.GridSpec.from_bounds(STVK61["diag"], STVK61["off"], STVK61["delta"])
+    mat = orc.Material(NH61["mu"], NH61["lam"], NH61["Dinf"], NH61["D0"], energy=2)
+    off = api.grid_r11(2)
+    W = orc.grid_energy(mat, go, STVK61["beta"], rule=1)
+    for _ in range(3):
+        Wo, d, lm, lp, dec = orc.grid_step(go, off, W)
+        Wn, lam, decg = cv.grid_step(gg, off, W)
+        lam = lam.cpu().numpy()
+        assert _eq_nan(Wn.cpu().numpy(), Wo)
+        assert np.array_equal(lam, np.stack([d, lm, lp], axis=1))
+        assert float(decg.cpu()[0]) == dec
+        W = Wo
+    gold = _load_npz("stvk61")
+    out = cv.grid_convexify(_params(api, energy=2), gg, STVK61["beta"], off, kmax=20, tol=1e-4,
+                            det_rule=1)
+    K = int(out["iters"].cpu()[0])
+    assert K == gold["decs"].size == 11
+    assert np.max(np.abs(out["decs"].cpu().numpy()[:K] - gold["decs"])) < 1e-12
+    WK = out["W"].cpu().numpy()[gold["idx"]]
+    assert np.max(np.abs(WK - gold["W_K"]) / (1 + np.abs(gold["W_K"]))) < 1e-12
+
+
+def test_nine_dimensional_steps_bit_exact(cv, orc):
+    """d = 3: a 5^3 x 3^6 grid on the stretches 1.0 .. 1.6 of the Sec. 6.8
+    study (3-D NH and 3-D STVK, where both relax),
+    two steps of Eq. (4.3) along the 169 directions from the oracle's
+    iterates, bit for bit; one run with a chunk of 7 directions."""
+    from paper_2211_14318_gb300 import api
+
+    n = (5, 3, 3, 3, 5, 3, 3, 3, 5)
+    lo = (1.0, -0.15, -0.15, -0.15, 1.0, -0.15, -0.15, -0.15, 1.0)
+    de = (0.15, 0.15, 0.15, 0.15, 0.15, 0.15, 0.15, 0.15, 0.15)
+    go, gg = _both_grids(orc, api, n, lo, de)
+    off = api.grid_r11(3)
+    assert (off == orc.r11_directions(3)).all()
+    old = os.environ.get("CVX_GRID_CHUNK_BYTES")
+    try:
+        for energy, chunk in ((0, None), (2, str(7 * 12 * go.count))):
+            if chunk:
+                os.environ["CVX_GRID_CHUNK_BYTES"] = chunk
+            mat = orc.Material(NH61["mu"], NH61["lam"], NH61["Dinf"], NH61["D0"], energy=energy)
+            W = orc.grid_energy(mat, go, 0.0625)
+            splits = 0
+            for _ in range(2):
+                Wo, d, lm, lp, dec = orc.grid_step(go, off, W)
+                Wn, lam, decg = cv.grid_step(gg, off, W)
+                lam = lam.cpu().numpy()
+                assert _eq_nan(Wn.cpu().numpy(), Wo)
+                assert np.array_equal(lam, np.stack([d, lm, lp], axis=1))
+                assert float(decg.cpu()[0]) == dec
+                splits += int((d >= 0).sum())
+                W = Wo
+            assert splits > 0
+    finally:
+        if old is None:
+            os.environ.pop("CVX_GRID_CHUNK_BYTES", None)
+        else:
+            os.environ["CVX_GRID_CHUNK_BYTES"] = old
+
+
+def test_nine_dimensional_study_reproduces_the_printed_curves(cv, orc):
+    """Sec. 6.8 on the device: the 3,581,577-point grid of Table
+    tab:3Dconvexification with the 169 directions, to tol 1e-4.  Steps,
+    decreases and W^K (4,096 grid points and the uni-, bi- and triaxial paths)
+    against the stored oracle run within 1e-12, the paths against the printed
+    relaxed curves within 1e-5; Algorithms 2 and 3 at the path points (grid
+    points: one corner each) give W^K, and at off-grid points the
+    interpolated W^K."""
+    from paper_2211_14318_gb300 import api
+    from conftest import load_golden
+
+    gold = _load_npz("grid3d")
+    printed = load_golden("nh3d_paths.txt")
+    gg = api.GridSpec.from_bounds(GRID3D["diag"], GRID3D["off"], GRID3D["delta"], dim=3)
+    off = api.grid_r11(3)
+    p = _params(api)
+    beta = gold["meta"]["beta"]
+    out = cv.grid_convexify(p, gg, beta, off, kmax=20, tol=1e-4)
+    K = int(out["iters"].cpu()[0])
+    assert K == gold["decs"].size == 5
+    assert np.max(np.abs(out["decs"].cpu().numpy()[:K] - gold["decs"])) < 1e-12
+    WK = out["W"].cpu().numpy()
+    for a, b in ((WK[gold["idx"]], gold["W_K"]), (WK[gold["paths"]], gold["W_paths"])):
+        assert np.max(np.abs(a - b) / (1 + np.abs(b))) < 1e-12
+    assert np.max(np.abs(WK[gold["paths"][1]] - printed[:, 4])) < 1e-5
+    assert np.max(np.abs(WK[gold["paths"][2]] - printed[:, 6])) < 1e-5
+    # the path points as query points
+    axes = [gg.lo[c] + np.arange(gg.n[c]) * gg.delta[c] for c in range(9)]
+    ii = np.array(np.unravel_index(gold["paths"].reshape(-1), gg.n)).T
+    Fp = np.stack([axes[c][ii[:, c]] for c in range(9)], axis=1)
+    wi, wt, P, nl = cv.grid_query(p, gg, beta, off, out["W"], out["forest"][:K], Fp)
+    wi, wt = wi.cpu().numpy(), wt.cpu().numpy()
+    assert np.array_equal(wi, WK[gold["paths"].reshape(-1)])
+    assert np.max(np.abs(wt - wi) / (1 + np.abs(wi))) < 1e-12
+    rng = np.random.default_rng(9)
+    lo = np.array(gg.lo)
+    hi = lo + (np.array(gg.n) - 1) * np.array(gg.delta)
+    Fr = rng.uniform(lo, hi, size=(256, 9))
+    wi, wt, P, nl = cv.grid_query(p, gg, beta, off, out["W"], out["forest"][:K], Fr)
+    wi, wt, nl = wi.cpu().numpy(), wt.cpu().numpy(), nl.cpu().numpy()
+    assert np.max(np.abs(wt - wi) / (1 + np.abs(wi))) < 1e-12
+    assert np.all(nl >= 512)  # 2^9 interpolation corners
