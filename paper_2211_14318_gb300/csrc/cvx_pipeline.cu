@@ -649,6 +649,14 @@ __device__ __forceinline__ void half_min_dk(double &v, int &k, bool prefer_low) 
 // the chord's slope) and the windows are taken around the new pair, at most
 // 4 times.  Returns false if that does not settle (the caller resamples the
 // whole line in FP64); n64 counts the FP64 spot samples.
+// Lines up to this many samples take FP64 windows of 16 samples per side in
+// the refinement (one sample per lane), longer lines 32 per side (two per
+// lane).  A window that misses a tangent point only costs a further round:
+// the certificate over the whole line moves it.
+#ifndef CVX_REFINE_NARROW_MAX_L
+#define CVX_REFINE_NARROW_MAX_L 513
+#endif
+
 __device__ bool refine_hinted(const double F[4], const double R[4], double beta, const NodeCands &nc,
                               const ProbDesc &pd, const LineSpec &ln, float4 d32, int hab, int lane,
                               int &a, int &b, double &wa, double &wb, unsigned &n64) {
@@ -657,7 +665,7 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
     a = hab & 0xffff;
     b = hab >> 16;
     if (!(a >= 0 && a < m0 && b > m0 && b < L)) return false;
-    const bool narrow = L <= 513;
+    const bool narrow = L <= CVX_REFINE_NARROW_MAX_L;
     const int W = narrow ? 16 : 32;
     const double kap = pd.kappa, C = nc.shift;
     const float kapf = pd.kappa_f, Cf = (float)C;
