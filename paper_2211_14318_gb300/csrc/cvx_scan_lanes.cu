@@ -35,7 +35,12 @@ namespace {
 
 constexpr int kLaneWarps = 8;
 constexpr int kLaneRounds = 4;  // passes per line at most
-constexpr int kLaneCoop = 6;    // fewer live lines than this: the whole warp on each line
+// fewer live lines than this in a later pass: the whole warp on each line
+// (64 samples per lane and a warp reduction) instead of one line per lane
+#ifndef CVX_LANE_COOP
+#define CVX_LANE_COOP 6
+#endif
+constexpr int kLaneCoop = CVX_LANE_COOP;
 
 constexpr int kConv = 1 << 28;    // bounds settled (pair repeated or within eps/4): no further pass
 constexpr int kDrop = 1 << 29;    // lower bound above the node's reference value
