@@ -254,12 +254,19 @@ __global__ void k_grid_energy(GridT<D> g, Material m, double beta, int rule, dou
 }
 
 // Line starts: per point (one index decomposition) and direction j, the point
-// starts a line if its predecessor along j lies outside the grid; written to
-// region j of `starts` (line_off[j] .. line_off[j + 1]), point order kept
-// within a warp.  The direction offsets are staged in shared memory.
+// starts a line if its predecessor along j lies outside the grid.  The starts
+// of region j of `starts` (line_off[j] .. line_off[j + 1]) are ordered by
+// line length, longest first, so that a warp of the line kernel takes lines
+// of one length (a counting sort: phase 0 counts the lines of each
+// (direction, length) in hist, k_grid_len_scan turns the counts into
+// offsets, phase 1 places each start at its offset; the order among lines of
+// one length is arbitrary and changes no result).  Lanes of a warp with the
+// same (direction, length) share one atomic.  The direction offsets are
+// staged in shared memory.
 template <int D>
 __global__ void k_grid_starts(GridT<D> g, const GridDirT<D> *dirs, int nd,
-                              const long long *line_off, unsigned *fill, int *starts) {
+                              const long long *line_off, unsigned *hist, int cap, int phase,
+                              int *starts) {
     extern __shared__ int soff[];  // nd x D offsets
     for (int k = threadIdx.x; k < nd * D; k += blockDim.x) soff[k] = dirs[k / D].o[k % D];
     __syncthreads();
@@ -272,19 +279,40 @@ __global__ void k_grid_starts(GridT<D> g, const GridDirT<D> *dirs, int nd,
         if (valid) grid_index<D>(g, (int)p, i);
         for (int j = 0; j < nd; ++j) {
             bool st = false;
+            int len = 0;
             if (valid) {
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
                     const int q = i[c] - soff[j * D + c];
                     st |= (q < 0) || (q >= g.n[c]);
                 }
+                if (st) len = line_length<D>(g, i, soff + j * D);
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, st);
+            const unsigned act = __ballot_sync(0xffffffffu, st);
+            if (!st) continue;
+            const unsigned grp = __match_any_sync(act, len);
+            const int leader = __ffs(grp) - 1;
+            unsigned* cell = hist + (size_t)j * (cap + 1) + len;
             unsigned base = 0;
-            if (lane == 0 && mask) base = atomicAdd(&fill[j], (unsigned)__popc(mask));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (st) starts[line_off[j] + base + __popc(mask & ((1u << lane) - 1))] = (int)p;
+            if (lane == leader) base = atomicAdd(cell, (unsigned)__popc(grp));
+            base = __shfl_sync(grp, base, leader);
+            if (phase == 1)
+                starts[line_off[j] + base + __popc(grp & ((1u << lane) - 1))] = (int)p;
         }
+    }
+}
+
+// Per direction: the counts of lines of each length become the offsets of
+// their first line in the region, longest lines first.
+__global__ void k_grid_len_scan(int nd, int cap, unsigned *hist) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nd) return;
+    unsigned *h = hist + (size_t)j * (cap + 1);
+    unsigned acc = 0;
+    for (int len = cap; len >= 0; --len) {
+        const unsigned c = h[len];
+        h[len] = acc;
+        acc += c;
     }
 }
 
@@ -639,7 +667,7 @@ template <int D>
 struct GridWork {
     GridDirT<D> *dirs;
     long long *line_off;
-    unsigned *fill;
+    unsigned *hist;  // nd x (longest line + 1): line counts, then offsets, by length
     int *starts;
     double *H;
     unsigned *S;
@@ -652,7 +680,8 @@ size_t grid_work_bytes(int nd, const GridT<D> &gd, long long lines, int &chunk) 
     const size_t per_dir = (size_t)gd.N * (sizeof(double) + sizeof(unsigned));
     chunk = (int)std::max<size_t>(1, std::min<size_t>(nd, grid_chunk_bytes() / per_dir));
     return up256(sizeof(GridDirT<D>) * nd) + up256(sizeof(long long) * (nd + 1)) +
-           up256(sizeof(unsigned) * nd) + up256(sizeof(int) * (size_t)lines) +
+           up256(sizeof(unsigned) * nd * (size_t)(kGridMaxLine + 1)) +
+           up256(sizeof(int) * (size_t)lines) +
            up256(sizeof(double) * (size_t)chunk * gd.N) +
            up256(sizeof(unsigned) * (size_t)chunk * gd.N) +
            up256(sizeof(double) * (2 * kGridMaxLine + 1));
@@ -665,8 +694,8 @@ void carve_grid_work(char *ws, int nd, const GridT<D> &gd, long long lines, int 
     ws += up256(sizeof(GridDirT<D>) * nd);
     w.line_off = (long long *)ws;
     ws += up256(sizeof(long long) * (nd + 1));
-    w.fill = (unsigned *)ws;
-    ws += up256(sizeof(unsigned) * nd);
+    w.hist = (unsigned *)ws;
+    ws += up256(sizeof(unsigned) * nd * (size_t)(kGridMaxLine + 1));
     w.starts = (int *)ws;
     ws += up256(sizeof(int) * (size_t)lines);
     w.H = (double *)ws;
@@ -697,13 +726,18 @@ int grid_setup(const GridT<D> &gd, const std::vector<GridDirT<D>> &dirs,
     CK(cudaMemcpyAsync(w.line_off, line_off.data(), sizeof(long long) * (nd + 1),
                        cudaMemcpyHostToDevice, s),
        "grid setup");
-    CK(cudaMemsetAsync(w.fill, 0, sizeof(unsigned) * nd, s), "grid setup");
+    const int cap = grid_line_cap<D>(gd);
+    CK(cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * nd * (size_t)(cap + 1), s), "grid setup");
     const size_t smem = sizeof(int) * (size_t)nd * D;
     CK(cudaFuncSetAttribute(k_grid_starts<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem),
        "grid line starts shared memory");
     const int bx = (int)std::min<long long>((gd.N + 255) / 256, 4096);
-    k_grid_starts<D><<<bx, 256, smem, s>>>(gd, w.dirs, nd, w.line_off, w.fill, w.starts);
+    k_grid_starts<D><<<bx, 256, smem, s>>>(gd, w.dirs, nd, w.line_off, w.hist, cap, 0, w.starts);
+    CK(cudaGetLastError(), "grid line counts");
+    k_grid_len_scan<<<(nd + 127) / 128, 128, 0, s>>>(nd, cap, w.hist);
+    CK(cudaGetLastError(), "grid line offsets");
+    k_grid_starts<D><<<bx, 256, smem, s>>>(gd, w.dirs, nd, w.line_off, w.hist, cap, 1, w.starts);
     CK(cudaGetLastError(), "grid line starts");
     k_grid_rcp<<<(2 * kGridMaxLine + 256) / 256, 256, 0, s>>>(w.rcp);
     CK(cudaGetLastError(), "grid reciprocal table");
