@@ -144,7 +144,10 @@ def lib() -> ctypes.CDLL:
         L.orc_grid_energy.restype = None
         L.orc_grid_energy.argtypes = [vp, vp, d, i32, vp, i32]
         L.orc_grid_query.restype = None
-        L.orc_grid_query.argtypes = [vp, vp, d, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, i32]
+        L.orc_grid_query.argtypes = [vp, vp, d, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp,
+                                     i32]
+        L.orc_tangent_dim.restype = None
+        L.orc_tangent_dim.argtypes = [vp, i32, vp, d, i32, vp]
         L.orc_grid_step.restype = d
         L.orc_grid_step.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, i32]
         assert L.orc_node_size() == NODE_DTYPE.itemsize, "node layout mismatch"
@@ -203,6 +206,14 @@ def stress_dim(mat: Material, F, beta_k: float, rule: int = 0) -> np.ndarray:
     P = np.zeros(F.size)
     lib().orc_stress_dim(mat.ref, 2 if F.size == 4 else 3, _p(F), beta_k, int(rule), _p(P))
     return P
+
+
+def tangent_dim(mat: Material, F, beta_k: float, rule: int = 0) -> np.ndarray:
+    """d^2 W / dF dF (D x D, row-major entries of F) of energy_dim."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    A = np.zeros(F.size * F.size)
+    lib().orc_tangent_dim(mat.ref, 2 if F.size == 4 else 3, _p(F), beta_k, int(rule), _p(A))
+    return A.reshape(F.size, F.size)
 
 
 def W_of_psi0(s: float, beta_k: float, Dinf: float, D0: float) -> float:
@@ -540,10 +551,11 @@ def forest_array(forest) -> np.ndarray:
 
 
 def grid_query(mat: Material, grid: Grid, beta_k: float, off: np.ndarray, WK: np.ndarray, forest,
-               F: np.ndarray, abs_det: bool = False, nthreads: int = 0, rule=None):
-    """(W_interp, W_tree, P, leaves) at points F (n x D) after K = len(forest)
-    iterations: the multilinear interpolation of W^K, and Algorithm 3 over
-    Algorithm 2's tree."""
+               F: np.ndarray, abs_det: bool = False, nthreads: int = 0, rule=None,
+               want_A: bool = False):
+    """(W_interp, W_tree, P, leaves[, A]) at points F (n x D) after
+    K = len(forest) iterations: the multilinear interpolation of W^K, and
+    Algorithm 3 over Algorithm 2's tree (A: n x D x D tangent)."""
     D = grid.D
     off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, D)
     fa = forest_array(forest) if not isinstance(forest, np.ndarray) else np.ascontiguousarray(forest, dtype=np.int32)
@@ -551,7 +563,9 @@ def grid_query(mat: Material, grid: Grid, beta_k: float, off: np.ndarray, WK: np
     n = F.shape[0]
     wi, wt, P = np.empty(n), np.empty(n), np.empty((n, D))
     nl = np.empty(n, dtype=np.int64)
+    A = np.empty((n, D, D)) if want_A else None
     lib().orc_grid_query(mat.ref, grid.ref, float(beta_k), _rule(abs_det, rule), _p(off),
                          fa.shape[0], _p(np.ascontiguousarray(WK, dtype=np.float64)), _p(fa), n,
-                         _p(F), _p(wi), _p(wt), _p(P), _p(nl), int(nthreads))
-    return wi, wt, P, nl
+                         _p(F), _p(wi), _p(wt), _p(P), _p(A) if want_A else None, _p(nl),
+                         int(nthreads))
+    return (wi, wt, P, nl, A) if want_A else (wi, wt, P, nl)

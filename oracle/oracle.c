@@ -1062,6 +1062,92 @@ static void grid_P(const orc_material *m, int32_t d, const double *F, double bet
         P[c] = gd * G[c];
 }
 
+/* d^2 W / dF dF at a grid point (D x D, A[D a + b] = dP_a / dF_b over the
+ * row-major entries): with g = 1 - D(max(s, beta_k)) and, on loading
+ * (s > beta_k), g' = -(D_inf / D_0) exp(-s / D_0),
+ *   A = g d^2 psi0 + g' dpsi0 (x) dpsi0,
+ *   Eq. (2.3), G = F^{-T}, ln|J|:
+ *     d^2 psi0 / dF_iJ dF_kL = mu d_ik d_JL + lam G_iJ G_kL + (mu - lam ln|J|) G_iL G_kJ;
+ *   Eq. (2.2), S = lam/2 (I1 - 3) 1 + mu (C - 1) (so dpsi0/dF = F S):
+ *     d^2 psi0 / dF_iJ dF_kL = d_ik S_LJ + lam F_iJ F_kL + mu F_iL F_kJ + mu (F F^T)_ik d_JL.
+ * NaN where grid_W is excluded; the double well through orc_tangent. */
+static void grid_A(const orc_material *m, int32_t d, const double *F, double beta_k,
+                   int32_t rule, double *A)
+{
+    int D = d * d;
+    if (m->energy == 1) {
+        if (d == 2) {
+            orc_tangent(m, F, beta_k, A);
+        } else {
+            for (int c = 0; c < D * D; ++c)
+                A[c] = NAN;
+        }
+        return;
+    }
+    double J;
+    double s = psi0_d(m, d, F, &J);
+    int excluded = !(J > 0.0) && (rule == 0 || (m->energy == 0 && !(J < 0.0)));
+    if (excluded) {
+        for (int c = 0; c < D * D; ++c)
+            A[c] = NAN;
+        return;
+    }
+    double beta = s > beta_k ? s : beta_k;
+    double g = 1.0 - orc_damage(beta, m->Dinf, m->D0);
+    double gp = s > beta_k ? -(m->Dinf / m->D0) * exp(-s / m->D0) : 0.0;
+    double dp[9];
+    dpsi0_d(m, d, F, dp);
+    double I1, I2, JJ;
+    orc_invariants(d, F, &I1, &I2, &JJ);
+    double C[9], S[9], FFt[9], G[9];
+    right_cauchy_green(d, F, C);
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < d; ++k)
+                v += F[d * i + k] * F[d * j + k];
+            FFt[d * i + j] = v;
+            S[d * i + j] = m->mu * (C[d * i + j] - (i == j ? 1.0 : 0.0))
+                         + (i == j ? 0.5 * m->lam * (I1 - 3.0) : 0.0);
+        }
+    double lj = 0.0;
+    if (m->energy == 0) {
+        double c[9];
+        if (d == 2) {
+            c[0] = F[3];
+            c[1] = -F[2];
+            c[2] = -F[1];
+            c[3] = F[0];
+        } else {
+            cof3(F, c);
+        }
+        for (int k = 0; k < D; ++k)
+            G[k] = c[k] / J;
+        lj = log(fabs(J));
+    }
+    for (int i = 0; i < d; ++i)
+        for (int Jc = 0; Jc < d; ++Jc)
+            for (int k = 0; k < d; ++k)
+                for (int L = 0; L < d; ++L) {
+                    double d2;
+                    if (m->energy == 2)
+                        d2 = (i == k ? S[d * L + Jc] : 0.0) + m->lam * F[d * i + Jc] * F[d * k + L]
+                           + m->mu * F[d * i + L] * F[d * k + Jc]
+                           + (Jc == L ? m->mu * FFt[d * i + k] : 0.0);
+                    else
+                        d2 = (i == k && Jc == L ? m->mu : 0.0)
+                           + m->lam * G[d * i + Jc] * G[d * k + L]
+                           + (m->mu - m->lam * lj) * G[d * i + L] * G[d * k + Jc];
+                    A[D * (d * i + Jc) + (d * k + L)] = g * d2 + gp * dp[d * i + Jc] * dp[d * k + L];
+                }
+}
+
+void orc_tangent_dim(const orc_material *m, int32_t d, const double *F, double beta_k,
+                     int32_t rule, double *A)
+{
+    grid_A(m, d, F, beta_k, rule, A);
+}
+
 /* W and P = dW/dF at one F in R^{d x d} under a grid rule (for tests). */
 double orc_energy_dim(const orc_material *m, int32_t d, const double *F, double beta_k,
                       int32_t rule)
@@ -1253,7 +1339,7 @@ static int32_t grid_decompose(const orc_grid *g, const double *F, int64_t *cidx,
  * where W and P are evaluated.  Adds weight * (W, P) of the leaves. */
 static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k, int32_t rule,
                       const int32_t *off, const int32_t *forest, int64_t idx, int32_t d,
-                      double weight, double *W, double *P, int64_t *leaves)
+                      double weight, double *W, double *P, double *A, int64_t *leaves)
 {
     int64_t N = orc_grid_count(g);
     int D = grid_D(g);
@@ -1267,6 +1353,12 @@ static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k,
         grid_P(mat, g->dim, F, beta_k, rule, Pl);
         for (int c = 0; c < D; ++c)
             P[c] += weight * Pl[c];
+        if (A) {
+            double Al[81];
+            grid_A(mat, g->dim, F, beta_k, rule, Al);
+            for (int c = 0; c < D * D; ++c)
+                A[c] += weight * Al[c];
+        }
         ++*leaves;
         return;
     }
@@ -1281,12 +1373,13 @@ static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k,
         ip[c] = i[c] + lp * o[c];
     }
     grid_tree(mat, g, beta_k, rule, off, forest, grid_flat(g, im), k - 1, weight * (1.0 - xi), W,
-              P, leaves);
-    grid_tree(mat, g, beta_k, rule, off, forest, grid_flat(g, ip), k - 1, weight * xi, W, P,
+              P, A, leaves);
+    grid_tree(mat, g, beta_k, rule, off, forest, grid_flat(g, ip), k - 1, weight * xi, W, P, A,
               leaves);
 }
 
-/* Relaxed energy and stress at arbitrary points from K global iterations:
+/* Relaxed energy, stress and tangent at arbitrary points from K global
+ * iterations (A: n x D^2, nullable; Algorithm 3's third output):
  * W_interp = the multilinear interpolation of W^K (Sec. 4.1: values off the
  * grid by interpolation); W_tree, P = Algorithm 3 over Algorithm 2's tree
  * (the interpolation corners at order K, then the forest).  F and P hold D
@@ -1296,7 +1389,7 @@ static void grid_tree(const orc_material *mat, const orc_grid *g, double beta_k,
 void orc_grid_query(const orc_material *mat, const orc_grid *g, double beta_k, int32_t rule,
                     const int32_t *off, int32_t K, const double *WK, const int32_t *forest,
                     int64_t n, const double *F, double *W_interp, double *W_tree, double *P,
-                    int64_t *leaves, int32_t nthreads)
+                    double *A, int64_t *leaves, int32_t nthreads)
 {
     int D = grid_D(g);
 #ifdef _OPENMP
@@ -1309,15 +1402,22 @@ void orc_grid_query(const orc_material *mat, const orc_grid *g, double beta_k, i
         double *cw = (double *)malloc(sizeof(double) << D);
         int32_t nc = grid_decompose(g, F + D * p, cidx, cw);
         double wi = 0.0, wt = 0.0, Pp[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        double *Ap = A ? A + (int64_t)D * D * p : NULL;
+        if (Ap)
+            for (int c = 0; c < D * D; ++c)
+                Ap[c] = 0.0;
         int64_t nl = 0;
         for (int32_t c = 0; c < nc; ++c) {
             wi += cw[c] * WK[cidx[c]];
-            grid_tree(mat, g, beta_k, rule, off, forest, cidx[c], K, cw[c], &wt, Pp, &nl);
+            grid_tree(mat, g, beta_k, rule, off, forest, cidx[c], K, cw[c], &wt, Pp, Ap, &nl);
         }
         if (nc == 0) {
             wi = wt = NAN;
             for (int c = 0; c < D; ++c)
                 Pp[c] = NAN;
+            if (Ap)
+                for (int c = 0; c < D * D; ++c)
+                    Ap[c] = NAN;
         }
         W_interp[p] = wi;
         W_tree[p] = wt;

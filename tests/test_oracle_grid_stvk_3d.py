@@ -203,3 +203,60 @@ def test_3d_study_reproduces_the_printed_relaxed_curves(orc):
         assert err.max() < 1e-5
         flat = g[:, col] == g[:, col - 1]  # printed as not relaxed
         assert flat.sum() >= 8 and err[flat].max() < 1e-14
+
+
+@pytest.mark.parametrize("energy,d,rule", [(0, 2, 0), (0, 2, 1), (2, 2, 1), (2, 3, 0), (0, 3, 0),
+                                           (1, 2, 0)])
+def test_tangents_are_derivatives_of_the_stresses(orc, energy, d, rule):
+    """A = dP/dF (Algorithm 3's third output) for Eq. (2.3) (with ln|det F|
+    under rule 1, det F < 0 included), Eq. (2.2) and the double well, in two
+    and three dimensions: central differences of P, symmetric, with beta_k
+    below and above psi0; in plane strain the NH tangent equals the
+    per-point oracle's."""
+    rng = np.random.default_rng(10 + 3 * energy + d + rule)
+    mat = _mat(orc, energy)
+    h = 1e-6
+    Fs = _random_F(rng, d, 6)
+    if rule == 1:  # mirror images with det F < 0
+        Fs += [np.diag([-1.0] + [1.0] * (d - 1)) @ F for F in Fs[:3]]
+    for F in Fs:
+        f = F.reshape(-1)
+        for beta in (0.01, 3.0):
+            A = orc.tangent_dim(mat, f, beta, rule)
+            fd = np.zeros_like(A)
+            for c in range(f.size):
+                e = np.zeros_like(f)
+                e[c] = h
+                fd[:, c] = (orc.stress_dim(mat, f + e, beta, rule) -
+                            orc.stress_dim(mat, f - e, beta, rule)) / (2 * h)
+            assert np.max(np.abs(A - fd)) < 2e-6 * (1 + np.max(np.abs(A)))
+            assert np.max(np.abs(A - A.T)) < 1e-12 * (1 + np.max(np.abs(A)))
+            if energy in (0, 1) and d == 2 and np.linalg.det(F) > 0:
+                np.testing.assert_allclose(A, orc.tangent(mat, f, beta), rtol=1e-12, atol=1e-12)
+
+
+def test_query_tangent_is_the_leaf_tangent_and_symmetric(orc):
+    """Algorithm 3's tangent over the tree: a grid point that no iteration
+    split is its own leaf (A = the tangent there); at random points A is
+    symmetric and, where every corner's tree is a leaf, the interpolation of
+    the corner tangents."""
+    mat = orc.Material(mu=1.0, lam=0.5, Dinf=0.9, D0=0.3)
+    g = orc.Grid((7, 5, 5, 7), (0.4, -0.6, -0.6, 0.4), (0.2, 0.3, 0.3, 0.2))
+    off = orc.r11_directions()
+    W, forest, decs = orc.grid_convexify(mat, g, 0.06, off, kmax=40, tol=0.0, abs_det=True)
+    P = g.points()
+    fa = orc.forest_array(forest)
+    detP = P[:, 0] * P[:, 3] - P[:, 1] * P[:, 2]
+    never = np.nonzero(np.all(fa[:, :, 0] < 0, axis=0) & (detP > 0))[0]
+    q = never[:8]
+    _, _, _, nl, A = orc.grid_query(mat, g, 0.06, off, W[-1], forest, P[q], abs_det=True,
+                                    want_A=True)
+    assert np.all(nl == 1)
+    for k, i in enumerate(q):
+        np.testing.assert_allclose(A[k], orc.tangent_dim(mat, P[i], 0.06, 1), rtol=1e-14,
+                                   atol=1e-14)
+    rng = np.random.default_rng(3)
+    F = rng.uniform(P.min(0), P.max(0), size=(32, 4))
+    _, _, _, _, A = orc.grid_query(mat, g, 0.06, off, W[-1], forest, F, abs_det=True,
+                                   want_A=True)
+    assert np.max(np.abs(A - np.transpose(A, (0, 2, 1)))) < 1e-12
