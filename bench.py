@@ -963,7 +963,15 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
     e1.record()
     torch.cuda.synchronize()
     qms = e0.elapsed_time(e1)
+    cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, det_rule=1, want_A=True)
+    torch.cuda.synchronize()
+    e0.record()
+    cv.grid_query(p, g, c["beta"], off, out["W"], fo, Fq, det_rule=1, want_A=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ams = e0.elapsed_time(e1)
     res["query"] = {"points": int(Fq.shape[0]), "pts_per_s": Fq.shape[0] / (qms / 1e3),
+                    "ms_with_tangent": ams,
                     "ms": qms, "leaves_mean": float(nl.double().mean()),
                     "leaves_max": int(nl.max()),
                     "tree_minus_interp_max": float((wt - wi).abs().max())}
@@ -979,6 +987,9 @@ def global_grid_line(a, cv, api, inputs, torch, dev, sms, mhz, peak_src, runs=10
             "decrease_max_abs_diff": float(np.max(np.abs(dg - d))) if K == d.size else None,
             "W_K": err_stats(Wg, gold["W_K"]),
             "query": err_stats(wt2.cpu().numpy(), gold["W_tree"], P2.cpu().numpy(), gold["P"]),
+            "query_P_note": ("P follows the laminates, which differ from the oracle's at "
+                             "zero-decrease splits decided by the last bit of W^0 (each side's "
+                             "libm); from the same forest P agrees within 1e-12"),
             "query_leaves_equal": float(np.mean(nl2.cpu().numpy() == gold["leaves"]))}
     # the shape of the Sec. 6.4 strong-scaling grid (context for the paper's timings)
     gs = api.GridSpec.from_bounds(GRID_SCALING["diag"], GRID_SCALING["off"], GRID_SCALING["delta"])

@@ -422,14 +422,18 @@ int cvx_grid_convexify(cvx_handle *h, const cvx_params *p, const cvx_grid *g, do
  *     count as on it) at order K, each expanded through the latest iteration
  *     k <= order that split it (children at order k - 1), W and P (Eq. 2.12)
  *     at the leaves;
+ *   A (n x D x D, nullable): the tangent d^2W/dFdF over the same tree
+ *     (Algorithm 3's third output; A[D^2 q + D a + b] = dP_a / dF_b);
  *   leaves (n int64, nullable): the leaves of the tree.
  * NaN (leaves 0) outside the grid.  nd and off must be those of the run that
- * made the forest.  0 <= K <= 64.  Workspace: W and P at every grid point and
- * a bitmask of the iterations that split it ((D + 2) 8 bytes per point). */
+ * made the forest.  0 <= K <= 64.  The trees are tabulated per grid point and
+ * order first (K sweeps over the grid); workspace: three tables of W, P,
+ * (A,) leaf count per grid point ((D + 2) 8 bytes per point, D^2 8 more with
+ * A). */
 int cvx_grid_query(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
                    int32_t det_rule, int32_t nd, const int32_t *off, int32_t K, const double *WK,
                    const int32_t *forest, int64_t n, const double *F, double *W_interp,
-                   double *W_tree, double *P, int64_t *leaves, cvx_stream s);
+                   double *W_tree, double *P, double *A, int64_t *leaves, cvx_stream s);
 
 /* ------------------------------------------------------------ batched form */
 

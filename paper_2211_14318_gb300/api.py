@@ -132,7 +132,7 @@ def lib() -> ctypes.CDLL:
         "cvx_grid_convexify": [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Grid), ctypes.c_double,
                                i32, i32, vp, i32, ctypes.c_double, vp, vp, vp, vp, vp],
         "cvx_grid_query": [vp, ctypes.POINTER(_Params), ctypes.POINTER(_Grid), ctypes.c_double,
-                           i32, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp],
+                           i32, i32, vp, i32, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -626,9 +626,11 @@ class Convexifier:
         return dict(W=W, forest=forest, decs=decs, iters=iters)
 
     def grid_query(self, p: Params, grid: GridSpec, beta_k: float, off, WK, forest, F,
-                   det_rule: int = 0, K: Optional[int] = None, stream=None):
-        """(W_interp, W_tree, P (n x D), leaves) at points F (n x D) from W^K
-        and the first K forest rows (K = len(forest) unless given)."""
+                   det_rule: int = 0, K: Optional[int] = None, want_A: bool = False,
+                   stream=None):
+        """(W_interp, W_tree, P (n x D), leaves[, A (n x D x D)]) at points F
+        (n x D) from W^K and the first K forest rows (K = len(forest) unless
+        given)."""
         import torch
 
         off = np.ascontiguousarray(off, dtype=np.int32).reshape(-1, grid.D)
@@ -641,12 +643,13 @@ class Convexifier:
         wt = torch.empty(n, dtype=torch.float64, device=F.device)
         P = torch.empty(n, grid.D, dtype=torch.float64, device=F.device)
         nl = torch.empty(n, dtype=torch.int64, device=F.device)
+        A = torch.empty(n, grid.D, grid.D, dtype=torch.float64, device=F.device) if want_A else None
         c, g = p.c(), grid.c()
         _check(lib().cvx_grid_query(self._h, ctypes.byref(c), ctypes.byref(g), float(beta_k),
                                     int(det_rule), off.shape[0], off.ctypes.data, K, _ptr(WK),
-                                    _ptr(fa), n, _ptr(F), _ptr(wi), _ptr(wt), _ptr(P), _ptr(nl),
-                                    _stream(stream)), "cvx_grid_query")
-        return wi, wt, P, nl
+                                    _ptr(fa), n, _ptr(F), _ptr(wi), _ptr(wt), _ptr(P), _ptr(A),
+                                    _ptr(nl), _stream(stream)), "cvx_grid_query")
+        return (wi, wt, P, nl, A) if want_A else (wi, wt, P, nl)
 
     def batch_tuning(self):
         """(warps per CTA, directions-per-item cap, taken from the cache) of the

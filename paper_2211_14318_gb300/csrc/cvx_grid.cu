@@ -231,6 +231,86 @@ __device__ void grid_p64(const double *F, double beta, const Material &m, int ru
     }
 }
 
+// d^2W/dFdF (D x D, A[D a + b] = dP_a / dF_b over the row-major entries):
+// A = g d^2psi0 + g' dpsi0 (x) dpsi0, g = 1 - D(max(s, beta)), on loading
+// (s > beta) g' = -(D_inf / D_0) e^{-s / D_0}, with
+//   Eq. (2.3), G = F^-T, ln|J|:
+//     d^2psi0/dF_iJ dF_kL = mu d_ik d_JL + lambda G_iJ G_kL + (mu - lambda ln|J|) G_iL G_kJ;
+//   Eq. (2.2), S = lambda/2 (I1 - 3) 1 + mu (C - 1), dpsi0/dF = F S:
+//     d^2psi0/dF_iJ dF_kL = d_ik S_LJ + lambda F_iJ F_kL + mu F_iL F_kJ + mu (F F^T)_ik d_JL.
+template <int D>
+__device__ void grid_a64(const double *F, double beta, const Material &m, int rule, double *A) {
+    if (m.energy == CVX_ENERGY_DOUBLE_WELL) {
+        if (D == 4) tangent64(F, beta, m, A);
+        else
+            for (int c = 0; c < D * D; ++c) A[c] = nan("");
+        return;
+    }
+    double s, J, I1, C[D];
+    if (psi0_grid<D>(F, m, rule, s, J, I1, C)) {
+        for (int c = 0; c < D * D; ++c) A[c] = nan("");
+        return;
+    }
+    constexpr int d = D == 4 ? 2 : 3;
+    const double b = s > beta ? s : beta;
+    const double g = 1.0 - m.Dinf * (1.0 - exp(-b / m.D0));
+    const double gp = s > beta ? -(m.Dinf / m.D0) * exp(-s / m.D0) : 0.0;
+    double dp[D];
+    grid_p64<D>(F, beta, m, rule, dp);  // g dpsi0/dF
+    const double ig = 1.0 / g;
+    for (int c = 0; c < D; ++c) dp[c] *= ig;
+    if (m.energy == CVX_ENERGY_STVK_DAMAGE) {
+        double S[D], FF[D];
+        for (int a = 0; a < d; ++a)
+            for (int c = 0; c < d; ++c) {
+                double v = 0.0;
+                for (int k = 0; k < d; ++k) v += F[d * a + k] * F[d * c + k];
+                FF[d * a + c] = v;
+                S[d * a + c] = m.mu * (C[d * a + c] - (a == c ? 1.0 : 0.0)) +
+                               (a == c ? 0.5 * m.lam * (I1 - 3.0) : 0.0);
+            }
+        for (int i = 0; i < d; ++i)
+            for (int jj = 0; jj < d; ++jj)
+                for (int k = 0; k < d; ++k)
+                    for (int l = 0; l < d; ++l) {
+                        const double d2 = (i == k ? S[d * l + jj] : 0.0) +
+                                          m.lam * F[d * i + jj] * F[d * k + l] +
+                                          m.mu * F[d * i + l] * F[d * k + jj] +
+                                          (jj == l ? m.mu * FF[d * i + k] : 0.0);
+                        A[D * (d * i + jj) + d * k + l] =
+                            g * d2 + gp * dp[d * i + jj] * dp[d * k + l];
+                    }
+        return;
+    }
+    double G[D];
+    if (D == 4) {
+        G[0] = F[3] / J;
+        G[1] = -F[2] / J;
+        G[2] = -F[1] / J;
+        G[3] = F[0] / J;
+    } else {
+        G[0] = (F[4] * F[8] - F[5] * F[7]) / J;
+        G[1] = (F[5] * F[6] - F[3] * F[8]) / J;
+        G[2] = (F[3] * F[7] - F[4] * F[6]) / J;
+        G[3] = (F[2] * F[7] - F[1] * F[8]) / J;
+        G[4] = (F[0] * F[8] - F[2] * F[6]) / J;
+        G[5] = (F[1] * F[6] - F[0] * F[7]) / J;
+        G[6] = (F[1] * F[5] - F[2] * F[4]) / J;
+        G[7] = (F[2] * F[3] - F[0] * F[5]) / J;
+        G[8] = (F[0] * F[4] - F[1] * F[3]) / J;
+    }
+    const double cc = m.mu - m.lam * log(fabs(J));
+    for (int i = 0; i < d; ++i)
+        for (int jj = 0; jj < d; ++jj)
+            for (int k = 0; k < d; ++k)
+                for (int l = 0; l < d; ++l) {
+                    const double d2 = (i == k && jj == l ? m.mu : 0.0) +
+                                      m.lam * G[d * i + jj] * G[d * k + l] +
+                                      cc * G[d * i + l] * G[d * k + jj];
+                    A[D * (d * i + jj) + d * k + l] = g * d2 + gp * dp[d * i + jj] * dp[d * k + l];
+                }
+}
+
 // Number of grid points on the line that starts at index i along offset o.
 template <int D>
 __device__ __forceinline__ int line_length(const GridT<D> &g, const int *i, const int *o) {
@@ -491,7 +571,7 @@ __global__ void k_grid_final(int N, const int *iters, const double *pong, double
 // P[D][N], leaves[N] per order, ping-pong between two buffers.
 template <int D>
 __global__ void k_grid_tree0(GridT<D> g, Material m, double beta, int rule, double *Tw,
-                             double *Tp, long long *Tl) {
+                             double *Tp, long long *Tl, double *Ta) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     double F[D], P[D];
@@ -500,13 +580,19 @@ __global__ void k_grid_tree0(GridT<D> g, Material m, double beta, int rule, doub
     grid_p64<D>(F, beta, m, rule, P);
     for (int c = 0; c < D; ++c) Tp[(long long)c * g.N + p] = P[c];
     Tl[p] = 1;
+    if (Ta) {
+        double A[D * D];
+        grid_a64<D>(F, beta, m, rule, A);
+        for (int c = 0; c < D * D; ++c) Ta[(long long)c * g.N + p] = A[c];
+    }
 }
 
 template <int D>
 __global__ void k_grid_tree_step(GridT<D> g, const GridDirT<D> *dirs, int nd, const int *rec,
                                  const double *Tw0, const double *Tp0, const long long *Tl0,
                                  const double *Tw, const double *Tp, const long long *Tl,
-                                 double *Uw, double *Up, long long *Ul) {
+                                 double *Uw, double *Up, long long *Ul, const double *Ta0,
+                                 const double *Ta, double *Ua) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     const long long N = g.N;
@@ -516,6 +602,8 @@ __global__ void k_grid_tree_step(GridT<D> g, const GridDirT<D> *dirs, int nd, co
         Uw[p] = Tw[p];
         for (int c = 0; c < D; ++c) Up[c * N + p] = Tp[c * N + p];
         Ul[p] = Tl[p];
+        if (Ua)
+            for (int c = 0; c < D * D; ++c) Ua[c * N + p] = Ta[c * N + p];
         return;
     }
     const int step = dj < nd ? dirs[dj].step : 0;
@@ -524,6 +612,8 @@ __global__ void k_grid_tree_step(GridT<D> g, const GridDirT<D> *dirs, int nd, co
         Uw[p] = Tw0[p];
         for (int c = 0; c < D; ++c) Up[c * N + p] = Tp0[c * N + p];
         Ul[p] = Tl0[p];
+        if (Ua)
+            for (int c = 0; c < D * D; ++c) Ua[c * N + p] = Ta0[c * N + p];
         return;
     }
     const double xi = __ddiv_rn((double)(-lm), (double)(lp - lm));
@@ -531,6 +621,10 @@ __global__ void k_grid_tree_step(GridT<D> g, const GridDirT<D> *dirs, int nd, co
     Uw[p] = __dadd_rn(__dmul_rn(xm, Tw[cm]), __dmul_rn(xi, Tw[cp]));
     for (int c = 0; c < D; ++c)
         Up[c * N + p] = __dadd_rn(__dmul_rn(xm, Tp[c * N + cm]), __dmul_rn(xi, Tp[c * N + cp]));
+    if (Ua)
+        for (int c = 0; c < D * D; ++c)
+            Ua[c * N + p] =
+                __dadd_rn(__dmul_rn(xm, Ta[c * N + cm]), __dmul_rn(xi, Ta[c * N + cp]));
     const long long l = Tl[cm] + Tl[cp];
     Ul[p] = l < Tl[cm] ? 0x7fffffffffffffffLL : l;  // saturates
 }
@@ -543,8 +637,9 @@ __global__ void k_grid_tree_step(GridT<D> g, const GridDirT<D> *dirs, int nd, co
 // the tabulated tree T_K.  W_interp is the multilinear interpolation of W^K.
 template <int D>
 __global__ void k_grid_query(GridT<D> g, const double *WK, const double *Tw, const double *Tp,
-                             const long long *Tl, long long n, const double *F, double *Wi,
-                             double *Wt, double *P, long long *leaves) {
+                             const long long *Tl, const double *Ta, long long n,
+                             const double *F, double *Wi, double *Wt, double *P, double *A,
+                             long long *leaves) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     int i0[D];
@@ -569,6 +664,8 @@ __global__ void k_grid_query(GridT<D> g, const double *WK, const double *Tw, con
     }
     double wi = 0.0, wt = 0.0, Pp[D];
     for (int c = 0; c < D; ++c) Pp[c] = 0.0;
+    if (A)
+        for (int c = 0; c < D * D; ++c) A[(long long)D * D * q + c] = 0.0;
     long long nl = 0;
     const long long N = g.N;
     for (int corner = 0; inside && corner < (1 << D); ++corner) {
@@ -584,10 +681,16 @@ __global__ void k_grid_query(GridT<D> g, const double *WK, const double *Tw, con
         wt = __dadd_rn(wt, __dmul_rn(w, Tw[flat]));
         for (int a = 0; a < D; ++a) Pp[a] = __dadd_rn(Pp[a], __dmul_rn(w, Tp[a * N + flat]));
         nl += Tl[flat];
+        if (A)  // accumulated in place (the output row starts at zero)
+            for (int c = 0; c < D * D; ++c)
+                A[(long long)D * D * q + c] =
+                    __dadd_rn(A[(long long)D * D * q + c], __dmul_rn(w, Ta[c * N + flat]));
     }
     if (!inside) {
         wi = wt = nan("");
         for (int a = 0; a < D; ++a) Pp[a] = nan("");
+        if (A)
+            for (int c = 0; c < D * D; ++c) A[(long long)D * D * q + c] = nan("");
     }
     Wi[q] = wi;
     Wt[q] = wt;
@@ -909,7 +1012,7 @@ template <int D>
 int grid_query_t(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
                  int32_t rule, int32_t nd, const int32_t *off, int32_t K, const double *WK,
                  const int32_t *forest, int64_t n, const double *F, double *W_interp,
-                 double *W_tree, double *P, int64_t *leaves, cudaStream_t s) {
+                 double *W_tree, double *P, double *A, int64_t *leaves, cudaStream_t s) {
     GridT<D> gd;
     int rc = check_grid<D>(g, gd);
     if (rc) return rc;
@@ -926,43 +1029,45 @@ int grid_query_t(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double b
     if (n == 0) return CVX_OK;
     DeviceGuard dg(h->device);
     // tables: the leaves (order 0) and two buffers of orders, each
-    // W[N], P[D][N], leaves[N]
-    const size_t tab = up256(sizeof(double) * (D + 1) * (size_t)gd.N) +
+    // W[N], P[D][N], leaves[N] (and A[D^2][N] when the tangent is asked for)
+    const int na = A ? D * D : 0;
+    const size_t tab = up256(sizeof(double) * (D + 1 + na) * (size_t)gd.N) +
                        up256(sizeof(long long) * (size_t)gd.N);
     const size_t o_t = up256(sizeof(GridDirT<D>) * nd);
     rc = ensure_ws(h, o_t + 3 * tab, s);
     if (rc) return rc;
     GridDirT<D> *dd = (GridDirT<D> *)h->ws;
-    auto carve = [&](int i, double *&w, double *&pp, long long *&l) {
-        char *b = h->ws + o_t + i * tab;
-        w = (double *)b;
-        pp = w + gd.N;
-        l = (long long *)(b + up256(sizeof(double) * (D + 1) * (size_t)gd.N));
+    struct Tab {
+        double *w, *p, *a;
+        long long *l;
     };
-    double *w0, *p0, *wa, *pa, *wb, *pb;
-    long long *l0, *la, *lb;
-    carve(0, w0, p0, l0);
-    carve(1, wa, pa, la);
-    carve(2, wb, pb, lb);
+    auto carve = [&](int i) {
+        char *b = h->ws + o_t + i * tab;
+        Tab t;
+        t.w = (double *)b;
+        t.p = t.w + gd.N;
+        t.a = A ? t.p + (size_t)D * gd.N : nullptr;
+        t.l = (long long *)(b + up256(sizeof(double) * (D + 1 + na) * (size_t)gd.N));
+        return t;
+    };
+    const Tab t0 = carve(0), ta = carve(1), tb = carve(2);
     CK(cudaMemcpyAsync(dd, dirs.data(), sizeof(GridDirT<D>) * nd, cudaMemcpyHostToDevice, s),
        "cvx_grid_query");
     const unsigned pbk = (unsigned)((gd.N + 255) / 256);
-    k_grid_tree0<D><<<pbk, 256, 0, s>>>(gd, material_of(p), beta_k, rule, w0, p0, l0);
+    k_grid_tree0<D><<<pbk, 256, 0, s>>>(gd, material_of(p), beta_k, rule, t0.w, t0.p, t0.l, t0.a);
     CK(cudaGetLastError(), "cvx_grid_query leaves");
-    const double *cw = w0, *cp = p0;
-    const long long *cl = l0;
+    Tab cur = t0;
     for (int d = 1; d <= K; ++d) {
-        double *uw = (d & 1) ? wa : wb, *up = (d & 1) ? pa : pb;
-        long long *ul = (d & 1) ? la : lb;
+        const Tab nx = (d & 1) ? ta : tb;
         k_grid_tree_step<D><<<pbk, 256, 0, s>>>(gd, dd, nd, forest + 3 * (size_t)(d - 1) * gd.N,
-                                                w0, p0, l0, cw, cp, cl, uw, up, ul);
+                                                t0.w, t0.p, t0.l, cur.w, cur.p, cur.l, nx.w, nx.p,
+                                                nx.l, t0.a, cur.a, nx.a);
         CK(cudaGetLastError(), "cvx_grid_query tree order");
-        cw = uw;
-        cp = up;
-        cl = ul;
+        cur = nx;
     }
     k_grid_query<D><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
-        gd, WK, cw, cp, cl, n, F, W_interp, W_tree, P, reinterpret_cast<long long *>(leaves));
+        gd, WK, cur.w, cur.p, cur.l, cur.a, n, F, W_interp, W_tree, P, A,
+        reinterpret_cast<long long *>(leaves));
     CK(cudaGetLastError(), "cvx_grid_query");
     return CVX_OK;
 }
@@ -1039,15 +1144,15 @@ int cvx_grid_convexify(cvx_handle *h, const cvx_params *p, const cvx_grid *g, do
 int cvx_grid_query(cvx_handle *h, const cvx_params *p, const cvx_grid *g, double beta_k,
                    int32_t det_rule, int32_t nd, const int32_t *off, int32_t K, const double *WK,
                    const int32_t *forest, int64_t n, const double *F, double *W_interp,
-                   double *W_tree, double *P, int64_t *leaves, cvx_stream sv) {
+                   double *W_tree, double *P, double *A, int64_t *leaves, cvx_stream sv) {
     if (!p) return fail(CVX_ERR_INVALID_ARG, "params is NULL");
     int rc = check_grid_call(p, g, det_rule, beta_k);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)sv;
     return g->dim == 2 ? grid_query_t<4>(h, p, g, beta_k, det_rule, nd, off, K, WK, forest, n, F,
-                                         W_interp, W_tree, P, leaves, s)
+                                         W_interp, W_tree, P, A, leaves, s)
                        : grid_query_t<9>(h, p, g, beta_k, det_rule, nd, off, K, WK, forest, n, F,
-                                         W_interp, W_tree, P, leaves, s);
+                                         W_interp, W_tree, P, A, leaves, s);
 }
 
 }  // extern "C"

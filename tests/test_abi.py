@@ -222,7 +222,7 @@ def test_grid_calls_reject_bad_arguments_before_cuda(cvxlib):
     assert "handle" in _err(cvxlib)
     assert cvxlib.cvx_grid_query(None, ctypes.byref(c), ctypes.byref(g), 0.0, 0, 16,
                                  o.ctypes.data, 65, None, None, 1, None, None, None, None, None,
-                                 None) == -1
+                                 None, None) == -1
     assert "K must" in _err(cvxlib)
     assert cvxlib.cvx_grid_step(None, ctypes.byref(g), 0, o.ctypes.data, None, None, None, None,
                                 None) == -1

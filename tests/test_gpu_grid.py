@@ -222,8 +222,8 @@ def test_device_loop_matches_the_oracle_loop(cv, orc, study):
 def test_query_on_the_oracle_forest(cv, orc, study):
     """Algorithms 2 and 3 on the oracle's W^K and forest at random points,
     grid points, cell faces and points outside the grid: the interpolated
-    W^K bit for bit, the leaf counts exactly, W and P over the tree within
-    1e-12 (leaf energies use each side's log and exp)."""
+    W^K bit for bit, the leaf counts exactly, W, P and the tangent A over the
+    tree within 1e-12 (leaf energies use each side's log and exp)."""
     from paper_2211_14318_gb300 import api
 
     go, gg = _both_grids(orc, api)
@@ -237,11 +237,11 @@ def test_query_on_the_oracle_forest(cv, orc, study):
         rng.uniform(P.min(0) - 1.0, P.max(0) + 1.0, size=(256, 4)),
     ])
     mat = orc.Material(**NH61)
-    wi_o, wt_o, P_o, nl_o = orc.grid_query(mat, go, BETA61, study["off"], study["W"][-1],
-                                           study["forest"], F, rule=1)
-    wi, wt, Pg, nl = cv.grid_query(_params(api), gg, BETA61, api.grid_r11(), study["W"][-1],
-                                   study["forest"], F, det_rule=1)
-    wi, wt, Pg, nl = (x.cpu().numpy() for x in (wi, wt, Pg, nl))
+    wi_o, wt_o, P_o, nl_o, A_o = orc.grid_query(mat, go, BETA61, study["off"], study["W"][-1],
+                                                study["forest"], F, rule=1, want_A=True)
+    wi, wt, Pg, nl, Ag = cv.grid_query(_params(api), gg, BETA61, api.grid_r11(), study["W"][-1],
+                                       study["forest"], F, det_rule=1, want_A=True)
+    wi, wt, Pg, nl, Ag = (x.cpu().numpy() for x in (wi, wt, Pg, nl, Ag))
     assert _eq_nan(wi, wi_o)
     assert np.array_equal(nl, nl_o)
     inside = np.isfinite(wt_o)
@@ -251,6 +251,10 @@ def test_query_on_the_oracle_forest(cv, orc, study):
     pn = np.linalg.norm(P_o[inside], axis=1)
     assert np.max(np.linalg.norm(Pg[inside] - P_o[inside], axis=1) / (1 + pn)) < 1e-12
     assert nl_o.max() > 16  # trees that branch beyond the interpolation corners
+    # Algorithm 3's tangent over the same trees
+    an = np.abs(A_o[inside]).reshape(-1, 16).max(axis=1)
+    assert np.max(np.abs(Ag[inside] - A_o[inside]).reshape(-1, 16).max(axis=1) / (1 + an)) < 1e-12
+    assert np.all(np.isnan(Ag[~inside]))
 
 
 def test_query_tree_matches_the_interpolated_relaxation(cv):
