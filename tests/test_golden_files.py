@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-NAMES = ["material1m_l201", "mesh128", "loadpath512_s01", "loadpath512_s10"]
+NAMES = ["material1m_l201", "mesh128", "loadpath512_s01", "loadpath512_s10", "loadpath512_s20"]
 MAT = dict(mu=1.0, lam=5.0, Dinf=0.99, D0=0.5)
 
 
