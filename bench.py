@@ -223,8 +223,10 @@ def fp32_peak_tflops(torch, dev):
     return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz, src
 
 
-SCAN_SOURCES = ("cvx_pipeline.cu", "cvx_bridge.cuh", "cvx_device.cuh", "cvx_line.cuh",
-                "cvx_internal.h", "cvx_scan_lanes.cu")
+# the translation unit of k_scan_lanes (the kernel and its launch) and the
+# headers it includes
+SCAN_SOURCES = ("cvx_scan_lanes.cu", "cvx_line.cuh", "cvx_bridge.cuh", "cvx_device.cuh",
+                "cvx_internal.h")
 
 
 GRID_SOURCES = ("cvx_grid.cu", "cvx_device.cuh", "cvx_internal.h", "cvx_handle.h")

@@ -551,11 +551,28 @@ __global__ void k_select(const Pipe P, int level) {
 // FP64 bridge of the left and right sets of one line held in shared memory:
 // supporting-slope iteration with full passes; ties go to the outermost sample
 // (Algorithm 1 keeps the outermost of collinear points).
+//
+// The minima of v - s x are compared as order-preserving integer keys of the
+// doubles, so that the comparisons run on the integer pipe: the FP64 pipe
+// (2 lanes per SM per clock) is what bounds the refinement, and a key compares
+// exactly as its double does.
 // -------------------------------------------------------------------------
-__device__ __forceinline__ void warp_min_dk(double &v, int &k, bool prefer_low) {
+
+// Integer key of a double that is not NaN: x < y iff dkey(x) < dkey(y), and
+// x == y iff the keys are equal (-0 and +0 share the key 0).
+__device__ __forceinline__ long long dkey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);
+}
+
+constexpr long long kKeyInf = 0x7ff0000000000000LL;  // dkey(+inf)
+
+// Warp-wide minimum of (key, sample index); ties to the lower index if
+// prefer_low, else to the higher.
+__device__ __forceinline__ void warp_min_key(long long &v, int &k, bool prefer_low) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-        const double v2 = __shfl_xor_sync(kFull, v, o);
+        const long long v2 = __shfl_xor_sync(kFull, v, o);
         const int k2 = __shfl_xor_sync(kFull, k, o);
         if (v2 < v || (v2 == v && (prefer_low ? k2 < k : k2 > k))) {
             v = v2;
@@ -568,13 +585,13 @@ __device__ void bridge64(const double *sw, int L, int m0, int lane, int &a, int 
     double s = 0.0;
     a = b = -1;
     for (int it = 0; it < 128; ++it) {
-        double bl = INFINITY, br = INFINITY;
+        long long bl = kKeyInf, br = kKeyInf;
         int kl = INT_MAX, kr = -1;
         for (int k = lane; k < L; k += 32) {
             if (k == m0) continue;
             const double v = sw[k];
             if (!(v < INFINITY)) continue;
-            const double e = v - s * (double)(k - m0);
+            const long long e = dkey(v - s * (double)(k - m0));
             if (k < m0) {
                 if (e < bl || (e == bl && k < kl)) {
                     bl = e;
@@ -585,8 +602,8 @@ __device__ void bridge64(const double *sw, int L, int m0, int lane, int &a, int 
                 kr = k;
             }
         }
-        warp_min_dk(bl, kl, true);
-        warp_min_dk(br, kr, false);
+        warp_min_key(bl, kl, true);
+        warp_min_key(br, kr, false);
         if (kl == INT_MAX || kr < 0) {
             a = b = -1;
             return;
@@ -604,13 +621,15 @@ __device__ void bridge64(const double *sw, int L, int m0, int lane, int &a, int 
 // sample, as in bridge64.  false if it does not settle.
 __device__ bool window_bridge64(double vA, double vB, int kA, int kB, int m0, int &a, int &b,
                                 double &wa, double &wb, int lane, int loA, int loB) {
+    const bool okA = vA < INFINITY, okB = vB < INFINITY;
+    const double xA = (double)(kA - m0), xB = (double)(kB - m0);
     for (int it = 0; it < 64; ++it) {
         const double s = (wb - wa) / (double)(b - a);
-        double eA = vA < INFINITY ? vA - s * (double)(kA - m0) : INFINITY;
-        double eB = vB < INFINITY ? vB - s * (double)(kB - m0) : INFINITY;
-        int ka = vA < INFINITY ? kA : INT_MAX, kb = vB < INFINITY ? kB : -1;
-        warp_min_dk(eA, ka, true);
-        warp_min_dk(eB, kb, false);
+        long long eA = okA ? dkey(vA - s * xA) : kKeyInf;
+        long long eB = okB ? dkey(vB - s * xB) : kKeyInf;
+        int ka = okA ? kA : INT_MAX, kb = okB ? kB : -1;
+        warp_min_key(eA, ka, true);
+        warp_min_key(eB, kb, false);
         if (ka == INT_MAX || kb < 0) return false;
         if (ka == a && kb == b) return true;
         a = ka;
@@ -623,10 +642,10 @@ __device__ bool window_bridge64(double vA, double vB, int kA, int kB, int m0, in
 
 // Half-warp minimum with the sample index (lanes 0-15 and 16-31 reduce
 // separately); ties to the lower index if prefer_low, else to the higher.
-__device__ __forceinline__ void half_min_dk(double &v, int &k, bool prefer_low) {
+__device__ __forceinline__ void half_min_key(long long &v, int &k, bool prefer_low) {
 #pragma unroll
     for (int o = 8; o; o >>= 1) {
-        const double v2 = __shfl_xor_sync(kFull, v, o);
+        const long long v2 = __shfl_xor_sync(kFull, v, o);
         const int k2 = __shfl_xor_sync(kFull, k, o);
         if (v2 < v || (v2 == v && (prefer_low ? k2 < k : k2 > k))) {
             v = v2;
@@ -694,24 +713,27 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
         wb = valB(b);
         if (!(wa < INFINITY && wb < INFINITY)) return false;
         bool settled = false;
+        // per round: which window samples count, and their abscissae
+        const bool left = lane < 16;
+        const double vN = left ? vA : vB;
+        const int kN = left ? kA : kB;
+        const bool okA = vA < INFINITY, okB = vB < INFINITY, okN = vN < INFINITY;
+        const double xA = (double)(kA - m0), xB = (double)(kB - m0), xN = (double)(kN - m0);
         for (int it = 0; it < 64 && !settled; ++it) {
             const double s = (wb - wa) / (double)(b - a);
             int na, nb;
             if (narrow) {
-                const bool left = lane < 16;
-                const double v = left ? vA : vB;
-                const int k = left ? kA : kB;
-                double e = v < INFINITY ? v - s * (double)(k - m0) : INFINITY;
-                int kk = v < INFINITY ? k : (left ? INT_MAX : -1);
-                half_min_dk(e, kk, left);
+                long long e = okN ? dkey(vN - s * xN) : kKeyInf;
+                int kk = okN ? kN : (left ? INT_MAX : -1);
+                half_min_key(e, kk, left);
                 na = __shfl_sync(kFull, kk, 0);
                 nb = __shfl_sync(kFull, kk, 16);
             } else {
-                double eA = vA < INFINITY ? vA - s * (double)(kA - m0) : INFINITY;
-                double eB = vB < INFINITY ? vB - s * (double)(kB - m0) : INFINITY;
-                int ka = vA < INFINITY ? kA : INT_MAX, kb = vB < INFINITY ? kB : -1;
-                warp_min_dk(eA, ka, true);
-                warp_min_dk(eB, kb, false);
+                long long eA = okA ? dkey(vA - s * xA) : kKeyInf;
+                long long eB = okB ? dkey(vB - s * xB) : kKeyInf;
+                int ka = okA ? kA : INT_MAX, kb = okB ? kB : -1;
+                warp_min_key(eA, ka, true);
+                warp_min_key(eB, kb, false);
                 na = ka;
                 nb = kb;
             }
@@ -727,8 +749,8 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
         const double s = (wb - wa) / (double)(b - a);
         const float la = (float)(kap * wa - C), ls = (float)(kap * s);
         const int hiA = min(loA + W, m0), hiB = min(loB + W, L);
-        double eL = INFINITY, eR = INFINITY;  // lowest v - s x of FP64 samples on or below
-        int kL = INT_MAX, kR = -1;            // the chord, per side
+        long long eL = kKeyInf, eR = kKeyInf;  // lowest v - s x of FP64 samples on or below
+        int kL = INT_MAX, kR = -1;              // the chord, per side (keys)
         unsigned c64 = 0;
         for (int k = lane; k < L; k += 32) {
             if (k == m0 || (k >= loA && k < hiA) || (k >= loB && k < hiB)) continue;
@@ -746,7 +768,7 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
             if (!(v == v)) continue;  // det <= 0: excluded
             const double line = wa + s * (double)(k - a);
             if (v > line + 1e-14 * fabs(line)) continue;
-            const double e = v - s * (double)(k - m0);
+            const long long e = dkey(v - s * (double)(k - m0));
             if (k < m0) {
                 if (e < eL || (e == eL && k < kL)) {
                     eL = e;
@@ -758,8 +780,8 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
             }
         }
         n64 += c64;
-        warp_min_dk(eL, kL, true);
-        warp_min_dk(eR, kR, false);
+        warp_min_key(eL, kL, true);
+        warp_min_key(eR, kR, false);
         if (kL == INT_MAX && kR < 0) return true;  // certified
         if (kL != INT_MAX) a = kL;
         if (kR >= 0) b = kR;

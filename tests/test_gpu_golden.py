@@ -14,7 +14,15 @@ rows, and the subsample is compared element by element:
 * on every point whose nodes are all untied: W^R within 1e-6 relative and P
   within 1e-5 relative (gamma = 1e-8, the paper's error measure of Sec. 6.2);
 * on tied points: W^R equals the oracle's energy summed over the GPU's own
-  tree leaves (the GPU's laminate is a valid one).
+  tree leaves (the GPU's laminate is a valid one);
+* at a node the GPU flags NODE_OVERFLOW (more directions within the FP32
+  screening band than it refines in FP64, so its decision is not certified
+  against every direction): the GPU's direction, resampled by the oracle,
+  gives a node value within 2.25 eps of the oracle's minimum over all
+  directions (eps = the FP32 sample error bound in W units), its bridge
+  indices are the oracle's on that line where that bridge is untied, and
+  the point's W^R is its own leaves' energy and lies within K x 2.25 eps of
+  the oracle's W^R (K = the scanned levels).
 
 The load-path workload (128 x 128 angles, L = 2049, depth 3) runs the full
 scan on the 4,096 subsample points at three load steps, as the benchmark's
@@ -63,13 +71,59 @@ def params(g):
                       line_points=m["line_points"], t_half=m["t_half"], depth=m["depth"], **MAT)
 
 
+def eps_w(w, beta):
+    """FP32 sample error bound of the screen in W units at a node of energy
+    w: 1.1e-6 max(1, |w - c| + c), c = D_inf D_0 exp(-beta_k / D_0) (the
+    screen samples kappa' W - C and bounds its error by 1.1e-6 max(kappa',
+    |kappa' W - C| + C), C / kappa' = c)."""
+    c = MAT["D_inf"] * MAT["D0"] * np.exp(-beta / MAT["D0"])
+    return 1.1e-6 * max(1.0, abs(w - c) + c)
+
+
+def overflow_node(orc, g, p, i, t):
+    """An uncertified decision of the GPU at node (p, i), whose F equals the
+    oracle's: the oracle's value along the GPU's direction is within 2.25 eps
+    of the oracle's node value, and the GPU's bridge is the oracle's on that
+    line unless that bridge is tied.  Returns eps at the node."""
+    from paper_2211_14318_gb300 import api
+
+    m = g["meta"]
+    mat = orc.Material(MAT["mu"], MAT["lambda_L"], MAT["D_inf"], MAT["D0"])
+    dirs = orc.angle_directions(*m["angles"])
+    F, beta = g["node_F"][p, i], float(g["beta"][p])
+    w = orc.energy(mat, F, beta)
+    L, th = m["line_points"], m["t_half"]
+
+    def bridge(j):
+        ws, ok = orc.sample_line(mat, F, beta, orc.rank_one(dirs[j]), L, th)
+        return orc.line_bridge(ws, ok)
+
+    v_orc = w
+    if g["flags"][p, i] & orc.LAMINATED:
+        h, mm, mp, _ = bridge(int(g["dir"][p, i]))
+        assert (mm, mp) == (int(g["m_minus"][p, i]), int(g["m_plus"][p, i]))
+        v_orc = min(w, h)
+    eps = eps_w(w, beta)
+    v_gpu = w
+    if t["flags"] & api.NODE_LAMINATED:
+        h, mm, mp, mg = bridge(int(t["dir"]))
+        if mg > TIE:
+            assert (t["m_minus"], t["m_plus"]) == (mm, mp), (p, i)
+        v_gpu = h
+    assert v_orc <= v_gpu + 1e-12 * (1 + abs(v_gpu)), (p, i)
+    assert v_gpu <= v_orc + 2.25 * eps, (p, i, v_gpu - v_orc, eps)
+    return eps
+
+
 def compare(orc, api, g, WR, P, st, tree):
-    """Element-by-element comparison of the subsample; returns (untied
-    fraction, compared nodes)."""
+    """Element-by-element comparison of the subsample; returns (fraction of
+    points compared exactly, compared nodes, points with an uncertified
+    node)."""
     n = g["F"].shape[0]
     SC, LM = orc.SCANNED, orc.LAMINATED
     assert np.all((st & api.PT_NONPOS_DET) == (g["status"] & 1))
     untied = np.ones(n, dtype=bool)
+    over = {}  # point -> largest eps of its uncertified nodes
     compared = 0
     for p in range(n):
         stack = [0]
@@ -78,11 +132,15 @@ def compare(orc, api, g, WR, P, st, tree):
             fo = int(g["flags"][p, i])
             if not fo & SC:
                 continue
+            t = tree[p, i]
+            if t["flags"] & api.NODE_OVERFLOW:
+                untied[p] = False
+                over[p] = max(over.get(p, 0.0), overflow_node(orc, g, p, i, t))
+                continue
             if g["margin"][p, i] <= TIE:
                 untied[p] = False
                 continue
             compared += 1
-            t = tree[p, i]
             assert t["flags"] & api.NODE_SCANNED, (p, i)
             lam = bool(fo & LM)
             assert bool(t["flags"] & api.NODE_LAMINATED) == lam, (p, i)
@@ -104,7 +162,10 @@ def compare(orc, api, g, WR, P, st, tree):
         Wl = sum(tr[i]["weight"] * orc.energy(mat, tr[i]["F"], g["beta"][p])
                  for i in np.nonzero(leaf)[0])
         assert abs(WR[p] - Wl) <= 1e-11 * (1 + abs(Wl)), p
-    return u.mean(), compared
+    K = int(g["meta"]["depth"])
+    for p, eps in over.items():
+        assert abs(WR[p] - g["W_R"][p]) <= K * 2.25 * eps, (p, WR[p] - g["W_R"][p], eps)
+    return u.mean(), compared, len(over)
 
 
 def run_full(cv, g, F_all, beta_all):
@@ -138,8 +199,8 @@ def test_golden_material_points_1m_l201(cv, orc):
     F, Fp = inputs.surrogate_inputs(1 << 20, seed=201)
     beta = cv.history_update(params(g), Fp).cpu().numpy()
     WR, P, st, tree = run_full(cv, g, F, beta)
-    frac, compared = compare(orc, api, g, WR, P, st, tree)
-    assert frac >= 0.95 and compared >= 4096
+    frac, compared, n_over = compare(orc, api, g, WR, P, st, tree)
+    assert frac >= 0.95 and compared >= 4096 and n_over == 0
 
 
 def test_golden_mesh128(cv, orc):
@@ -151,8 +212,8 @@ def test_golden_mesh128(cv, orc):
     F, Fp = inputs.mesh_points(128, stretch=1.3, seed=0)
     beta = cv.history_update(params(g), Fp).cpu().numpy()
     WR, P, st, tree = run_full(cv, g, F, beta)
-    frac, compared = compare(orc, api, g, WR, P, st, tree)
-    assert frac >= 0.9 and compared >= 4096
+    frac, compared, n_over = compare(orc, api, g, WR, P, st, tree)
+    assert compared >= 4096 and frac + n_over / len(WR) >= 0.9
 
 
 @pytest.mark.parametrize("step", [1, 10, 20])
@@ -170,6 +231,8 @@ def test_golden_load_path(cv, orc, step):
     out = cv.convexify_points(p, g["F"], g["beta"], want_tree=True)
     n = g["F"].shape[0]
     tree = api.tree_numpy(out["tree"], n, p.tree_size)
-    frac, compared = compare(orc, api, g, out["W_R"].cpu().numpy(), out["P"].cpu().numpy(),
-                             out["status"].cpu().numpy(), tree)
-    assert frac >= 0.9 and compared >= 4096
+    frac, compared, n_over = compare(orc, api, g, out["W_R"].cpu().numpy(),
+                                     out["P"].cpu().numpy(), out["status"].cpu().numpy(), tree)
+    print(f"step {step}: exact on {frac:.3f} of the points, {compared} nodes, "
+          f"{n_over} points with an uncertified node")
+    assert compared >= 4096 and frac + n_over / n >= 0.9

@@ -378,6 +378,9 @@ def test_stats_account_for_the_work(cv, orc):
     assert s["points"] == 50
     assert s["lines"] == s["nodes_scanned"] * 144
     assert 0.9 * s["lines"] * 301 <= s["valid_samples"] <= s["lines"] * 301
+    # an uncertified node (more than 16 directions inside the FP32 screening
+    # band, whose decision is then within 2.25 eps of the FP64 minimum: the
+    # golden tests check that bar against the oracle) is rare at 12 x 12 angles
     assert s["iter_caps"] == 0 and s["overflow"] <= 0.1 * s["nodes_scanned"]
     assert s["laminated"] <= s["refined"] <= 16 * s["nodes_scanned"]
 
