@@ -678,7 +678,8 @@ __device__ __forceinline__ void half_min_key(long long &v, int &k, bool prefer_l
 
 __device__ bool refine_hinted(const double F[4], const double R[4], double beta, const NodeCands &nc,
                               const ProbDesc &pd, const LineSpec &ln, float4 d32, int hab, int lane,
-                              int &a, int &b, double &wa, double &wb, unsigned &n64) {
+                              int &a, int &b, double &wa, double &wb, unsigned &n64,
+                              int *spot_q) {
     const int m0 = ln.m0, L = ln.L;
     const double ek = nc.ek;
     a = hab & 0xffff;
@@ -752,22 +753,13 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
         long long eL = kKeyInf, eR = kKeyInf;  // lowest v - s x of FP64 samples on or below
         int kL = INT_MAX, kR = -1;              // the chord, per side (keys)
         unsigned c64 = 0;
-        for (int k = lane; k < L; k += 32) {
-            if (k == m0 || (k >= loA && k < hiA) || (k >= loB && k < hiB)) continue;
-            const float v32 =
-                sample_w<CVX_ENERGY_NH_DAMAGE>(nc.nl, dl, __fmul_rn((float)(k - m0), ln.h32));
-            if (v32 < INFINITY && v32 > -INFINITY) {
-                const float x = (float)(k - a);
-                const float Lv = __fmaf_rn(ls, x, la);
-                const float err = 2.0f * kU32 * (fabsf(la) + fabsf(ls * x) + fabsf(Lv)) +
-                                  kEps32 * fmaxf(kapf, fabsf(v32) + Cf) + 1e-30f;
-                if (__fsub_rn(v32, Lv) > 1.001f * err) continue;  // above the chord
-            }
+        // FP64 spot sample k, compared with the chord exactly
+        auto spot = [&](int k) {
             ++c64;
             const double v = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
-            if (!(v == v)) continue;  // det <= 0: excluded
+            if (!(v == v)) return;  // det <= 0: excluded
             const double line = wa + s * (double)(k - a);
-            if (v > line + 1e-14 * fabs(line)) continue;
+            if (v > line + 1e-14 * fabs(line)) return;
             const long long e = dkey(v - s * (double)(k - m0));
             if (k < m0) {
                 if (e < eL || (e == eL && k < kL)) {
@@ -778,7 +770,42 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
                 eR = e;
                 kR = k;
             }
+        };
+        // samples whose FP32 test is inconclusive queue up in the warp's
+        // shared-memory buffer and are taken in FP64 32 at a time, one per
+        // lane, so that a few scattered ones do not each cost the whole warp
+        // an FP64 sample; the minima do not depend on the order
+        int nq = 0;
+        for (int base = 0; base < L; base += 32) {
+            const int k = base + lane;
+            bool need = false;
+            if (k < L && k != m0 && !(k >= loA && k < hiA) && !(k >= loB && k < hiB)) {
+                const float v32 =
+                    sample_w<CVX_ENERGY_NH_DAMAGE>(nc.nl, dl, __fmul_rn((float)(k - m0), ln.h32));
+                need = true;
+                if (v32 < INFINITY && v32 > -INFINITY) {
+                    const float x = (float)(k - a);
+                    const float Lv = __fmaf_rn(ls, x, la);
+                    const float err = 2.0f * kU32 * (fabsf(la) + fabsf(ls * x) + fabsf(Lv)) +
+                                      kEps32 * fmaxf(kapf, fabsf(v32) + Cf) + 1e-30f;
+                    need = !(__fsub_rn(v32, Lv) > 1.001f * err);  // else above the chord
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, need);
+            if (need) spot_q[nq + __popc(bal & ((1u << lane) - 1u))] = k;
+            nq += __popc(bal);
+            __syncwarp();
+            if (nq >= 32) {
+                spot(spot_q[lane]);
+                const int rest = nq - 32;
+                __syncwarp();
+                if (lane < rest) spot_q[lane] = spot_q[32 + lane];
+                nq = rest;
+                __syncwarp();
+            }
         }
+        if (lane < nq) spot(spot_q[lane]);
+        __syncwarp();
         n64 += c64;
         warp_min_key(eL, kL, true);
         warp_min_key(eR, kR, false);
@@ -833,7 +860,7 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
             int a, b;
             double wa = 0.0, wb = 0.0;
             bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, ln, P.dir32[pd.dir_off + dir], hab,
-                                    lane, a, b, wa, wb, n_spot);
+                                    lane, a, b, wa, wb, n_spot, reinterpret_cast<int *>(sw));
             if (!ok) {
                 ++n_full;
                 const double ek = P.cands[qi].ek;
