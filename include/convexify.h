@@ -167,7 +167,10 @@ typedef struct cvx_node {
     int32_t m_minus; /* sample index of F- on the chosen line (0..L-1)         */
     int32_t m_plus;  /* sample index of F+                                     */
     int32_t flags;   /* CVX_NODE_* bits                                        */
-    float gap;       /* FP32 gap between the two best directions' hull values  */
+    float gap;       /* gap between the two best directions' FP64 hull values,
+                        rounded to FP32; where the second best was not
+                        resampled in FP64 (its FP32 screen bound already lay
+                        above the best), a lower bound of that gap           */
     int32_t window_exp; /* the node's line window is t_half 2^window_exp       */
 } cvx_node;
 

@@ -467,6 +467,10 @@ int scan_max_blocks_per_sm(int energy, int warps, int stride) {
                                           : occ_t<CVX_ENERGY_DOUBLE_WELL>(warps, stride);
 }
 
+// RefineOut.pad of a candidate k_refine did not refine: q holds a lower bound
+// of its FP64 value, above the node's minimum.
+constexpr int kScreened = 2;
+
 // -------------------------------------------------------------------------
 // k_select: one thread per queued node.  eps bounds |q_FP32 - q_FP64|
 // (1-Lipschitz in the samples), q_lo <= q_R^FP32 <= q_hi per direction.  The
@@ -494,6 +498,7 @@ __global__ void k_select(const Pipe P, int level) {
     }
     NodeCands nc;
     nc.n = 0;
+    float cq[kNodeCand];  // the candidates' FP32 lower bounds
     const float shift = (float)line_shift(pd.mat, pd.beta[P.qp[level][qi] - pd.point_off]);
     const float kap = pd.kappa_f;
     // a direction is a candidate iff q - eps(q) <= m + eps(m), m = min(W(F), U)
@@ -519,6 +524,7 @@ __global__ void k_select(const Pipe P, int level) {
                 qcut = fminf(qcut, q);
                 break;
             }
+            cq[nc.n] = q;
             nc.dir[nc.n] = r[bc].dir[pos[bc]];
             nc.ab[nc.n++] = r[bc].ab[pos[bc]];
             ++pos[bc];
@@ -543,7 +549,19 @@ __global__ void k_select(const Pipe P, int level) {
     if (nc.n) {
         const int pos = atomicAdd(P.cnt + (P.K + 1) + level, nc.n);
         for (int c = 0; c < nc.n; ++c) P.work[pos + c] = make_int2(qi, c);
-        atomicAdd(P.counters + C_REFINED, (unsigned long long)nc.n);
+        // per candidate, a lower bound of its FP64 value in W units (as for
+        // qcut in k_commit): (q - eps(q) + C) / kappa'; k_refine's second
+        // phase skips a candidate whose bound exceeds the first one's value
+        RefineOut *ro = P.refined + (long long)qi * kNodeCand;
+        for (int c = 0; c < nc.n; ++c) {
+            const float q = cq[c];
+            RefineOut o;
+            o.q = ((double)q - (double)eps32_at(q, kap, shift) + nc.shift) / pd.kappa;
+            o.a = o.b = -1;
+            o.ok = 0;
+            o.pad = kScreened;
+            ro[c] = o;
+        }
     }
 }
 
@@ -816,140 +834,37 @@ __device__ bool refine_hinted(const double F[4], const double R[4], double beta,
     return false;
 }
 
-// k_refine: one warp per screened (node, direction).  The FP64 bridge of the
-// left and right sample sets is searched in two 32-sample FP64 windows around
-// the FP32 bridge and certified against the whole line with the FP32 samples:
-// every sample m outside the windows must satisfy
-//   (v32_m - kEps32 max(kappa', |v32_m| + C) + C) / kappa' > the FP64 bridge line at m,
-// i.e. its FP64 value lies strictly above the line, so the windows' bridge is
-// the bridge of all samples.  Otherwise (and where the FP32 samples are not
-// finite) the whole line is resampled in FP64 (bridge64).
+// The FP64 refinement of candidate c of queued node qi (one warp): writes
+// P.refined[qi][c].
 template <int EK>
-__global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
-    extern __shared__ double sm64[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double *sw = sm64 + warp * P.stride64;
+__device__ __forceinline__ void refine_one(const Pipe &P, int level, int qi, int c, int lane,
+                                           double *sw, HullCounters &hc,
+                                           unsigned long long &n_full, unsigned &n_spot) {
     float *sw32 = reinterpret_cast<float *>(sw);
-    __shared__ unsigned s_hc[4][HC_N];  // the screen's event counters (not reported here)
-    if (lane == 0)
-        for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
-    __syncwarp();
-    HullCounters hc{s_hc[warp]};
-    const int nwork = P.cnt[(P.K + 1) + level];
     const int32_t *qp = P.qp[level], *qh = P.qh[level];
-    unsigned long long n_full = 0;
-    unsigned n_spot = 0;  // FP64 spot samples of the certificates (per lane)
-    for (int w = blockIdx.x * (blockDim.x >> 5) + warp; w < nwork;
-         w += gridDim.x * (blockDim.x >> 5)) {
-        const int2 wk = P.work[w];
-        const int qi = wk.x, c = wk.y;
-        const int p = qp[qi], hi = qh[qi];
-        const ProbDesc &pd = P.probs[P.pid[p]];
-        const cvx_node *nd = node_ptr(pd, p, hi);
-        const LineSpec ln = scaled_line(pd.line, nd->window_exp);
-        const int m0 = ln.m0;
-        const int dir = P.cands[qi].dir[c];
-        const double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
-        const double *d = P.dir64 + 4 * ((long long)pd.dir_off + dir);
-        const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
-                             __dmul_rn(d[1], d[3])};
-        const double beta = pd.beta[p - pd.point_off];
-        const int hab = P.cands[qi].ab[c];
-        if (EK == CVX_ENERGY_NH_DAMAGE && hab >= 0) {
-            // the scan's FP32 pair as the start, windows in FP64, FP32 certificate
-            int a, b;
-            double wa = 0.0, wb = 0.0;
-            bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, ln, P.dir32[pd.dir_off + dir], hab,
-                                    lane, a, b, wa, wb, n_spot, reinterpret_cast<int *>(sw));
-            if (!ok) {
-                ++n_full;
-                const double ek = P.cands[qi].ek;
-                for (int k = lane; k < ln.L; k += 32)
-                    sw[k] = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
-                __syncwarp();
-                bridge64(sw, ln.L, m0, lane, a, b);
-                if (a >= 0) {
-                    wa = sw[a];
-                    wb = sw[b];
-                }
-            }
-            if (lane == 0) {
-                RefineOut o;
-                o.a = a;
-                o.b = b;
-                o.pad = 0;
-                if (a >= 0) {
-                    const double xa = (double)(a - m0), xb = (double)(b - m0);
-                    o.q = (xb * wa - xa * wb) / (xb - xa);
-                    o.ok = 1;
-                } else {
-                    o.q = INFINITY;
-                    o.ok = 0;
-                }
-                P.refined[(long long)qi * kNodeCand + c] = o;
-            }
-            __syncwarp();
-            continue;
-        }
-        // FP32 line and its approximate bridge
-        const NodeLine nl = P.cands[qi].nl;
-        const DirLine dl = make_dir_line<EK>(nl, P.dir32[pd.dir_off + dir]);
-        float tl[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - m0) * ln.h32;
-        sample_line<EK>(sw32, nl, dl, ln, lane, tl);
-        __syncwarp();
-        const LineGeom g{ln.L, m0, ln.nfull};
-        const ScreenOut so = warp_screen(sw32, g, lane, -1, -1, hc);
-        int a = so.a, b = so.b;
-        bool ok = a >= 0 && b >= 0;
+    const int p = qp[qi], hi = qh[qi];
+    const ProbDesc &pd = P.probs[P.pid[p]];
+    const cvx_node *nd = node_ptr(pd, p, hi);
+    const LineSpec ln = scaled_line(pd.line, nd->window_exp);
+    const int m0 = ln.m0;
+    const int dir = P.cands[qi].dir[c];
+    const double F[4] = {nd->F[0], nd->F[1], nd->F[2], nd->F[3]};
+    const double *d = P.dir64 + 4 * ((long long)pd.dir_off + dir);
+    const double R[4] = {__dmul_rn(d[0], d[2]), __dmul_rn(d[0], d[3]), __dmul_rn(d[1], d[2]),
+                         __dmul_rn(d[1], d[3])};
+    const double beta = pd.beta[p - pd.point_off];
+    const int hab = P.cands[qi].ab[c];
+    if (EK == CVX_ENERGY_NH_DAMAGE && hab >= 0) {
+        // the scan's FP32 pair as the start, windows in FP64, FP32 certificate
+        int a, b;
         double wa = 0.0, wb = 0.0;
-        int loA = 0, loB = 0;
-        if (ok) {
-            loA = max(0, min(a - 16, m0 - 32));
-            loB = min(max(m0 + 1, b - 15), ln.L - 32);
-            loB = max(loB, m0 + 1);
-            const int kA = loA + lane, kB = loB + lane;
-            double vA = INFINITY, vB = INFINITY;
-            if (kA < m0) {
-                const double v = sample_w64(F, R, kA, m0, ln.h64, beta, pd.mat);
-                vA = v == v ? v : INFINITY;
-            }
-            if (kB < ln.L) {
-                const double v = sample_w64(F, R, kB, m0, ln.h64, beta, pd.mat);
-                vB = v == v ? v : INFINITY;
-            }
-            wa = __shfl_sync(kFull, vA, a - loA);
-            wb = __shfl_sync(kFull, vB, b - loB);
-            ok = wa < INFINITY && wb < INFINITY &&
-                 window_bridge64(vA, vB, kA, kB, m0, a, b, wa, wb, lane, loA, loB);
-        }
-        if (ok) {
-            // certificate over the samples outside the windows
-            const double s = (wb - wa) / (double)(b - a);
-            const double kap = pd.kappa, shift = P.cands[qi].shift;
-            bool good = true;
-            for (int k = lane; k < ln.L && good; k += 32) {
-                if (k == m0 || (k >= loA && k < loA + 32 && k < m0) || (k >= loB && k < loB + 32))
-                    continue;
-                const double line = wa + s * (double)(k - a);
-                const float v32 = sw32[k];
-                if (v32 < INFINITY && v32 > -INFINITY) {
-                    const double e = (double)kEps32 * fmax(kap, fabs((double)v32) + shift);
-                    const double lb = ((double)v32 - e + shift) / kap;
-                    good = lb > line + 1e-14 * (fabs(line) + fabs(lb));
-                } else {
-                    const double v = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
-                    good = !(v == v) || v > line + 1e-14 * fabs(line);
-                }
-            }
-            ok = __all_sync(kFull, good);
-        }
-        __syncwarp();
+        bool ok = refine_hinted(F, R, beta, P.cands[qi], pd, ln, P.dir32[pd.dir_off + dir], hab,
+                                lane, a, b, wa, wb, n_spot, reinterpret_cast<int *>(sw));
         if (!ok) {
-            // resample the whole line in FP64
             ++n_full;
-            for (int k = lane; k < ln.L; k += 32) sw[k] = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
+            const double ek = P.cands[qi].ek;
+            for (int k = lane; k < ln.L; k += 32)
+                sw[k] = sample_w64_ek(F, R, k, m0, ln.h64, beta, ek, pd.mat);
             __syncwarp();
             bridge64(sw, ln.L, m0, lane, a, b);
             if (a >= 0) {
@@ -973,8 +888,160 @@ __global__ void __launch_bounds__(128) k_refine(const Pipe P, int level) {
             P.refined[(long long)qi * kNodeCand + c] = o;
         }
         __syncwarp();
+        return;
+    }
+    // FP32 line and its approximate bridge
+    const NodeLine nl = P.cands[qi].nl;
+    const DirLine dl = make_dir_line<EK>(nl, P.dir32[pd.dir_off + dir]);
+    float tl[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tl[i] = (float)(4 * lane + i - m0) * ln.h32;
+    sample_line<EK>(sw32, nl, dl, ln, lane, tl);
+    __syncwarp();
+    const LineGeom g{ln.L, m0, ln.nfull};
+    const ScreenOut so = warp_screen(sw32, g, lane, -1, -1, hc);
+    int a = so.a, b = so.b;
+    bool ok = a >= 0 && b >= 0;
+    double wa = 0.0, wb = 0.0;
+    int loA = 0, loB = 0;
+    if (ok) {
+        loA = max(0, min(a - 16, m0 - 32));
+        loB = min(max(m0 + 1, b - 15), ln.L - 32);
+        loB = max(loB, m0 + 1);
+        const int kA = loA + lane, kB = loB + lane;
+        double vA = INFINITY, vB = INFINITY;
+        if (kA < m0) {
+            const double v = sample_w64(F, R, kA, m0, ln.h64, beta, pd.mat);
+            vA = v == v ? v : INFINITY;
+        }
+        if (kB < ln.L) {
+            const double v = sample_w64(F, R, kB, m0, ln.h64, beta, pd.mat);
+            vB = v == v ? v : INFINITY;
+        }
+        wa = __shfl_sync(kFull, vA, a - loA);
+        wb = __shfl_sync(kFull, vB, b - loB);
+        ok = wa < INFINITY && wb < INFINITY &&
+             window_bridge64(vA, vB, kA, kB, m0, a, b, wa, wb, lane, loA, loB);
+    }
+    if (ok) {
+        // certificate over the samples outside the windows
+        const double s = (wb - wa) / (double)(b - a);
+        const double kap = pd.kappa, shift = P.cands[qi].shift;
+        bool good = true;
+        for (int k = lane; k < ln.L && good; k += 32) {
+            if (k == m0 || (k >= loA && k < loA + 32 && k < m0) || (k >= loB && k < loB + 32))
+                continue;
+            const double line = wa + s * (double)(k - a);
+            const float v32 = sw32[k];
+            if (v32 < INFINITY && v32 > -INFINITY) {
+                const double e = (double)kEps32 * fmax(kap, fabs((double)v32) + shift);
+                const double lb = ((double)v32 - e + shift) / kap;
+                good = lb > line + 1e-14 * (fabs(line) + fabs(lb));
+            } else {
+                const double v = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
+                good = !(v == v) || v > line + 1e-14 * fabs(line);
+            }
+        }
+        ok = __all_sync(kFull, good);
+    }
+    __syncwarp();
+    if (!ok) {
+        // resample the whole line in FP64
+        ++n_full;
+        for (int k = lane; k < ln.L; k += 32) sw[k] = sample_w64(F, R, k, m0, ln.h64, beta, pd.mat);
+        __syncwarp();
+        bridge64(sw, ln.L, m0, lane, a, b);
+        if (a >= 0) {
+            wa = sw[a];
+            wb = sw[b];
+        }
+    }
+    if (lane == 0) {
+        RefineOut o;
+        o.a = a;
+        o.b = b;
+        o.pad = 0;
+        if (a >= 0) {
+            const double xa = (double)(a - m0), xb = (double)(b - m0);
+            o.q = (xb * wa - xa * wb) / (xb - xa);
+            o.ok = 1;
+        } else {
+            o.q = INFINITY;
+            o.ok = 0;
+        }
+        P.refined[(long long)qi * kNodeCand + c] = o;
+    }
+    __syncwarp();
+}
+
+// k_refine: one warp per screened (node, direction).  The FP64 bridge of the
+// left and right sample sets is searched in two 32-sample FP64 windows around
+// the FP32 bridge and certified against the whole line with the FP32 samples:
+// every sample m outside the windows must satisfy
+//   (v32_m - kEps32 max(kappa', |v32_m| + C) + C) / kappa' > the FP64 bridge line at m,
+// i.e. its FP64 value lies strictly above the line, so the windows' bridge is
+// the bridge of all samples.  Otherwise (and where the FP32 samples are not
+// finite) the whole line is resampled in FP64 (bridge64).
+//
+// Two launches per level.  Phase 0 refines each node's first candidate (the
+// smallest FP32 lower bound); its FP64 value gives the node an upper bound
+// V0 = min(W(F), q_0) of the FP64 minimum.  Phase 1 refines the others,
+// except a candidate whose FP64 value is bounded below by more than V0 (the
+// bound k_select stored: its FP32 lower bound less the FP32 error bound), as
+// it can neither be the minimiser nor tie with it.  The decisions are those
+// of refining every candidate.
+template <int EK>
+__global__ void __launch_bounds__(128) k_refine(const Pipe P, int level, int phase) {
+    extern __shared__ double sm64[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *sw = sm64 + warp * P.stride64;
+    __shared__ unsigned s_hc[4][HC_N];  // the screen's event counters (not reported here)
+    if (lane == 0)
+        for (int i = 0; i < HC_N; ++i) s_hc[warp][i] = 0u;
+    __syncwarp();
+    HullCounters hc{s_hc[warp]};
+    unsigned long long n_full = 0, n_ref = 0;
+    unsigned n_spot = 0;  // FP64 spot samples of the certificates (per lane)
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    // the warp's next (node, candidate): phase 0 takes 32 nodes per step and
+    // their first candidates one after another, phase 1 the work list
+    const int nn = P.cnt[level], nwork = P.cnt[(P.K + 1) + level];
+    const int32_t *qp = P.qp[level], *qh = P.qh[level];
+    int next = phase == 0 ? gw * 32 : gw, cur = 0;
+    unsigned bal = 0;
+    for (;;) {
+        int qi = -1, c = 0;
+        if (phase == 0) {
+            while (!bal && next < nn) {
+                cur = next;
+                bal = __ballot_sync(kFull, cur + lane < nn && P.cands[cur + lane].n > 0);
+                next += nwarps * 32;
+            }
+            if (!bal) break;
+            qi = cur + __ffs(bal) - 1;
+            bal &= bal - 1;
+        } else {
+            while (next < nwork) {
+                const int2 wk = P.work[next];
+                next += nwarps;
+                if (wk.y == 0) continue;
+                const RefineOut *ro = P.refined + (long long)wk.x * kNodeCand;
+                const ProbDesc &pd = P.probs[P.pid[qp[wk.x]]];
+                const double w_node = node_ptr(pd, qp[wk.x], qh[wk.x])->w;
+                const double V0 = ro[0].ok && ro[0].q < w_node ? ro[0].q : w_node;
+                if (ro[wk.y].q > V0) continue;  // the stored lower bound: screened out
+                qi = wk.x;
+                c = wk.y;
+                break;
+            }
+            if (qi < 0) break;
+        }
+        refine_one<EK>(P, level, qi, c, lane, sw, hc, n_full, n_spot);
+        ++n_ref;
     }
     if (lane == 0) add_counter(P.counters, C_REFFULL, n_full);
+    if (lane == 0) add_counter(P.counters, C_REFINED, n_ref);
     n_spot = __reduce_add_sync(kFull, n_spot);
     if (lane == 0) add_counter(P.counters, C_FP64, n_spot);
 }
@@ -1029,7 +1096,12 @@ __global__ void k_commit(const Pipe P, int level) {
     int bc = -1;
     double second = INFINITY;
     for (int c = 0; c < nc.n; ++c) {
-        if (!ro[c].ok) continue;
+        if (!ro[c].ok) {
+            // skipped by k_refine: only its lower bound is known (above the
+            // node's minimum), which bounds the gap to the second best
+            if (ro[c].pad == kScreened) second = fmin(second, ro[c].q);
+            continue;
+        }
         if (bc < 0 || ro[c].q < ro[bc].q || (ro[c].q == ro[bc].q && nc.dir[c] < nc.dir[bc])) {
             if (bc >= 0) second = fmin(second, ro[bc].q);
             bc = c;
@@ -1584,7 +1656,9 @@ cudaError_t pipe_level(const Pipe &p, int l, int warps, int grid, cudaStream_t s
     if ((e = cudaFuncSetAttribute(kr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm)) !=
         cudaSuccess)
         return e;
-    kr<<<rg, 128, rsm, s>>>(p, l);
+    kr<<<rg, 128, rsm, s>>>(p, l, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    kr<<<rg, 128, rsm, s>>>(p, l, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_commit<<<nb, 128, 0, s>>>(p, l);
     return cudaGetLastError();
