@@ -66,3 +66,30 @@ def test_golden_inputs_match_generators():
     g = _load("material1m_l201")
     F, _ = inputs.surrogate_inputs(1 << 20, seed=201)
     np.testing.assert_allclose(F[g["idx"]], g["F"], rtol=0, atol=1e-14)
+
+
+def test_uncertified_node_bar_rejects_a_worse_direction(orc):
+    """The GPU tests' bar for an uncertified node (test_gpu_golden's
+    overflow_node), applied to the oracle's own tree at load step 20 with the
+    node relabelled as a GPU decision: the oracle's direction and a direction
+    whose hull value lies 5e-8 above it (inside 2.25 eps) pass with their own
+    bridges; the same direction with another bridge index, and direction
+    8000 with its own (unsplit) bridge, 4.2e-6 above the minimum, fail."""
+    import sys
+
+    sys.path.insert(0, HERE)
+    import test_gpu_golden as T
+    from paper_2211_14318_gb300 import api
+
+    g = T.load("loadpath512_s20")
+    t = np.zeros((), dtype=[("flags", "<i4"), ("dir", "<i4"), ("m_minus", "<i4"),
+                            ("m_plus", "<i4")])
+    t["flags"] = api.NODE_SCANNED | api.NODE_LAMINATED | api.NODE_OVERFLOW
+    for d, mm, mp, ok in [(0, 0, 1086, True), (516, 0, 1085, True), (516, 0, 1086, False),
+                          (8000, 1024, 1024, False)]:
+        t["dir"], t["m_minus"], t["m_plus"] = d, mm, mp
+        if ok:
+            assert T.overflow_node(orc, g, 300, 6, t) == pytest.approx(1.1e-6)
+        else:
+            with pytest.raises(AssertionError):
+                T.overflow_node(orc, g, 300, 6, t)
