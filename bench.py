@@ -61,7 +61,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-points", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--form", default="loadpath",
-                    choices=["loadpath", "full-scan", "northstar", "batch", "surrogate", "train",
+                    choices=["loadpath", "full-scan", "points1m", "batch", "surrogate", "train",
                              "grid"],
                     help="loadpath: the metric's workload (default); full-scan: the 65,536-point "
                          "mesh alone; surrogate: the load path with the older report; train: "
@@ -78,8 +78,8 @@ def args_parse():
                     help="loadpath with N > 1: weak = one load path per rank; strong = one "
                          "load path split into contiguous point ranges weighted by expected "
                          "tree size")
-    ap.add_argument("--ns-points", type=int, default=1 << 20,
-                    help="northstar: material points (default 1,048,576)")
+    ap.add_argument("--mp-points", type=int, default=1 << 20,
+                    help="points1m: material points (default 1,048,576)")
     ap.add_argument("--profile-step", type=int, default=0,
                     help="loadpath: bracket this timed load step with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -465,7 +465,7 @@ def run_ours(a):
 
 # ----------------------------------------------------- load path (the metric)
 LP_STEPS, LP_ANGLES, LP_LINE, LP_DEPTH, LP_SEED, LP_STRETCH = 20, 128, 2049, 3, 7, 1.8
-NS_ANGLES, NS_LINE, NS_DEPTH, NS_POINTS, NS_SEED = 16, 201, 2, 1 << 20, 201
+MP_ANGLES, MP_LINE, MP_DEPTH, MP_POINTS, MP_SEED = 16, 201, 2, 1 << 20, 201
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 CHECK_STEPS = (1, 10, 20)
 
@@ -739,9 +739,9 @@ def run_loadpath(a):
             full[f"step_{k}"] = row
         extras = {}
         if not a.no_extras:
-            extras["north_star"] = north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz,
-                                                   peak_src, K)
-            extras["north_star_adaptive_window"] = north_star_line(
+            extras["material_points_l201"] = material_points_line(
+                a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, K)
+            extras["material_points_l201_adaptive_window"] = material_points_line(
                 a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, 3, doublings=5)
             extras["mesh128"] = mesh128_line(cv, api, torch, dev, peak, sms, mhz, peak_src,
                                              min(K, 5))
@@ -800,7 +800,7 @@ def run_loadpath(a):
         dist.destroy_process_group()
 
 
-def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, steps, doublings=0):
+def material_points_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, steps, doublings=0):
     """1,048,576 material points at 16 x 16 angles, L = 201, depth 2 (the
     full scan): throughput, the line scan's roofline and the error against the
     stored oracle results of 4,096 points (placed at their rows).  With
@@ -809,12 +809,12 @@ def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, st
     results: its W^R is compared with the fixed window's instead)."""
     import numpy as np
 
-    npts = getattr(a, "ns_points", NS_POINTS)
-    F, Fp = inputs.surrogate_inputs(npts, seed=NS_SEED)
-    p = api.Params(n_theta_a=NS_ANGLES, n_theta_b=NS_ANGLES, line_points=NS_LINE, depth=NS_DEPTH,
+    npts = getattr(a, "mp_points", MP_POINTS)
+    F, Fp = inputs.surrogate_inputs(npts, seed=MP_SEED)
+    p = api.Params(n_theta_a=MP_ANGLES, n_theta_b=MP_ANGLES, line_points=MP_LINE, depth=MP_DEPTH,
                    window_doublings=doublings, **MAT)
     beta = cv.history_update(p, Fp).cpu().numpy()
-    g = load_golden("material1m_l201") if npts == NS_POINTS else None
+    g = load_golden("material1m_l201") if npts == MP_POINTS else None
     if g is not None:
         F[g["idx"]] = g["F"]
         beta[g["idx"]] = g["beta"]
@@ -822,10 +822,10 @@ def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, st
     bd = torch.from_numpy(beta).to(dev)
     ms, scan_ms, launches, st, out = timed_full_scan(cv, p, Fd, bd, steps, torch)
     res = {"workload": (f"{npts} material points (F = Q diag(lam, lam^-0.3) Q^T + noise, "
-                        f"lam ~ U[1, 2]), {NS_ANGLES}x{NS_ANGLES} angles, L={NS_LINE}, "
+                        f"lam ~ U[1, 2]), {MP_ANGLES}x{MP_ANGLES} angles, L={MP_LINE}, "
                         f"t in [-0.5,0.5]" + (f" doubled up to {doublings} times per node"
                                               if doublings else "") +
-                        f", depth {NS_DEPTH}, full scan"),
+                        f", depth {MP_DEPTH}, full scan"),
            "value": npts * steps / (ms / 1e3), "unit": "points/s", "steps": steps,
            "ms_per_step": ms / steps,
            "roofline": roofline_obj(st, scan_ms, launches, ms, peak, sms, mhz, peak_src,
@@ -836,8 +836,8 @@ def north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, st
         res["accuracy_vs_oracle"] = err_stats(out["W_R"][it].cpu().numpy(), g["W_R"],
                                               out["P"][it].cpu().numpy(), g["P"])
     if doublings:
-        q = api.Params(n_theta_a=NS_ANGLES, n_theta_b=NS_ANGLES, line_points=NS_LINE,
-                       depth=NS_DEPTH, **MAT)
+        q = api.Params(n_theta_a=MP_ANGLES, n_theta_b=MP_ANGLES, line_points=MP_LINE,
+                       depth=MP_DEPTH, **MAT)
         fixed = cv.convexify_points(q, Fd, bd)["W_R"]
         d = fixed - out["W_R"]  # W units: how much lower the wider windows relax
         res["W_R_drop_vs_fixed_window"] = {
@@ -1486,7 +1486,7 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
-def run_northstar(a):
+def run_material_points(a):
     """The full scan of material points at 16 x 16 angles, L = 201, depth 2
     (1,048,576 points by default) on its own: one JSON line."""
     import torch
@@ -1500,7 +1500,7 @@ def run_northstar(a):
     torch.cuda.set_device(0)
     cv = api.Convexifier(0)
     peak, sms, mhz, peak_src = fp32_peak_tflops(torch, dev)
-    res = north_star_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, a.steps)
+    res = material_points_line(a, cv, api, inputs, torch, dev, peak, sms, mhz, peak_src, a.steps)
     res.update(metric="quadrature points convexified/s (W^R+P), full scan", n_gpus=1,
                warmup=2, higher_is_better=True, dtype="f32/f64", data="synthetic")
     print(json.dumps(res), flush=True)
@@ -1515,8 +1515,8 @@ def main():
         run_loadpath(a)
     elif a.form == "batch":
         run_batch(a)
-    elif a.form == "northstar":
-        run_northstar(a)
+    elif a.form == "points1m":
+        run_material_points(a)
     elif a.form == "grid":
         run_grid(a)
     elif a.form == "surrogate":

@@ -480,8 +480,8 @@ int cvx_get_batch_tuning(cvx_handle *h, int *warps_per_cta, int *dirs_per_item_c
 /* ------------------------------------------- surrogate proposal network */
 
 /* A small network that proposes, per tree node, where the line scan should
- * look (not in the paper: an addition; the full scan stays the judge and the
- * fallback).  Inputs per node x = (F11, F12, F21, F22, beta_k, ln det F),
+ * look (not in the paper: an addition; the full scan stays the reference and
+ * the fallback).  Inputs per node x = (F11, F12, F21, F22, beta_k, ln det F),
  * standardised with a per-feature mean and std; 4 hidden layers of width 256
  * with GELU; 7 outputs: the angles theta_a, theta_b of a (x) b (period pi),
  * the logit of the volume fraction xi of F+, the four entries of the jump

@@ -37,8 +37,8 @@ struct GemmEpi {
 };
 
 // 2-D tensor map of a row-major bf16 matrix (rows x cols, leading dimension ld
-// elements) read in boxes of 8 columns x box_rows rows.  false if the driver
-// entry point is missing or the layout breaks the TMA rules.
+// elements) read in boxes of 8 columns x box_rows rows.  false if the CUDA
+// driver's entry point is missing or the layout breaks the TMA rules.
 bool make_tmap_bf16(CUtensorMap *map, const void *ptr, long long rows, long long cols,
                     long long ld, int box_rows);
 

@@ -192,7 +192,8 @@ def run_full(cv, g, F_all, beta_all):
 
 def test_golden_material_points_1m_l201(cv, orc):
     """1,048,576 material points, 16 x 16 angles, L = 201, depth 2: the
-    spec resolution; 4,096 points against the oracle."""
+    resolution of the 1M-material-point workload; 4,096 points against the
+    oracle."""
     from paper_2211_14318_gb300 import api, inputs
 
     g = load("material1m_l201")
