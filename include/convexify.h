@@ -584,10 +584,9 @@ int cvx_gemm_bf16(cvx_handle *h, int M, int N, int K, const uint16_t *A, const u
  * n * (88 (2^{K+1} - 1) + 600 * 2^{K-1}) bytes plus 48 bytes per direction)
  * fits in 64 MiB; larger problems are rejected with CVX_ERR_INVALID_ARG.
  * Runs on the calling thread's current device.  The first call on a device
- * looks up the array's device address there (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Every call shares the array and
- * leaves its contents behind (each call clears what must start at zero), so
- * calls that overlap on the GPU — on different streams, or from different
+ * looks up the array's device address there (cudaGetSymbolAddress).  Every
+ * call shares the array and leaves its contents behind (each call clears what
+ * must start at zero), so calls that overlap on the GPU — on different streams, or from different
  * host threads — race and must be serialised by the caller. */
 int convexify_points_static(const cvx_params *p, int64_t n, const double *F,
                             const double *beta_k, double *W_R, double *P, int32_t *status,
